@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark of the two-level sampling-based clustering on GB300.
+
+One step = one whole job on one batch of synthetic input: min-max scaling, the landmark
+peel into subclusters, Lloyd on every subcluster, Lloyd on the pooled local centers and
+the SSE of every point (all kernels of the library, recorded once into a CUDA graph and
+replayed).  Workload: 2^20 points, d=16, 64 Gaussian blobs (sigma ~ U[0.2, 1]) + 1%
+uniform outliers, subclusters of 4096 (256 of them), 64 local centers, 25 Lloyd
+iterations, final k=64.
+
+Metric: Lloyd distance evaluations per second of the whole job,
+    sum over subclusters of |s| * k_eff * iters + pooled * final_k * iters,
+divided by the job's device time (so peel, scaling and SSE count against it).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun every rank runs its own independent job (another seed): weak scaling,
+no collective on the data path; rank 0 prints the line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1412_1947_gb300 import synth  # noqa: E402
+
+METRIC = "Lloyd dist-evals/s"
+UNIT = "dist-evals/s"
+L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2
+FP32_ALU_PEAK = 152 * 128 * 2 * 2.07e9   # SMs x FP32 lanes x 2 flop (FMA) x max SM clock
+
+
+def workload_evals(w: synth.Workload) -> int:
+    """Distance evaluations of one job (local Lloyd + final Lloyd)."""
+    full, rem = divmod(w.n, w.N)
+    ev = full * w.N * min(w.local_k, w.N)
+    P = full * min(w.local_k, w.N)
+    if rem:
+        ev += rem * min(w.local_k, rem)
+        P += min(w.local_k, rem)
+    return (ev + P * w.final_k) * w.iters
+
+
+def config_of(w: synth.Workload, extra=None):
+    c = {"workload": w.name, "n": w.n, "d": w.d, "blobs": w.blobs, "N": w.N, "local_k": w.local_k,
+         "final_k": w.final_k, "iters": w.iters, "outliers": w.outlier_frac,
+         "l2": "flushed (256 MiB write) between timed steps", "storage": "f32"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+def oracle_sample(w: synth.Workload, n_sample: int):
+    return synth.Workload(w.name + f"_sample{n_sample}", n=n_sample, d=w.d, blobs=w.blobs, N=w.N,
+                          local_k=w.local_k, final_k=w.final_k, iters=w.iters, sigma=w.sigma,
+                          outlier_frac=w.outlier_frac, seed=w.seed)
+
+
+def run_oracle_once(ws: synth.Workload, raw, threads: int) -> float:
+    import oracle
+    t0 = time.perf_counter()
+    oracle.two_level(raw, ws.N, ws.local_k, ws.final_k, ws.iters, seed=1, threads=threads)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(w: synth.Workload, n_sample: int, reps: int = 1):
+    threads = os.cpu_count() or 1
+    ws = oracle_sample(w, n_sample)
+    raw = ws.points()
+    secs = min(run_oracle_once(ws, raw, threads) for _ in range(reps))
+    ev = workload_evals(ws)
+    return {"value": ev / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"the whole two-level job (scale, peel, Lloyd, final Lloyd, SSE) on n={n_sample} "
+                      f"points of the same recipe ({-(-n_sample // w.N)} subclusters of {w.N}), "
+                      f"{secs:.2f} s, float64 C oracle, OpenMP over subclusters"}
+
+
+# ------------------------------------------------------------------ reference arm
+def reference_arm(args, w: synth.Workload):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_sample = args.oracle_n
+    ws = oracle_sample(w, n_sample)
+    raw = ws.points()
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        run_oracle_once(ws, raw, threads)
+    times = [run_oracle_once(ws, raw, threads) for _ in range(args.steps)]
+    ev = workload_evals(ws)
+    value = ev / statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(w, {"sample_n": n_sample}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"n={n_sample} points of the same recipe per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def main_arm(args, w: synth.Workload):
+    import numpy as np
+    import torch
+
+    from paper_1412_1947_gb300 import binding as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    wr = synth.Workload(w.name, n=w.n, d=w.d, blobs=w.blobs, N=w.N, local_k=w.local_k, final_k=w.final_k,
+                        iters=w.iters, sigma=w.sigma, outlier_frac=w.outlier_frac, seed=w.seed + 1000 * rank)
+    raw = wr.points()
+    evals = workload_evals(wr)
+    seed = 12345
+    x_dev = torch.from_numpy(raw).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    ctx = B.pscl_ctx_create(local, 0, stream.cuda_stream)
+    job = B.Job(x_dev, ctx=ctx)
+    job.option(B.PSCL_OPT_GRAPH)
+    run = lambda: job.run(wr.N, wr.local_k, wr.final_k, wr.iters, seed)  # noqa: E731
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        run()
+    torch.cuda.synchronize()
+    launches_per_step = sum(v[0] for v in job.kernel_times().values())
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    clk.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()                                  # outside the timed interval
+        starts[i].record(stream)
+        run()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    mean_ms = statistics.mean(step_ms)
+    if dist:
+        t = torch.tensor([mean_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        mean_ms = float(t.item())
+    _, _, sse = job.result(labels=False)
+
+    # ---- end to end through the public API with host buffers: H2D of the points from
+    # pinned memory, the job, D2H of the final centers and SSE, every step
+    host = torch.from_numpy(raw).pin_memory()
+    ctx_e = B.pscl_ctx_create(local, 0, stream.cuda_stream)
+    job_e = B.Job(host, ctx=ctx_e)
+    job_e.option(B.PSCL_OPT_GRAPH)
+    for _ in range(max(1, args.warmup)):
+        job_e.load(host)
+        job_e.run(wr.N, wr.local_k, wr.final_k, wr.iters, seed)
+        job_e.result(labels=False)
+    e2e_s = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        job_e.load(host)
+        job_e.run(wr.N, wr.local_k, wr.final_k, wr.iters, seed)
+        c, _, sse_e = job_e.result(labels=False)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_mean = statistics.mean(e2e_s)
+    if dist:
+        t = torch.tensor([e2e_mean], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_mean = float(t.item())
+    job_e.close()
+    B.pscl_ctx_destroy(ctx_e)
+
+    # ---- per-kernel device times (events around every launch, unrecorded runs)
+    job_k = B.Job(x_dev, ctx=ctx)
+    job_k.option(B.PSCL_OPT_KERNEL_TIMING)
+    kt = None
+    for _ in range(2):
+        flush.zero_()
+        job_k.steps(wr.N, wr.local_k, wr.final_k, wr.iters, seed)
+        kt = job_k.kernel_times()
+    phases = job_k.phase_ms()
+    job_k.close()
+
+    # ---- the plain per-subcluster float32 form on the same data
+    plain = None
+    if not args.no_plain:
+        job_p = B.Job(x_dev, ctx=ctx)
+        job_p.option(B.PSCL_OPT_PLAIN_LLOYD)
+        pl_ms = []
+        for _ in range(2):
+            flush.zero_()
+            torch.cuda.synchronize()
+            job_p.steps(wr.N, wr.local_k, wr.final_k, wr.iters, seed)
+            ph = job_p.phase_ms()
+            pl_ms.append(ph)
+        _, _, sse_p = job_p.result(labels=False)
+        ph = pl_ms[-1]
+        local_evals = evals - 0
+        plain = {"form": "plain float32, one launch pair per subcluster per iteration",
+                 "ms_per_job": float(sum(ph)), "local_lloyd_ms": float(ph[2]),
+                 "value": evals / (float(sum(ph)) * 1e-3), "sse": sse_p, "sse_equal": sse_p == sse}
+        job_p.close()
+        del local_evals
+
+    job.close()
+    B.pscl_ctx_destroy(ctx)
+
+    # ---- roofline of the dominant kernel
+    name, (nl, ms) = max(kt.items(), key=lambda kv: kv[1][1])
+    S = -(-wr.n // wr.N)
+    if name == "lloyd_assign":
+        flops = evals * 3 * wr.d                     # (x-c), square, add per attribute
+        roof = {"kernel": "k_lloyd_assign (float32 direct)", "bound": "alu",
+                "achieved": flops / (ms * 1e-3) / 1e12, "peak": FP32_ALU_PEAK / 1e12, "unit": "TFLOP/s",
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "per_launch_ms": ms / nl, "launches": nl, "traffic": None}
+    else:
+        rem = sum(wr.n - r * wr.N for r in range(S - 1))
+        per_pt = {"peel_dist": wr.d * 4 + 8, "peel_compact": wr.d * 4 + 13, "peel_classify": 5,
+                  "peel_hist": 4}.get(name, wr.d * 4)
+        byts = rem * per_pt
+        roof = {"kernel": name, "bound": "hbm", "achieved": byts / (ms * 1e-3) / 1e9,
+                "peak": 6691.5, "unit": "GB/s", "peak_kind": "measured (MEASURED_PEAKS hbm_gbs)",
+                "per_launch_ms": ms / nl, "launches": nl, "traffic": None}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+
+    value = evals * world / (mean_ms * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_of(wr, {"parallelism": f"replicas{world}" if world > 1 else "single"}),
+            "latency_ms": {"p50": statistics.median(step_ms),
+                           "p99": sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]},
+            "sse": sse,
+            "e2e": {"value": evals * world / e2e_mean, "unit": UNIT,
+                    "h2d_bytes_per_step": int(raw.nbytes), "d2h_bytes_per_step": wr.final_k * wr.d * 4 + 8},
+            "gpu_launches": int(launches_per_step * args.steps),
+            "roofline": roof,
+            "kernels_ms": {k: round(v[1], 4) for k, v in kt.items()},
+            "kernel_launches": {k: v[0] for k, v in kt.items()},
+            "phase_ms": {"scale": float(phases[0]), "peel": float(phases[1]), "local_lloyd": float(phases[2]),
+                         "final_lloyd": float(phases[3]), "sse": float(phases[4])},
+            "lloyd_only_value": evals / (float(phases[2] + phases[3]) * 1e-3),
+            "plain_fp32": plain, "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w, args.oracle_n)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="medium", choices=["small", "medium", "large"])
+    ap.add_argument("--oracle-n", type=int, default=1 << 17)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    w = {"small": synth.SMALL, "medium": synth.MEDIUM, "large": synth.LARGE}[args.workload]
+    if args.impl == "reference":
+        reference_arm(args, w)
+    else:
+        main_arm(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * pscl.h -- C ABI of the GB300 (sm_103a) library for the two-level sampling-based
+ * clustering of "A parallel sampling based clustering" (Sastry & Netti, arXiv 1412.1947).
+ *
+ * The method (Algorithm 1 and §V of the paper):
+ *   1. scale every attribute (Algorithm 1, step 1)             -> pscl_scale_features
+ *   2. peel equal-sized subclusters around a landmark and run
+ *      Lloyd's k-means on each (Algorithm 1, steps 2-5; §II)    -> pscl_subcluster
+ *   3. run Lloyd's k-means on the pooled local centers (§V)    -> pscl_cluster
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns a pscl_status; none aborts.  pscl_last_error() gives a
+ *     message for the calling thread's last failure.
+ *   - Points are n x d, row-major (all d attributes of a point are contiguous, the
+ *     paper's "row major flattening", §V), float32.  n >= 1, 1 <= d <= 1024.
+ *   - Work is queued on the context's CUDA stream and runs asynchronously; the
+ *     pscl_get_* calls synchronise that stream before copying results out.
+ *   - The library allocates and owns all device memory it uses; caller buffers are
+ *     only read (inputs) or written (outputs) and are never retained, except the
+ *     device input pointer of pscl_job_create/pscl_job_load, which must stay valid
+ *     until the next pscl_scale_features on that job has completed.
+ *   - Calls on one job must come in the order scale -> subcluster -> cluster
+ *     (PSCL_ESTATE otherwise); a job is used by one host thread at a time.
+ *   - Inputs must be finite; a non-finite value makes pscl_scale_features' result
+ *     undefined and is reported as PSCL_EINVAL by the next pscl_get_* call.
+ */
+#ifndef PSCL_H
+#define PSCL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pscl_ctx pscl_ctx;
+typedef struct pscl_job pscl_job;
+
+typedef enum {
+    PSCL_OK = 0,
+    PSCL_EINVAL = 1,   /* bad argument (size, pointer, enum value)                    */
+    PSCL_ESTATE = 2,   /* call out of order (e.g. cluster before subcluster)           */
+    PSCL_ENOMEM = 3,   /* the job would exceed the context's device-memory budget      */
+    PSCL_EBUSY = 4,    /* serving queue full; retry later (never blocks)               */
+    PSCL_ETIMEOUT = 5, /* a bounded wait gave up                                       */
+    PSCL_ECUDA = 6     /* a CUDA runtime call failed; see pscl_last_error()            */
+} pscl_status;
+
+/* Storage type of the points (only float32 is accepted at present). */
+typedef enum { PSCL_F32 = 0, PSCL_BF16 = 1 } pscl_dtype;
+
+/* Arithmetic of the Lloyd assignment step (§I's "nearest center").
+ *  PSCL_PREC_FP32: direct float32 sum of (x_j - c_j)^2 on the CUDA cores.
+ *  PSCL_PREC_TF32, PSCL_PREC_BF16: the -2 x.c part on the tensor cores with TF32 or
+ *      BF16 inputs and float32 accumulation, every point whose best two centers are
+ *      closer than the contraction's error bound re-decided by the float32 direct sum.
+ *  Every mode yields the same partition into subclusters; the update step is the same
+ *  exact fixed-point mean in all modes. */
+typedef enum { PSCL_PREC_FP32 = 0, PSCL_PREC_TF32 = 1, PSCL_PREC_BF16 = 2 } pscl_prec;
+
+/* Job options (pscl_job_set_option). */
+typedef enum {
+    /* 1: run the local Lloyd as one launch pair per subcluster per iteration (the
+     *    plain per-subcluster form) instead of batching all subclusters.  Default 0. */
+    PSCL_OPT_PLAIN_LLOYD = 1,
+    /* 1: keep the labels of every Lloyd iteration for pscl_get_label_trace. Default 0. */
+    PSCL_OPT_TRACE_LABELS = 2,
+    /* 1: every Lloyd run starts from the first k_eff members of its point set instead
+     *    of the seeded shuffle (used by worked examples).  Default 0. */
+    PSCL_OPT_INIT_FIRST_K = 3,
+    /* 1: record the pipeline's launches into a CUDA graph on first use and replay it
+     *    on later runs with the same parameters.  Default 0. */
+    PSCL_OPT_GRAPH = 4,
+    /* 1: time every kernel launch of later unrecorded runs with CUDA events on the
+     *    context's stream (pscl_get_kernel_times).  Default 0. */
+    PSCL_OPT_KERNEL_TIMING = 5
+} pscl_option;
+
+/* The library's kernels, for pscl_get_kernel_times. */
+typedef enum {
+    PSCL_K_SCALE_MINMAX = 0, /* column minima / maxima                           */
+    PSCL_K_SCALE_APPLY,      /* element-wise min-max scaling                     */
+    PSCL_K_PEEL_DIST,        /* float32 landmark distances + first histogram     */
+    PSCL_K_PEEL_HIST,        /* second histogram of the N-th key's bin           */
+    PSCL_K_PEEL_CLASSIFY,    /* in / out / float64 band, band selection          */
+    PSCL_K_PEEL_COMPACT,     /* stable compaction + next landmark                */
+    PSCL_K_PEEL_TAKE,        /* last round: the remaining points                 */
+    PSCL_K_GATHER,           /* subcluster-packed copy of the points             */
+    PSCL_K_LLOYD_INIT,       /* seeded initial centers                           */
+    PSCL_K_LLOYD_ASSIGN,     /* nearest center + fixed-point sums                */
+    PSCL_K_LLOYD_FINALIZE,   /* centers = sums / counts                          */
+    PSCL_K_FINAL_SSE,        /* nearest final center and SSE of every point      */
+    PSCL_K_COUNT
+} pscl_kernel;
+
+/* Context: one device, one stream, one device-memory budget.
+ *   device            CUDA device ordinal.
+ *   hbm_budget_bytes  upper bound on device memory the context's jobs may hold
+ *                     (0 = no bound beyond what the device has).
+ *   stream            a cudaStream_t to queue work on, or NULL for a stream the
+ *                     context creates (and destroys) itself.
+ * Errors: PSCL_EINVAL (out is NULL, bad device), PSCL_ECUDA. */
+int pscl_ctx_create(pscl_ctx **out, int device, size_t hbm_budget_bytes, void *stream);
+int pscl_ctx_destroy(pscl_ctx *ctx);
+/* Bytes of device memory currently held by the context's jobs. */
+size_t pscl_ctx_bytes_in_use(const pscl_ctx *ctx);
+/* Message of the calling thread's last failed call ("" if none). Never NULL. */
+const char *pscl_last_error(void);
+
+/* Job: one clustering problem.
+ *   points            n x d row-major float32, on the host (points_on_device = 0; copied
+ *                     to the device before the call returns its status) or on the
+ *                     context's device (points_on_device = 1; read later, by
+ *                     pscl_scale_features).
+ * Errors: PSCL_EINVAL (NULL pointer, n < 1, d outside 1..1024, dtype not PSCL_F32),
+ *         PSCL_ENOMEM (over budget), PSCL_ECUDA. */
+int pscl_job_create(pscl_ctx *ctx, const void *points, int dtype, int64_t n, int32_t d,
+                    int points_on_device, pscl_job **out);
+/* Replace the job's points by another n x d set (same n, d) and reset it to the state
+ * right after pscl_job_create.  Buffers and recorded graphs are kept. */
+int pscl_job_load(pscl_job *job, const void *points, int points_on_device);
+int pscl_job_set_option(pscl_job *job, int option, int64_t value);
+int pscl_job_destroy(pscl_job *job);
+
+/* Feature scaling (Algorithm 1, step 1): per attribute j, with mn_j / mx_j the
+ * minimum / maximum over all points, x'_ij = float((double(x_ij) - mn_j) * (1 / (mx_j -
+ * mn_j))) computed in double; a constant attribute becomes 0.  All later steps work on
+ * the scaled points. */
+int pscl_scale_features(pscl_job *job);
+
+/* Equal-sized subclustering (Algorithm 1 steps 2-5, repeated on the points left out as
+ * in §II) followed by Lloyd's k-means on every subcluster (Algorithm 1 step 4, §I).
+ *   N        subcluster size, >= 1.  S = ceil(n / N) subclusters; the last one holds
+ *            the n - (S-1) N points left.
+ *   local_k  local centers per subcluster, >= 1; a subcluster of m < local_k points gets
+ *            k_eff = m centers.  P = sum of k_eff pooled centers.
+ *   iters    Lloyd iterations (>= 0), exactly this many.
+ *   seed     initial centers: the first k_eff entries of a Fisher-Yates shuffle of the
+ *            subcluster driven by SplitMix64 keyed by (seed, stage 0, subcluster index).
+ *   prec     a pscl_prec.
+ * Round r: L = per-attribute minimum of the remaining points; the N remaining points
+ * nearest to L by squared Euclidean distance (float64, ascending attribute order; equal
+ * distances by ascending point index) form subcluster r and are removed.
+ * Errors: PSCL_EINVAL, PSCL_ESTATE (not scaled yet), PSCL_ENOMEM, PSCL_ECUDA. */
+int pscl_subcluster(pscl_job *job, int64_t N, int32_t local_k, int32_t iters, uint64_t seed,
+                    int prec);
+
+/* Final clustering of the P pooled local centers (§V) into final_k centers with Lloyd
+ * (initial centers keyed by (seed, stage 1, 0)), then the nearest final center and the
+ * sum of squared errors of every scaled point.
+ * Errors: PSCL_EINVAL (final_k < 1 or > P), PSCL_ESTATE, PSCL_ENOMEM, PSCL_ECUDA. */
+int pscl_cluster(pscl_job *job, int32_t final_k, int32_t iters, uint64_t seed, int prec);
+
+/* The three steps in one call: pscl_scale_features, pscl_subcluster(N, local_k, iters,
+ * seed, prec) and pscl_cluster(final_k, iters, seed, prec).  With PSCL_OPT_GRAPH the
+ * launches are recorded into a CUDA graph on the first call and replayed by later calls
+ * with the same arguments and input pointer (the input's contents may change).
+ * Errors: as the three calls. */
+int pscl_run(pscl_job *job, int64_t N, int32_t local_k, int32_t final_k, int32_t iters,
+             uint64_t seed, int prec);
+
+/* Wait for all queued work of the job. */
+int pscl_job_sync(pscl_job *job);
+
+/* Results (each synchronises the stream first; any pointer may be NULL to skip it).
+ *   pscl_get_scaled:        out n*d float, the scaled points (original order).
+ *   pscl_get_partition:     perm n (original index of the i-th point in subcluster-packed
+ *                           order; subcluster s is perm[seg_off[s] .. seg_off[s+1]-1], in
+ *                           ascending index), seg_off S+1, *n_seg = S.
+ *   pscl_get_local_centers: centers P*d float in (subcluster, center) order, k_eff S,
+ *                           counts P (members of each local center, last iteration).
+ *   pscl_get_result:        centers final_k*d float, labels n (nearest final center of
+ *                           every point, original order), *sse. */
+int pscl_get_scaled(pscl_job *job, float *out);
+int pscl_get_partition(pscl_job *job, int64_t *perm, int64_t *seg_off, int64_t *n_seg);
+int pscl_get_local_centers(pscl_job *job, float *centers, int32_t *k_eff, int32_t *counts);
+int pscl_get_result(pscl_job *job, float *centers, int32_t *labels, double *sse);
+/* Sizes of the current plan: *n_seg = S, *n_pooled = P (after pscl_subcluster). */
+int pscl_get_sizes(pscl_job *job, int64_t *n_seg, int64_t *n_pooled);
+/* Labels of every Lloyd iteration (needs PSCL_OPT_TRACE_LABELS before the run).
+ *   stage 0: iters*n int32, iteration-major, subcluster-packed order;
+ *   stage 1: iters*P int32, the final Lloyd over the pooled centers. */
+int pscl_get_label_trace(pscl_job *job, int stage, int32_t *out);
+/* Launches of every kernel (PSCL_K_COUNT entries) queued by the last run, and, if
+ * PSCL_OPT_KERNEL_TIMING was on for it, their summed device time in milliseconds (else
+ * 0).  Either pointer may be NULL. */
+int pscl_get_kernel_times(pscl_job *job, int64_t *launches, float *ms);
+/* Device time of the phases of the last run in milliseconds: [0] scale, [1] peel,
+ * [2] local Lloyd (incl. init), [3] final Lloyd, [4] SSE pass. */
+int pscl_get_phase_ms(pscl_job *job, float *ms5);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSCL_H */

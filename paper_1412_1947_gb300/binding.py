@@ -1,0 +1,280 @@
+"""Thin Python binding of the pscl C ABI (include/pscl.h).
+
+Every function has the name of the C entry point it calls and only marshals arguments
+(numpy arrays or torch CUDA tensors in, numpy arrays out); all work runs in the CUDA
+library.  There is no other code path: if libpscl.so is missing or cannot be loaded,
+``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpscl.so")
+
+PSCL_OK, PSCL_EINVAL, PSCL_ESTATE, PSCL_ENOMEM, PSCL_EBUSY, PSCL_ETIMEOUT, PSCL_ECUDA = range(7)
+PSCL_F32, PSCL_BF16 = 0, 1
+PSCL_PREC_FP32, PSCL_PREC_TF32, PSCL_PREC_BF16 = 0, 1, 2
+PSCL_OPT_PLAIN_LLOYD, PSCL_OPT_TRACE_LABELS, PSCL_OPT_INIT_FIRST_K, PSCL_OPT_GRAPH = 1, 2, 3, 4
+PSCL_OPT_KERNEL_TIMING = 5
+
+# entry point -> (restype, argtypes); the list is the C ABI of include/pscl.h
+_P, _I, _I32, _I64, _U64, _SZ = C.c_void_p, C.c_int, C.c_int32, C.c_int64, C.c_uint64, C.c_size_t
+SIGNATURES = {
+    "pscl_ctx_create": (_I, [_P, _I, _SZ, _P]),
+    "pscl_ctx_destroy": (_I, [_P]),
+    "pscl_ctx_bytes_in_use": (_SZ, [_P]),
+    "pscl_last_error": (C.c_char_p, []),
+    "pscl_job_create": (_I, [_P, _P, _I, _I64, _I32, _I, _P]),
+    "pscl_job_load": (_I, [_P, _P, _I]),
+    "pscl_job_set_option": (_I, [_P, _I, _I64]),
+    "pscl_job_destroy": (_I, [_P]),
+    "pscl_scale_features": (_I, [_P]),
+    "pscl_subcluster": (_I, [_P, _I64, _I32, _I32, _U64, _I]),
+    "pscl_cluster": (_I, [_P, _I32, _I32, _U64, _I]),
+    "pscl_run": (_I, [_P, _I64, _I32, _I32, _I32, _U64, _I]),
+    "pscl_job_sync": (_I, [_P]),
+    "pscl_get_scaled": (_I, [_P, _P]),
+    "pscl_get_sizes": (_I, [_P, _P, _P]),
+    "pscl_get_partition": (_I, [_P, _P, _P, _P]),
+    "pscl_get_local_centers": (_I, [_P, _P, _P, _P]),
+    "pscl_get_result": (_I, [_P, _P, _P, _P]),
+    "pscl_get_label_trace": (_I, [_P, _I, _P]),
+    "pscl_get_phase_ms": (_I, [_P, _P]),
+    "pscl_get_kernel_times": (_I, [_P, _P, _P]),
+}
+KERNELS = ["scale_minmax", "scale_apply", "peel_dist", "peel_hist", "peel_classify", "peel_compact",
+           "peel_take", "gather", "lloyd_init", "lloyd_assign", "lloyd_finalize", "final_sse"]
+
+_lib = None
+
+
+class PsclError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pscl error {code}: {msg}")
+        self.code = code
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _chk(rc):
+    if rc != PSCL_OK:
+        raise PsclError(rc, lib().pscl_last_error().decode())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()       # torch tensor
+
+
+def _points(points):
+    """(pointer, on_device, n, d, keep-alive) for a numpy array or a torch CUDA tensor."""
+    if isinstance(points, np.ndarray):
+        a = np.ascontiguousarray(points, dtype=np.float32)
+        return a.ctypes.data, 0, a.shape[0], a.shape[1], a
+    t = points
+    if t.dtype.itemsize != 4 or not t.is_contiguous() or t.dim() != 2:
+        raise ValueError("points must be a contiguous 2-D float32 tensor")
+    return t.data_ptr(), 1 if t.is_cuda else 0, t.shape[0], t.shape[1], t
+
+
+# ---------------------------------------------------------------- C entry points
+def pscl_ctx_create(device=0, hbm_budget_bytes=0, stream=None):
+    h = C.c_void_p()
+    _chk(lib().pscl_ctx_create(C.byref(h), device, hbm_budget_bytes, stream))
+    return h
+
+
+def pscl_ctx_destroy(ctx):
+    _chk(lib().pscl_ctx_destroy(ctx))
+
+
+def pscl_ctx_bytes_in_use(ctx):
+    return lib().pscl_ctx_bytes_in_use(ctx)
+
+
+def pscl_job_create(ctx, points, dtype=PSCL_F32):
+    p, dev, n, d, keep = _points(points)
+    h = C.c_void_p()
+    _chk(lib().pscl_job_create(ctx, p, dtype, n, d, dev, C.byref(h)))
+    return h, keep
+
+
+def pscl_job_load(job, points):
+    p, dev, _, _, keep = _points(points)
+    _chk(lib().pscl_job_load(job, p, dev))
+    return keep
+
+
+def pscl_job_set_option(job, option, value):
+    _chk(lib().pscl_job_set_option(job, option, int(value)))
+
+
+def pscl_job_destroy(job):
+    _chk(lib().pscl_job_destroy(job))
+
+
+def pscl_scale_features(job):
+    _chk(lib().pscl_scale_features(job))
+
+
+def pscl_subcluster(job, N, local_k, iters, seed, prec=PSCL_PREC_FP32):
+    _chk(lib().pscl_subcluster(job, N, local_k, iters, seed, prec))
+
+
+def pscl_cluster(job, final_k, iters, seed, prec=PSCL_PREC_FP32):
+    _chk(lib().pscl_cluster(job, final_k, iters, seed, prec))
+
+
+def pscl_run(job, N, local_k, final_k, iters, seed, prec=PSCL_PREC_FP32):
+    _chk(lib().pscl_run(job, N, local_k, final_k, iters, seed, prec))
+
+
+def pscl_job_sync(job):
+    _chk(lib().pscl_job_sync(job))
+
+
+def pscl_get_sizes(job):
+    s, p = C.c_int64(), C.c_int64()
+    _chk(lib().pscl_get_sizes(job, C.byref(s), C.byref(p)))
+    return s.value, p.value
+
+
+def pscl_get_scaled(job, n, d):
+    out = np.empty((n, d), np.float32)
+    _chk(lib().pscl_get_scaled(job, _ptr(out)))
+    return out
+
+
+def pscl_get_partition(job, n):
+    S, _ = pscl_get_sizes(job)
+    perm = np.empty(n, np.int64)
+    off = np.empty(S + 1, np.int64)
+    ns = C.c_int64()
+    _chk(lib().pscl_get_partition(job, _ptr(perm), _ptr(off), C.byref(ns)))
+    return perm, off
+
+
+def pscl_get_local_centers(job, d):
+    S, P = pscl_get_sizes(job)
+    c = np.empty((P, d), np.float32)
+    ke = np.empty(S, np.int32)
+    cnt = np.empty(P, np.int32)
+    _chk(lib().pscl_get_local_centers(job, _ptr(c), _ptr(ke), _ptr(cnt)))
+    return c, ke, cnt
+
+
+def pscl_get_result(job, final_k, d, n=None):
+    c = np.empty((final_k, d), np.float32)
+    lab = None if n is None else np.empty(n, np.int32)
+    sse = C.c_double()
+    _chk(lib().pscl_get_result(job, _ptr(c), _ptr(lab), C.byref(sse)))
+    return c, lab, sse.value
+
+
+def pscl_get_label_trace(job, stage, length):
+    out = np.empty(length, np.int32)
+    _chk(lib().pscl_get_label_trace(job, stage, _ptr(out)))
+    return out
+
+
+def pscl_get_phase_ms(job):
+    ms = np.empty(5, np.float32)
+    _chk(lib().pscl_get_phase_ms(job, _ptr(ms)))
+    return ms
+
+
+def pscl_get_kernel_times(job):
+    """{kernel name: (launches, total ms)} of the last run."""
+    n = np.empty(len(KERNELS), np.int64)
+    ms = np.empty(len(KERNELS), np.float32)
+    _chk(lib().pscl_get_kernel_times(job, _ptr(n), _ptr(ms)))
+    return {k: (int(n[i]), float(ms[i])) for i, k in enumerate(KERNELS)}
+
+
+# ---------------------------------------------------------------- convenience
+class Job:
+    """One clustering problem on one device (a light owner of the C handles)."""
+
+    def __init__(self, points, device=0, hbm_budget_bytes=0, stream=None, ctx=None):
+        self._own_ctx = ctx is None
+        self.ctx = pscl_ctx_create(device, hbm_budget_bytes, stream) if ctx is None else ctx
+        self.h, self._keep = pscl_job_create(self.ctx, points)
+        self.n, self.d = int(points.shape[0]), int(points.shape[1])
+        self.final_k = None
+
+    def option(self, opt, value=1):
+        pscl_job_set_option(self.h, opt, value)
+        return self
+
+    def load(self, points):
+        self._keep = pscl_job_load(self.h, points)
+
+    def run(self, N, local_k, final_k, iters, seed, prec=PSCL_PREC_FP32):
+        pscl_run(self.h, N, local_k, final_k, iters, seed, prec)
+        self.final_k = final_k
+
+    def steps(self, N, local_k, final_k, iters, seed, prec=PSCL_PREC_FP32):
+        pscl_scale_features(self.h)
+        pscl_subcluster(self.h, N, local_k, iters, seed, prec)
+        pscl_cluster(self.h, final_k, iters, seed, prec)
+        self.final_k = final_k
+
+    def scaled(self):
+        return pscl_get_scaled(self.h, self.n, self.d)
+
+    def partition(self):
+        return pscl_get_partition(self.h, self.n)
+
+    def local_centers(self):
+        return pscl_get_local_centers(self.h, self.d)
+
+    def result(self, labels=True):
+        return pscl_get_result(self.h, self.final_k, self.d, self.n if labels else None)
+
+    def sizes(self):
+        return pscl_get_sizes(self.h)
+
+    def trace(self, stage, iters):
+        S, P = self.sizes()
+        return pscl_get_label_trace(self.h, stage, iters * (self.n if stage == 0 else P)).reshape(iters, -1)
+
+    def phase_ms(self):
+        return pscl_get_phase_ms(self.h)
+
+    def kernel_times(self):
+        return pscl_get_kernel_times(self.h)
+
+    def close(self):
+        if self.h is not None:
+            pscl_job_destroy(self.h)
+            self.h = None
+        if self._own_ctx and self.ctx is not None:
+            pscl_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

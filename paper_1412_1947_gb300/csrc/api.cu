@@ -1,0 +1,801 @@
+// C ABI of the pscl library: contexts, jobs, planning and the order of launches.
+// The kernels live in scale.cu, peel.cu and lloyd.cu; this file only allocates,
+// uploads the small index tables, queues launches and copies results out.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pscl_internal.cuh"
+
+using namespace pscl;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(PSCL_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                                \
+    } while (0)
+
+// ------------------------------------------------------------------ objects
+struct pscl_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0;
+    size_t in_use = 0;
+    int sm_count = 0;
+};
+
+struct Alloc {
+    void *p;
+    size_t bytes;
+};
+
+// One Lloyd launch plan: tables on the device and their host copies.
+struct LloydPlan {
+    int n_seg = 0, n_units = 0, kmax = 0, d = 0;
+    int64_t rows = 0, P = 0;
+    std::vector<int64_t> seg_start;
+    std::vector<int32_t> seg_size, cen_off, k_eff, unit_seg, unit_start, unit_count, seg_unit0;
+    int64_t *d_seg_start = nullptr;
+    int32_t *d_i32 = nullptr;       // seg_size | cen_off | k_eff | unit_seg | unit_start | unit_count
+    SegTable table() const
+    {
+        SegTable t;
+        t.seg_start = d_seg_start;
+        t.seg_size = d_i32;
+        t.cen_off = d_i32 + n_seg;
+        t.k_eff = d_i32 + 2 * n_seg;
+        t.unit_seg = d_i32 + 3 * n_seg;
+        t.unit_start = d_i32 + 3 * n_seg + n_units;
+        t.unit_count = d_i32 + 3 * n_seg + 2 * n_units;
+        t.n_seg = n_seg;
+        t.n_units = n_units;
+        return t;
+    }
+};
+
+struct pscl_job {
+    pscl_ctx *ctx = nullptr;
+    int64_t n = 0;
+    int d = 0;
+    std::vector<Alloc> allocs;
+    int state = 0;                    // 0 loaded, 1 scaled, 2 subclustered, 3 clustered
+    // options
+    int plain = 0, trace = 0, first_k = 0, graph = 0, ktiming = 0;
+    KTimer kt;                        // launch counts (+ events when timing) of the last run
+    // input and scaling
+    const float *dev_in = nullptr;    // caller's device buffer, or raw
+    float *raw = nullptr;             // owned copy of host input
+    float *x = nullptr;               // scaled points (original order)
+    double *mn = nullptr, *mx = nullptr;
+    float *part = nullptr;
+    uint32_t *tickets = nullptr;      // [0] scale, [1] sse
+    PeelCtl *ctl = nullptr;
+    // subcluster plan
+    int64_t N = 0;
+    int local_k = 0, iters = 0, prec = 0;
+    uint64_t seed = 0;
+    int64_t S = 0, P = 0;
+    std::vector<int64_t> seg_off;
+    PeelBuffers pb{};
+    bool peel_alloc = false;
+    LloydPlan lp;
+    float *cl = nullptr;              // P x d local centers
+    unsigned long long *acc_l = nullptr;
+    int32_t *cnt_l = nullptr;         // 2P
+    int32_t *lab_l = nullptr;         // n (packed order)
+    int32_t *trace_l = nullptr;       // iters x n
+    int64_t trace_l_len = 0;
+    // final plan
+    int final_k = 0, fiters = 0, fprec = 0;
+    uint64_t fseed = 0;
+    LloydPlan fp;
+    float *cf = nullptr;
+    unsigned long long *acc_f = nullptr;
+    int32_t *cnt_f = nullptr;
+    int32_t *lab_f = nullptr;         // P
+    int32_t *trace_f = nullptr;
+    int64_t trace_f_len = 0;
+    int32_t *labels = nullptr;        // n
+    double *blk_sse = nullptr;
+    double *sse = nullptr;
+    int sse_blocks = 0;
+    // phases
+    cudaEvent_t ev[6] = {};
+    bool ev_ok = false;
+    // recorded pipeline
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t gkey[8] = {};
+};
+
+// ------------------------------------------------------------------ memory
+static int job_alloc(pscl_job *j, void **p, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    pscl_ctx *c = j->ctx;
+    if (c->budget && c->in_use + bytes > c->budget)
+        return fail(PSCL_ENOMEM, "device-memory budget exceeded: %zu in use + %zu requested > %zu",
+                    c->in_use, bytes, c->budget);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? PSCL_ENOMEM : PSCL_ECUDA,
+                    "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    j->allocs.push_back({*p, bytes});
+    c->in_use += bytes;
+    return PSCL_OK;
+}
+
+static void job_free(pscl_job *j, void *p)
+{
+    if (!p) return;
+    for (size_t i = 0; i < j->allocs.size(); i++) {
+        if (j->allocs[i].p == p) {
+            cudaFree(p);
+            j->ctx->in_use -= j->allocs[i].bytes;
+            j->allocs.erase(j->allocs.begin() + i);
+            return;
+        }
+    }
+}
+
+template <class T>
+static int A(pscl_job *j, T **p, size_t count)
+{
+    void *v = nullptr;
+    int rc = job_alloc(j, &v, count * sizeof(T));
+    *p = static_cast<T *>(v);
+    return rc;
+}
+
+#define TRY(x)                    \
+    do {                          \
+        int rc_ = (x);            \
+        if (rc_ != PSCL_OK) return rc_; \
+    } while (0)
+
+static void drop_graph(pscl_job *j)
+{
+    if (j->gexec) {
+        cudaGraphExecDestroy(j->gexec);
+        j->gexec = nullptr;
+    }
+}
+
+// ------------------------------------------------------------------ context
+extern "C" int pscl_ctx_create(pscl_ctx **out, int device, size_t budget, void *stream)
+{
+    if (!out) return fail(PSCL_EINVAL, "out is NULL");
+    int ndev = 0;
+    CU(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(PSCL_EINVAL, "device %d out of range (%d devices)", device, ndev);
+    CU(cudaSetDevice(device));
+    pscl_ctx *c = new pscl_ctx();
+    c->device = device;
+    c->budget = budget;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (stream) {
+        c->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(PSCL_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        }
+        c->own_stream = true;
+    }
+    *out = c;
+    g_err.clear();
+    return PSCL_OK;
+}
+
+extern "C" int pscl_ctx_destroy(pscl_ctx *c)
+{
+    if (!c) return fail(PSCL_EINVAL, "ctx is NULL");
+    cudaSetDevice(c->device);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return PSCL_OK;
+}
+
+extern "C" size_t pscl_ctx_bytes_in_use(const pscl_ctx *c) { return c ? c->in_use : 0; }
+
+extern "C" const char *pscl_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------ jobs
+static int load_points(pscl_job *j, const void *points, int on_device)
+{
+    if (!points) return fail(PSCL_EINVAL, "points is NULL");
+    if (on_device) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, points) != cudaSuccess || at.type != cudaMemoryTypeDevice ||
+            at.device != j->ctx->device) {
+            cudaGetLastError();
+            return fail(PSCL_EINVAL, "points_on_device=1 but the pointer is not device memory of device %d",
+                        j->ctx->device);
+        }
+        if (((uintptr_t)points & 15) != 0) return fail(PSCL_EINVAL, "device points must be 16-byte aligned");
+        j->dev_in = static_cast<const float *>(points);
+    } else {
+        if (!j->raw) TRY(A(j, &j->raw, (size_t)j->n * j->d));
+        CU(cudaMemcpyAsync(j->raw, points, (size_t)j->n * j->d * sizeof(float), cudaMemcpyHostToDevice,
+                           j->ctx->stream));
+        j->dev_in = j->raw;
+    }
+    j->state = 0;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_job_create(pscl_ctx *c, const void *points, int dtype, int64_t n, int32_t d,
+                               int on_device, pscl_job **out)
+{
+    if (!c || !out) return fail(PSCL_EINVAL, "ctx or out is NULL");
+    if (dtype != PSCL_F32) return fail(PSCL_EINVAL, "only PSCL_F32 storage is supported");
+    if (n < 1 || n > (int64_t)INT32_MAX) return fail(PSCL_EINVAL, "n=%lld outside 1..2^31-1", (long long)n);
+    if (d < 1 || d > kMaxD) return fail(PSCL_EINVAL, "d=%d outside 1..%d", d, kMaxD);
+    CU(cudaSetDevice(c->device));
+    pscl_job *j = new pscl_job();
+    j->ctx = c;
+    j->n = n;
+    j->d = d;
+    int rc = PSCL_OK;
+    if (!rc) rc = A(j, &j->x, (size_t)n * d);
+    if (!rc) rc = A(j, &j->mn, d);
+    if (!rc) rc = A(j, &j->mx, d);
+    if (!rc) rc = A(j, &j->part, scale_part_floats(n, d, c->sm_count));
+    if (!rc) rc = A(j, &j->tickets, 8);
+    if (!rc) rc = A(j, &j->ctl, 1);
+    if (!rc && cudaMemsetAsync(j->tickets, 0, 8 * sizeof(uint32_t), c->stream) != cudaSuccess) rc = PSCL_ECUDA;
+    if (!rc && cudaMemsetAsync(j->ctl, 0, sizeof(PeelCtl), c->stream) != cudaSuccess) rc = PSCL_ECUDA;
+    if (!rc) rc = load_points(j, points, on_device);
+    if (!rc) {
+        for (int i = 0; i < 6 && !rc; i++)
+            if (cudaEventCreate(&j->ev[i]) != cudaSuccess) rc = PSCL_ECUDA;
+    }
+    if (rc) {
+        std::string msg = g_err;
+        pscl_job_destroy(j);
+        g_err = msg;
+        return rc;
+    }
+    *out = j;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_job_load(pscl_job *j, const void *points, int on_device)
+{
+    if (!j) return fail(PSCL_EINVAL, "job is NULL");
+    CU(cudaSetDevice(j->ctx->device));
+    return load_points(j, points, on_device);
+}
+
+extern "C" int pscl_job_set_option(pscl_job *j, int opt, int64_t v)
+{
+    if (!j) return fail(PSCL_EINVAL, "job is NULL");
+    switch (opt) {
+    case PSCL_OPT_PLAIN_LLOYD: j->plain = v != 0; break;
+    case PSCL_OPT_TRACE_LABELS: j->trace = v != 0; break;
+    case PSCL_OPT_INIT_FIRST_K: j->first_k = v != 0; break;
+    case PSCL_OPT_GRAPH: j->graph = v != 0; break;
+    case PSCL_OPT_KERNEL_TIMING: j->ktiming = v != 0; break;
+    default: return fail(PSCL_EINVAL, "unknown option %d", opt);
+    }
+    drop_graph(j);
+    return PSCL_OK;
+}
+
+extern "C" int pscl_job_destroy(pscl_job *j)
+{
+    if (!j) return fail(PSCL_EINVAL, "job is NULL");
+    cudaSetDevice(j->ctx->device);
+    cudaStreamSynchronize(j->ctx->stream);
+    drop_graph(j);
+    for (auto &a : j->allocs) {
+        cudaFree(a.p);
+        j->ctx->in_use -= a.bytes;
+    }
+    for (int i = 0; i < 6; i++)
+        if (j->ev[i]) cudaEventDestroy(j->ev[i]);
+    if (j->kt.ev) {
+        for (int i = 0; i < 2 * j->kt.cap; i++) cudaEventDestroy(j->kt.ev[i]);
+        delete[] j->kt.ev;
+        delete[] j->kt.tag;
+    }
+    delete j;
+    return PSCL_OK;
+}
+
+// ------------------------------------------------------------------ planning
+// Work units: every set is cut into ceil(m / target) near-equal pieces (multiples of 32
+// rows), target chosen so that a launch has a few units per SM.
+static int build_lloyd_plan(pscl_job *j, LloydPlan &p, const std::vector<int64_t> &starts,
+                            const std::vector<int32_t> &sizes, const std::vector<int32_t> &keff)
+{
+    p.n_seg = (int)sizes.size();
+    p.seg_start = starts;
+    p.seg_size = sizes;
+    p.k_eff = keff;
+    p.cen_off.assign(p.n_seg, 0);
+    p.kmax = 0;
+    int64_t P = 0, rows = 0;
+    for (int s = 0; s < p.n_seg; s++) {
+        p.cen_off[s] = (int32_t)P;
+        P += keff[s];
+        rows += sizes[s];
+        p.kmax = std::max(p.kmax, keff[s]);
+    }
+    p.P = P;
+    p.rows = rows;
+    int64_t target = rows / ((int64_t)j->ctx->sm_count * 4);
+    target = std::max<int64_t>(128, std::min<int64_t>(1024, target));
+    p.unit_seg.clear();
+    p.unit_start.clear();
+    p.unit_count.clear();
+    p.seg_unit0.assign(p.n_seg + 1, 0);
+    for (int s = 0; s < p.n_seg; s++) {
+        p.seg_unit0[s] = (int32_t)p.unit_seg.size();
+        int64_t m = sizes[s];
+        int64_t nu = (m + target - 1) / target;
+        int64_t us = ((m + nu - 1) / nu + 31) / 32 * 32;
+        for (int64_t r = 0; r < m; r += us) {
+            p.unit_seg.push_back(s);
+            p.unit_start.push_back((int32_t)r);
+            p.unit_count.push_back((int32_t)std::min<int64_t>(us, m - r));
+        }
+    }
+    p.n_units = (int)p.unit_seg.size();
+    p.seg_unit0[p.n_seg] = p.n_units;
+    job_free(j, p.d_seg_start);
+    job_free(j, p.d_i32);
+    p.d_seg_start = nullptr;
+    p.d_i32 = nullptr;
+    TRY(A(j, &p.d_seg_start, p.n_seg));
+    TRY(A(j, &p.d_i32, 3 * (size_t)p.n_seg + 3 * (size_t)p.n_units));
+    std::vector<int32_t> packed;
+    packed.reserve(3 * p.n_seg + 3 * p.n_units);
+    packed.insert(packed.end(), p.seg_size.begin(), p.seg_size.end());
+    packed.insert(packed.end(), p.cen_off.begin(), p.cen_off.end());
+    packed.insert(packed.end(), p.k_eff.begin(), p.k_eff.end());
+    packed.insert(packed.end(), p.unit_seg.begin(), p.unit_seg.end());
+    packed.insert(packed.end(), p.unit_start.begin(), p.unit_start.end());
+    packed.insert(packed.end(), p.unit_count.begin(), p.unit_count.end());
+    CU(cudaMemcpy(p.d_seg_start, p.seg_start.data(), p.n_seg * sizeof(int64_t), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(p.d_i32, packed.data(), packed.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    return PSCL_OK;
+}
+
+static int check_prec(int prec)
+{
+    if (prec != PSCL_PREC_FP32 && prec != PSCL_PREC_TF32 && prec != PSCL_PREC_BF16)
+        return fail(PSCL_EINVAL, "unknown precision %d", prec);
+    if (prec != PSCL_PREC_FP32) return fail(PSCL_EINVAL, "precision %d is not available in this build", prec);
+    return PSCL_OK;
+}
+
+static int plan_subcluster(pscl_job *j, int64_t N, int32_t local_k, int32_t iters, uint64_t seed, int prec)
+{
+    if (N < 1) return fail(PSCL_EINVAL, "N=%lld < 1", (long long)N);
+    if (local_k < 1 || local_k > kMaxK) return fail(PSCL_EINVAL, "local_k=%d outside 1..%d", local_k, kMaxK);
+    if (iters < 0) return fail(PSCL_EINVAL, "iters < 0");
+    TRY(check_prec(prec));
+    const int64_t n = j->n;
+    const int d = j->d;
+    if (!j->peel_alloc) {
+        PeelBuffers &b = j->pb;
+        b.x = j->x;
+        TRY(A(j, &b.idx[0], n));
+        TRY(A(j, &b.idx[1], n));
+        TRY(A(j, &b.key, n));
+        TRY(A(j, &b.status, n + 16));
+        TRY(A(j, &b.band_key, n));
+        TRY(A(j, &b.band_pos, n));
+        size_t nblk = (size_t)(n + kBlkItems - 1) / kBlkItems;
+        TRY(A(j, &b.blk_cnt, nblk));
+        TRY(A(j, &b.blk_off, nblk));
+        TRY(A(j, &b.lpart, nblk * d));
+        TRY(A(j, &b.L, d));
+        TRY(A(j, &b.perm, n));
+        TRY(A(j, &b.xseg, (size_t)n * d));
+        TRY(A(j, &j->lab_l, n));
+        b.ctl = j->ctl;
+        j->peel_alloc = true;
+    }
+    const bool same = N == j->N && local_k == j->local_k;
+    j->iters = iters;
+    j->seed = seed;
+    j->prec = prec;
+    if (!same) {
+        drop_graph(j);
+        j->N = N;
+        j->local_k = local_k;
+        j->S = (n + N - 1) / N;
+        j->seg_off.assign(j->S + 1, 0);
+        std::vector<int64_t> starts(j->S);
+        std::vector<int32_t> sizes(j->S), keff(j->S);
+        for (int64_t s = 0; s < j->S; s++) {
+            j->seg_off[s] = s * N;
+            starts[s] = s * N;
+            sizes[s] = (int32_t)std::min<int64_t>(N, n - s * N);
+            keff[s] = std::min<int32_t>(local_k, sizes[s]);
+        }
+        j->seg_off[j->S] = n;
+        job_free(j, j->pb.landmarks);
+        j->pb.landmarks = nullptr;
+        TRY(A(j, &j->pb.landmarks, (size_t)j->S * d));
+        TRY(build_lloyd_plan(j, j->lp, starts, sizes, keff));
+        j->P = j->lp.P;
+        job_free(j, j->cl);
+        job_free(j, j->acc_l);
+        job_free(j, j->cnt_l);
+        j->cl = nullptr;
+        j->acc_l = nullptr;
+        j->cnt_l = nullptr;
+        TRY(A(j, &j->cl, (size_t)j->P * d));
+        TRY(A(j, &j->acc_l, (size_t)j->P * d));
+        TRY(A(j, &j->cnt_l, 2 * (size_t)j->P));
+        j->final_k = 0;              // the final plan depends on P
+    }
+    int64_t tl = j->trace ? (int64_t)iters * n : 0;
+    if (tl != j->trace_l_len) {
+        job_free(j, j->trace_l);
+        j->trace_l = nullptr;
+        j->trace_l_len = tl;
+        if (tl) TRY(A(j, &j->trace_l, tl));
+    }
+    return PSCL_OK;
+}
+
+static int plan_cluster(pscl_job *j, int32_t final_k, int32_t iters, uint64_t seed, int prec)
+{
+    if (j->state < 2) return fail(PSCL_ESTATE, "pscl_cluster needs pscl_subcluster first");
+    if (final_k < 1 || final_k > kMaxK) return fail(PSCL_EINVAL, "final_k=%d outside 1..%d", final_k, kMaxK);
+    if ((int64_t)final_k > j->P)
+        return fail(PSCL_EINVAL, "final_k=%d exceeds the %lld pooled local centers", final_k, (long long)j->P);
+    if (iters < 0) return fail(PSCL_EINVAL, "iters < 0");
+    TRY(check_prec(prec));
+    const int d = j->d;
+    j->fiters = iters;
+    j->fseed = seed;
+    j->fprec = prec;
+    if (final_k != j->final_k) {
+        drop_graph(j);
+        j->final_k = final_k;
+        std::vector<int64_t> starts(1, 0);
+        std::vector<int32_t> sizes(1, (int32_t)j->P), keff(1, final_k);
+        TRY(build_lloyd_plan(j, j->fp, starts, sizes, keff));
+        job_free(j, j->cf);
+        job_free(j, j->acc_f);
+        job_free(j, j->cnt_f);
+        job_free(j, j->lab_f);
+        j->cf = nullptr;
+        j->acc_f = nullptr;
+        j->cnt_f = nullptr;
+        j->lab_f = nullptr;
+        TRY(A(j, &j->cf, (size_t)final_k * d));
+        TRY(A(j, &j->acc_f, (size_t)final_k * d));
+        TRY(A(j, &j->cnt_f, 2 * (size_t)final_k));
+        TRY(A(j, &j->lab_f, j->P));
+    }
+    if (!j->labels) {
+        TRY(A(j, &j->labels, j->n));
+        j->sse_blocks = sse_grid(j->n, j->ctx->sm_count);
+        TRY(A(j, &j->blk_sse, j->sse_blocks));
+        TRY(A(j, &j->sse, 1));
+    }
+    int64_t tl = j->trace ? (int64_t)iters * j->P : 0;
+    if (tl != j->trace_f_len) {
+        job_free(j, j->trace_f);
+        j->trace_f = nullptr;
+        j->trace_f_len = tl;
+        if (tl) TRY(A(j, &j->trace_f, tl));
+    }
+    return PSCL_OK;
+}
+
+// ------------------------------------------------------------------ enqueue (launches only)
+static int run_lloyd(pscl_job *j, const LloydPlan &p, const float *pts, float *centers,
+                     unsigned long long *acc, int32_t *cnt2, int32_t *labels, int32_t *trace,
+                     int iters, uint64_t seed, uint32_t stage, bool plain)
+{
+    cudaStream_t st = j->ctx->stream;
+    const SegTable t = p.table();
+    LloydBuffers b{};
+    b.pts = pts;
+    b.centers = centers;
+    b.acc = acc;
+    b.count = cnt2;
+    b.labels = labels;
+    b.trace = trace;
+    b.rows = p.rows;
+    CU(launch_lloyd_init(b, t, j->d, p.P, seed, stage, j->first_k, p.kmax, st, &j->kt));
+    if (!plain) {
+        for (int it = 0; it < iters; it++) {
+            b.count = cnt2 + (size_t)(it & 1) * p.P;
+            CU(launch_lloyd_iter(b, cnt2 + (size_t)((it + 1) & 1) * p.P, t, j->d, it, 0, p.n_units, 0, p.P,
+                                 p.kmax, j->ctx->sm_count, st, &j->kt));
+        }
+    } else {
+        for (int s = 0; s < p.n_seg; s++) {
+            for (int it = 0; it < iters; it++) {
+                b.count = cnt2 + (size_t)(it & 1) * p.P;
+                CU(launch_lloyd_iter(b, cnt2 + (size_t)((it + 1) & 1) * p.P, t, j->d, it, p.seg_unit0[s],
+                                     p.seg_unit0[s + 1], p.cen_off[s], (int64_t)p.cen_off[s] + p.k_eff[s],
+                                     p.k_eff[s], j->ctx->sm_count, st, &j->kt));
+            }
+        }
+    }
+    return PSCL_OK;
+}
+
+static int enqueue_scale(pscl_job *j, bool events)
+{
+    cudaStream_t st = j->ctx->stream;
+    if (events) CU(cudaEventRecord(j->ev[0], st));
+    CU(launch_scale(j->dev_in, j->x, j->n, j->d, j->part, j->tickets, j->mn, j->mx, j->ctl,
+                    j->ctx->sm_count, st, &j->kt));
+    if (events) CU(cudaEventRecord(j->ev[1], st));
+    return PSCL_OK;
+}
+
+static int enqueue_subcluster(pscl_job *j, bool events)
+{
+    cudaStream_t st = j->ctx->stream;
+    CU(launch_peel(j->pb, j->n, j->d, j->N, j->ctx->sm_count, st, &j->kt));
+    if (events) CU(cudaEventRecord(j->ev[2], st));
+    TRY(run_lloyd(j, j->lp, j->pb.xseg, j->cl, j->acc_l, j->cnt_l, j->lab_l, j->trace_l, j->iters, j->seed, 0u,
+                  j->plain != 0));
+    if (events) CU(cudaEventRecord(j->ev[3], st));
+    return PSCL_OK;
+}
+
+static int enqueue_cluster(pscl_job *j, bool events)
+{
+    cudaStream_t st = j->ctx->stream;
+    TRY(run_lloyd(j, j->fp, j->cl, j->cf, j->acc_f, j->cnt_f, j->lab_f, j->trace_f, j->fiters, j->fseed, 1u,
+                  false));
+    if (events) CU(cudaEventRecord(j->ev[4], st));
+    CU(launch_final_sse(j->x, j->n, j->d, j->cf, j->final_k, j->labels, j->blk_sse, j->sse, j->tickets + 1,
+                        j->ctx->sm_count, st, &j->kt));
+    if (events) CU(cudaEventRecord(j->ev[5], st));
+    return PSCL_OK;
+}
+
+// Count launches of a new run; bracket them with events if timing is on and the run is
+// not being recorded into a graph.
+static int timer_start(pscl_job *j, bool recording)
+{
+    KTimer &k = j->kt;
+    k.reset();
+    if (j->ktiming && !recording) {
+        if (!k.ev) {
+            k.cap = 1 << 14;
+            k.ev = new cudaEvent_t[2 * k.cap];
+            k.tag = new int[k.cap];
+            for (int i = 0; i < 2 * k.cap; i++) CU(cudaEventCreate(&k.ev[i]));
+        }
+        k.n = 0;
+    } else if (k.ev) {
+        k.n = k.cap;                 // keep the events but record none
+    }
+    return PSCL_OK;
+}
+
+// ------------------------------------------------------------------ method entry points
+extern "C" int pscl_scale_features(pscl_job *j)
+{
+    if (!j) return fail(PSCL_EINVAL, "job is NULL");
+    CU(cudaSetDevice(j->ctx->device));
+    TRY(timer_start(j, false));
+    TRY(enqueue_scale(j, true));
+    j->state = 1;
+    j->ev_ok = false;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_subcluster(pscl_job *j, int64_t N, int32_t local_k, int32_t iters, uint64_t seed, int prec)
+{
+    if (!j) return fail(PSCL_EINVAL, "job is NULL");
+    if (j->state < 1) return fail(PSCL_ESTATE, "pscl_subcluster needs pscl_scale_features first");
+    CU(cudaSetDevice(j->ctx->device));
+    TRY(plan_subcluster(j, N, local_k, iters, seed, prec));
+    TRY(enqueue_subcluster(j, true));
+    j->state = 2;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_cluster(pscl_job *j, int32_t final_k, int32_t iters, uint64_t seed, int prec)
+{
+    if (!j) return fail(PSCL_EINVAL, "job is NULL");
+    CU(cudaSetDevice(j->ctx->device));
+    TRY(plan_cluster(j, final_k, iters, seed, prec));
+    TRY(enqueue_cluster(j, true));
+    j->state = 3;
+    j->ev_ok = true;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_run(pscl_job *j, int64_t N, int32_t local_k, int32_t final_k, int32_t iters,
+                        uint64_t seed, int prec)
+{
+    if (!j) return fail(PSCL_EINVAL, "job is NULL");
+    CU(cudaSetDevice(j->ctx->device));
+    // planning (allocation, table uploads) happens outside any recording
+    j->state = 1;
+    TRY(plan_subcluster(j, N, local_k, iters, seed, prec));
+    j->state = 2;
+    TRY(plan_cluster(j, final_k, iters, seed, prec));
+    cudaStream_t st = j->ctx->stream;
+    if (!j->graph) {
+        TRY(timer_start(j, false));
+        TRY(enqueue_scale(j, true));
+        TRY(enqueue_subcluster(j, true));
+        TRY(enqueue_cluster(j, true));
+        j->state = 3;
+        j->ev_ok = true;
+        return PSCL_OK;
+    }
+    uint64_t key[8] = {(uint64_t)N, (uint64_t)local_k, (uint64_t)final_k, (uint64_t)iters, seed, (uint64_t)prec,
+                       (uint64_t)(uintptr_t)j->dev_in, (uint64_t)(j->plain | j->trace << 1 | j->first_k << 2)};
+    if (j->gexec && memcmp(key, j->gkey, sizeof key) != 0) drop_graph(j);
+    if (!j->gexec) {
+        cudaGraph_t g = nullptr;
+        TRY(timer_start(j, true));
+        CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_scale(j, false);
+        if (!rc) rc = enqueue_subcluster(j, false);
+        if (!rc) rc = enqueue_cluster(j, false);
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(PSCL_ECUDA, "stream capture failed: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&j->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            j->gexec = nullptr;
+            return fail(PSCL_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+        }
+        memcpy(j->gkey, key, sizeof key);
+    }
+    CU(cudaGraphLaunch(j->gexec, st));
+    j->state = 3;
+    j->ev_ok = false;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_job_sync(pscl_job *j)
+{
+    if (!j) return fail(PSCL_EINVAL, "job is NULL");
+    CU(cudaSetDevice(j->ctx->device));
+    CU(cudaStreamSynchronize(j->ctx->stream));
+    PeelCtl h;
+    CU(cudaMemcpy(&h.nonfinite, &j->ctl->nonfinite, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (h.nonfinite) return fail(PSCL_EINVAL, "the input holds a value that is not finite");
+    if (h.error) return fail(PSCL_ECUDA, "internal error: the peel's float32 filter bound was violated");
+    return PSCL_OK;
+}
+
+// ------------------------------------------------------------------ results
+extern "C" int pscl_get_scaled(pscl_job *j, float *out)
+{
+    TRY(pscl_job_sync(j));
+    if (j->state < 1) return fail(PSCL_ESTATE, "not scaled");
+    if (out) CU(cudaMemcpy(out, j->x, (size_t)j->n * j->d * sizeof(float), cudaMemcpyDeviceToHost));
+    return PSCL_OK;
+}
+
+extern "C" int pscl_get_sizes(pscl_job *j, int64_t *n_seg, int64_t *n_pooled)
+{
+    if (!j) return fail(PSCL_EINVAL, "job is NULL");
+    if (j->state < 2) return fail(PSCL_ESTATE, "no subcluster plan yet");
+    if (n_seg) *n_seg = j->S;
+    if (n_pooled) *n_pooled = j->P;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_get_partition(pscl_job *j, int64_t *perm, int64_t *seg_off, int64_t *n_seg)
+{
+    TRY(pscl_job_sync(j));
+    if (j->state < 2) return fail(PSCL_ESTATE, "not subclustered");
+    if (perm) {
+        std::vector<uint32_t> h(j->n);
+        CU(cudaMemcpy(h.data(), j->pb.perm, j->n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < j->n; i++) perm[i] = h[i];
+    }
+    if (seg_off) memcpy(seg_off, j->seg_off.data(), (j->S + 1) * sizeof(int64_t));
+    if (n_seg) *n_seg = j->S;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_get_local_centers(pscl_job *j, float *centers, int32_t *k_eff, int32_t *counts)
+{
+    TRY(pscl_job_sync(j));
+    if (j->state < 2) return fail(PSCL_ESTATE, "not subclustered");
+    if (centers) CU(cudaMemcpy(centers, j->cl, (size_t)j->P * j->d * sizeof(float), cudaMemcpyDeviceToHost));
+    if (k_eff) memcpy(k_eff, j->lp.k_eff.data(), j->S * sizeof(int32_t));
+    if (counts) {
+        if (j->iters == 0) {
+            memset(counts, 0, j->P * sizeof(int32_t));
+        } else {
+            const int32_t *src = j->cnt_l + (size_t)((j->iters - 1) & 1) * j->P;
+            CU(cudaMemcpy(counts, src, j->P * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        }
+    }
+    return PSCL_OK;
+}
+
+extern "C" int pscl_get_result(pscl_job *j, float *centers, int32_t *labels, double *sse)
+{
+    TRY(pscl_job_sync(j));
+    if (j->state < 3) return fail(PSCL_ESTATE, "not clustered");
+    if (centers) CU(cudaMemcpy(centers, j->cf, (size_t)j->final_k * j->d * sizeof(float), cudaMemcpyDeviceToHost));
+    if (labels) CU(cudaMemcpy(labels, j->labels, j->n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (sse) CU(cudaMemcpy(sse, j->sse, sizeof(double), cudaMemcpyDeviceToHost));
+    return PSCL_OK;
+}
+
+extern "C" int pscl_get_label_trace(pscl_job *j, int stage, int32_t *out)
+{
+    TRY(pscl_job_sync(j));
+    if (!out) return fail(PSCL_EINVAL, "out is NULL");
+    if (stage == 0) {
+        if (j->state < 2 || !j->trace_l) return fail(PSCL_ESTATE, "no local label trace recorded");
+        CU(cudaMemcpy(out, j->trace_l, j->trace_l_len * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    } else if (stage == 1) {
+        if (j->state < 3 || !j->trace_f) return fail(PSCL_ESTATE, "no final label trace recorded");
+        CU(cudaMemcpy(out, j->trace_f, j->trace_f_len * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    } else {
+        return fail(PSCL_EINVAL, "stage must be 0 or 1");
+    }
+    return PSCL_OK;
+}
+
+extern "C" int pscl_get_kernel_times(pscl_job *j, int64_t *launches, float *ms)
+{
+    TRY(pscl_job_sync(j));
+    if (launches)
+        for (int i = 0; i < PSCL_K_COUNT; i++) launches[i] = j->kt.launches[i];
+    if (ms) {
+        for (int i = 0; i < PSCL_K_COUNT; i++) ms[i] = 0.0f;
+        const int used = j->kt.ev && j->ktiming ? std::min(j->kt.n, j->kt.cap) : 0;
+        for (int e = 0; e < used; e++) {
+            float t = 0.0f;
+            CU(cudaEventElapsedTime(&t, j->kt.ev[2 * e], j->kt.ev[2 * e + 1]));
+            ms[j->kt.tag[e]] += t;
+        }
+    }
+    return PSCL_OK;
+}
+
+extern "C" int pscl_get_phase_ms(pscl_job *j, float *ms)
+{
+    TRY(pscl_job_sync(j));
+    if (!ms) return fail(PSCL_EINVAL, "ms is NULL");
+    if (!j->ev_ok) return fail(PSCL_ESTATE, "no timed run (phase times need an unrecorded pscl_run or the three calls)");
+    for (int i = 0; i < 5; i++) CU(cudaEventElapsedTime(&ms[i], j->ev[i], j->ev[i + 1]));
+    return PSCL_OK;
+}

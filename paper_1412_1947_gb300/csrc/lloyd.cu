@@ -1,0 +1,415 @@
+// Lloyd's k-means (§I) on many point sets at once: every subcluster of Algorithm 1
+// step 4, and the pooled local centers of §V.
+//
+// Layout: the points of all sets are packed row-major one set after another (the
+// paper's "flattening while subgrouping", §V); set s has seg_size[s] rows starting at
+// seg_start[s] and k_eff[s] centers starting at cen_off[s] in one P x d center array.
+// Work is cut into units of at most a few thousand rows of one set, so a launch keeps
+// every SM busy whatever the mix of set sizes.
+//
+// One iteration = k_lloyd_assign (nearest center of every row, lowest index on ties,
+// and the row's coordinates added to its center's sum) + k_lloyd_finalize (center =
+// sum / count; an empty cluster keeps its center).  The sums are exact: coordinates
+// (scaled to [0, 1]) are rounded once to 32.32 fixed point and added as 64-bit
+// integers, first in shared memory, then with one global atomic per (center,
+// attribute) and unit.  Integer addition is associative, so the result does not depend
+// on how units are scheduled or batched with other work.
+#include "pscl_internal.cuh"
+
+namespace pscl {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr float kFix = 4294967296.0f;                  // 2^32
+constexpr size_t kSmemAccMax = 96 * 1024;              // shared accumulators up to this size
+constexpr int kCenterChunkBytes = 48 * 1024;           // center chunk held in shared memory
+
+// ---------------------------------------------------------------- SplitMix64
+// Steele, Lea & Flood (OOPSLA 2014): the state advances by the golden-ratio constant
+// and each output is the variant-13 mix of the state.
+__device__ __forceinline__ uint64_t sm64_next(uint64_t &s)
+{
+    s += 0x9E3779B97F4A7C15ULL;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// Initial centers of set s: the first k positions of a Fisher-Yates shuffle of its m
+// rows (step i swaps i with i + r mod (m - i)), the stream keyed by (seed, stage, s).
+// Only positions < k and at most k others are ever touched, so the shuffle keeps a
+// dense table for 0..k-1 and an open-addressing table for the rest.
+__global__ void k_lloyd_init(const float *__restrict__ pts, SegTable t, int d, float *centers,
+                             unsigned long long *acc, int32_t *count2, int64_t P,
+                             uint64_t seed, uint32_t stage, int first_k)
+{
+    extern __shared__ int32_t sh[];
+    for (int s = blockIdx.x; s < t.n_seg; s += gridDim.x) {
+        const int k = t.k_eff[s];
+        const int32_t m = t.seg_size[s];
+        int cap = 1;
+        while (cap < 2 * k) cap <<= 1;
+        int32_t *A = sh;                       // k
+        int32_t *hk = sh + k;                  // cap keys (-1 = empty)
+        int32_t *hv = hk + cap;                // cap values
+        for (int i = threadIdx.x; i < k; i += blockDim.x) A[i] = i;
+        for (int i = threadIdx.x; i < cap; i += blockDim.x) hk[i] = -1;
+        __syncthreads();
+        if (threadIdx.x == 0 && !first_k) {
+            uint64_t key = ((uint64_t)stage << 32) | (uint64_t)(uint32_t)s;
+            uint64_t st = seed ^ sm64_next(key);
+            for (int i = 0; i < k; i++) {
+                uint64_t r = sm64_next(st);
+                int32_t j = i + (int32_t)(r % (uint64_t)(m - i));
+                if (j < k) {
+                    int32_t tmp = A[i];
+                    A[i] = A[j];
+                    A[j] = tmp;
+                } else {
+                    uint32_t h = ((uint32_t)j * 0x9E3779B1u) & (uint32_t)(cap - 1);
+                    while (hk[h] != -1 && hk[h] != j) h = (h + 1) & (uint32_t)(cap - 1);
+                    int32_t vj = hk[h] == j ? hv[h] : j;
+                    hk[h] = j;
+                    hv[h] = A[i];
+                    A[i] = vj;
+                }
+            }
+        }
+        __syncthreads();
+        const int64_t row0 = t.seg_start[s];
+        const int64_t c0 = t.cen_off[s];
+        for (int e = threadIdx.x; e < k * d; e += blockDim.x) {
+            int j = e / d, a = e - j * d;
+            centers[(c0 + j) * d + a] = pts[(row0 + A[j]) * d + a];
+            acc[(c0 + j) * d + a] = 0ull;
+        }
+        for (int j = threadIdx.x; j < k; j += blockDim.x) {
+            count2[c0 + j] = 0;
+            count2[P + c0 + j] = 0;
+        }
+        __syncthreads();
+    }
+}
+
+// float32 direct squared distance, ascending attributes, one fused rounding per term.
+template <int D>
+__device__ __forceinline__ float dist_direct(const float *x, const float *c, int d)
+{
+    float acc = 0.0f;
+    const int dd = D > 0 ? D : d;
+#pragma unroll
+    for (int j = 0; j < dd; j++) {
+        float t = __fsub_rn(x[j], c[j]);
+        acc = __fmaf_rn(t, t, acc);
+    }
+    return acc;
+}
+
+__device__ __forceinline__ unsigned long long to_fix(float v)
+{
+    return (unsigned long long)__float2ll_rn(v * kFix);
+}
+
+// One assignment step over work units [unit_lo, unit_hi).
+//   D > 0: d == D known at compile time (row kept in registers); D == 0: any d.
+template <int D, bool kSmemAcc>
+__global__ void __launch_bounds__(kThreads)
+k_lloyd_assign(const float *__restrict__ pts, SegTable t, int d, const float *__restrict__ centers,
+               unsigned long long *acc, int32_t *count, int32_t *labels, int32_t *trace,
+               int64_t trace_off, int unit_lo, int chunk_k)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int u = unit_lo + blockIdx.x;
+    const int s = t.unit_seg[u];
+    const int k = t.k_eff[s];
+    const int64_t c0 = t.cen_off[s];
+    const int64_t row0 = t.seg_start[s] + t.unit_start[u];
+    const int rows = t.unit_count[u];
+    const int dd = D > 0 ? D : d;
+
+    // [center chunk | sums | counts], each 16-byte aligned
+    const size_t c_bytes = ((size_t)min(chunk_k, k) * dd * 4 + 15) & ~(size_t)15;
+    float *sc = reinterpret_cast<float *>(smem);
+    unsigned long long *sacc = reinterpret_cast<unsigned long long *>(smem + c_bytes);
+    int32_t *scnt = reinterpret_cast<int32_t *>(smem + c_bytes + (size_t)k * dd * 8);
+    if (kSmemAcc) {
+        for (int e = threadIdx.x; e < k * dd; e += kThreads) sacc[e] = 0ull;
+        for (int j = threadIdx.x; j < k; j += kThreads) scnt[j] = 0;
+    }
+    const bool one_chunk = chunk_k >= k;
+    if (one_chunk) {
+        for (int e = threadIdx.x; e < k * dd; e += kThreads) sc[e] = centers[c0 * dd + e];
+    }
+    __syncthreads();
+
+    for (int p0 = 0; p0 < rows; p0 += kThreads) {
+        const int p = p0 + threadIdx.x;
+        const bool live = p < rows;
+        const float *xr = pts + (row0 + (live ? p : 0)) * dd;
+        float xv[D > 0 ? D : 1];
+        if (D > 0) {
+#pragma unroll
+            for (int j = 0; j < (D > 0 ? D : 1); j++) xv[j] = __ldg(&xr[j]);
+        }
+        const float *xp = D > 0 ? xv : xr;
+        float best = __int_as_float(0x7f800000);
+        int bj = 0;
+        for (int cb = 0; cb < k; cb += chunk_k) {
+            const int ce = min(k, cb + chunk_k);
+            if (!one_chunk) {
+                __syncthreads();
+                for (int e = threadIdx.x; e < (ce - cb) * dd; e += kThreads)
+                    sc[e] = centers[(c0 + cb) * dd + e];
+                __syncthreads();
+            }
+            const float *cbase = one_chunk ? sc + (size_t)cb * dd : sc;
+            if (live) {
+                for (int j = cb; j < ce; j++) {
+                    float v = dist_direct<D>(xp, cbase + (size_t)(j - cb) * dd, dd);
+                    if (v < best) { best = v; bj = j; }
+                }
+            }
+        }
+        if (live) {
+            const int64_t row = row0 + p;
+            labels[row] = bj;
+            if (trace) trace[trace_off + row] = bj;
+            if (kSmemAcc) {
+                atomicAdd(&scnt[bj], 1);
+#pragma unroll
+                for (int j = 0; j < dd; j++) atomicAdd(&sacc[(size_t)bj * dd + j], to_fix(xp[j]));
+            } else {
+                atomicAdd(&count[c0 + bj], 1);
+#pragma unroll
+                for (int j = 0; j < dd; j++) atomicAdd(&acc[(c0 + bj) * dd + j], to_fix(xp[j]));
+            }
+        }
+    }
+    if (kSmemAcc) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < k * dd; e += kThreads) {
+            unsigned long long v = sacc[e];
+            if (v) atomicAdd(&acc[c0 * dd + e], v);
+        }
+        for (int j = threadIdx.x; j < k; j += kThreads) {
+            int v = scnt[j];
+            if (v) atomicAdd(&count[c0 + j], v);
+        }
+    }
+}
+
+// center = exact sum / count (double), rounded once to float; empty clusters keep their
+// center.  Clears the sums and the other parity's counts for the next iteration.
+__global__ void k_lloyd_finalize(float *centers, unsigned long long *acc, const int32_t *count,
+                                 int32_t *count_next, int64_t cen_lo, int64_t cen_hi, int d)
+{
+    const int64_t e0 = cen_lo * d, e1 = cen_hi * d;
+    for (int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < e1;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / d;
+        const int32_t n = count[c];
+        const long long sum = (long long)acc[e];
+        if (n > 0) {
+            double mean = __dmul_rn(__dmul_rn((double)sum, 0x1p-32), __drcp_rn((double)n));
+            centers[e] = __double2float_rn(mean);
+        }
+        acc[e] = 0ull;
+        if (e - c * d == 0) count_next[c] = 0;
+    }
+}
+
+// Nearest final center of every scaled point (original order) and the sum of squared
+// errors: each point's float32 direct distance is added in double, per thread, then
+// per block in a fixed tree, then over blocks in block order.
+template <int D>
+__global__ void __launch_bounds__(kThreads)
+k_final_sse(const float *__restrict__ x, int64_t n, int d, const float *__restrict__ centers,
+            int k, int chunk_k, int32_t *labels, double *blk_sse, double *sse, uint32_t *ticket)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *sc = reinterpret_cast<float *>(smem);
+    const int dd = D > 0 ? D : d;
+    const bool one_chunk = chunk_k >= k;
+    if (one_chunk) {
+        for (int e = threadIdx.x; e < k * dd; e += kThreads) sc[e] = centers[e];
+        __syncthreads();
+    }
+    double part = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    const int64_t nround = (n + stride - 1) / stride;
+    for (int64_t it = 0; it < nround; it++) {
+        const int64_t i = it * stride + (int64_t)blockIdx.x * kThreads + threadIdx.x;
+        const bool live = i < n;
+        const float *xr = x + (live ? i : 0) * dd;
+        float xv[D > 0 ? D : 1];
+        if (D > 0) {
+#pragma unroll
+            for (int j = 0; j < (D > 0 ? D : 1); j++) xv[j] = __ldg(&xr[j]);
+        }
+        const float *xp = D > 0 ? xv : xr;
+        float best = __int_as_float(0x7f800000);
+        int bj = 0;
+        for (int cb = 0; cb < k; cb += chunk_k) {
+            const int ce = min(k, cb + chunk_k);
+            if (!one_chunk) {
+                __syncthreads();
+                for (int e = threadIdx.x; e < (ce - cb) * dd; e += kThreads) sc[e] = centers[(size_t)cb * dd + e];
+                __syncthreads();
+            }
+            const float *cbase = one_chunk ? sc + (size_t)cb * dd : sc;
+            if (live) {
+                for (int j = cb; j < ce; j++) {
+                    float v = dist_direct<D>(xp, cbase + (size_t)(j - cb) * dd, dd);
+                    if (v < best) { best = v; bj = j; }
+                }
+            }
+        }
+        if (live) {
+            labels[i] = bj;
+            part = __dadd_rn(part, (double)best);
+        }
+    }
+    // fixed-order block reduction
+    for (int o = 16; o; o >>= 1) part = __dadd_rn(part, __shfl_down_sync(0xffffffffu, part, o));
+    __shared__ double ws[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = ws[0];
+        for (int w = 1; w < kThreads / 32; w++) b = __dadd_rn(b, ws[w]);
+        blk_sse[blockIdx.x] = b;
+    }
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last || threadIdx.x != 0) return;
+    __threadfence();
+    double tot = 0.0;
+    for (unsigned b = 0; b < gridDim.x; b++) tot = __dadd_rn(tot, __ldcg(&blk_sse[b]));
+    *sse = tot;
+    *ticket = 0;
+}
+
+int center_chunk(int d, int k)
+{
+    int c = kCenterChunkBytes / (d * 4);
+    if (c < 1) c = 1;
+    return c >= k ? k : c;
+}
+
+template <int D>
+cudaError_t assign_dispatch(const LloydBuffers &b, const SegTable &t, int d, int iter, int unit_lo,
+                            int unit_hi, int kmax, cudaStream_t st, KTimer *kt)
+{
+    const int chunk = center_chunk(d, kmax);
+    const size_t acc_bytes = (size_t)kmax * d * 8 + (size_t)kmax * 4;
+    const size_t c_bytes = ((size_t)chunk * d * 4 + 15) & ~(size_t)15;
+    const bool smem_acc = acc_bytes <= kSmemAccMax;
+    const size_t smem = (smem_acc ? acc_bytes : 0) + c_bytes;
+    const int grid = unit_hi - unit_lo;
+    if (grid <= 0) return cudaSuccess;
+    if (smem_acc) {
+        auto kern = k_lloyd_assign<D, true>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kt->begin(st);
+        kern<<<grid, kThreads, smem, st>>>(b.pts, t, d, b.centers, b.acc, b.count, b.labels, b.trace,
+                                           (int64_t)iter * b.rows, unit_lo, chunk);
+        kt->end(PSCL_K_LLOYD_ASSIGN, st);
+    } else {
+        auto kern = k_lloyd_assign<D, false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kt->begin(st);
+        kern<<<grid, kThreads, smem, st>>>(b.pts, t, d, b.centers, b.acc, b.count, b.labels, b.trace,
+                                           (int64_t)iter * b.rows, unit_lo, chunk);
+        kt->end(PSCL_K_LLOYD_ASSIGN, st);
+    }
+    return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t sse_dispatch(const float *x, int64_t n, int d, const float *centers, int k, int32_t *labels,
+                         double *blk_sse, double *sse, uint32_t *ticket, int sm_count, cudaStream_t st,
+                         KTimer *kt)
+{
+    const int chunk = center_chunk(d, k);
+    const size_t smem = (size_t)chunk * d * 4;
+    int64_t want = (n + kThreads - 1) / kThreads;
+    int grid = (int)(want < (int64_t)sm_count * 8 ? want : (int64_t)sm_count * 8);
+    if (grid < 1) grid = 1;
+    auto kern = k_final_sse<D>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kt->begin(st);
+    kern<<<grid, kThreads, smem, st>>>(x, n, d, centers, k, chunk, labels, blk_sse, sse, ticket);
+    kt->end(PSCL_K_FINAL_SSE, st);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int sse_grid(int64_t n, int sm_count)
+{
+    int64_t want = (n + kThreads - 1) / kThreads;
+    return (int)(want < (int64_t)sm_count * 8 ? want : (int64_t)sm_count * 8);
+}
+
+cudaError_t launch_lloyd_init(const LloydBuffers &b, const SegTable &t, int d, int64_t P,
+                              uint64_t seed, uint32_t stage, int first_k, int kmax, cudaStream_t st,
+                              KTimer *kt)
+{
+    int cap = 1;
+    while (cap < 2 * kmax) cap <<= 1;
+    size_t smem = ((size_t)kmax + 2 * (size_t)cap) * sizeof(int32_t);
+    cudaFuncSetAttribute(k_lloyd_init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int grid = t.n_seg < 65535 ? t.n_seg : 65535;
+    kt->begin(st);
+    k_lloyd_init<<<grid, 256, smem, st>>>(b.pts, t, d, b.centers, b.acc, b.count, P, seed, stage, first_k);
+    kt->end(PSCL_K_LLOYD_INIT, st);
+    return cudaGetLastError();
+}
+
+// One Lloyd iteration over units [unit_lo, unit_hi) and centers [cen_lo, cen_hi).
+// b.count must point at this iteration's count buffer; count_next at the other one.
+cudaError_t launch_lloyd_iter(const LloydBuffers &b, int32_t *count_next, const SegTable &t, int d,
+                              int iter, int unit_lo, int unit_hi, int64_t cen_lo, int64_t cen_hi,
+                              int kmax, int sm_count, cudaStream_t st, KTimer *kt)
+{
+    cudaError_t e;
+    switch (d) {
+    case 2: e = assign_dispatch<2>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt); break;
+    case 4: e = assign_dispatch<4>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt); break;
+    case 8: e = assign_dispatch<8>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt); break;
+    case 16: e = assign_dispatch<16>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt); break;
+    case 32: e = assign_dispatch<32>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt); break;
+    case 64: e = assign_dispatch<64>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt); break;
+    default: e = assign_dispatch<0>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt); break;
+    }
+    if (e != cudaSuccess) return e;
+    int64_t work = (cen_hi - cen_lo) * d;
+    int64_t g = (work + 255) / 256;
+    if (g > (int64_t)sm_count * 8) g = (int64_t)sm_count * 8;
+    if (g < 1) g = 1;
+    kt->begin(st);
+    k_lloyd_finalize<<<(int)g, 256, 0, st>>>(b.centers, b.acc, b.count, count_next, cen_lo, cen_hi, d);
+    kt->end(PSCL_K_LLOYD_FINALIZE, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_final_sse(const float *x, int64_t n, int d, const float *centers, int k,
+                             int32_t *labels, double *blk_sse, double *sse, uint32_t *ticket,
+                             int sm_count, cudaStream_t st, KTimer *kt)
+{
+    switch (d) {
+    case 2: return sse_dispatch<2>(x, n, d, centers, k, labels, blk_sse, sse, ticket, sm_count, st, kt);
+    case 4: return sse_dispatch<4>(x, n, d, centers, k, labels, blk_sse, sse, ticket, sm_count, st, kt);
+    case 8: return sse_dispatch<8>(x, n, d, centers, k, labels, blk_sse, sse, ticket, sm_count, st, kt);
+    case 16: return sse_dispatch<16>(x, n, d, centers, k, labels, blk_sse, sse, ticket, sm_count, st, kt);
+    case 32: return sse_dispatch<32>(x, n, d, centers, k, labels, blk_sse, sse, ticket, sm_count, st, kt);
+    case 64: return sse_dispatch<64>(x, n, d, centers, k, labels, blk_sse, sse, ticket, sm_count, st, kt);
+    default: return sse_dispatch<0>(x, n, d, centers, k, labels, blk_sse, sse, ticket, sm_count, st, kt);
+    }
+}
+
+}  // namespace pscl

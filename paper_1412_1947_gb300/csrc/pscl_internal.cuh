@@ -1,0 +1,127 @@
+// Internal declarations of the pscl CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pscl.h"
+
+namespace pscl {
+
+constexpr int kMaxD = 1024;          // attributes per point
+constexpr int kMaxK = 4096;          // centers of one Lloyd run
+constexpr int kHistBins = 4096;      // 12-bit radix digits of the peel's key select
+constexpr int kBlkItems = 1024;      // points per block in the peel's classify/compact
+constexpr int kFixShift = 32;        // fixed-point scale 2^32 of the centroid sums
+
+// Device-resident control block of one peel (one round at a time).
+struct PeelCtl {
+    uint32_t hist0[kHistBins];
+    uint32_t hist1[kHistBins];
+    uint32_t ticket[4];              // last-block tickets of the per-round kernels
+    uint32_t b0;                     // digit 0 (key bits 31..20) holding the N-th key
+    uint32_t rank0;                  // rank of the N-th key inside that digit
+    uint32_t in_key;                 // key < in_key  => certainly among the N nearest
+    uint32_t out_key;                // key > out_key => certainly not
+    uint32_t band_count;             // points between the two (decided in float64)
+    uint32_t n_in;
+    uint32_t need;                   // N - n_in: how many of the band are taken
+    uint32_t nonfinite;              // set by scaling if an input value is not finite
+    uint32_t error;
+};
+
+// Segment table of one batched Lloyd launch (device arrays).
+struct SegTable {
+    const int64_t *seg_start;        // first row of each segment in the packed points
+    const int32_t *seg_size;
+    const int32_t *cen_off;          // first center of each segment
+    const int32_t *k_eff;            // centers of each segment
+    const int32_t *unit_seg;         // work units: segment, first row (relative), rows
+    const int32_t *unit_start;
+    const int32_t *unit_count;
+    int n_seg;
+    int n_units;
+};
+
+// Launch bookkeeping: every launcher counts its launches per pscl_kernel tag and, when
+// `ev` is set, brackets each launch with a pair of CUDA events on the stream.
+struct KTimer {
+    int64_t launches[PSCL_K_COUNT] = {};
+    cudaEvent_t *ev = nullptr;       // 2 * cap events, or NULL (count only)
+    int *tag = nullptr;
+    int cap = 0;
+    int n = 0;                       // event pairs used
+    void reset()
+    {
+        for (int i = 0; i < PSCL_K_COUNT; i++) launches[i] = 0;
+        n = 0;
+    }
+    void begin(cudaStream_t st)
+    {
+        if (ev && n < cap) cudaEventRecord(ev[2 * n], st);
+    }
+    void end(int k, cudaStream_t st)
+    {
+        launches[k]++;
+        if (ev && n < cap) {
+            cudaEventRecord(ev[2 * n + 1], st);
+            tag[n++] = k;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------- launchers
+// All launchers queue work on `st` and return cudaGetLastError().
+
+// scale.cu
+cudaError_t launch_scale(const float *raw, float *x, int64_t n, int d, float *part,
+                         uint32_t *ticket, double *mn, double *mx, PeelCtl *ctl, int sm_count,
+                         cudaStream_t st, KTimer *kt);
+size_t scale_part_floats(int64_t n, int d, int sm_count);
+
+// peel.cu
+struct PeelBuffers {
+    const float *x;                  // n x d scaled points
+    uint32_t *idx[2];                // remaining point indices (ping-pong)
+    uint32_t *key;                   // float32 distance keys of the remaining points
+    uint8_t *status;                 // 0 out, 1 in, 2 band (per remaining point)
+    uint64_t *band_key;              // float64 distance bits of band points
+    uint32_t *band_pos;              // their positions among the remaining points
+    uint32_t *blk_cnt;               // per classify block: selected count
+    uint32_t *blk_off;               // per classify block: exclusive prefix of selections
+    float *lpart;                    // per block partial minima (blocks x d)
+    float *L;                        // current landmark (d)
+    float *landmarks;                // all landmarks (S x d), for inspection
+    uint32_t *perm;                  // n: subcluster-packed original indices
+    float *xseg;                     // n x d: subcluster-packed points
+    PeelCtl *ctl;
+};
+cudaError_t launch_peel(const PeelBuffers &b, int64_t n, int d, int64_t N, int sm_count,
+                        cudaStream_t st, KTimer *kt);
+
+// lloyd.cu
+struct LloydBuffers {
+    const float *pts;                // rows of all segments, packed
+    float *centers;                  // P x d
+    unsigned long long *acc;         // P x d fixed-point sums
+    int32_t *count;                  // P counts of the current iteration (init: 2P, both)
+    int32_t *labels;                 // rows
+    int32_t *trace;                  // iters x rows (or NULL)
+    int64_t rows;
+};
+cudaError_t launch_lloyd_init(const LloydBuffers &b, const SegTable &t, int d, int64_t P,
+                              uint64_t seed, uint32_t stage, int first_k, int kmax,
+                              cudaStream_t st, KTimer *kt);
+cudaError_t launch_lloyd_iter(const LloydBuffers &b, int32_t *count_next, const SegTable &t,
+                              int d, int iter, int unit_lo, int unit_hi, int64_t cen_lo,
+                              int64_t cen_hi, int kmax, int sm_count, cudaStream_t st,
+                              KTimer *kt);
+cudaError_t launch_final_sse(const float *x, int64_t n, int d, const float *centers, int k,
+                             int32_t *labels, double *blk_sse, double *sse, uint32_t *ticket,
+                             int sm_count, cudaStream_t st, KTimer *kt);
+int sse_grid(int64_t n, int sm_count);
+
+}  // namespace pscl
