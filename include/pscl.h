@@ -81,11 +81,7 @@ typedef enum {
 typedef enum {
     PSCL_K_SCALE_MINMAX = 0, /* column minima / maxima                           */
     PSCL_K_SCALE_APPLY,      /* element-wise min-max scaling                     */
-    PSCL_K_PEEL_DIST,        /* float32 landmark distances + first histogram     */
-    PSCL_K_PEEL_HIST,        /* second histogram of the N-th key's bin           */
-    PSCL_K_PEEL_CLASSIFY,    /* in / out / float64 band, band selection          */
-    PSCL_K_PEEL_COMPACT,     /* stable compaction + next landmark                */
-    PSCL_K_PEEL_TAKE,        /* last round: the remaining points                 */
+    PSCL_K_PEEL,             /* all peel rounds (one persistent launch)          */
     PSCL_K_GATHER,           /* subcluster-packed copy of the points             */
     PSCL_K_LLOYD_INIT,       /* seeded initial centers                           */
     PSCL_K_LLOYD_ASSIGN,     /* nearest center + fixed-point sums                */

@@ -48,13 +48,14 @@ def lib():
         L.or_init_indices.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int64, C.c_int32, P]
         L.or_scale.argtypes = [P, C.c_int64, C.c_int32, P, P, P]
         L.or_peel.argtypes = [P, C.c_int64, C.c_int32, C.c_int64, P, P, P, P]
+        L.or_peel_select.argtypes = [P, C.c_int64, C.c_int32, C.c_int64, P, P, P, P]
         L.or_assign.argtypes = [P, C.c_int64, C.c_int32, P, C.c_int32, P, P, P]
         L.or_lloyd.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P,
                                C.c_double, P, P]
         L.or_lloyd_seeded.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
                                       C.c_uint32, C.c_uint32, C.c_int, P, P, P, P]
         L.or_two_level.argtypes = [P]
-        for f in ("or_init_indices", "or_scale", "or_peel", "or_assign", "or_lloyd",
+        for f in ("or_init_indices", "or_scale", "or_peel", "or_peel_select", "or_assign", "or_lloyd",
                   "or_lloyd_seeded", "or_two_level"):
             getattr(L, f).restype = C.c_int
         _lib = L
@@ -91,8 +92,9 @@ def scale(raw: np.ndarray):
     return out, mn, mx
 
 
-def peel(x: np.ndarray, N: int):
-    """Returns (perm[n], seg_off[S+1], landmarks[S, d])."""
+def peel(x: np.ndarray, N: int, select: bool = False):
+    """Returns (perm[n], seg_off[S+1], landmarks[S, d]).  select=True uses the O(n_r)
+    per-round selection form (same result, for large inputs)."""
     x = np.ascontiguousarray(x, np.float32)
     n, d = x.shape
     S_max = -(-n // N)
@@ -100,7 +102,8 @@ def peel(x: np.ndarray, N: int):
     seg_off = np.empty(S_max + 1, np.int64)
     lm = np.empty((S_max, d), np.float32)
     S = C.c_int64(0)
-    _check(lib().or_peel(_p(x), n, d, N, _p(perm), _p(seg_off), C.byref(S), _p(lm)), "peel")
+    f = lib().or_peel_select if select else lib().or_peel
+    _check(f(_p(x), n, d, N, _p(perm), _p(seg_off), C.byref(S), _p(lm)), "peel")
     S = S.value
     return perm, seg_off[:S + 1].copy(), lm[:S].copy()
 
@@ -153,7 +156,7 @@ class _Args(C.Structure):
         ("raw", C.c_void_p), ("n", C.c_int64), ("N", C.c_int64), ("d", C.c_int32),
         ("local_k", C.c_int32), ("final_k", C.c_int32), ("iters", C.c_int32),
         ("seed", C.c_uint64), ("first_k", C.c_int32), ("n_threads", C.c_int32),
-        ("force_local", C.c_void_p), ("force_final", C.c_void_p), ("tie_tol", C.c_double),
+        ("select_peel", C.c_int32), ("force_local", C.c_void_p), ("force_final", C.c_void_p), ("tie_tol", C.c_double),
         ("scaled", C.c_void_p), ("perm", C.c_void_p), ("seg_off", C.c_void_p),
         ("landmarks", C.c_void_p), ("local_centers", C.c_void_p), ("local_k_eff", C.c_void_p),
         ("local_labels", C.c_void_p), ("local_sse", C.c_void_p), ("final_centers", C.c_void_p),
@@ -197,6 +200,7 @@ def pooled_count(n: int, N: int, local_k: int) -> tuple[int, int]:
 
 def two_level(raw: np.ndarray, N: int, local_k: int, final_k: int, iters: int, seed: int,
               first_k: bool = False, threads: int = 0, force_local=None, force_final=None,
+              select_peel: bool = False,
               tie_tol: float = 0.0) -> TwoLevel:
     raw = np.ascontiguousarray(raw, np.float32)
     n, d = raw.shape
@@ -217,6 +221,7 @@ def two_level(raw: np.ndarray, N: int, local_k: int, final_k: int, iters: int, s
     a.n, a.N, a.d = n, N, d
     a.local_k, a.final_k, a.iters, a.seed = local_k, final_k, iters, seed
     a.first_k, a.n_threads = int(first_k), int(threads)
+    a.select_peel = int(select_peel)
     a.force_local = None if fl is None else fl.ctypes.data
     a.force_final = None if ff is None else ff.ctypes.data
     a.tie_tol = tie_tol

@@ -370,6 +370,7 @@ typedef struct {
     uint64_t seed;
     int32_t first_k;          /* 1: every Lloyd starts from its first k_eff points */
     int32_t n_threads;        /* threads over subclusters (0 = library default)    */
+    int32_t select_peel;      /* 1: or_peel_select instead of or_peel (same result) */
     const int32_t *force_local; /* optional iters*n trace, subcluster-packed order */
     const int32_t *force_final; /* optional iters*P trace                          */
     double tie_tol;
@@ -395,6 +396,9 @@ typedef struct {
     int64_t n_bad;
 } or_two_level_args;
 
+int or_peel_select(const float *x, int64_t n, int32_t d, int64_t N, int64_t *perm, int64_t *seg_off,
+                   int64_t *n_seg, float *landmarks);
+
 int or_two_level(or_two_level_args *A)
 {
     int64_t n = A->n, S, P = 0, s, i;
@@ -412,7 +416,10 @@ int or_two_level(or_two_level_args *A)
 
     rc = or_scale(A->raw, n, d, A->scaled, mn, mx);
     if (rc) goto done;
-    rc = or_peel(A->scaled, n, d, A->N, A->perm, A->seg_off, &S, A->landmarks);
+    if (A->select_peel)
+        rc = or_peel_select(A->scaled, n, d, A->N, A->perm, A->seg_off, &S, A->landmarks);
+    else
+        rc = or_peel(A->scaled, n, d, A->N, A->perm, A->seg_off, &S, A->landmarks);
     if (rc) goto done;
     A->n_seg = S;
     /* subcluster-packed copy of the points ("flattening while subgrouping", §V) */
@@ -507,4 +514,90 @@ done:
     free(packed);
     free(cen_off);
     return rc;
+}
+
+/* ------------------------------------------------------------------------------ */
+/* The same peel with a selection instead of a sort: per round, the N-th smallest     */
+/* distance K is found by quickselect; the subcluster is every remaining point with   */
+/* distance < K plus, in ascending index, as many with distance == K as are needed.   */
+/* Identical output to or_peel (pinned by the tests), O(n_r) per round.               */
+/* ------------------------------------------------------------------------------ */
+static double kth_smallest(double *a, int64_t n, int64_t k)
+{
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2, i = lo, j = hi;
+        double x = a[lo], y = a[mid], z = a[hi], pivot, t;
+        /* median of three */
+        if ((x <= y && y <= z) || (z <= y && y <= x)) pivot = y;
+        else if ((y <= x && x <= z) || (z <= x && x <= y)) pivot = x;
+        else pivot = z;
+        while (i <= j) {
+            while (a[i] < pivot) i++;
+            while (a[j] > pivot) j--;
+            if (i <= j) { t = a[i]; a[i] = a[j]; a[j] = t; i++; j--; }
+        }
+        if (k <= j) hi = j;
+        else if (k >= i) lo = i;
+        else return a[k];
+    }
+    return a[k];
+}
+
+int or_peel_select(const float *x, int64_t n, int32_t d, int64_t N, int64_t *perm, int64_t *seg_off,
+                   int64_t *n_seg, float *landmarks)
+{
+    int64_t *rem, nr, pos = 0, S = 0, i;
+    double *delta, *tmp, *L;
+    int32_t j;
+    if (n < 1 || d < 1 || N < 1) return OR_EINVAL;
+    rem = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    delta = (double *)malloc((size_t)n * sizeof(double));
+    tmp = (double *)malloc((size_t)n * sizeof(double));
+    L = (double *)malloc((size_t)d * sizeof(double));
+    if (!rem || !delta || !tmp || !L) { free(rem); free(delta); free(tmp); free(L); return OR_ENOMEM; }
+    for (i = 0; i < n; i++) rem[i] = i;
+    nr = n;
+    while (nr > 0) {
+        int64_t kept = 0, take, need;
+        double K;
+        for (j = 0; j < d; j++) {
+            float lo = x[rem[0] * d + j];
+            for (i = 1; i < nr; i++) {
+                float v = x[rem[i] * d + j];
+                if (v < lo) lo = v;
+            }
+            L[j] = (double)lo;
+            if (landmarks) landmarks[S * d + j] = lo;
+        }
+        for (i = 0; i < nr; i++) delta[i] = sqdist(x + rem[i] * d, L, d);
+        seg_off[S] = pos;
+        if (nr <= N) {
+            for (i = 0; i < nr; i++) perm[pos + i] = rem[i];
+            pos += nr;
+            S++;
+            break;
+        }
+        memcpy(tmp, delta, (size_t)nr * sizeof(double));
+        K = kth_smallest(tmp, nr, N - 1);
+        need = N;
+        for (i = 0; i < nr; i++) need -= delta[i] < K;
+        take = 0;
+        for (i = 0; i < nr; i++) {         /* rem is in ascending index order */
+            int sel = delta[i] < K || (delta[i] == K && need > 0);
+            if (delta[i] == K && sel) need--;
+            if (sel) perm[pos + take++] = rem[i];
+            else rem[kept++] = rem[i];
+        }
+        pos += take;
+        S++;
+        nr = kept;
+    }
+    seg_off[S] = n;
+    *n_seg = S;
+    free(rem);
+    free(delta);
+    free(tmp);
+    free(L);
+    return OR_OK;
 }

@@ -46,8 +46,8 @@ SIGNATURES = {
     "pscl_get_phase_ms": (_I, [_P, _P]),
     "pscl_get_kernel_times": (_I, [_P, _P, _P]),
 }
-KERNELS = ["scale_minmax", "scale_apply", "peel_dist", "peel_hist", "peel_classify", "peel_compact",
-           "peel_take", "gather", "lloyd_init", "lloyd_assign", "lloyd_finalize", "final_sse"]
+KERNELS = ["scale_minmax", "scale_apply", "peel", "gather", "lloyd_init", "lloyd_assign", "lloyd_finalize",
+           "final_sse"]
 
 _lib = None
 

@@ -92,6 +92,7 @@ struct pscl_job {
     float *part = nullptr;
     uint32_t *tickets = nullptr;      // [0] scale, [1] sse
     PeelCtl *ctl = nullptr;
+    uint32_t *flags = nullptr;        // kFlagWords
     // subcluster plan
     int64_t N = 0;
     int local_k = 0, iters = 0, prec = 0;
@@ -268,8 +269,9 @@ extern "C" int pscl_job_create(pscl_ctx *c, const void *points, int dtype, int64
     if (!rc) rc = A(j, &j->part, scale_part_floats(n, d, c->sm_count));
     if (!rc) rc = A(j, &j->tickets, 8);
     if (!rc) rc = A(j, &j->ctl, 1);
+    if (!rc) rc = A(j, &j->flags, kFlagWords);
     if (!rc && cudaMemsetAsync(j->tickets, 0, 8 * sizeof(uint32_t), c->stream) != cudaSuccess) rc = PSCL_ECUDA;
-    if (!rc && cudaMemsetAsync(j->ctl, 0, sizeof(PeelCtl), c->stream) != cudaSuccess) rc = PSCL_ECUDA;
+    if (!rc && cudaMemsetAsync(j->flags, 0, kFlagWords * sizeof(uint32_t), c->stream) != cudaSuccess) rc = PSCL_ECUDA;
     if (!rc) rc = load_points(j, points, on_device);
     if (!rc) {
         for (int i = 0; i < 6 && !rc; i++)
@@ -412,15 +414,12 @@ static int plan_subcluster(pscl_job *j, int64_t N, int32_t local_k, int32_t iter
         TRY(A(j, &b.status, n + 16));
         TRY(A(j, &b.band_key, n));
         TRY(A(j, &b.band_pos, n));
-        size_t nblk = (size_t)(n + kBlkItems - 1) / kBlkItems;
-        TRY(A(j, &b.blk_cnt, nblk));
-        TRY(A(j, &b.blk_off, nblk));
-        TRY(A(j, &b.lpart, nblk * d));
-        TRY(A(j, &b.L, d));
+        TRY(A(j, &b.band_k32, n));
         TRY(A(j, &b.perm, n));
         TRY(A(j, &b.xseg, (size_t)n * d));
         TRY(A(j, &j->lab_l, n));
         b.ctl = j->ctl;
+        b.flags = j->flags;
         j->peel_alloc = true;
     }
     const bool same = N == j->N && local_k == j->local_k;
@@ -554,7 +553,7 @@ static int enqueue_scale(pscl_job *j, bool events)
 {
     cudaStream_t st = j->ctx->stream;
     if (events) CU(cudaEventRecord(j->ev[0], st));
-    CU(launch_scale(j->dev_in, j->x, j->n, j->d, j->part, j->tickets, j->mn, j->mx, j->ctl,
+    CU(launch_scale(j->dev_in, j->x, j->n, j->d, j->part, j->tickets, j->mn, j->mx, j->flags,
                     j->ctx->sm_count, st, &j->kt));
     if (events) CU(cudaEventRecord(j->ev[1], st));
     return PSCL_OK;
@@ -692,10 +691,11 @@ extern "C" int pscl_job_sync(pscl_job *j)
     if (!j) return fail(PSCL_EINVAL, "job is NULL");
     CU(cudaSetDevice(j->ctx->device));
     CU(cudaStreamSynchronize(j->ctx->stream));
-    PeelCtl h;
-    CU(cudaMemcpy(&h.nonfinite, &j->ctl->nonfinite, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost));
-    if (h.nonfinite) return fail(PSCL_EINVAL, "the input holds a value that is not finite");
-    if (h.error) return fail(PSCL_ECUDA, "internal error: the peel's float32 filter bound was violated");
+    uint32_t h[kFlagWords];
+    CU(cudaMemcpy(h, j->flags, sizeof h, cudaMemcpyDeviceToHost));
+    if (h[0]) return fail(PSCL_EINVAL, "the input holds a value that is not finite");
+    if (h[1] & 2u) return fail(PSCL_ETIMEOUT, "a bounded device-side wait gave up (peel barrier)");
+    if (h[1] & 1u) return fail(PSCL_ECUDA, "internal error: the peel's float32 filter bound was contradicted");
     return PSCL_OK;
 }
 

@@ -111,15 +111,52 @@ __device__ __forceinline__ unsigned long long to_fix(float v)
     return (unsigned long long)__float2ll_rn(v * kFix);
 }
 
-// One assignment step over work units [unit_lo, unit_hi).
-//   D > 0: d == D known at compile time (row kept in registers); D == 0: any d.
-template <int D, bool kSmemAcc>
+// Squared distances of R rows (registers) to one center (shared memory), float32
+// direct form, ascending attributes; the center is read as float4 when D % 4 == 0.
+template <int D, int R>
+__device__ __forceinline__ void dist_rows(const float (&xv)[R][D], const float *c, float (&out)[R])
+{
+#pragma unroll
+    for (int q = 0; q < R; q++) out[q] = 0.0f;
+    if (D % 4 == 0) {
+        const float4 *c4 = reinterpret_cast<const float4 *>(c);
+#pragma unroll
+        for (int j4 = 0; j4 < D / 4; j4++) {
+            const float4 cv = c4[j4];
+            const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+#pragma unroll
+                for (int q = 0; q < R; q++) {
+                    const float tq = __fsub_rn(xv[q][4 * j4 + e], cc[e]);
+                    out[q] = __fmaf_rn(tq, tq, out[q]);
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < D; j++) {
+            const float cj = c[j];
+#pragma unroll
+            for (int q = 0; q < R; q++) {
+                const float tq = __fsub_rn(xv[q][j], cj);
+                out[q] = __fmaf_rn(tq, tq, out[q]);
+            }
+        }
+    }
+}
+
+// One assignment step over work units [unit_lo, unit_lo + gridDim.x).
+//   D > 0: d == D known at compile time, each thread keeps R rows in registers and
+//          reads every center once for all of them; D == 0: any d, one row at a time.
+template <int D, int R, bool kSmemAcc>
 __global__ void __launch_bounds__(kThreads)
 k_lloyd_assign(const float *__restrict__ pts, SegTable t, int d, const float *__restrict__ centers,
                unsigned long long *acc, int32_t *count, int32_t *labels, int32_t *trace,
                int64_t trace_off, int unit_lo, int chunk_k)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int DR = D > 0 ? D : 1;
     const int u = unit_lo + blockIdx.x;
     const int s = t.unit_seg[u];
     const int k = t.k_eff[s];
@@ -143,18 +180,39 @@ k_lloyd_assign(const float *__restrict__ pts, SegTable t, int d, const float *__
     }
     __syncthreads();
 
-    for (int p0 = 0; p0 < rows; p0 += kThreads) {
-        const int p = p0 + threadIdx.x;
-        const bool live = p < rows;
-        const float *xr = pts + (row0 + (live ? p : 0)) * dd;
-        float xv[D > 0 ? D : 1];
-        if (D > 0) {
+    for (int p0 = 0; p0 < rows; p0 += kThreads * R) {
+        float xv[R][DR];
+        bool live[R];
+        int prow[R];
 #pragma unroll
-            for (int j = 0; j < (D > 0 ? D : 1); j++) xv[j] = __ldg(&xr[j]);
+        for (int q = 0; q < R; q++) {
+            prow[q] = p0 + q * kThreads + threadIdx.x;
+            live[q] = prow[q] < rows;
+            if (D > 0) {
+                const float *xr = pts + (row0 + (live[q] ? prow[q] : 0)) * dd;
+                if (D % 4 == 0) {
+                    const float4 *x4 = reinterpret_cast<const float4 *>(xr);
+#pragma unroll
+                    for (int j4 = 0; j4 < DR / 4; j4++) {
+                        const float4 v = __ldg(&x4[j4]);
+                        xv[q][4 * j4 + 0] = v.x;
+                        xv[q][4 * j4 + 1] = v.y;
+                        xv[q][4 * j4 + 2] = v.z;
+                        xv[q][4 * j4 + 3] = v.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < DR; j++) xv[q][j] = __ldg(&xr[j]);
+                }
+            }
         }
-        const float *xp = D > 0 ? xv : xr;
-        float best = __int_as_float(0x7f800000);
-        int bj = 0;
+        float best[R];
+        int bj[R];
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+            best[q] = __int_as_float(0x7f800000);
+            bj[q] = 0;
+        }
         for (int cb = 0; cb < k; cb += chunk_k) {
             const int ce = min(k, cb + chunk_k);
             if (!one_chunk) {
@@ -164,25 +222,47 @@ k_lloyd_assign(const float *__restrict__ pts, SegTable t, int d, const float *__
                 __syncthreads();
             }
             const float *cbase = one_chunk ? sc + (size_t)cb * dd : sc;
-            if (live) {
-                for (int j = cb; j < ce; j++) {
-                    float v = dist_direct<D>(xp, cbase + (size_t)(j - cb) * dd, dd);
-                    if (v < best) { best = v; bj = j; }
+            for (int j = cb; j < ce; j++) {
+                const float *cj = cbase + (size_t)(j - cb) * dd;
+                float v[R];
+                if (D > 0) {
+                    dist_rows<DR, R>(xv, cj, v);
+                } else {
+                    const float *xr = pts + (row0 + (live[0] ? prow[0] : 0)) * dd;
+                    v[0] = 0.0f;
+                    for (int a = 0; a < dd; a++) {
+                        const float tq = __fsub_rn(__ldg(&xr[a]), cj[a]);
+                        v[0] = __fmaf_rn(tq, tq, v[0]);
+                    }
                 }
+#pragma unroll
+                for (int q = 0; q < R; q++)
+                    if (v[q] < best[q]) { best[q] = v[q]; bj[q] = j; }
             }
         }
-        if (live) {
-            const int64_t row = row0 + p;
-            labels[row] = bj;
-            if (trace) trace[trace_off + row] = bj;
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+            if (!live[q]) continue;
+            const int64_t row = row0 + prow[q];
+            labels[row] = bj[q];
+            if (trace) trace[trace_off + row] = bj[q];
+            const float *xr = pts + row * dd;
             if (kSmemAcc) {
-                atomicAdd(&scnt[bj], 1);
+                atomicAdd(&scnt[bj[q]], 1);
+                if (D > 0) {
 #pragma unroll
-                for (int j = 0; j < dd; j++) atomicAdd(&sacc[(size_t)bj * dd + j], to_fix(xp[j]));
+                    for (int j = 0; j < DR; j++) atomicAdd(&sacc[(size_t)bj[q] * dd + j], to_fix(xv[q][j]));
+                } else {
+                    for (int j = 0; j < dd; j++) atomicAdd(&sacc[(size_t)bj[q] * dd + j], to_fix(__ldg(&xr[j])));
+                }
             } else {
-                atomicAdd(&count[c0 + bj], 1);
+                atomicAdd(&count[c0 + bj[q]], 1);
+                if (D > 0) {
 #pragma unroll
-                for (int j = 0; j < dd; j++) atomicAdd(&acc[(c0 + bj) * dd + j], to_fix(xp[j]));
+                    for (int j = 0; j < DR; j++) atomicAdd(&acc[(c0 + bj[q]) * dd + j], to_fix(xv[q][j]));
+                } else {
+                    for (int j = 0; j < dd; j++) atomicAdd(&acc[(c0 + bj[q]) * dd + j], to_fix(__ldg(&xr[j])));
+                }
             }
         }
     }
@@ -293,6 +373,13 @@ k_final_sse(const float *__restrict__ x, int64_t n, int d, const float *__restri
     *ticket = 0;
 }
 
+// rows kept in registers per thread: 64 floats of rows at most
+template <int D>
+__host__ __device__ constexpr int kRowsPerThread()
+{
+    return D <= 0 ? 1 : (D >= 64 ? 1 : 64 / D > 4 ? 4 : 64 / D);
+}
+
 int center_chunk(int d, int k)
 {
     int c = kCenterChunkBytes / (d * 4);
@@ -312,14 +399,14 @@ cudaError_t assign_dispatch(const LloydBuffers &b, const SegTable &t, int d, int
     const int grid = unit_hi - unit_lo;
     if (grid <= 0) return cudaSuccess;
     if (smem_acc) {
-        auto kern = k_lloyd_assign<D, true>;
+        auto kern = k_lloyd_assign<D, kRowsPerThread<D>(), true>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kt->begin(st);
         kern<<<grid, kThreads, smem, st>>>(b.pts, t, d, b.centers, b.acc, b.count, b.labels, b.trace,
                                            (int64_t)iter * b.rows, unit_lo, chunk);
         kt->end(PSCL_K_LLOYD_ASSIGN, st);
     } else {
-        auto kern = k_lloyd_assign<D, false>;
+        auto kern = k_lloyd_assign<D, kRowsPerThread<D>(), false>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kt->begin(st);
         kern<<<grid, kThreads, smem, st>>>(b.pts, t, d, b.centers, b.acc, b.count, b.labels, b.trace,

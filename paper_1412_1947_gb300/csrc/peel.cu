@@ -6,29 +6,28 @@
 // Membership is defined by the float64 distance
 //     delta64_i = sum_{j ascending} (double(x_ij) - double(L_j))^2   (one rounding per op)
 // with equal distances taken in ascending point index.  Computing delta64 for every
-// point would run the whole peel on the slow float64 pipe, so each round works in
-// float32 and keeps float64 for a thin band:
-//   1. k_peel_dist:     delta32_i by a float32 FMA chain, stored as its bit pattern
-//                       (order-preserving for non-negative floats) + a 4096-bin
-//                       histogram of bits 31..20; the last block finds the bin holding
-//                       the N-th smallest key.
-//   2. k_peel_hist1:    a 4096-bin histogram of bits 19..8 inside that bin; the last
-//                       block finds the 24-bit prefix [A, B] of the N-th smallest key and
-//                       turns it into two float32 cut-offs:
-//                       |delta32 - delta64| <= eps*delta32 + ea with eps = (d+4)*2^-23,
-//                       ea = 2^-120, so the N-th smallest delta64 lies in
-//                       [A(1-eps)-ea, B(1+eps)+ea]; a point whose upper bound lies below
-//                       that interval is certainly taken, one whose lower bound lies above
-//                       it certainly not.
-//   3. k_peel_classify: marks every point in / out / band; band points get delta64
-//                       (exactly the definition above) and are listed; the last block
-//                       picks the (N - #in) smallest band points by (delta64, position)
-//                       with a 96-bit radix select and turns per-block counts into
-//                       output offsets.
-//   4. k_peel_compact:  stable compaction: taken points go to subcluster r in ascending
-//                       index, the others stay in ascending index; the per-attribute
-//                       minimum of the points that stay is the next landmark.
+// point would run the peel on the slow float64 pipe, so each round works in float32 and
+// keeps float64 for a thin band around the N-th distance:
+//   A. delta32_i by a float32 FMA chain, kept as its bit pattern (order-preserving for
+//      non-negative floats), and a 2048-bin histogram of key bits 31..21;
+//   B. the bin holding the N-th smallest key, and a 2048-bin histogram of bits 20..10 of
+//      the keys inside it: the N-th smallest key lies in a 22-bit prefix [A, B];
+//   C. |delta32 - delta64| <= eps*delta32 + ea with eps = (d+4)*2^-23, ea = 2^-120, so
+//      the N-th smallest delta64 lies in [A(1-eps)-ea, B(1+eps)+ea]: a point whose upper
+//      bound is below that interval is certainly taken, one whose lower bound is above
+//      it certainly not; the few in between (the band) get delta64 exactly as defined;
+//   D. the (N - #certain) smallest band points by (delta64, position) are taken; taken
+//      points go to subcluster r in ascending index, the rest stay in ascending index
+//      (stable compaction of indices), and the per-attribute minimum of the points that
+//      stay is the next landmark.
 // The partition is therefore exactly the float64 definition's, whatever float32 does.
+//
+// All rounds run in one persistent cooperative launch: every CTA owns a contiguous slice
+// of the remaining points in each round and the phases are separated by grid barriers
+// (four per round).  Every barrier wait is bounded; a CTA that gives up sets the abort
+// flag, every other CTA then leaves at its next wait, and the host sees PSCL_ETIMEOUT.
+#include <algorithm>
+
 #include "pscl_internal.cuh"
 
 namespace pscl {
@@ -36,6 +35,12 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr uint32_t kInfBits = 0x7f800000u;
+constexpr int kBandSmem = 1024;               // band entries settled in shared memory
+constexpr int kBandBins = 4096;               // one-ulp bins over a band's float32 keys
+constexpr int kTight = 256;                   // band entries near the cut-off, decided exactly
+constexpr int kPeelDynWords = 2 * kHistBins > kBandBins + 7 * kTight
+                                  ? 2 * kHistBins : kBandBins + 7 * kTight;
+constexpr unsigned kSpinLimit = 1u << 25;      // ~1-2 s of polling per barrier at most
 
 // ------------------------------------------------------------------ block helpers
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
@@ -71,12 +76,19 @@ __device__ uint32_t block_excl_scan(uint32_t v, uint32_t &total)
     return r;
 }
 
-// In a 4096-bin histogram (global memory), find the bin holding rank `target` (0-based)
-// and the rank inside that bin.  Called by a whole block.
-__device__ void find_bin(const uint32_t *hist, uint32_t target, uint32_t *bin, uint32_t *rank)
+__device__ uint32_t block_sum(uint32_t v)
 {
     uint32_t tot;
-    constexpr int per = kHistBins / kThreads;     // 16 bins per thread
+    block_excl_scan(v, tot);
+    return tot;
+}
+
+// In a kHistBins-bin histogram (global memory), find the bin holding rank `target` (0-based)
+// and the rank inside that bin.  Called by the whole block; every thread gets the result.
+__device__ void find_bin(const uint32_t *hist, uint32_t target, uint32_t &bin, uint32_t &rank)
+{
+    __shared__ uint32_t sb, sr;
+    constexpr int per = kHistBins / kThreads;     // 8 bins per thread
     const int t = threadIdx.x;
     uint32_t loc[per];
     uint32_t s = 0;
@@ -85,29 +97,55 @@ __device__ void find_bin(const uint32_t *hist, uint32_t target, uint32_t *bin, u
         loc[q] = __ldcg(&hist[t * per + q]);
         s += loc[q];
     }
+    uint32_t tot;
     uint32_t before = block_excl_scan(s, tot);
     if (target >= before && target < before + s) {
         uint32_t c = before;
 #pragma unroll
         for (int q = 0; q < per; q++) {
             if (target >= c && target < c + loc[q]) {
-                *bin = (uint32_t)(t * per + q);
-                *rank = target - c;
+                sb = (uint32_t)(t * per + q);
+                sr = target - c;
             }
             c += loc[q];
         }
     }
+    __syncthreads();
+    bin = sb;
+    rank = sr;
+    __syncthreads();
 }
 
-__device__ __forceinline__ bool last_block(uint32_t *ticket)
+// Grid-wide barrier with a bounded wait: a monotonic arrival counter (release on
+// arrival, acquire while polling), so no reset is needed within a launch.  Returns false
+// if the launch is being aborted.
+__device__ bool grid_sync(PeelCtl *ctl, uint32_t *flags, unsigned &target)
 {
-    __shared__ bool is_last;
-    __threadfence();
+    __shared__ int ok;
+    target += gridDim.x;
     __syncthreads();
-    if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) {
+        int good = 1;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctl->bar_count) : "memory");
+        unsigned spins = 0, v;
+        for (;;) {
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ctl->bar_count) : "memory");
+            if ((int)(v - target) >= 0) break;
+            if ((++spins & 63) == 0) {
+                if (*(volatile unsigned *)&ctl->abort) { good = 0; break; }
+                if (spins > kSpinLimit) {
+                    atomicExch(&ctl->abort, 1u);
+                    atomicOr(&flags[1], 2u);           // timed out
+                    good = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        ok = good;
+    }
     __syncthreads();
-    if (is_last) __threadfence();
-    return is_last;
+    return ok != 0;
 }
 
 // ------------------------------------------------------------------ distances
@@ -152,73 +190,64 @@ __device__ double dist64(const float *__restrict__ row, const float *Ls, int d)
     return s;
 }
 
-// ------------------------------------------------------------------ kernels
-template <int D>
-__global__ void __launch_bounds__(kThreads)
-k_peel_dist(const float *__restrict__ x, int d, const uint32_t *__restrict__ idx, uint32_t nr,
-            const float *__restrict__ L, uint32_t *__restrict__ key, PeelCtl *ctl, uint32_t target)
+// Compensated float32 distance (h + l, |l| <= ulp(h)/2): each difference is split exactly
+// into s + e (TwoSum), s^2 is kept exactly as p + pe (FMA), 2*s*e is folded into the low
+// part (e^2 <= 2^-48 s^2 is dropped) and the high parts are summed error-free (TwoSum).
+// Its distance to the float64 definition is below eps_ff(d) * (h + l).
+__device__ __forceinline__ void dist_ff(const float *__restrict__ row, const float *Ls, int d, float &h, float &l)
 {
-    __shared__ uint32_t h[kHistBins];
-    __shared__ float Ls[D > 0 ? D : kMaxD];
-    for (int b = threadIdx.x; b < kHistBins; b += kThreads) h[b] = 0;
-    for (int j = threadIdx.x; j < d; j += kThreads) Ls[j] = L[j];
-    __syncthreads();
-    for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < nr; i += gridDim.x * kThreads) {
-        uint32_t row = idx ? idx[i] : i;
-        float dl = dist32<D>(x + (size_t)row * d, Ls, d);
-        uint32_t k = __float_as_uint(dl);
-        key[i] = k;
-        atomicAdd(&h[k >> 20], 1u);
+    float hi = 0.0f, lo = 0.0f;
+    for (int j = 0; j < d; j++) {
+        const float a = __ldg(&row[j]), b = Ls[j];
+        const float s = __fsub_rn(a, b);
+        const float bb = __fsub_rn(s, a);                       // TwoSum(a, -b)
+        const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(-b, bb));
+        const float p = __fmul_rn(s, s);
+        const float pe = __fmaf_rn(s, s, -p);
+        const float q = __fmaf_rn(__fmul_rn(2.0f, s), e, pe);
+        const float t = __fadd_rn(hi, p);                       // TwoSum(hi, p)
+        const float bv = __fsub_rn(t, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+        hi = t;
+        lo = __fadd_rn(lo, __fadd_rn(err, q));
     }
-    __syncthreads();
-    for (int b = threadIdx.x; b < kHistBins; b += kThreads)
-        if (h[b]) atomicAdd(&ctl->hist0[b], h[b]);
-    if (!last_block(&ctl->ticket[0])) return;
-    find_bin(ctl->hist0, target, &ctl->b0, &ctl->rank0);
-    __syncthreads();
-    for (int b = threadIdx.x; b < kHistBins; b += kThreads) ctl->hist0[b] = 0;
-    if (threadIdx.x == 0) ctl->ticket[0] = 0;
+    h = __fadd_rn(hi, lo);                                      // normalise (Fast2Sum)
+    l = __fsub_rn(lo, __fsub_rn(h, hi));
 }
 
-__global__ void __launch_bounds__(kThreads)
-k_peel_hist1(const uint32_t *__restrict__ key, uint32_t nr, PeelCtl *ctl, int d)
+// Bound on |dff - delta64| / delta64: (d^2 + 8d) u^2 for the compensated sum
+// (u = 2^-24) plus (d + 2) 2^-53 for the float64 one, with a factor two of margin.
+__device__ __forceinline__ float eps_ff(int d)
 {
-    __shared__ uint32_t h[kHistBins];
-    for (int b = threadIdx.x; b < kHistBins; b += kThreads) h[b] = 0;
-    __syncthreads();
-    const uint32_t b0 = ctl->b0;
-    for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < nr; i += gridDim.x * kThreads) {
-        uint32_t k = key[i];
-        if ((k >> 20) == b0) atomicAdd(&h[(k >> 8) & 0xFFFu], 1u);
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < kHistBins; b += kThreads)
-        if (h[b]) atomicAdd(&ctl->hist1[b], h[b]);
-    if (!last_block(&ctl->ticket[1])) return;
-    __shared__ uint32_t b1, r1;
-    find_bin(ctl->hist1, ctl->rank0, &b1, &r1);
-    __syncthreads();
-    for (int b = threadIdx.x; b < kHistBins; b += kThreads) ctl->hist1[b] = 0;
-    if (threadIdx.x == 0) {
-        uint32_t lo = (b0 << 20) | (b1 << 8);
-        uint32_t hi = lo | 0xFFu;
-        double A = (double)__uint_as_float(lo), B = (double)__uint_as_float(hi);
-        double eps = (double)(d + 4) * 0x1p-23;
-        double ea = 0x1p-120;
-        double klo = A * (1.0 - eps) - ea;
-        double khi = B * (1.0 + eps) + ea;
-        double in_thr = (klo - ea) / (1.0 + eps) * (1.0 - 0x1p-40);
-        double out_thr = (khi + ea) / (1.0 - eps) * (1.0 + 0x1p-40);
-        ctl->in_key = in_thr > 0.0 ? __float_as_uint(__double2float_rd(in_thr)) : 0u;
-        ctl->out_key = __float_as_uint(__double2float_ru(out_thr));
-        ctl->ticket[1] = 0;
-    }
+    return (float)((double)d * d + 8.0 * d + 1.0) * 0x1p-47f;
 }
 
-// Single-block selection of the `need` smallest (key, pos) pairs of the band list by an
-// 8-bit radix select over the 96-bit composite; marks them taken.
-__device__ void select_band(const uint64_t *bkey, const uint32_t *bpos, uint32_t nb, uint32_t need,
-                            uint8_t *status, uint32_t *blk_cnt)
+// Thresholds of phase C from the 22-bit key prefix [A, B] of the N-th smallest key.
+// With eps = (d+4) 2^-23 and ea = 2^-120 the N-th smallest delta64 lies in
+// [A(1-eps) - ea, B(1+eps) + ea]; a point is certainly in if delta32 (1+eps) + ea is below
+// that interval, which holds for delta32 < A(1-2eps) - 2ea, and certainly out if
+// delta32 (1-eps) - ea is above it, which holds for delta32 > B(1+3eps) + 3ea.  Both
+// cut-offs are evaluated in float32 rounded towards the safe side.
+__device__ void band_cutoffs_key(uint32_t lo, uint32_t hi, int d, uint32_t &in_key, uint32_t &out_key)
+{
+    const float A = __uint_as_float(lo), B = __uint_as_float(hi);
+    const float eps = (float)(d + 4) * 0x1p-23f;
+    const float in_thr = __fsub_rd(__fmul_rd(A, __fsub_rd(1.0f, 2.0f * eps)), 0x1p-119f);
+    const float out_thr = __fadd_ru(__fmul_ru(B, __fadd_ru(1.0f, 3.0f * eps)), 0x1.8p-119f);
+    in_key = in_thr > 0.0f ? __float_as_uint(in_thr) : 0u;
+    out_key = __float_as_uint(out_thr);
+}
+
+__device__ void band_cutoffs(uint32_t b0, uint32_t b1, int d, uint32_t &in_key, uint32_t &out_key)
+{
+    const uint32_t lo = (b0 << 21) | (b1 << 10);
+    band_cutoffs_key(lo, lo | 0x3FFu, d, in_key, out_key);
+}
+
+// Single-block radix select (8-bit digits over the 96-bit (key, pos) composite) of the
+// `need`-th smallest band entry in global memory; for bands too large for shared memory.
+__device__ void select_band_global(const uint64_t *bkey, const uint32_t *bpos, uint32_t nb, uint32_t need,
+                                   uint64_t &K, uint32_t &Pp)
 {
     __shared__ uint32_t h[256];
     __shared__ uint64_t pk;
@@ -226,7 +255,7 @@ __device__ void select_band(const uint64_t *bkey, const uint32_t *bpos, uint32_t
     if (threadIdx.x == 0) { pk = 0; pp = 0; rank = need - 1; }
     __syncthreads();
     for (int pass = 0; pass < 12; pass++) {
-        for (int b = threadIdx.x; b < 256; b += kThreads) h[b] = 0;
+        h[threadIdx.x] = 0;
         __syncthreads();
         const uint64_t cpk = pk;
         const uint32_t cpp = pp;
@@ -246,216 +275,517 @@ __device__ void select_band(const uint64_t *bkey, const uint32_t *bpos, uint32_t
             if (match) atomicAdd(&h[digit], 1u);
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t c = 0, r = rank;
-            for (int b = 0; b < 256; b++) {
-                if (r < c + h[b]) {
-                    if (pass < 8) pk |= (uint64_t)b << (56 - 8 * pass);
-                    else pp |= (uint32_t)b << (24 - 8 * (pass - 8));
-                    rank = r - c;
-                    break;
-                }
-                c += h[b];
-            }
+        const uint32_t v = h[threadIdx.x];
+        uint32_t tot;
+        const uint32_t before = block_excl_scan(v, tot);
+        const uint32_t r = rank;
+        __syncthreads();
+        if (r >= before && r < before + v) {
+            if (pass < 8) pk = cpk | ((uint64_t)threadIdx.x << (56 - 8 * pass));
+            else pp = cpp | ((uint32_t)threadIdx.x << (24 - 8 * (pass - 8)));
+            rank = r - before;
         }
         __syncthreads();
     }
-    const uint64_t K = pk;
-    const uint32_t Pp = pp;
-    for (uint32_t i = threadIdx.x; i < nb; i += kThreads) {
-        uint64_t k = __ldcg(&bkey[i]);
-        uint32_t p = __ldcg(&bpos[i]);
-        if (k < K || (k == K && p <= Pp)) {
-            status[p] = 1;
-            atomicAdd(&blk_cnt[p / kBlkItems], 1u);
-        }
-    }
+    K = pk;
+    Pp = pp;
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ the kernel
+struct PeelArgs {
+    const float *x;
+    int d;
+    int64_t n, N, S;
+    uint32_t *idx0, *idx1;       // remaining indices, ping-pong
+    uint32_t *key;
+    uint8_t *status;             // 0 out, 1 taken, 2 band
+    uint64_t *band_key;          // float64 distance bits (wide bands only)
+    uint32_t *band_k32;          // float32 keys of the band
+    uint32_t *band_pos;
+    uint32_t *perm;
+    float *landmarks;            // S x d or NULL
+    PeelCtl *ctl;
+    uint32_t *flags;             // job flags: [1] |= 1 bound violated, 2 barrier timed out
+};
+
+// rows a thread keeps in flight at once (64 floats of rows at most)
+template <int D>
+__host__ __device__ constexpr int kPeelBatch()
+{
+    return D <= 0 ? 1 : (D >= 64 ? 1 : (64 / D > 4 ? 4 : 64 / D));
 }
 
 template <int D>
-__global__ void __launch_bounds__(kThreads)
-k_peel_classify(const float *__restrict__ x, int d, const uint32_t *__restrict__ idx, uint32_t nr,
-                const uint32_t *__restrict__ key, const float *__restrict__ L, uint8_t *status,
-                uint64_t *band_key, uint32_t *band_pos, uint32_t *blk_cnt, uint32_t *blk_off,
-                PeelCtl *ctl, uint32_t N)
+__global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
 {
+    constexpr int DM = D > 0 && D <= 64 ? D : 1;       // register minima when D is small
+    constexpr int B = kPeelBatch<D>();
+    constexpr int QT = 16;                             // tiles of kThreads items per scan
+    constexpr int W = kThreads / 32;
+    // dynamic shared memory: [first histogram | guessed second-digit histogram], all of
+    // it reused for the band in phase D
+    extern __shared__ __align__(16) uint32_t dyn[];
+    uint32_t *sh = dyn;
+    uint32_t *gh = dyn + kHistBins;
     __shared__ float Ls[D > 0 ? D : kMaxD];
-    uint32_t tot;
-    for (int j = threadIdx.x; j < d; j += kThreads) Ls[j] = L[j];
-    __syncthreads();
-    const uint32_t in_key = ctl->in_key, out_key = ctl->out_key;
-    const uint32_t base = blockIdx.x * kBlkItems + threadIdx.x * 4;
-    uint32_t n_in = 0;
-    uint8_t st[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        uint32_t i = base + q;
-        if (i >= nr) break;
-        uint32_t k = key[i];
-        uint8_t s = k < in_key ? 1 : (k > out_key ? 0 : 2);
-        if (s == 2) {
-            uint32_t row = idx ? idx[i] : i;
-            double dl = dist64(x + (size_t)row * d, Ls, d);
-            uint32_t slot = atomicAdd(&ctl->band_count, 1u);
-            band_key[slot] = (uint64_t)__double_as_longlong(dl);
-            band_pos[slot] = i;
-        }
-        n_in += s == 1;
-        st[q] = s;
-    }
-    if (base + 3 < nr) {
-        *reinterpret_cast<uchar4 *>(&status[base]) = make_uchar4(st[0], st[1], st[2], st[3]);
-    } else {
-        for (int q = 0; q < 4; q++)
-            if (base + q < nr) status[base + q] = st[q];
-    }
-    block_excl_scan(n_in, tot);
-    if (threadIdx.x == 0) blk_cnt[blockIdx.x] = tot;
-    if (!last_block(&ctl->ticket[2])) return;
+    __shared__ uint32_t s_in_key, s_out_key, s_nt, s_na, s_v, s_t32;
+    __shared__ float wmin[W][DM];
+    __shared__ uint32_t gmin[D > 0 && D <= 64 ? 1 : kMaxD];
+    __shared__ uint32_t off_t[QT * W], off_u[QT * W], s_tot[2];
+    PeelCtl *ctl = a.ctl;
+    const int d = a.d;
+    const int t = threadIdx.x;
+    const int lane = t & 31, w = t >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const unsigned G = gridDim.x, c = blockIdx.x;
+    unsigned gen = 0;
+    uint32_t guess = 0xFFFFFFFFu;      // first digit of the previous round's N-th key
 
-    // ---- last block: settle the band, then per-block output offsets
-    __shared__ uint32_t all_in, nb, need;
-    const uint32_t nblk = gridDim.x;
-    uint32_t s = 0;
-    for (uint32_t b = threadIdx.x; b < nblk; b += kThreads) s += __ldcg(&blk_cnt[b]);
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    __shared__ uint32_t ws[kThreads / 32];
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t a = 0;
-        for (int w = 0; w < kThreads / 32; w++) a += ws[w];
-        all_in = a;
-        nb = __ldcg(&ctl->band_count);
-        need = N > a ? N - a : 0;
-        ctl->n_in = a;
-        ctl->need = need;
-        if (a > N || need > nb) ctl->error = 1;   // would contradict the error bound
-    }
-    __syncthreads();
-    if (need > 0 && need <= nb) {
-        if (need == nb) {
-            for (uint32_t i = threadIdx.x; i < nb; i += kThreads) {
-                uint32_t p = __ldcg(&band_pos[i]);
-                status[p] = 1;
-                atomicAdd(&blk_cnt[p / kBlkItems], 1u);
+    for (int64_t r = 0; r < a.S; r++) {
+        const int64_t nr = a.n - r * a.N;
+        const int par = (int)(r & 1);
+        const uint32_t *idx_in = r == 0 ? nullptr : (par ? a.idx1 : a.idx0);
+        uint32_t *idx_out = par ? a.idx0 : a.idx1;
+        uint32_t *seg_out = a.perm + r * a.N;
+        const uint32_t s0 = (uint32_t)((int64_t)c * nr / G), s1 = (uint32_t)((int64_t)(c + 1) * nr / G);
+        if (nr <= a.N) {                              // the last subcluster: all that is left
+            for (uint32_t i = s0 + t; i < s1; i += kThreads) seg_out[i] = idx_in ? __ldcg(&idx_in[i]) : i;
+            if (c == 0 && a.landmarks)
+                for (int j = t; j < d; j += kThreads)
+                    a.landmarks[r * d + j] = __uint_as_float(__ldcg(&ctl->Lbits[par][j]));
+            break;
+        }
+        uint32_t *hist0 = ctl->hist[par][0], *hist1 = ctl->hist[par][1];
+
+        // ---- A: float32 distances and the first histogram
+        for (int j = t; j < d; j += kThreads) Ls[j] = __uint_as_float(__ldcg(&ctl->Lbits[par][j]));
+        const bool have_guess = guess != 0xFFFFFFFFu;
+        for (int b = t; b < (have_guess ? 2 : 1) * kHistBins; b += kThreads) dyn[b] = 0;
+        if (c == 0) {
+            for (int j = t; j < d; j += kThreads) {
+                ctl->Lbits[par ^ 1][j] = kInfBits;
+                if (a.landmarks) a.landmarks[r * d + j] = __uint_as_float(__ldcg(&ctl->Lbits[par][j]));
+            }
+            if (t == 0) ctl->band_cnt[par ^ 1] = 0;
+        }
+        __syncthreads();
+        for (uint32_t i0 = s0 + t; i0 < s1; i0 += B * kThreads) {
+            uint32_t rows[B];
+#pragma unroll
+            for (int q = 0; q < B; q++) {
+                const uint32_t i = i0 + q * kThreads;
+                rows[q] = i < s1 ? (idx_in ? __ldcg(&idx_in[i]) : i) : 0u;
+            }
+            float dl[B];
+#pragma unroll
+            for (int q = 0; q < B; q++) dl[q] = dist32<D>(a.x + (size_t)rows[q] * d, Ls, d);
+#pragma unroll
+            for (int q = 0; q < B; q++) {
+                const uint32_t i = i0 + q * kThreads;
+                if (i < s1) {
+                    const uint32_t k = __float_as_uint(dl[q]);
+                    a.key[i] = k;
+                    atomicAdd(&sh[k >> 21], 1u);
+                    if (have_guess && (k >> 21) == guess) atomicAdd(&gh[(k >> 10) & (kHistBins - 1)], 1u);
+                }
+            }
+        }
+        __syncthreads();
+        for (int b = t; b < kHistBins; b += kThreads)
+            if (sh[b]) atomicAdd(&hist0[b], sh[b]);
+        if (have_guess) {
+            uint32_t *gg = &ctl->ghist[par][0];
+            for (int b = t; b < kHistBins; b += kThreads)
+                if (gh[b]) atomicAdd(&gg[b], gh[b]);
+        }
+        if (!grid_sync(ctl, a.flags, gen)) return;
+
+        // ---- B: second histogram inside the N-th key's bin (skipped when the bin was
+        // guessed: the previous round's N-th key is almost always in the same bin)
+        uint32_t b0, rank0;
+        find_bin(hist0, (uint32_t)(a.N - 1), b0, rank0);
+        const bool hit = have_guess && b0 == guess;
+        guess = b0;
+        if (hit) {
+            hist1 = &ctl->ghist[par][0];
+        } else {
+        for (int b = t; b < kHistBins; b += kThreads) sh[b] = 0;
+        __syncthreads();
+        for (uint32_t i0 = s0 + t; i0 < s1; i0 += 4 * kThreads) {
+            uint32_t k4[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const uint32_t i = i0 + q * kThreads;
+                k4[q] = i < s1 ? a.key[i] : 0xFFFFFFFFu;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                if ((k4[q] >> 21) == b0 && k4[q] != 0xFFFFFFFFu) atomicAdd(&sh[(k4[q] >> 10) & (kHistBins - 1)], 1u);
+        }
+        __syncthreads();
+        for (int b = t; b < kHistBins; b += kThreads)
+            if (sh[b]) atomicAdd(&hist1[b], sh[b]);
+        if (!grid_sync(ctl, a.flags, gen)) return;
+        }
+
+        // ---- C: classify; the band is listed
+        uint32_t b1, rank1;
+        find_bin(hist1, rank0, b1, rank1);
+        if (t == 0) band_cutoffs(b0, b1, d, s_in_key, s_out_key);
+        {   // clear next round's histograms (last read in the previous round)
+            uint32_t *nh = &ctl->hist[par ^ 1][0][0];
+            for (uint32_t b = c * kThreads + t; b < 2u * kHistBins; b += G * kThreads) nh[b] = 0;
+            uint32_t *ng = &ctl->ghist[par ^ 1][0];
+            for (uint32_t b = c * kThreads + t; b < (uint32_t)kHistBins; b += G * kThreads) ng[b] = 0;
+        }
+        __syncthreads();
+        const uint32_t in_key = s_in_key, out_key = s_out_key;
+        uint32_t n_in = 0;
+        for (uint32_t i0 = s0 + t; i0 < s1; i0 += 4 * kThreads) {
+            uint32_t k4[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const uint32_t i = i0 + q * kThreads;
+                k4[q] = i < s1 ? a.key[i] : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const uint32_t i = i0 + q * kThreads;
+                if (i >= s1) continue;
+                const uint32_t k = k4[q];
+                uint8_t s = k < in_key ? 1 : (k > out_key ? 0 : 2);
+                if (s == 2) {
+                    const uint32_t slot = atomicAdd(&ctl->band_cnt[par], 1u);
+                    a.band_k32[slot] = k;
+                    a.band_pos[slot] = i;
+                }
+                n_in += s == 1;
+                a.status[i] = s;
+            }
+        }
+        n_in = block_sum(n_in);
+        if (t == 0) ctl->cnt_in[c] = n_in;
+        if (!grid_sync(ctl, a.flags, gen)) return;
+
+        // ---- D: settle the band, compact, next landmark
+        uint32_t all_in = 0, in_before = 0;
+        for (uint32_t q = t; q < G; q += kThreads) {
+            const uint32_t v = __ldcg(&ctl->cnt_in[q]);
+            all_in += v;
+            if (q < c) in_before += v;
+        }
+        all_in = block_sum(all_in);
+        in_before = block_sum(in_before);
+        const uint32_t nb = __ldcg(&ctl->band_cnt[par]);
+        const uint32_t need = (uint32_t)a.N > all_in ? (uint32_t)a.N - all_in : 0u;
+        if ((all_in > (uint32_t)a.N || need > nb) && c == 0 && t == 0) atomicOr(&a.flags[1], 1u);
+        uint32_t band_before = 0;
+        bool slow = false;
+        if (need > 0 && need < nb) {
+            // Fast path, in shared memory (every CTA redundantly).  The need-th smallest
+            // float32 key T32 of the band comes from a one-ulp histogram; the float32 error
+            // bound around T32 leaves a tight set of a few entries; their distances in
+            // compensated float32 (dff, within eps_ff of the float64 definition) settle all
+            // of them but those within the dff error of the cut-off (in practice only exact
+            // ties), which are decided in float64.
+            uint32_t *hb = dyn;                                    // kBandBins one-ulp bins
+            uint32_t *tpos = dyn + kBandBins;                      // kTight tight entries
+            float *th = reinterpret_cast<float *>(tpos + kTight);
+            float *tl = th + kTight;
+            uint32_t *tcls = reinterpret_cast<uint32_t *>(tl + kTight);   // 1 taken, 0 not
+            uint32_t *tamb = tcls + kTight;                        // undecided tight entries
+            unsigned long long *td = reinterpret_cast<unsigned long long *>(tamb + kTight);
+            const uint32_t range = out_key - in_key + 1u;
+            slow = range > (uint32_t)kBandBins;
+            if (!slow) {
+                for (int b = t; b < kBandBins; b += kThreads) hb[b] = 0;
+                if (t == 0) {
+                    s_nt = 0;
+                    s_na = 0;
+                }
+                __syncthreads();
+                for (uint32_t q = t; q < nb; q += kThreads) atomicAdd(&hb[__ldcg(&a.band_k32[q]) - in_key], 1u);
+                __syncthreads();
+                {   // the one-ulp bin of the need-th smallest band key
+                    constexpr int per = kBandBins / kThreads;
+                    uint32_t loc = 0;
+#pragma unroll
+                    for (int q = 0; q < per; q++) loc += hb[t * per + q];
+                    uint32_t tot;
+                    const uint32_t before = block_excl_scan(loc, tot);
+                    const uint32_t target = need - 1;
+                    if (target >= before && target < before + loc) {
+                        uint32_t cc = before;
+                        for (int q = 0; q < per; q++) {
+                            const uint32_t h = hb[t * per + q];
+                            if (target >= cc && target < cc + h) s_t32 = in_key + (uint32_t)(t * per + q);
+                            cc += h;
+                        }
+                    }
+                }
+                __syncthreads();
+                uint32_t tin, tout;
+                band_cutoffs_key(s_t32, s_t32, d, tin, tout);
+                uint32_t n_cert = 0;
+                for (uint32_t q = t; q < nb; q += kThreads) {
+                    const uint32_t k = __ldcg(&a.band_k32[q]);
+                    if (k < tin) {
+                        n_cert++;
+                    } else if (k <= tout) {
+                        const uint32_t slot = atomicAdd(&s_nt, 1u);
+                        if (slot < (uint32_t)kTight) tpos[slot] = __ldcg(&a.band_pos[q]);
+                    }
+                }
+                n_cert = block_sum(n_cert);
+                const uint32_t nt = s_nt;
+                slow = nt > (uint32_t)kTight || n_cert > need || need - n_cert > nt;
+                if (!slow) {
+                    const uint32_t need2 = need - n_cert;
+                    for (uint32_t q = t; q < nt; q += kThreads) {
+                        const uint32_t pq = tpos[q];
+                        const uint32_t row = idx_in ? __ldcg(&idx_in[pq]) : pq;
+                        float h, l;
+                        dist_ff(a.x + (size_t)row * d, Ls, d, h, l);
+                        th[q] = h;
+                        tl[q] = l;
+                    }
+                    __syncthreads();
+                    // V: the tight entry of rank need2-1 in (dff, position) order
+                    for (uint32_t q = t; q < nt; q += kThreads) {
+                        uint32_t rk = 0;
+                        for (uint32_t o = 0; o < nt; o++)
+                            rk += (uint32_t)((th[o] < th[q]) |
+                                             ((th[o] == th[q]) & ((tl[o] < tl[q]) | ((tl[o] == tl[q]) & (tpos[o] < tpos[q])))));
+                        if (rk == need2 - 1) s_v = q;
+                    }
+                    __syncthreads();
+                    // the need2-th smallest delta64 lies within eps*hv of hv (order statistics
+                    // move by at most the per-entry error); an entry is decided if its own
+                    // error cannot bridge the gap (plus an absolute floor against underflow)
+                    const float hv = th[s_v], lv = tl[s_v];
+                    const float win = 2.0f * eps_ff(d) * hv + 0x1p-120f;
+                    uint32_t n_take = 0;
+                    for (uint32_t q = t; q < nt; q += kThreads) {
+                        const float diff = __fadd_rn(__fsub_rn(th[q], hv), __fsub_rn(tl[q], lv));
+                        uint32_t cls = diff < -win ? 1u : 0u;
+                        if (diff >= -win && diff <= win) {
+                            const uint32_t slot = atomicAdd(&s_na, 1u);
+                            tamb[slot] = q;
+                        }
+                        n_take += cls;
+                        tcls[q] = cls;
+                    }
+                    n_take = block_sum(n_take);
+                    const uint32_t na = s_na;
+                    const uint32_t need3 = need2 >= n_take ? need2 - n_take : 0u;
+                    if (need3 > na && t == 0) atomicOr(&a.flags[1], 1u);
+                    if (need3 >= na) {
+                        for (uint32_t q = t; q < na; q += kThreads) tcls[tamb[q]] = 1u;
+                    } else if (need3 > 0) {
+                        for (uint32_t q = t; q < na; q += kThreads) {
+                            const uint32_t pq = tpos[tamb[q]];
+                            const uint32_t row = idx_in ? __ldcg(&idx_in[pq]) : pq;
+                            td[q] = (unsigned long long)__double_as_longlong(dist64(a.x + (size_t)row * d, Ls, d));
+                        }
+                        __syncthreads();
+                        for (uint32_t q = t; q < na; q += kThreads) {
+                            const unsigned long long kq = td[q];
+                            const uint32_t pq = tpos[tamb[q]];
+                            uint32_t rk = 0;
+                            for (uint32_t o = 0; o < na; o++) rk += (td[o] < kq) || (td[o] == kq && tpos[tamb[o]] < pq);
+                            tcls[tamb[q]] = rk < need3 ? 1u : 0u;
+                        }
+                    }
+                    __syncthreads();
+                    for (uint32_t q = t; q < nb; q += kThreads) {
+                        const uint32_t k = __ldcg(&a.band_k32[q]);
+                        const uint32_t pq = __ldcg(&a.band_pos[q]);
+                        bool take = k < tin;
+                        if (!take && k <= tout)
+                            for (uint32_t o = 0; o < nt; o++)
+                                if (tpos[o] == pq) take = tcls[o] != 0;
+                        if (take) {
+                            if (pq < s0) band_before++;
+                            else if (pq < s1) a.status[pq] = 1;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+            if (slow) {
+                // wide band (e.g. many equal distances): float64 for every band entry, spread
+                // over all CTAs, then one CTA selects while the rest wait
+                for (uint32_t q = c * kThreads + t; q < nb; q += G * kThreads) {
+                    const uint32_t pq = __ldcg(&a.band_pos[q]);
+                    const uint32_t row = idx_in ? __ldcg(&idx_in[pq]) : pq;
+                    a.band_key[q] = (uint64_t)__double_as_longlong(dist64(a.x + (size_t)row * d, Ls, d));
+                }
+                if (!grid_sync(ctl, a.flags, gen)) return;
+                uint64_t K = 0;
+                uint32_t Pp = 0;
+                if (c == 0) {
+                    select_band_global(a.band_key, a.band_pos, nb, need, K, Pp);
+                    if (t == 0) {
+                        ctl->sel_key = K;
+                        ctl->sel_pos = Pp;
+                    }
+                }
+                if (!grid_sync(ctl, a.flags, gen)) return;
+                K = __ldcg(&ctl->sel_key);
+                Pp = __ldcg(&ctl->sel_pos);
+                band_before = 0;
+                for (uint32_t q = t; q < nb; q += kThreads) {
+                    const uint64_t kq = __ldcg(&a.band_key[q]);
+                    const uint32_t pq = __ldcg(&a.band_pos[q]);
+                    if (kq < K || (kq == K && pq <= Pp)) {
+                        if (pq < s0) band_before++;
+                        else if (pq < s1) a.status[pq] = 1;
+                    }
+                }
+            }
+        } else if (need > 0) {
+            // need >= nb: the whole band is taken (need > nb contradicts the bound; flagged)
+            for (uint32_t q = t; q < nb; q += kThreads) {
+                const uint32_t pq = __ldcg(&a.band_pos[q]);
+                if (pq < s0) band_before++;
+                else if (pq < s1) a.status[pq] = 1;
+            }
+        }
+        band_before = block_sum(band_before);       // its barrier also orders the status writes
+        uint32_t sel_base = in_before + band_before;
+        uint32_t uns_base = s0 - sel_base;
+
+        float mn[DM];
+#pragma unroll
+        for (int j = 0; j < DM; j++) mn[j] = __int_as_float(kInfBits);
+        if (!(D > 0 && D <= 64)) {
+            for (int j = t; j < d; j += kThreads) gmin[j] = kInfBits;
+            __syncthreads();
+        }
+        // stable compaction, QT tiles of kThreads items per scan: item (q, t) of a chunk
+        // is preceded by the earlier tiles, by the earlier warps of its tile and by the
+        // lower lanes of its warp
+        for (uint32_t cb = s0; cb < s1; cb += QT * kThreads) {
+            uint32_t tk = 0, vl = 0;                 // bit q: item (q, t) taken / valid
+            uint32_t ids[QT];
+#pragma unroll
+            for (int q = 0; q < QT; q++) {
+                const uint32_t i = cb + q * kThreads + t;
+                const bool v = i < s1;
+                const uint8_t st = v ? a.status[i] : 0;
+                ids[q] = v ? (idx_in ? __ldcg(&idx_in[i]) : i) : 0u;
+                vl |= (uint32_t)v << q;
+                tk |= (uint32_t)(st == 1) << q;
+            }
+#pragma unroll
+            for (int q = 0; q < QT; q++) {
+                const uint32_t bt = __ballot_sync(0xffffffffu, (tk >> q) & 1u);
+                const uint32_t bv = __ballot_sync(0xffffffffu, (vl >> q) & 1u);
+                if (lane == 0) {
+                    off_t[q * W + w] = __popc(bt);
+                    off_u[q * W + w] = __popc(bv & ~bt);
+                }
+            }
+            __syncthreads();
+            if (w == 0) {                           // exclusive scan of the QT*W counts in order
+                constexpr int PER = QT * W / 32;
+                uint32_t at[PER], au[PER], st_ = 0, su = 0;
+#pragma unroll
+                for (int e = 0; e < PER; e++) {
+                    at[e] = off_t[lane * PER + e];
+                    au[e] = off_u[lane * PER + e];
+                    st_ += at[e];
+                    su += au[e];
+                }
+                uint32_t it = warp_incl_scan(st_), iu = warp_incl_scan(su);
+                uint32_t et = it - st_, eu = iu - su;
+#pragma unroll
+                for (int e = 0; e < PER; e++) {
+                    off_t[lane * PER + e] = et;
+                    off_u[lane * PER + e] = eu;
+                    et += at[e];
+                    eu += au[e];
+                }
+                if (lane == 31) {
+                    s_tot[0] = it;
+                    s_tot[1] = iu;
+                }
+            }
+            __syncthreads();
+            uint32_t urows[QT];
+            int nu = 0;
+#pragma unroll
+            for (int q = 0; q < QT; q++) {
+                const uint32_t bt = __ballot_sync(0xffffffffu, (tk >> q) & 1u);
+                const uint32_t bv = __ballot_sync(0xffffffffu, (vl >> q) & 1u);
+                if ((vl >> q) & 1u) {
+                    if ((tk >> q) & 1u) {
+                        seg_out[sel_base + off_t[q * W + w] + __popc(bt & lt_mask)] = ids[q];
+                    } else {
+                        idx_out[uns_base + off_u[q * W + w] + __popc(bv & ~bt & lt_mask)] = ids[q];
+                        urows[nu++] = ids[q];
+                    }
+                }
+            }
+            // minima of the rows that stay, B rows in flight at a time
+            if (D > 0 && D <= 64) {
+                for (int q0 = 0; q0 < nu; q0 += B) {
+                    float rv[B][DM];
+#pragma unroll
+                    for (int q = 0; q < B; q++) {
+                        const uint32_t id = q0 + q < nu ? urows[q0 + q] : urows[q0];
+                        const float *row = a.x + (size_t)id * d;
+                        if (DM % 4 == 0) {
+                            const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+                            for (int j4 = 0; j4 < DM / 4; j4++) {
+                                const float4 v = __ldg(&r4[j4]);
+                                rv[q][4 * j4 + 0] = v.x;
+                                rv[q][4 * j4 + 1] = v.y;
+                                rv[q][4 * j4 + 2] = v.z;
+                                rv[q][4 * j4 + 3] = v.w;
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < DM; j++) rv[q][j] = __ldg(&row[j]);
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < B; q++)
+#pragma unroll
+                        for (int j = 0; j < DM; j++) mn[j] = fminf(mn[j], rv[q][j]);
+                }
+            } else {
+                for (int q = 0; q < nu; q++) {
+                    const float *row = a.x + (size_t)urows[q] * d;
+                    for (int j = 0; j < d; j++) atomicMin(&gmin[j], __float_as_uint(__ldg(&row[j])));
+                }
+            }
+            sel_base += s_tot[0];
+            uns_base += s_tot[1];
+            __syncthreads();
+        }
+        if (D > 0 && D <= 64) {
+#pragma unroll
+            for (int j = 0; j < DM; j++) {
+                float v = mn[j];
+                for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+                if (lane == 0) wmin[w][j] = v;
+            }
+            __syncthreads();
+            for (int j = t; j < d; j += kThreads) {
+                float v = wmin[0][j];
+                for (int q = 1; q < W; q++) v = fminf(v, wmin[q][j]);
+                if (__float_as_uint(v) < kInfBits) atomicMin(&ctl->Lbits[par ^ 1][j], __float_as_uint(v));
             }
         } else {
-            select_band(band_key, band_pos, nb, need, status, blk_cnt);
+            __syncthreads();
+            for (int j = t; j < d; j += kThreads)
+                if (gmin[j] < kInfBits) atomicMin(&ctl->Lbits[par ^ 1][j], gmin[j]);
         }
+        if (!grid_sync(ctl, a.flags, gen)) return;
     }
-    __threadfence();
-    __syncthreads();
-    // exclusive prefix of the per-block taken counts
-    __shared__ uint32_t carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (uint32_t b0 = 0; b0 < nblk; b0 += kThreads) {
-        uint32_t b = b0 + threadIdx.x;
-        uint32_t v = b < nblk ? __ldcg(&blk_cnt[b]) : 0;
-        uint32_t chunk = 0;
-        uint32_t ex = block_excl_scan(v, chunk);
-        if (b < nblk) blk_off[b] = carry + ex;
-        __syncthreads();
-        if (threadIdx.x == 0) carry += chunk;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        ctl->band_count = 0;
-        ctl->ticket[2] = 0;
-    }
-    (void)all_in;
-}
-
-template <int D>
-__global__ void __launch_bounds__(kThreads)
-k_peel_compact(const float *__restrict__ x, int d, const uint32_t *__restrict__ idx, uint32_t nr,
-               const uint8_t *__restrict__ status, const uint32_t *__restrict__ blk_off,
-               uint32_t *__restrict__ seg_out, uint32_t *__restrict__ idx_out, float *lpart,
-               float *L, float *landmark_next, PeelCtl *ctl)
-{
-    uint32_t tot;
-    __shared__ uint32_t smin[D > 0 && D <= 64 ? 1 : kMaxD];
-    const uint32_t base = blockIdx.x * kBlkItems + threadIdx.x * 4;
-    uint8_t st[4] = {0, 0, 0, 0};
-    uint32_t ids[4] = {0, 0, 0, 0};
-    uint32_t nsel = 0, nval = 0;
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        uint32_t i = base + q;
-        if (i < nr) {
-            st[q] = status[i];
-            ids[q] = idx ? idx[i] : i;
-            nsel += st[q] == 1;
-            nval++;
-        }
-    }
-    uint32_t pre = block_excl_scan(nsel, tot);
-    const uint32_t off = blk_off[blockIdx.x];
-    const uint32_t blk_base = blockIdx.x * kBlkItems;
-    uint32_t valid_before = base < nr ? base - blk_base : (nr > blk_base ? nr - blk_base : 0);
-    uint32_t sel_pos = off + pre;
-    uint32_t uns_pos = (blk_base - off) + (valid_before - pre);
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        if (q < (int)nval) {
-            if (st[q] == 1) seg_out[sel_pos++] = ids[q];
-            else idx_out[uns_pos++] = ids[q];
-        }
-    }
-    // per-attribute minimum of the points that stay (non-negative floats: compare bits)
-    if (D > 0 && D <= 64) {
-        float mn[D > 0 ? D : 1];
-#pragma unroll
-        for (int j = 0; j < (D > 0 ? D : 1); j++) mn[j] = __int_as_float(kInfBits);
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            if (q < (int)nval && st[q] != 1) {
-                const float *row = x + (size_t)ids[q] * d;
-#pragma unroll
-                for (int j = 0; j < (D > 0 ? D : 1); j++) mn[j] = fminf(mn[j], __ldg(&row[j]));
-            }
-        }
-        __shared__ float wmin[kThreads / 32][D > 0 && D <= 64 ? D : 1];
-#pragma unroll
-        for (int j = 0; j < (D > 0 ? D : 1); j++) {
-            float v = mn[j];
-            for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-            if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5][j] = v;
-        }
-        __syncthreads();
-        for (int j = threadIdx.x; j < d; j += kThreads) {
-            float v = wmin[0][j];
-            for (int w = 1; w < kThreads / 32; w++) v = fminf(v, wmin[w][j]);
-            lpart[(size_t)blockIdx.x * d + j] = v;
-        }
-    } else {
-        for (int j = threadIdx.x; j < d; j += kThreads) smin[j] = kInfBits;
-        __syncthreads();
-        for (int q = 0; q < 4; q++) {
-            if (q < (int)nval && st[q] != 1) {
-                const float *row = x + (size_t)ids[q] * d;
-                for (int j = 0; j < d; j++) atomicMin(&smin[j], __float_as_uint(row[j]));
-            }
-        }
-        __syncthreads();
-        for (int j = threadIdx.x; j < d; j += kThreads)
-            lpart[(size_t)blockIdx.x * d + j] = __uint_as_float(smin[j]);
-    }
-    if (!last_block(&ctl->ticket[3])) return;
-    for (int j = threadIdx.x; j < d; j += kThreads) {
-        float v = __int_as_float(kInfBits);
-        for (uint32_t b = 0; b < gridDim.x; b++) v = fminf(v, __ldcg(&lpart[(size_t)b * d + j]));
-        L[j] = v;
-        if (landmark_next) landmark_next[j] = v;
-    }
-    if (threadIdx.x == 0) ctl->ticket[3] = 0;
-}
-
-__global__ void k_peel_take_all(const uint32_t *__restrict__ idx, uint32_t nr, uint32_t *seg_out)
-{
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x)
-        seg_out[i] = idx ? idx[i] : i;
 }
 
 template <bool kVec4>
@@ -483,45 +813,56 @@ __global__ void k_gather_rows(const float *__restrict__ x, const uint32_t *__res
 }
 
 template <int D>
-cudaError_t peel_rounds(const PeelBuffers &b, int64_t n, int d, int64_t N, int sm_count,
+cudaError_t peel_launch(const PeelBuffers &b, int64_t n, int d, int64_t N, int sm_count,
                         cudaStream_t st, KTimer *kt)
 {
     const int64_t S = (n + N - 1) / N;
-    cudaMemsetAsync(b.L, 0, sizeof(float) * d, st);            // scaled minima are exactly 0
-    if (b.landmarks) cudaMemsetAsync(b.landmarks, 0, sizeof(float) * d, st);
-    for (int64_t r = 0; r < S; r++) {
-        const uint32_t nr = (uint32_t)(n - r * N);
-        const uint32_t *idx_in = r == 0 ? nullptr : b.idx[r & 1];
-        uint32_t *idx_out = b.idx[(r + 1) & 1];
-        uint32_t *seg_out = b.perm + r * N;
-        if ((int64_t)nr <= N) {
-            int g = (int)((nr + 255) / 256);
-            kt->begin(st);
-            k_peel_take_all<<<g, 256, 0, st>>>(idx_in, nr, seg_out);
-            kt->end(PSCL_K_PEEL_TAKE, st);
-            break;
-        }
-        int g1 = (int)((nr + kThreads - 1) / kThreads);
-        if (g1 > sm_count * 8) g1 = sm_count * 8;
-        const int nblk = (int)((nr + kBlkItems - 1) / kBlkItems);
-        kt->begin(st);
-        k_peel_dist<D><<<g1, kThreads, 0, st>>>(b.x, d, idx_in, nr, b.L, b.key, b.ctl, (uint32_t)(N - 1));
-        kt->end(PSCL_K_PEEL_DIST, st);
-        kt->begin(st);
-        k_peel_hist1<<<g1, kThreads, 0, st>>>(b.key, nr, b.ctl, d);
-        kt->end(PSCL_K_PEEL_HIST, st);
-        kt->begin(st);
-        k_peel_classify<D><<<nblk, kThreads, 0, st>>>(b.x, d, idx_in, nr, b.key, b.L, b.status,
-                                                       b.band_key, b.band_pos, b.blk_cnt, b.blk_off,
-                                                       b.ctl, (uint32_t)N);
-        kt->end(PSCL_K_PEEL_CLASSIFY, st);
-        kt->begin(st);
-        k_peel_compact<D><<<nblk, kThreads, 0, st>>>(b.x, d, idx_in, nr, b.status, b.blk_off, seg_out,
-                                                      idx_out, b.lpart, b.L,
-                                                      b.landmarks ? b.landmarks + (r + 1) * d : nullptr,
-                                                      b.ctl);
-        kt->end(PSCL_K_PEEL_COMPACT, st);
-    }
+    // all control state starts cleared; round 0's landmark is the origin (the scaled
+    // minimum of every attribute is exactly 0)
+    cudaError_t e = cudaMemsetAsync(b.ctl, 0, sizeof(PeelCtl), st);
+    if (e != cudaSuccess) return e;
+    const size_t smem = kPeelDynWords * sizeof(uint32_t);
+    e = cudaFuncSetAttribute(k_peel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_peel<D>, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int64_t grid = (int64_t)sm_count * std::min(per_sm, 4);
+    if (grid > kMaxPeelGrid) grid = kMaxPeelGrid;
+    const int64_t want = (n + 63) / 64;             // at least ~64 points per CTA in round 0
+    if (grid > want) grid = std::max<int64_t>(1, want);
+    PeelArgs a;
+    a.x = b.x;
+    a.d = d;
+    a.n = n;
+    a.N = N;
+    a.S = S;
+    a.idx0 = b.idx[0];
+    a.idx1 = b.idx[1];
+    a.key = b.key;
+    a.status = b.status;
+    a.band_key = b.band_key;
+    a.band_k32 = b.band_k32;
+    a.band_pos = b.band_pos;
+    a.perm = b.perm;
+    a.landmarks = b.landmarks;
+    a.ctl = b.ctl;
+    a.flags = b.flags;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    kt->begin(st);
+    e = cudaLaunchKernelEx(&cfg, k_peel<D>, a);
+    kt->end(PSCL_K_PEEL, st);
+    if (e != cudaSuccess) return e;
     int64_t work = (d % 4 == 0) ? n * d / 4 : n * d;
     int64_t g = (work + 255) / 256;
     if (g > (int64_t)sm_count * 16) g = (int64_t)sm_count * 16;
@@ -540,13 +881,13 @@ cudaError_t launch_peel(const PeelBuffers &b, int64_t n, int d, int64_t N, int s
                         cudaStream_t st, KTimer *kt)
 {
     switch (d) {
-    case 2: return peel_rounds<2>(b, n, d, N, sm_count, st, kt);
-    case 4: return peel_rounds<4>(b, n, d, N, sm_count, st, kt);
-    case 8: return peel_rounds<8>(b, n, d, N, sm_count, st, kt);
-    case 16: return peel_rounds<16>(b, n, d, N, sm_count, st, kt);
-    case 32: return peel_rounds<32>(b, n, d, N, sm_count, st, kt);
-    case 64: return peel_rounds<64>(b, n, d, N, sm_count, st, kt);
-    default: return peel_rounds<0>(b, n, d, N, sm_count, st, kt);
+    case 2: return peel_launch<2>(b, n, d, N, sm_count, st, kt);
+    case 4: return peel_launch<4>(b, n, d, N, sm_count, st, kt);
+    case 8: return peel_launch<8>(b, n, d, N, sm_count, st, kt);
+    case 16: return peel_launch<16>(b, n, d, N, sm_count, st, kt);
+    case 32: return peel_launch<32>(b, n, d, N, sm_count, st, kt);
+    case 64: return peel_launch<64>(b, n, d, N, sm_count, st, kt);
+    default: return peel_launch<0>(b, n, d, N, sm_count, st, kt);
     }
 }
 

@@ -13,25 +13,30 @@ namespace pscl {
 
 constexpr int kMaxD = 1024;          // attributes per point
 constexpr int kMaxK = 4096;          // centers of one Lloyd run
-constexpr int kHistBins = 4096;      // 12-bit radix digits of the peel's key select
+constexpr int kHistBins = 2048;      // 11-bit radix digits of the peel's key select
 constexpr int kBlkItems = 1024;      // points per block in the peel's classify/compact
 constexpr int kFixShift = 32;        // fixed-point scale 2^32 of the centroid sums
 
-// Device-resident control block of one peel (one round at a time).
+constexpr int kMaxPeelGrid = 2048;   // CTAs of the persistent peel launch
+
+// Device-resident control block of one persistent peel launch (cleared before it).
 struct PeelCtl {
-    uint32_t hist0[kHistBins];
-    uint32_t hist1[kHistBins];
-    uint32_t ticket[4];              // last-block tickets of the per-round kernels
-    uint32_t b0;                     // digit 0 (key bits 31..20) holding the N-th key
-    uint32_t rank0;                  // rank of the N-th key inside that digit
-    uint32_t in_key;                 // key < in_key  => certainly among the N nearest
-    uint32_t out_key;                // key > out_key => certainly not
-    uint32_t band_count;             // points between the two (decided in float64)
-    uint32_t n_in;
-    uint32_t need;                   // N - n_in: how many of the band are taken
-    uint32_t nonfinite;              // set by scaling if an input value is not finite
-    uint32_t error;
+    uint32_t hist[2][2][kHistBins];  // [round parity][digit level][bin]
+    uint32_t ghist[2][kHistBins];    // [round parity][bin]: second digit inside the guessed first
+    uint32_t Lbits[2][kMaxD];        // landmark of this / next round (float bits, min by atomicMin)
+    uint32_t cnt_in[kMaxPeelGrid];   // per CTA: points certainly taken this round
+    uint32_t band_cnt[2];            // band entries of this / next round
+    uint32_t bar_count;              // grid barrier: arrivals since the launch
+    uint32_t abort;                  // set when a barrier wait gave up
+    uint32_t sel_pos;                // large-band selection threshold (key, position)
+    unsigned long long sel_key;
 };
+
+// Job flags read by the host at every synchronisation.
+//   [0] != 0: an input value is not finite
+//   [1] bit 0: the peel's float32 bound was contradicted (internal error)
+//       bit 1: a bounded device-side wait gave up
+constexpr int kFlagWords = 4;
 
 // Segment table of one batched Lloyd launch (device arrays).
 struct SegTable {
@@ -78,7 +83,7 @@ struct KTimer {
 
 // scale.cu
 cudaError_t launch_scale(const float *raw, float *x, int64_t n, int d, float *part,
-                         uint32_t *ticket, double *mn, double *mx, PeelCtl *ctl, int sm_count,
+                         uint32_t *ticket, double *mn, double *mx, uint32_t *flags, int sm_count,
                          cudaStream_t st, KTimer *kt);
 size_t scale_part_floats(int64_t n, int d, int sm_count);
 
@@ -87,17 +92,15 @@ struct PeelBuffers {
     const float *x;                  // n x d scaled points
     uint32_t *idx[2];                // remaining point indices (ping-pong)
     uint32_t *key;                   // float32 distance keys of the remaining points
-    uint8_t *status;                 // 0 out, 1 in, 2 band (per remaining point)
-    uint64_t *band_key;              // float64 distance bits of band points
+    uint8_t *status;                 // 0 out, 1 taken, 2 band (per remaining point)
+    uint64_t *band_key;              // float64 distance bits of band points (wide bands)
+    uint32_t *band_k32;              // float32 keys of band points
     uint32_t *band_pos;              // their positions among the remaining points
-    uint32_t *blk_cnt;               // per classify block: selected count
-    uint32_t *blk_off;               // per classify block: exclusive prefix of selections
-    float *lpart;                    // per block partial minima (blocks x d)
-    float *L;                        // current landmark (d)
     float *landmarks;                // all landmarks (S x d), for inspection
     uint32_t *perm;                  // n: subcluster-packed original indices
     float *xseg;                     // n x d: subcluster-packed points
     PeelCtl *ctl;
+    uint32_t *flags;
 };
 cudaError_t launch_peel(const PeelBuffers &b, int64_t n, int d, int64_t N, int sm_count,
                         cudaStream_t st, KTimer *kt);

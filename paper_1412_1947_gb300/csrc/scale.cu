@@ -15,7 +15,7 @@ constexpr uint32_t kInfBits = 0x7f800000u;
 
 // Block layout: blockDim.x = d * rows_per_pass, so thread t always sees attribute t % d.
 __global__ void k_minmax(const float *__restrict__ raw, int64_t n, int d, float *part,
-                         uint32_t *ticket, double *mn, double *mx, PeelCtl *ctl)
+                         uint32_t *ticket, double *mn, double *mx, uint32_t *flags)
 {
     extern __shared__ float sm[];                 // 2 * blockDim.x
     const int t = threadIdx.x;
@@ -33,7 +33,7 @@ __global__ void k_minmax(const float *__restrict__ raw, int64_t n, int d, float 
             hi = fmaxf(hi, v);
         }
     }
-    if (bad) atomicOr(&ctl->nonfinite, 1u);
+    if (bad) atomicOr(&flags[0], 1u);
     sm[t] = lo;
     sm[blockDim.x + t] = hi;
     __syncthreads();
@@ -109,7 +109,7 @@ __global__ void k_scale_apply(const float *__restrict__ raw, float *__restrict__
 }  // namespace
 
 cudaError_t launch_scale(const float *raw, float *x, int64_t n, int d, float *part,
-                         uint32_t *ticket, double *mn, double *mx, PeelCtl *ctl, int sm_count,
+                         uint32_t *ticket, double *mn, double *mx, uint32_t *flags, int sm_count,
                          cudaStream_t st, KTimer *kt)
 {
     int threads = d * (1024 / d);
@@ -118,7 +118,7 @@ cudaError_t launch_scale(const float *raw, float *x, int64_t n, int d, float *pa
     int grid = (int)(want < (int64_t)sm_count * 4 ? want : (int64_t)sm_count * 4);
     if (grid < 1) grid = 1;
     kt->begin(st);
-    k_minmax<<<grid, threads, 2 * threads * sizeof(float), st>>>(raw, n, d, part, ticket, mn, mx, ctl);
+    k_minmax<<<grid, threads, 2 * threads * sizeof(float), st>>>(raw, n, d, part, ticket, mn, mx, flags);
     kt->end(PSCL_K_SCALE_MINMAX, st);
     bool vec = (d % 4) == 0;
     int64_t work = vec ? n * d / 4 : n * d;

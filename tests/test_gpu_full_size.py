@@ -1,0 +1,22 @@
+"""The headline workload at full size (2^20 points, d=16, 256 subclusters of 4096, 64 local
+centers, 25 iterations, final k=64), run the way bench.py times it (pipeline recorded
+into a CUDA graph, device-resident input), against the oracle on the same seeded input."""
+import numpy as np
+import pytest
+
+from paper_1412_1947_gb300 import synth
+from tests.parity import TIE_TOL, compare, run_gpu
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def test_medium_workload_full_size():
+    w = synth.MEDIUM
+    raw = w.points()
+    seed = 12345
+    g = run_gpu(raw, w.N, w.local_k, w.final_k, w.iters, seed, graph=True, runs=2, device_points=True)
+    o = oracle.two_level(raw, w.N, w.local_k, w.final_k, w.iters, seed, select_peel=True,
+                         force_local=g.trace_local, force_final=g.trace_final, tie_tol=TIE_TOL)
+    stats = compare(g, o)
+    print("full-size parity:", stats)

@@ -286,3 +286,29 @@ def test_replay_follows_only_near_ties():
     f[lab2 == 2] = 4
     *_, nf, nb = oracle.lloyd(x, cdup, 1, force=f[None, :], tie_tol=1e-5)
     assert nb == 0 and nf == int((lab2 == 2).sum()) > 0
+
+
+@pytest.mark.parametrize("n,d,N,grid", [(2000, 3, 128, 0), (3001, 2, 97, 6), (1024, 8, 1, 0), (777, 4, 1000, 0),
+                                        (5000, 1, 333, 4), (4096, 16, 256, 0)])
+def test_select_peel_equals_sorted_peel(n, d, N, grid):
+    # the O(n_r) selection form of the peel is the same function as the sort form,
+    # ties included (grid > 0: coordinates on a coarse grid, thousands of equal distances)
+    g = np.random.default_rng(n + d)
+    if grid:
+        raw = g.integers(0, grid, size=(n, d)).astype(np.float32)
+    else:
+        raw = synth.mixture(n, d, 5, outlier_frac=0.01, seed=n)
+    x, _, _ = oracle.scale(raw)
+    a = oracle.peel(x, N)
+    b = oracle.peel(x, N, select=True)
+    for u, v in zip(a, b):
+        np.testing.assert_array_equal(u, v)
+
+
+def test_two_level_select_peel_flag_changes_nothing():
+    raw = synth.mixture(3000, 4, 6, outlier_frac=0.01, seed=61)
+    a = oracle.two_level(raw, 256, 8, 5, 4, seed=2)
+    b = oracle.two_level(raw, 256, 8, 5, 4, seed=2, select_peel=True)
+    np.testing.assert_array_equal(a.perm, b.perm)
+    np.testing.assert_array_equal(a.final_centers, b.final_centers)
+    assert a.sse == b.sse
