@@ -165,13 +165,20 @@ k_lloyd_assign(const float *__restrict__ pts, SegTable t, int d, const float *__
     const int rows = t.unit_count[u];
     const int dd = D > 0 ? D : d;
 
-    // [center chunk | sums | counts], each 16-byte aligned
+    // [center chunk | high sums | low sums | counts], each 16-byte aligned.  A fixed-point
+    // value q <= 2^32 is added as q >> 11 (<= 2^21) and q & 0x7FF with two native 32-bit
+    // shared atomics; a unit has at most 1024 rows, so neither sum can wrap, and the
+    // flush recombines them exactly into the 64-bit global sums.
     const size_t c_bytes = ((size_t)min(chunk_k, k) * dd * 4 + 15) & ~(size_t)15;
     float *sc = reinterpret_cast<float *>(smem);
-    unsigned long long *sacc = reinterpret_cast<unsigned long long *>(smem + c_bytes);
-    int32_t *scnt = reinterpret_cast<int32_t *>(smem + c_bytes + (size_t)k * dd * 8);
+    uint32_t *shi = reinterpret_cast<uint32_t *>(smem + c_bytes);
+    uint32_t *slo = shi + (size_t)k * dd;
+    int32_t *scnt = reinterpret_cast<int32_t *>(slo + (size_t)k * dd);
     if (kSmemAcc) {
-        for (int e = threadIdx.x; e < k * dd; e += kThreads) sacc[e] = 0ull;
+        for (int e = threadIdx.x; e < k * dd; e += kThreads) {
+            shi[e] = 0u;
+            slo[e] = 0u;
+        }
         for (int j = threadIdx.x; j < k; j += kThreads) scnt[j] = 0;
     }
     const bool one_chunk = chunk_k >= k;
@@ -249,11 +256,20 @@ k_lloyd_assign(const float *__restrict__ pts, SegTable t, int d, const float *__
             const float *xr = pts + row * dd;
             if (kSmemAcc) {
                 atomicAdd(&scnt[bj[q]], 1);
+                const size_t e0 = (size_t)bj[q] * dd;
                 if (D > 0) {
 #pragma unroll
-                    for (int j = 0; j < DR; j++) atomicAdd(&sacc[(size_t)bj[q] * dd + j], to_fix(xv[q][j]));
+                    for (int j = 0; j < DR; j++) {
+                        const unsigned long long v = to_fix(xv[q][j]);
+                        atomicAdd(&shi[e0 + j], (uint32_t)(v >> 11));
+                        atomicAdd(&slo[e0 + j], (uint32_t)(v & 0x7FFu));
+                    }
                 } else {
-                    for (int j = 0; j < dd; j++) atomicAdd(&sacc[(size_t)bj[q] * dd + j], to_fix(__ldg(&xr[j])));
+                    for (int j = 0; j < dd; j++) {
+                        const unsigned long long v = to_fix(__ldg(&xr[j]));
+                        atomicAdd(&shi[e0 + j], (uint32_t)(v >> 11));
+                        atomicAdd(&slo[e0 + j], (uint32_t)(v & 0x7FFu));
+                    }
                 }
             } else {
                 atomicAdd(&count[c0 + bj[q]], 1);
@@ -269,7 +285,7 @@ k_lloyd_assign(const float *__restrict__ pts, SegTable t, int d, const float *__
     if (kSmemAcc) {
         __syncthreads();
         for (int e = threadIdx.x; e < k * dd; e += kThreads) {
-            unsigned long long v = sacc[e];
+            const unsigned long long v = ((unsigned long long)shi[e] << 11) + slo[e];
             if (v) atomicAdd(&acc[c0 * dd + e], v);
         }
         for (int j = threadIdx.x; j < k; j += kThreads) {
