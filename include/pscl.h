@@ -186,6 +186,30 @@ int pscl_get_kernel_times(pscl_job *job, int64_t *launches, float *ms);
  * [2] local Lloyd (incl. init), [3] final Lloyd, [4] SSE pass. */
 int pscl_get_phase_ms(pscl_job *job, float *ms5);
 
+/* Nearest center and sum of squared errors of n points, allocating nothing.
+ *
+ * The paper has no counterpart: this is a service for callers that cannot allocate
+ * device memory (a framework whose allocator owns the device, a real-time host that
+ * forbids allocation after start-up, code where an allocation would synchronise).  It
+ * runs the kernel of the SSE step of pscl_cluster: labels[i] = the nearest of the k
+ * centers to points[i] (float32 squared distance, lowest index on ties) and *sse = the
+ * sum over points of that distance, added in double in a fixed order.
+ *   points   n x d float32 row-major, device memory of the current device
+ *   centers  k x d float32 row-major, device memory
+ *   labels   n int32, device memory (written)
+ *   sse      one double, device memory (written)
+ *   stream   cudaStream_t to run on, or NULL for the default stream
+ * Limits: 1 <= n <= 2^31-1, 1 <= d <= 1024, 1 <= k <= 4096; PSCL_EINVAL beyond.
+ * Scratch: a fixed array of 4096 float64 partial sums plus a counter (33 KB) that every
+ * device loading the library holds until exit.  Every call on a device shares it and it
+ * keeps the last call's contents (the counter is cleared at the start of each call), so
+ * calls whose work overlaps on the GPU race: order them on one stream or synchronise.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Nothing is allocated or freed.
+ * Errors: PSCL_EINVAL, PSCL_ECUDA (see pscl_last_error()). */
+int pscl_assign_sse_noalloc(const float *points, int64_t n, int32_t d, const float *centers,
+                            int32_t k, int32_t *labels, double *sse, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

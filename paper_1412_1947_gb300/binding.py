@@ -45,6 +45,7 @@ SIGNATURES = {
     "pscl_get_label_trace": (_I, [_P, _I, _P]),
     "pscl_get_phase_ms": (_I, [_P, _P]),
     "pscl_get_kernel_times": (_I, [_P, _P, _P]),
+    "pscl_assign_sse_noalloc": (_I, [_P, _I64, _I32, _P, _I32, _P, _P, _P]),
 }
 KERNELS = ["scale_minmax", "scale_apply", "peel", "gather", "lloyd_init", "lloyd_assign", "lloyd_finalize",
            "final_sse"]
@@ -210,6 +211,15 @@ def pscl_get_kernel_times(job):
     ms = np.empty(len(KERNELS), np.float32)
     _chk(lib().pscl_get_kernel_times(job, _ptr(n), _ptr(ms)))
     return {k: (int(n[i]), float(ms[i])) for i, k in enumerate(KERNELS)}
+
+
+def pscl_assign_sse_noalloc(points, centers, labels, sse, stream=None):
+    """points (n x d float32), centers (k x d float32), labels (n int32) and sse (1 double)
+    are CUDA tensors of the current device; nothing is allocated by the library."""
+    n, d = points.shape
+    k = centers.shape[0]
+    _chk(lib().pscl_assign_sse_noalloc(points.data_ptr(), n, d, centers.data_ptr(), k,
+                                       labels.data_ptr(), sse.data_ptr(), stream))
 
 
 # ---------------------------------------------------------------- convenience

@@ -28,6 +28,8 @@ static int fail(int code, const char *fmt, ...)
     return code;
 }
 
+void pscl::set_last_error(const char *msg) { g_err = msg; }
+
 #define CU(call)                                                                            \
     do {                                                                                    \
         cudaError_t e_ = (call);                                                            \

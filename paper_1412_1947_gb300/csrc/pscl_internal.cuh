@@ -127,4 +127,7 @@ cudaError_t launch_final_sse(const float *x, int64_t n, int d, const float *cent
                              int sm_count, cudaStream_t st, KTimer *kt);
 int sse_grid(int64_t n, int sm_count);
 
+// api.cu: the message pscl_last_error() returns for the calling thread.
+void set_last_error(const char *msg);
+
 }  // namespace pscl
