@@ -182,13 +182,14 @@ def main_arm(args, w: synth.Workload):
     raw = wr.points()
     evals = workload_evals(wr)
     seed = 12345
+    prec = B.PRECISIONS[args.prec]
     x_dev = torch.from_numpy(raw).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     ctx = B.pscl_ctx_create(local, 0, stream.cuda_stream)
     job = B.Job(x_dev, ctx=ctx)
     job.option(B.PSCL_OPT_GRAPH)
-    run = lambda: job.run(wr.N, wr.local_k, wr.final_k, wr.iters, seed)  # noqa: E731
+    run = lambda: job.run(wr.N, wr.local_k, wr.final_k, wr.iters, seed, prec)  # noqa: E731
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -228,7 +229,7 @@ def main_arm(args, w: synth.Workload):
     job_e.option(B.PSCL_OPT_GRAPH)
     for _ in range(max(1, args.warmup)):
         job_e.load(host)
-        job_e.run(wr.N, wr.local_k, wr.final_k, wr.iters, seed)
+        job_e.run(wr.N, wr.local_k, wr.final_k, wr.iters, seed, prec)
         job_e.result(labels=False)
     e2e_s = []
     for _ in range(args.steps):
@@ -236,7 +237,7 @@ def main_arm(args, w: synth.Workload):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         job_e.load(host)
-        job_e.run(wr.N, wr.local_k, wr.final_k, wr.iters, seed)
+        job_e.run(wr.N, wr.local_k, wr.final_k, wr.iters, seed, prec)
         c, _, sse_e = job_e.result(labels=False)
         e2e_s.append(time.perf_counter() - t0)
     e2e_mean = statistics.mean(e2e_s)
@@ -253,8 +254,9 @@ def main_arm(args, w: synth.Workload):
     kt = None
     for _ in range(2):
         flush.zero_()
-        job_k.steps(wr.N, wr.local_k, wr.final_k, wr.iters, seed)
+        job_k.steps(wr.N, wr.local_k, wr.final_k, wr.iters, seed, prec)
         kt = job_k.kernel_times()
+    rechecked, assigned = job_k.recheck_stats()
     phases = job_k.phase_ms()
     job_k.close()
 
@@ -303,7 +305,8 @@ def main_arm(args, w: synth.Workload):
     value = evals * world / (mean_ms * 1e-3)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else args.prec + "+f32", "data": "synthetic",
+            "near_ties": {"rechecked_rows": rechecked, "tensor_core_rows": assigned},
             "config": config_of(wr, {"parallelism": f"replicas{world}" if world > 1 else "single"}),
             "latency_ms": {"p50": statistics.median(step_ms),
                            "p99": sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]},
@@ -336,6 +339,8 @@ def main():
     ap.add_argument("--oracle-n", type=int, default=1 << 17)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16", "tf32x3", "bf16x3"],
+                    help="arithmetic of the Lloyd assignment (tf32/bf16: tensor cores + float32 near-tie recheck)")
     args = ap.parse_args()
     w = {"small": synth.SMALL, "medium": synth.MEDIUM, "large": synth.LARGE}[args.workload]
     if args.impl == "reference":

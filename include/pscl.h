@@ -55,9 +55,20 @@ typedef enum { PSCL_F32 = 0, PSCL_BF16 = 1 } pscl_dtype;
  *  PSCL_PREC_TF32, PSCL_PREC_BF16: the -2 x.c part on the tensor cores with TF32 or
  *      BF16 inputs and float32 accumulation, every point whose best two centers are
  *      closer than the contraction's error bound re-decided by the float32 direct sum.
- *  Every mode yields the same partition into subclusters; the update step is the same
- *  exact fixed-point mean in all modes. */
-typedef enum { PSCL_PREC_FP32 = 0, PSCL_PREC_TF32 = 1, PSCL_PREC_BF16 = 2 } pscl_prec;
+ *  PSCL_PREC_TF32X3, PSCL_PREC_BF16X3: the same with every operand split into a high
+ *      and a low TF32 / BF16 part and the three leading products summed in one
+ *      contraction (far fewer near ties to re-decide).
+ *  The contraction covers d in {4, 8, 16, 32, 64} and at most 256 centers per point set;
+ *  other shapes use the float32 direct sum.  The near-tie bound is rigorous, so every
+ *  mode assigns exactly as PSCL_PREC_FP32 does.  Every mode yields the same partition
+ *  into subclusters; the update step is the same exact fixed-point mean in all modes. */
+typedef enum {
+    PSCL_PREC_FP32 = 0,
+    PSCL_PREC_TF32 = 1,
+    PSCL_PREC_BF16 = 2,
+    PSCL_PREC_TF32X3 = 3,
+    PSCL_PREC_BF16X3 = 4
+} pscl_prec;
 
 /* Job options (pscl_job_set_option). */
 typedef enum {
@@ -182,6 +193,10 @@ int pscl_get_label_trace(pscl_job *job, int stage, int32_t *out);
  * PSCL_OPT_KERNEL_TIMING was on for it, their summed device time in milliseconds (else
  * 0).  Either pointer may be NULL. */
 int pscl_get_kernel_times(pscl_job *job, int64_t *launches, float *ms);
+/* Near-tie statistics of the last run's tensor-core assignments (PSCL_PREC_TF32/BF16):
+ * *rechecked rows re-decided by the float32 direct distance out of *assigned rows
+ * (both 0 under PSCL_PREC_FP32).  Either pointer may be NULL. */
+int pscl_get_recheck_stats(pscl_job *job, int64_t *rechecked, int64_t *assigned);
 /* Device time of the phases of the last run in milliseconds: [0] scale, [1] peel,
  * [2] local Lloyd (incl. init), [3] final Lloyd, [4] SSE pass. */
 int pscl_get_phase_ms(pscl_job *job, float *ms5);

@@ -17,7 +17,9 @@ LIB_PATH = os.path.join(_PKG, "libpscl.so")
 
 PSCL_OK, PSCL_EINVAL, PSCL_ESTATE, PSCL_ENOMEM, PSCL_EBUSY, PSCL_ETIMEOUT, PSCL_ECUDA = range(7)
 PSCL_F32, PSCL_BF16 = 0, 1
-PSCL_PREC_FP32, PSCL_PREC_TF32, PSCL_PREC_BF16 = 0, 1, 2
+PSCL_PREC_FP32, PSCL_PREC_TF32, PSCL_PREC_BF16, PSCL_PREC_TF32X3, PSCL_PREC_BF16X3 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp32": PSCL_PREC_FP32, "tf32": PSCL_PREC_TF32, "bf16": PSCL_PREC_BF16,
+              "tf32x3": PSCL_PREC_TF32X3, "bf16x3": PSCL_PREC_BF16X3}
 PSCL_OPT_PLAIN_LLOYD, PSCL_OPT_TRACE_LABELS, PSCL_OPT_INIT_FIRST_K, PSCL_OPT_GRAPH = 1, 2, 3, 4
 PSCL_OPT_KERNEL_TIMING = 5
 
@@ -45,6 +47,7 @@ SIGNATURES = {
     "pscl_get_label_trace": (_I, [_P, _I, _P]),
     "pscl_get_phase_ms": (_I, [_P, _P]),
     "pscl_get_kernel_times": (_I, [_P, _P, _P]),
+    "pscl_get_recheck_stats": (_I, [_P, _P, _P]),
     "pscl_assign_sse_noalloc": (_I, [_P, _I64, _I32, _P, _I32, _P, _P, _P]),
 }
 KERNELS = ["scale_minmax", "scale_apply", "peel", "gather", "lloyd_init", "lloyd_assign", "lloyd_finalize",
@@ -205,6 +208,12 @@ def pscl_get_phase_ms(job):
     return ms
 
 
+def pscl_get_recheck_stats(job):
+    a, b = C.c_int64(), C.c_int64()
+    _chk(lib().pscl_get_recheck_stats(job, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
 def pscl_get_kernel_times(job):
     """{kernel name: (launches, total ms)} of the last run."""
     n = np.empty(len(KERNELS), np.int64)
@@ -274,6 +283,9 @@ class Job:
 
     def kernel_times(self):
         return pscl_get_kernel_times(self.h)
+
+    def recheck_stats(self):
+        return pscl_get_recheck_stats(self.h)
 
     def close(self):
         if self.h is not None:

@@ -33,9 +33,11 @@ void pscl::set_last_error(const char *msg) { g_err = msg; }
 #define CU(call)                                                                            \
     do {                                                                                    \
         cudaError_t e_ = (call);                                                            \
-        if (e_ != cudaSuccess)                                                              \
+        if (e_ != cudaSuccess) {                                                            \
+            cudaGetLastError(); /* clear a non-sticky error so later calls start clean */   \
             return fail(PSCL_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
                         __FILE__, __LINE__);                                                \
+        }                                                                                   \
     } while (0)
 
 // ------------------------------------------------------------------ objects
@@ -393,9 +395,8 @@ static int build_lloyd_plan(pscl_job *j, LloydPlan &p, const std::vector<int64_t
 
 static int check_prec(int prec)
 {
-    if (prec != PSCL_PREC_FP32 && prec != PSCL_PREC_TF32 && prec != PSCL_PREC_BF16)
+    if (prec < PSCL_PREC_FP32 || prec > PSCL_PREC_BF16X3)
         return fail(PSCL_EINVAL, "unknown precision %d", prec);
-    if (prec != PSCL_PREC_FP32) return fail(PSCL_EINVAL, "precision %d is not available in this build", prec);
     return PSCL_OK;
 }
 
@@ -519,7 +520,7 @@ static int plan_cluster(pscl_job *j, int32_t final_k, int32_t iters, uint64_t se
 // ------------------------------------------------------------------ enqueue (launches only)
 static int run_lloyd(pscl_job *j, const LloydPlan &p, const float *pts, float *centers,
                      unsigned long long *acc, int32_t *cnt2, int32_t *labels, int32_t *trace,
-                     int iters, uint64_t seed, uint32_t stage, bool plain)
+                     int iters, uint64_t seed, uint32_t stage, bool plain, int prec)
 {
     cudaStream_t st = j->ctx->stream;
     const SegTable t = p.table();
@@ -536,7 +537,7 @@ static int run_lloyd(pscl_job *j, const LloydPlan &p, const float *pts, float *c
         for (int it = 0; it < iters; it++) {
             b.count = cnt2 + (size_t)(it & 1) * p.P;
             CU(launch_lloyd_iter(b, cnt2 + (size_t)((it + 1) & 1) * p.P, t, j->d, it, 0, p.n_units, 0, p.P,
-                                 p.kmax, j->ctx->sm_count, st, &j->kt));
+                                 p.kmax, prec, j->flags, j->ctx->sm_count, st, &j->kt));
         }
     } else {
         for (int s = 0; s < p.n_seg; s++) {
@@ -544,7 +545,7 @@ static int run_lloyd(pscl_job *j, const LloydPlan &p, const float *pts, float *c
                 b.count = cnt2 + (size_t)(it & 1) * p.P;
                 CU(launch_lloyd_iter(b, cnt2 + (size_t)((it + 1) & 1) * p.P, t, j->d, it, p.seg_unit0[s],
                                      p.seg_unit0[s + 1], p.cen_off[s], (int64_t)p.cen_off[s] + p.k_eff[s],
-                                     p.k_eff[s], j->ctx->sm_count, st, &j->kt));
+                                     p.k_eff[s], prec, j->flags, j->ctx->sm_count, st, &j->kt));
             }
         }
     }
@@ -555,6 +556,7 @@ static int enqueue_scale(pscl_job *j, bool events)
 {
     cudaStream_t st = j->ctx->stream;
     if (events) CU(cudaEventRecord(j->ev[0], st));
+    CU(cudaMemsetAsync(j->flags, 0, kFlagWords * sizeof(uint32_t), st));   // errors and counters of this run
     CU(launch_scale(j->dev_in, j->x, j->n, j->d, j->part, j->tickets, j->mn, j->mx, j->flags,
                     j->ctx->sm_count, st, &j->kt));
     if (events) CU(cudaEventRecord(j->ev[1], st));
@@ -567,7 +569,7 @@ static int enqueue_subcluster(pscl_job *j, bool events)
     CU(launch_peel(j->pb, j->n, j->d, j->N, j->ctx->sm_count, st, &j->kt));
     if (events) CU(cudaEventRecord(j->ev[2], st));
     TRY(run_lloyd(j, j->lp, j->pb.xseg, j->cl, j->acc_l, j->cnt_l, j->lab_l, j->trace_l, j->iters, j->seed, 0u,
-                  j->plain != 0));
+                  j->plain != 0, j->prec));
     if (events) CU(cudaEventRecord(j->ev[3], st));
     return PSCL_OK;
 }
@@ -576,7 +578,7 @@ static int enqueue_cluster(pscl_job *j, bool events)
 {
     cudaStream_t st = j->ctx->stream;
     TRY(run_lloyd(j, j->fp, j->cl, j->cf, j->acc_f, j->cnt_f, j->lab_f, j->trace_f, j->fiters, j->fseed, 1u,
-                  false));
+                  false, j->fprec));
     if (events) CU(cudaEventRecord(j->ev[4], st));
     CU(launch_final_sse(j->x, j->n, j->d, j->cf, j->final_k, j->labels, j->blk_sse, j->sse, j->tickets + 1,
                         j->ctx->sm_count, st, &j->kt));
@@ -697,6 +699,7 @@ extern "C" int pscl_job_sync(pscl_job *j)
     CU(cudaMemcpy(h, j->flags, sizeof h, cudaMemcpyDeviceToHost));
     if (h[0]) return fail(PSCL_EINVAL, "the input holds a value that is not finite");
     if (h[1] & 2u) return fail(PSCL_ETIMEOUT, "a bounded device-side wait gave up (peel barrier)");
+    if (h[1] & 4u) return fail(PSCL_ETIMEOUT, "a bounded device-side wait gave up (tensor-core commit)");
     if (h[1] & 1u) return fail(PSCL_ECUDA, "internal error: the peel's float32 filter bound was contradicted");
     return PSCL_OK;
 }
@@ -790,6 +793,16 @@ extern "C" int pscl_get_kernel_times(pscl_job *j, int64_t *launches, float *ms)
             ms[j->kt.tag[e]] += t;
         }
     }
+    return PSCL_OK;
+}
+
+extern "C" int pscl_get_recheck_stats(pscl_job *j, int64_t *rechecked, int64_t *assigned)
+{
+    TRY(pscl_job_sync(j));
+    uint32_t h[kFlagWords];
+    CU(cudaMemcpy(h, j->flags, sizeof h, cudaMemcpyDeviceToHost));
+    if (rechecked) *rechecked = h[2];
+    if (assigned) *assigned = h[3];
     return PSCL_OK;
 }
 

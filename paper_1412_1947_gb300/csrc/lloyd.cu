@@ -477,10 +477,13 @@ cudaError_t launch_lloyd_init(const LloydBuffers &b, const SegTable &t, int d, i
 // b.count must point at this iteration's count buffer; count_next at the other one.
 cudaError_t launch_lloyd_iter(const LloydBuffers &b, int32_t *count_next, const SegTable &t, int d,
                               int iter, int unit_lo, int unit_hi, int64_t cen_lo, int64_t cen_hi,
-                              int kmax, int sm_count, cudaStream_t st, KTimer *kt)
+                              int kmax, int prec, uint32_t *flags, int sm_count, cudaStream_t st,
+                              KTimer *kt)
 {
     cudaError_t e;
-    switch (d) {
+    if (prec != PSCL_PREC_FP32 && tc_supported(d, kmax, prec)) {
+        e = launch_lloyd_assign_tc(b, t, d, iter, unit_lo, unit_hi, kmax, prec, flags, st, kt);
+    } else switch (d) {
     case 2: e = assign_dispatch<2>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt); break;
     case 4: e = assign_dispatch<4>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt); break;
     case 8: e = assign_dispatch<8>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt); break;

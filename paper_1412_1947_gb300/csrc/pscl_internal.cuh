@@ -35,7 +35,10 @@ struct PeelCtl {
 // Job flags read by the host at every synchronisation.
 //   [0] != 0: an input value is not finite
 //   [1] bit 0: the peel's float32 bound was contradicted (internal error)
-//       bit 1: a bounded device-side wait gave up
+//       bit 1: a bounded device-side wait gave up (peel barrier)
+//       bit 2: a bounded device-side wait gave up (tensor-core commit)
+//   [2] rows the tensor-core assignment re-scored in float32 (near ties)
+//   [3] rows the tensor-core assignment assigned
 constexpr int kFlagWords = 4;
 
 // Segment table of one batched Lloyd launch (device arrays).
@@ -118,10 +121,17 @@ struct LloydBuffers {
 cudaError_t launch_lloyd_init(const LloydBuffers &b, const SegTable &t, int d, int64_t P,
                               uint64_t seed, uint32_t stage, int first_k, int kmax,
                               cudaStream_t st, KTimer *kt);
+// prec: a pscl_prec; TF32/BF16 use the tensor-core assignment where tc_supported().
 cudaError_t launch_lloyd_iter(const LloydBuffers &b, int32_t *count_next, const SegTable &t,
                               int d, int iter, int unit_lo, int unit_hi, int64_t cen_lo,
-                              int64_t cen_hi, int kmax, int sm_count, cudaStream_t st,
-                              KTimer *kt);
+                              int64_t cen_hi, int kmax, int prec, uint32_t *flags, int sm_count,
+                              cudaStream_t st, KTimer *kt);
+
+// lloyd_tc.cu
+bool tc_supported(int d, int kmax, int prec);
+cudaError_t launch_lloyd_assign_tc(const LloydBuffers &b, const SegTable &t, int d, int iter,
+                                   int unit_lo, int unit_hi, int kmax, int prec, uint32_t *flags,
+                                   cudaStream_t st, KTimer *kt);
 cudaError_t launch_final_sse(const float *x, int64_t n, int d, const float *centers, int k,
                              int32_t *labels, double *blk_sse, double *sse, uint32_t *ticket,
                              int sm_count, cudaStream_t st, KTimer *kt);

@@ -36,6 +36,8 @@ class GpuRun:
     sse: float
     trace_local: np.ndarray | None
     trace_final: np.ndarray | None
+    rechecked: int = 0
+    assigned: int = 0
 
 
 def run_gpu(raw, N, local_k, final_k, iters, seed, *, trace=True, plain=False, first_k=False,
@@ -63,7 +65,8 @@ def run_gpu(raw, N, local_k, final_k, iters, seed, *, trace=True, plain=False, f
         fc, lab, sse = j.result()
         tl = j.trace(0, iters) if trace and iters else None
         tf = j.trace(1, iters) if trace and iters else None
-        return GpuRun(j.scaled(), perm, seg_off, lc, ke, cnt, fc, lab, sse, tl, tf)
+        rc, asg = j.recheck_stats()
+        return GpuRun(j.scaled(), perm, seg_off, lc, ke, cnt, fc, lab, sse, tl, tf, rc, asg)
 
 
 def run_oracle(raw, N, local_k, final_k, iters, seed, gpu: GpuRun | None = None, first_k=False):
