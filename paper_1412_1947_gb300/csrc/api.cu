@@ -411,10 +411,13 @@ static int plan_subcluster(pscl_job *j, int64_t N, int32_t local_k, int32_t iter
     if (!j->peel_alloc) {
         PeelBuffers &b = j->pb;
         b.x = j->x;
-        TRY(A(j, &b.idx[0], n));
-        TRY(A(j, &b.idx[1], n));
+        b.ord_ld = (n + 3) & ~(int64_t)3;
+        b.nbuckets = peel_buckets(n);
         TRY(A(j, &b.key, n));
-        TRY(A(j, &b.status, n + 16));
+        TRY(A(j, &b.ord, (size_t)d * b.ord_ld));
+        TRY(A(j, &b.bcnt, (size_t)d * b.nbuckets));
+        TRY(A(j, &b.bcs, (size_t)d * b.nbuckets));
+        TRY(A(j, &b.lidx, 2 * (size_t)n));
         TRY(A(j, &b.band_key, n));
         TRY(A(j, &b.band_pos, n));
         TRY(A(j, &b.band_k32, n));

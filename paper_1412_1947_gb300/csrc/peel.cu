@@ -11,21 +11,31 @@
 //   A. delta32_i by a float32 FMA chain, kept as its bit pattern (order-preserving for
 //      non-negative floats), and a 2048-bin histogram of key bits 31..21;
 //   B. the bin holding the N-th smallest key, and a 2048-bin histogram of bits 20..10 of
-//      the keys inside it: the N-th smallest key lies in a 22-bit prefix [A, B];
+//      the keys inside it: the N-th smallest key lies in a 22-bit prefix [A, B].  The bin
+//      is nearly always the previous round's, whose second histogram phase A already
+//      built, and then this pass is skipped;
 //   C. |delta32 - delta64| <= eps*delta32 + ea with eps = (d+4)*2^-23, ea = 2^-120, so
 //      the N-th smallest delta64 lies in [A(1-eps)-ea, B(1+eps)+ea]: a point whose upper
 //      bound is below that interval is certainly taken, one whose lower bound is above
-//      it certainly not; the few in between (the band) get delta64 exactly as defined;
-//   D. the (N - #certain) smallest band points by (delta64, position) are taken; taken
-//      points go to subcluster r in ascending index, the rest stay in ascending index
-//      (stable compaction of indices), and the per-attribute minimum of the points that
-//      stay is the next landmark.
+//      it certainly not; the few in between form the band;
+//   D. the (N - #certain) smallest band points by (delta64, index) are taken, settled in
+//      float32, then compensated float32, then float64 for what each step leaves open;
+//      taken points go to subcluster r in ascending index and are marked removed.
 // The partition is therefore exactly the float64 definition's, whatever float32 does.
 //
-// All rounds run in one persistent cooperative launch: every CTA owns a contiguous slice
-// of the remaining points in each round and the phases are separated by grid barriers
-// (four per round).  Every barrier wait is bounded; a CTA that gives up sets the abort
-// flag, every other CTA then leaves at its next wait, and the host sees PSCL_ETIMEOUT.
+// Points never move: CTA c owns the index slice [c n/G, (c+1) n/G) in every round and keeps
+// the ids of its points left in a list, in ascending order; a removed point gets the key
+// 0xFFFFFFFF.  The next landmark needs no pass over the rows.  Before round 0 a counting
+// sort lists, per attribute, the point ids by value bucket (buckets are monotone in the
+// value) with a live count per bucket that every removal decrements.  The minimum over the
+// points left is the smallest value left in the first bucket that still has a point, and
+// the buckets in front of it never get one back, so one bucket pointer per attribute only
+// moves forward.
+//
+// All rounds run in one persistent cooperative launch, the phases separated by grid
+// barriers (three per round).  Every barrier wait is bounded; a CTA that gives up sets the
+// abort flag, every other CTA then leaves at its next wait, and the host sees
+// PSCL_ETIMEOUT.
 #include <algorithm>
 
 #include "pscl_internal.cuh"
@@ -35,11 +45,14 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr uint32_t kInfBits = 0x7f800000u;
-constexpr int kBandSmem = 1024;               // band entries settled in shared memory
+constexpr uint32_t kGone = 0xFFFFFFFFu;       // key of a point removed in an earlier round
+constexpr uint32_t kTaken = 0xFFFFFFFEu;      // key of a wide-band point taken this round
 constexpr int kBandBins = 4096;               // one-ulp bins over a band's float32 keys
 constexpr int kTight = 256;                   // band entries near the cut-off, decided exactly
-constexpr int kPeelDynWords = 2 * kHistBins > kBandBins + 7 * kTight
-                                  ? 2 * kHistBins : kBandBins + 7 * kTight;
+constexpr int kKeyCache = 4096;               // keys of a slice kept in shared memory, if it fits
+constexpr int kPeelScratch = 2 * kHistBins > kBandBins + 7 * kTight ? 2 * kHistBins : kBandBins + 7 * kTight;
+constexpr int kPeelDynWords = kPeelScratch + kKeyCache;
+constexpr int kQT = 8;                        // tiles of kThreads items per compaction scan
 constexpr unsigned kSpinLimit = 1u << 25;      // ~1-2 s of polling per barrier at most
 
 // ------------------------------------------------------------------ block helpers
@@ -292,17 +305,256 @@ __device__ void select_band_global(const uint64_t *bkey, const uint32_t *bpos, u
     __syncthreads();
 }
 
+// Exclusive scans of two values over the block in one pass (blockDim.x == kThreads).
+__device__ void block_excl_scan2(uint32_t v0, uint32_t v1, uint32_t &e0, uint32_t &e1, uint32_t &t0,
+                                 uint32_t &t1)
+{
+    constexpr int W = kThreads / 32;
+    __shared__ uint32_t ws0[W], ws1[W], wt[2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t i0 = warp_incl_scan(v0), i1 = warp_incl_scan(v1);
+    if (lane == 31) {
+        ws0[w] = i0;
+        ws1[w] = i1;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t a = lane < W ? ws0[lane] : 0u, b = lane < W ? ws1[lane] : 0u;
+        const uint32_t ia = warp_incl_scan(a), ib = warp_incl_scan(b);
+        if (lane < W) {
+            ws0[lane] = ia - a;
+            ws1[lane] = ib - b;
+        }
+        if (lane == W - 1) {
+            wt[0] = ia;
+            wt[1] = ib;
+        }
+    }
+    __syncthreads();
+    e0 = ws0[w] + i0 - v0;
+    e1 = ws1[w] + i1 - v1;
+    t0 = wt[0];
+    t1 = wt[1];
+    __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t warp_min(uint32_t v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// The bin of rank `target` (0-based) of histogram h0 and the rank inside it; when hg (the
+// second-digit histogram inside bin `guess`) is given and `guess` is that bin, also the
+// bin of that rank in hg (hit).  Both histograms are read and scanned in one pass.
+__device__ void find_bins(const uint32_t *h0, const uint32_t *hg, uint32_t guess, uint32_t target,
+                          uint32_t &b0, uint32_t &r0, uint32_t &b1, uint32_t &r1, bool &hit)
+{
+    __shared__ uint32_t sb0, sr0, sb1, sr1;
+    constexpr int per = kHistBins / kThreads;       // 8 bins per thread
+    static_assert(per == 8, "two uint4 loads per thread");
+    const int t = threadIdx.x;
+    uint32_t l0[per], l1[per];
+    {
+        const uint4 *p = reinterpret_cast<const uint4 *>(h0 + t * per);
+        const uint4 u = __ldcg(p), v = __ldcg(p + 1);
+        l0[0] = u.x; l0[1] = u.y; l0[2] = u.z; l0[3] = u.w;
+        l0[4] = v.x; l0[5] = v.y; l0[6] = v.z; l0[7] = v.w;
+    }
+    if (hg) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(hg + t * per);
+        const uint4 u = __ldcg(p), v = __ldcg(p + 1);
+        l1[0] = u.x; l1[1] = u.y; l1[2] = u.z; l1[3] = u.w;
+        l1[4] = v.x; l1[5] = v.y; l1[6] = v.z; l1[7] = v.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < per; q++) l1[q] = 0;
+    }
+    uint32_t s0 = 0, s1 = 0;
+#pragma unroll
+    for (int q = 0; q < per; q++) {
+        s0 += l0[q];
+        s1 += l1[q];
+    }
+    uint32_t e0, e1, tot0, tot1;
+    block_excl_scan2(s0, s1, e0, e1, tot0, tot1);
+    if (target >= e0 && target < e0 + s0) {
+        uint32_t cc = e0;
+#pragma unroll
+        for (int q = 0; q < per; q++) {
+            if (target >= cc && target < cc + l0[q]) {
+                sb0 = (uint32_t)(t * per + q);
+                sr0 = target - cc;
+            }
+            cc += l0[q];
+        }
+    }
+    __syncthreads();
+    b0 = sb0;
+    r0 = sr0;
+    hit = hg != nullptr && b0 == guess;
+    if (hit) {
+        if (r0 >= e1 && r0 < e1 + s1) {
+            uint32_t cc = e1;
+#pragma unroll
+            for (int q = 0; q < per; q++) {
+                if (r0 >= cc && r0 < cc + l1[q]) {
+                    sb1 = (uint32_t)(t * per + q);
+                    sr1 = r0 - cc;
+                }
+                cc += l1[q];
+            }
+        }
+        __syncthreads();
+        b1 = sb1;
+        r1 = sr1;
+    }
+    __syncthreads();
+}
+
+// Splits the n_in ids of a CTA's list (in[q], or first + q when `in` is NULL), keeping their
+// order, into those with pred(position, id), written to sel[0..) with on_sel(id) called for
+// each, and
+// the rest, written to keep[0..) when `keep` is given.  Returns how many were selected (to every
+// thread).
+template <class Pred, class OnSel>
+__device__ uint32_t compact_list(const uint32_t *in, uint32_t first, uint32_t n_in, uint32_t *sel, uint32_t *keep,
+                                 Pred pred, OnSel on_sel)
+{
+    constexpr int W = kThreads / 32;
+    constexpr int PER = kQT * W / 32;
+    static_assert(PER * 32 == kQT * W, "one warp scans the tile counts");
+    __shared__ uint32_t woff_s[kQT * W + 1], woff_k[kQT * W + 1];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t done_s = 0, done_k = 0;
+    // item (q, t) of a chunk is preceded by the earlier tiles, the earlier warps of its tile
+    // and the lower lanes of its warp
+    for (uint32_t cb = 0; cb < n_in; cb += kQT * kThreads) {
+        uint32_t ids[kQT], vl = 0, tk = 0;
+#pragma unroll
+        for (int q = 0; q < kQT; q++) {
+            const uint32_t qi = cb + q * kThreads + t;
+            const bool v = qi < n_in;
+            ids[q] = v ? (in ? __ldcg(&in[qi]) : first + qi) : 0u;
+            vl |= (uint32_t)v << q;
+        }
+#pragma unroll
+        for (int q = 0; q < kQT; q++) tk |= (uint32_t)(((vl >> q) & 1u) && pred(cb + q * kThreads + t, ids[q])) << q;
+        uint32_t bt[kQT], bv[kQT];
+#pragma unroll
+        for (int q = 0; q < kQT; q++) {
+            bt[q] = __ballot_sync(0xffffffffu, (tk >> q) & 1u);
+            bv[q] = __ballot_sync(0xffffffffu, (vl >> q) & 1u);
+            if (lane == 0) {
+                woff_s[q * W + w] = __popc(bt[q]);
+                woff_k[q * W + w] = __popc(bv[q] & ~bt[q]);
+            }
+        }
+        __syncthreads();
+        if (w == 0) {
+            uint32_t vs[PER], vk[PER], ss = 0, sk = 0;
+#pragma unroll
+            for (int e = 0; e < PER; e++) {
+                vs[e] = woff_s[lane * PER + e];
+                vk[e] = woff_k[lane * PER + e];
+                ss += vs[e];
+                sk += vk[e];
+            }
+            const uint32_t is = warp_incl_scan(ss), ik = warp_incl_scan(sk);
+            uint32_t es = is - ss, ek = ik - sk;
+#pragma unroll
+            for (int e = 0; e < PER; e++) {
+                woff_s[lane * PER + e] = es;
+                woff_k[lane * PER + e] = ek;
+                es += vs[e];
+                ek += vk[e];
+            }
+            if (lane == 31) {
+                woff_s[kQT * W] = is;
+                woff_k[kQT * W] = ik;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kQT; q++) {
+            if ((tk >> q) & 1u) {
+                sel[done_s + woff_s[q * W + w] + __popc(bt[q] & lt)] = ids[q];
+                on_sel(ids[q]);
+            } else if (((vl >> q) & 1u) && keep) {
+                keep[done_k + woff_k[q * W + w] + __popc(bv[q] & ~bt[q] & lt)] = ids[q];
+            }
+        }
+        done_s += woff_s[kQT * W];
+        done_k += woff_k[kQT * W];
+        __syncthreads();
+    }
+    return done_s;
+}
+
+// Bucket of a scaled value (in [0, 1]) among nb equal buckets: monotone in the value.
+__device__ __forceinline__ uint32_t bucket_of(float v, uint32_t nb)
+{
+    v = fminf(fmaxf(v, 0.0f), 1.0f);
+    const uint32_t b = __float2uint_rz(v * (float)nb);
+    return b < nb ? b : nb - 1u;
+}
+
+// The round's selection: a point with key k is taken if k < lo, if it is a wide-band point
+// marked kTaken, or if lo <= k <= tout and the tight set lists it as taken.
+struct Rule {
+    uint32_t lo, tout, nt;
+    const uint32_t *tpos, *tcls;
+};
+
+__device__ __forceinline__ bool taken(const Rule &R, uint32_t k, uint32_t id)
+{
+    if (k < R.lo || k == kTaken) return true;
+    if (k > R.tout) return false;
+    for (uint32_t o = 0; o < R.nt; o++)
+        if (R.tpos[o] == id) return R.tcls[o] != 0;
+    return false;
+}
+
+// A removed point leaves the live count of its bucket in every attribute.
+template <int D>
+__device__ __forceinline__ void drop_buckets(const float *__restrict__ x, int d, uint32_t id, uint4 *bcs, uint32_t nbk)
+{
+    const float *row = x + (size_t)id * d;
+    if (D > 0 && D % 4 == 0) {
+        float v[D > 0 ? D : 1];
+        const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+        for (int q = 0; q < D / 4; q++) {
+            const float4 u = __ldg(&r4[q]);
+            v[4 * q + 0] = u.x;
+            v[4 * q + 1] = u.y;
+            v[4 * q + 2] = u.z;
+            v[4 * q + 3] = u.w;
+        }
+#pragma unroll
+        for (int j = 0; j < D; j++) atomicSub(&bcs[(size_t)j * nbk + bucket_of(v[j], nbk)].x, 1u);
+    } else {
+        for (int j = 0; j < d; j++) atomicSub(&bcs[(size_t)j * nbk + bucket_of(__ldg(&row[j]), nbk)].x, 1u);
+    }
+}
+
 // ------------------------------------------------------------------ the kernel
 struct PeelArgs {
     const float *x;
     int d;
     int64_t n, N, S;
-    uint32_t *idx0, *idx1;       // remaining indices, ping-pong
-    uint32_t *key;
-    uint8_t *status;             // 0 out, 1 taken, 2 band
+    uint32_t *key;               // n: this round's float32 key per point; kGone once removed
+    uint32_t *ord;               // d x ord_ld: point ids by value bucket, per attribute
+    uint32_t *bcnt;              // d x nbk: bucket counts, then cursors (zeroed before)
+    uint4 *bcs;                  // d x nbk: (points left, first entry, end entry, 0)
+    uint32_t *lidx;              // 2 x n: per CTA slice, the ids of its points left
+    int64_t ord_ld;
+    uint32_t nbk;
     uint64_t *band_key;          // float64 distance bits (wide bands only)
     uint32_t *band_k32;          // float32 keys of the band
-    uint32_t *band_pos;
+    uint32_t *band_pos;          // point ids of the band
     uint32_t *perm;
     float *landmarks;            // S x d or NULL
     PeelCtl *ctl;
@@ -319,119 +571,210 @@ __host__ __device__ constexpr int kPeelBatch()
 template <int D>
 __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
 {
-    constexpr int DM = D > 0 && D <= 64 ? D : 1;       // register minima when D is small
     constexpr int B = kPeelBatch<D>();
-    constexpr int QT = 16;                             // tiles of kThreads items per scan
     constexpr int W = kThreads / 32;
-    // dynamic shared memory: [first histogram | guessed second-digit histogram], all of
-    // it reused for the band in phase D
+    // dynamic shared memory: [first histogram | guessed second-digit histogram] in phase A;
+    // in phase D the band's one-ulp bins and, kept to the end of the round, the tight set
     extern __shared__ __align__(16) uint32_t dyn[];
     uint32_t *sh = dyn;
     uint32_t *gh = dyn + kHistBins;
+    uint32_t *hb = dyn;
+    uint32_t *tpos = dyn + kBandBins;
+    uint32_t *tcls = tpos + kTight;                    // 1 taken, 0 not
+    float *th = reinterpret_cast<float *>(tcls + kTight);
+    float *tl = th + kTight;
+    uint32_t *tamb = reinterpret_cast<uint32_t *>(tl + kTight);    // undecided tight entries
+    unsigned long long *td = reinterpret_cast<unsigned long long *>(tamb + kTight);
+    uint32_t *skey = dyn + kPeelScratch;               // keys by list position (kc)
     __shared__ float Ls[D > 0 ? D : kMaxD];
-    __shared__ uint32_t s_in_key, s_out_key, s_nt, s_na, s_v, s_t32;
-    __shared__ float wmin[W][DM];
-    __shared__ uint32_t gmin[D > 0 && D <= 64 ? 1 : kMaxD];
-    __shared__ uint32_t off_t[QT * W], off_u[QT * W], s_tot[2];
+    __shared__ uint32_t s_in_key, s_out_key, s_nt, s_na, s_v, s_t32, s_st, s_en;
+    __shared__ uint32_t red_a[W], red_b[W];
     PeelCtl *ctl = a.ctl;
     const int d = a.d;
+    const uint32_t n = (uint32_t)a.n, N = (uint32_t)a.N, nbk = a.nbk;
     const int t = threadIdx.x;
     const int lane = t & 31, w = t >> 5;
-    const uint32_t lt_mask = (1u << lane) - 1u;
     const unsigned G = gridDim.x, c = blockIdx.x;
+    // With 16 CTAs or more, the last Gl CTAs own no points and only build landmarks, which
+    // then overlaps with the others' compaction; otherwise every CTA does both.
+    const int Gl = G >= 16 ? min(d, (int)(G / 8)) : 0;
+    const unsigned Gs = G - (unsigned)Gl;
+    const uint32_t s0 = c < Gs ? (uint32_t)((uint64_t)c * n / Gs) : n;
+    const uint32_t s1 = c < Gs ? (uint32_t)((uint64_t)(c + 1) * n / Gs) : n;
+    const int lm_first = Gl ? (int)c - (int)Gs : (int)(G - 1 - c);
+    const int lm_step = Gl ? Gl : (int)G;
+    uint32_t n_live = s1 - s0;           // points of the slice left (ids in lidx after round 0)
+    const bool kc = s1 - s0 <= (uint32_t)kKeyCache;   // the round's keys stay in shared memory
     unsigned gen = 0;
-    uint32_t guess = 0xFFFFFFFFu;      // first digit of the previous round's N-th key
 
+    // ---- before round 0: per attribute, the point ids by value bucket (counting sort)
+    {
+        const uint64_t stride = (uint64_t)G * kThreads;
+        const uint32_t si = (uint32_t)(stride / (uint64_t)d), sj = (uint32_t)(stride % (uint64_t)d);
+        const uint64_t e0 = (uint64_t)c * kThreads + t;
+        for (int pass = 0; pass < 2; pass++) {
+            uint32_t i = (uint32_t)(e0 / (uint64_t)d), j = (uint32_t)(e0 % (uint64_t)d);
+            while (i < n) {
+                const float v = __ldg(&a.x[(size_t)i * d + j]);
+                uint32_t *cnt = &a.bcnt[(size_t)j * nbk + bucket_of(v, nbk)];
+                if (pass == 0) atomicAdd(cnt, 1u);
+                else a.ord[(size_t)j * a.ord_ld + atomicAdd(cnt, 1u)] = i;
+                i += si;
+                j += sj;
+                if (j >= (uint32_t)d) {
+                    j -= (uint32_t)d;
+                    i++;
+                }
+            }
+            if (!grid_sync(ctl, a.flags, gen)) return;
+            if (pass == 1) break;
+            // exclusive scan of each attribute's counts in place: they become the cursors
+            for (int jj = (int)c; jj < d; jj += (int)G) {
+                uint32_t *cj = a.bcnt + (size_t)jj * nbk;
+                uint32_t run = 0;
+                for (uint32_t b0 = 0; b0 < nbk; b0 += 16 * kThreads) {
+                    uint4 *p4 = reinterpret_cast<uint4 *>(cj + b0 + 16 * t);
+                    uint32_t v[16];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const uint4 u = __ldcg(p4 + q);
+                        v[4 * q + 0] = u.x;
+                        v[4 * q + 1] = u.y;
+                        v[4 * q + 2] = u.z;
+                        v[4 * q + 3] = u.w;
+                    }
+                    uint32_t s = 0;
+#pragma unroll
+                    for (int q = 0; q < 16; q++) s += v[q];
+                    uint32_t tot;
+                    uint32_t acc = run + block_excl_scan(s, tot);
+                    uint4 *bs = a.bcs + (size_t)jj * nbk + b0 + 16 * t;
+#pragma unroll
+                    for (int q = 0; q < 16; q++) {
+                        const uint32_t cur = v[q];
+                        bs[q] = make_uint4(cur, acc, acc + cur, 0u);
+                        v[q] = acc;
+                        acc += cur;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; q++) p4[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    run += tot;
+                }
+            }
+            if (!grid_sync(ctl, a.flags, gen)) return;
+        }
+    }
+
+    uint32_t guess = kGone;            // first digit of the previous round's N-th key
     for (int64_t r = 0; r < a.S; r++) {
-        const int64_t nr = a.n - r * a.N;
+        const uint32_t nr = (uint32_t)(a.n - r * a.N);
         const int par = (int)(r & 1);
-        const uint32_t *idx_in = r == 0 ? nullptr : (par ? a.idx1 : a.idx0);
-        uint32_t *idx_out = par ? a.idx0 : a.idx1;
         uint32_t *seg_out = a.perm + r * a.N;
-        const uint32_t s0 = (uint32_t)((int64_t)c * nr / G), s1 = (uint32_t)((int64_t)(c + 1) * nr / G);
-        if (nr <= a.N) {                              // the last subcluster: all that is left
-            for (uint32_t i = s0 + t; i < s1; i += kThreads) seg_out[i] = idx_in ? __ldcg(&idx_in[i]) : i;
-            if (c == 0 && a.landmarks)
-                for (int j = t; j < d; j += kThreads)
-                    a.landmarks[r * d + j] = __uint_as_float(__ldcg(&ctl->Lbits[par][j]));
+        if (c == 0 && a.landmarks)
+            for (int j = t; j < d; j += kThreads)
+                a.landmarks[r * d + j] = __uint_as_float(__ldcg(&ctl->Lbits[par][j]));
+        const uint32_t *lin = r == 0 ? nullptr : a.lidx + (size_t)par * n + s0;
+        if (nr <= N) {                                // the last subcluster: all that is left
+            if (t == 0) ctl->cnt_in[c] = n_live;
+            if (!grid_sync(ctl, a.flags, gen)) return;
+            uint32_t before = 0;
+            for (uint32_t q = t; q < c; q += kThreads) before += __ldcg(&ctl->cnt_in[q]);
+            before = block_sum(before);
+            for (uint32_t q = t; q < n_live; q += kThreads) seg_out[before + q] = lin ? __ldcg(&lin[q]) : s0 + q;
             break;
         }
-        uint32_t *hist0 = ctl->hist[par][0], *hist1 = ctl->hist[par][1];
 
-        // ---- A: float32 distances and the first histogram
+        // ---- A: float32 distances of the points left and the first histogram
         for (int j = t; j < d; j += kThreads) Ls[j] = __uint_as_float(__ldcg(&ctl->Lbits[par][j]));
-        const bool have_guess = guess != 0xFFFFFFFFu;
+        const bool have_guess = guess != kGone;
         for (int b = t; b < (have_guess ? 2 : 1) * kHistBins; b += kThreads) dyn[b] = 0;
-        if (c == 0) {
-            for (int j = t; j < d; j += kThreads) {
-                ctl->Lbits[par ^ 1][j] = kInfBits;
-                if (a.landmarks) a.landmarks[r * d + j] = __uint_as_float(__ldcg(&ctl->Lbits[par][j]));
+        if (c == 0 && t == 0) ctl->band_cnt[par ^ 1] = 0;
+        if (Gl > 0 && c >= Gs && r > 0) {
+            // the previous subcluster's points: marked removed, out of their buckets' counts
+            // (this round's landmark needs both, its other CTAs have rows to read)
+            const uint32_t *prev = a.perm + (r - 1) * a.N;
+            for (uint32_t q = (c - Gs) * kThreads + t; q < N; q += (uint32_t)Gl * kThreads) {
+                const uint32_t id = __ldcg(&prev[q]);
+                a.key[id] = kGone;
+                drop_buckets<D>(a.x, d, id, a.bcs, nbk);
             }
-            if (t == 0) ctl->band_cnt[par ^ 1] = 0;
         }
         __syncthreads();
-        for (uint32_t i0 = s0 + t; i0 < s1; i0 += B * kThreads) {
-            uint32_t rows[B];
+        for (uint32_t base = 0; base < n_live; base += B * kThreads) {
+            bool lv[B];
+            uint32_t ids[B];
 #pragma unroll
             for (int q = 0; q < B; q++) {
-                const uint32_t i = i0 + q * kThreads;
-                rows[q] = i < s1 ? (idx_in ? __ldcg(&idx_in[i]) : i) : 0u;
+                const uint32_t qi = base + q * kThreads + t;
+                lv[q] = qi < n_live;
+                ids[q] = lv[q] ? (lin ? __ldcg(&lin[qi]) : s0 + qi) : s0;
             }
+            // past the end a thread reads the slice's first row again (an L1 hit), so every
+            // thread keeps B rows in flight without branching
             float dl[B];
 #pragma unroll
-            for (int q = 0; q < B; q++) dl[q] = dist32<D>(a.x + (size_t)rows[q] * d, Ls, d);
+            for (int q = 0; q < B; q++) dl[q] = dist32<D>(a.x + (size_t)ids[q] * d, Ls, d);
 #pragma unroll
             for (int q = 0; q < B; q++) {
-                const uint32_t i = i0 + q * kThreads;
-                if (i < s1) {
-                    const uint32_t k = __float_as_uint(dl[q]);
-                    a.key[i] = k;
-                    atomicAdd(&sh[k >> 21], 1u);
-                    if (have_guess && (k >> 21) == guess) atomicAdd(&gh[(k >> 10) & (kHistBins - 1)], 1u);
+                const uint32_t k = __float_as_uint(dl[q]);
+                if (lv[q]) {
+                    a.key[ids[q]] = k;
+                    if (kc) skey[base + q * kThreads + t] = k;
+                }
+                // the keys of a round crowd into a few bins: one shared atomic per bin and warp
+                const uint32_t b = lv[q] ? (k >> 21) : kGone;
+                const uint32_t peers = __match_any_sync(0xffffffffu, b);
+                if (lv[q] && lane == __ffs(peers) - 1) atomicAdd(&sh[b], (uint32_t)__popc(peers));
+                if (have_guess) {
+                    const uint32_t g2 = lv[q] && (k >> 21) == guess ? (k >> 10) & (kHistBins - 1) : kGone;
+                    const uint32_t pg = __match_any_sync(0xffffffffu, g2);
+                    if (g2 != kGone && lane == __ffs(pg) - 1) atomicAdd(&gh[g2], (uint32_t)__popc(pg));
                 }
             }
         }
         __syncthreads();
-        for (int b = t; b < kHistBins; b += kThreads)
-            if (sh[b]) atomicAdd(&hist0[b], sh[b]);
-        if (have_guess) {
-            uint32_t *gg = &ctl->ghist[par][0];
+        {
+            uint32_t *hist0 = ctl->hist[par][0];
             for (int b = t; b < kHistBins; b += kThreads)
-                if (gh[b]) atomicAdd(&gg[b], gh[b]);
+                if (sh[b]) atomicAdd(&hist0[b], sh[b]);
+            if (have_guess) {
+                uint32_t *gg = &ctl->ghist[par][0];
+                for (int b = t; b < kHistBins; b += kThreads)
+                    if (gh[b]) atomicAdd(&gg[b], gh[b]);
+            }
         }
         if (!grid_sync(ctl, a.flags, gen)) return;
 
-        // ---- B: second histogram inside the N-th key's bin (skipped when the bin was
-        // guessed: the previous round's N-th key is almost always in the same bin)
-        uint32_t b0, rank0;
-        find_bin(hist0, (uint32_t)(a.N - 1), b0, rank0);
-        const bool hit = have_guess && b0 == guess;
+        // ---- B: the bin of the N-th key and the second digit inside it (the second
+        // histogram is only built here when the bin was not guessed)
+        uint32_t b0, rank0, b1 = 0, rank1 = 0;
+        bool hit;
+        find_bins(ctl->hist[par][0], have_guess ? ctl->ghist[par] : nullptr, guess, N - 1u, b0, rank0, b1,
+                  rank1, hit);
         guess = b0;
-        if (hit) {
-            hist1 = &ctl->ghist[par][0];
-        } else {
-        for (int b = t; b < kHistBins; b += kThreads) sh[b] = 0;
-        __syncthreads();
-        for (uint32_t i0 = s0 + t; i0 < s1; i0 += 4 * kThreads) {
-            uint32_t k4[4];
+        if (!hit) {
+            uint32_t *hist1 = ctl->hist[par][1];
+            for (int b = t; b < kHistBins; b += kThreads) sh[b] = 0;
+            __syncthreads();
+            for (uint32_t q0 = t; q0 < n_live; q0 += 4 * kThreads) {
+                uint32_t k4[4];
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const uint32_t i = i0 + q * kThreads;
-                k4[q] = i < s1 ? a.key[i] : 0xFFFFFFFFu;
+                for (int q = 0; q < 4; q++) {
+                    const uint32_t qi = q0 + q * kThreads;
+                    k4[q] = qi >= n_live ? kGone : kc ? skey[qi] : __ldcg(&a.key[lin ? __ldcg(&lin[qi]) : s0 + qi]);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    if ((k4[q] >> 21) == b0 && k4[q] != kGone) atomicAdd(&sh[(k4[q] >> 10) & (kHistBins - 1)], 1u);
             }
-#pragma unroll
-            for (int q = 0; q < 4; q++)
-                if ((k4[q] >> 21) == b0 && k4[q] != 0xFFFFFFFFu) atomicAdd(&sh[(k4[q] >> 10) & (kHistBins - 1)], 1u);
-        }
-        __syncthreads();
-        for (int b = t; b < kHistBins; b += kThreads)
-            if (sh[b]) atomicAdd(&hist1[b], sh[b]);
-        if (!grid_sync(ctl, a.flags, gen)) return;
+            __syncthreads();
+            for (int b = t; b < kHistBins; b += kThreads)
+                if (sh[b]) atomicAdd(&hist1[b], sh[b]);
+            if (!grid_sync(ctl, a.flags, gen)) return;
+            find_bin(hist1, rank0, b1, rank1);
         }
 
         // ---- C: classify; the band is listed
-        uint32_t b1, rank1;
-        find_bin(hist1, rank0, b1, rank1);
         if (t == 0) band_cutoffs(b0, b1, d, s_in_key, s_out_key);
         {   // clear next round's histograms (last read in the previous round)
             uint32_t *nh = &ctl->hist[par ^ 1][0][0];
@@ -442,44 +785,45 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
         __syncthreads();
         const uint32_t in_key = s_in_key, out_key = s_out_key;
         uint32_t n_in = 0;
-        for (uint32_t i0 = s0 + t; i0 < s1; i0 += 4 * kThreads) {
+        for (uint32_t q0 = t; q0 < n_live; q0 += 4 * kThreads) {
             uint32_t k4[4];
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                const uint32_t i = i0 + q * kThreads;
-                k4[q] = i < s1 ? a.key[i] : 0u;
+                const uint32_t qi = q0 + q * kThreads;
+                k4[q] = qi >= n_live ? kGone : kc ? skey[qi] : __ldcg(&a.key[lin ? __ldcg(&lin[qi]) : s0 + qi]);
             }
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                const uint32_t i = i0 + q * kThreads;
-                if (i >= s1) continue;
-                const uint32_t k = k4[q];
-                uint8_t s = k < in_key ? 1 : (k > out_key ? 0 : 2);
-                if (s == 2) {
+                const uint32_t k = k4[q];           // past the end: kGone, above out_key
+                if (k < in_key) {
+                    n_in++;
+                } else if (k <= out_key) {
+                    const uint32_t qi = q0 + q * kThreads;
                     const uint32_t slot = atomicAdd(&ctl->band_cnt[par], 1u);
                     a.band_k32[slot] = k;
-                    a.band_pos[slot] = i;
+                    a.band_pos[slot] = lin ? __ldcg(&lin[qi]) : s0 + qi;
                 }
-                n_in += s == 1;
-                a.status[i] = s;
             }
         }
         n_in = block_sum(n_in);
         if (t == 0) ctl->cnt_in[c] = n_in;
         if (!grid_sync(ctl, a.flags, gen)) return;
 
-        // ---- D: settle the band, compact, next landmark
-        uint32_t all_in = 0, in_before = 0;
-        for (uint32_t q = t; q < G; q += kThreads) {
-            const uint32_t v = __ldcg(&ctl->cnt_in[q]);
-            all_in += v;
-            if (q < c) in_before += v;
+        // ---- D: settle the band, take the subcluster, next landmark
+        uint32_t all_in, in_before;
+        {
+            uint32_t va = 0, vb = 0, e0, e1;
+            for (uint32_t q = t; q < G; q += kThreads) {
+                const uint32_t v = __ldcg(&ctl->cnt_in[q]);
+                va += v;
+                if (q < c) vb += v;
+            }
+            block_excl_scan2(va, vb, e0, e1, all_in, in_before);
         }
-        all_in = block_sum(all_in);
-        in_before = block_sum(in_before);
         const uint32_t nb = __ldcg(&ctl->band_cnt[par]);
-        const uint32_t need = (uint32_t)a.N > all_in ? (uint32_t)a.N - all_in : 0u;
-        if ((all_in > (uint32_t)a.N || need > nb) && c == 0 && t == 0) atomicOr(&a.flags[1], 1u);
+        const uint32_t need = N > all_in ? N - all_in : 0u;
+        if ((all_in > N || need > nb) && c == 0 && t == 0) atomicOr(&a.flags[1], 1u);
+        uint32_t lo = in_key, tout = 0, ntt = 0;       // the rule (see taken())
         uint32_t band_before = 0;
         bool slow = false;
         if (need > 0 && need < nb) {
@@ -489,13 +833,6 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
             // compensated float32 (dff, within eps_ff of the float64 definition) settle all
             // of them but those within the dff error of the cut-off (in practice only exact
             // ties), which are decided in float64.
-            uint32_t *hb = dyn;                                    // kBandBins one-ulp bins
-            uint32_t *tpos = dyn + kBandBins;                      // kTight tight entries
-            float *th = reinterpret_cast<float *>(tpos + kTight);
-            float *tl = th + kTight;
-            uint32_t *tcls = reinterpret_cast<uint32_t *>(tl + kTight);   // 1 taken, 0 not
-            uint32_t *tamb = tcls + kTight;                        // undecided tight entries
-            unsigned long long *td = reinterpret_cast<unsigned long long *>(tamb + kTight);
             const uint32_t range = out_key - in_key + 1u;
             slow = range > (uint32_t)kBandBins;
             if (!slow) {
@@ -525,16 +862,18 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
                     }
                 }
                 __syncthreads();
-                uint32_t tin, tout;
-                band_cutoffs_key(s_t32, s_t32, d, tin, tout);
-                uint32_t n_cert = 0;
+                uint32_t tin, tt;
+                band_cutoffs_key(s_t32, s_t32, d, tin, tt);
+                uint32_t n_cert = 0, cert_before = 0;
                 for (uint32_t q = t; q < nb; q += kThreads) {
                     const uint32_t k = __ldcg(&a.band_k32[q]);
+                    const uint32_t pq = __ldcg(&a.band_pos[q]);
                     if (k < tin) {
                         n_cert++;
-                    } else if (k <= tout) {
+                        cert_before += pq < s0;
+                    } else if (k <= tt) {
                         const uint32_t slot = atomicAdd(&s_nt, 1u);
-                        if (slot < (uint32_t)kTight) tpos[slot] = __ldcg(&a.band_pos[q]);
+                        if (slot < (uint32_t)kTight) tpos[slot] = pq;
                     }
                 }
                 n_cert = block_sum(n_cert);
@@ -543,15 +882,13 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
                 if (!slow) {
                     const uint32_t need2 = need - n_cert;
                     for (uint32_t q = t; q < nt; q += kThreads) {
-                        const uint32_t pq = tpos[q];
-                        const uint32_t row = idx_in ? __ldcg(&idx_in[pq]) : pq;
                         float h, l;
-                        dist_ff(a.x + (size_t)row * d, Ls, d, h, l);
+                        dist_ff(a.x + (size_t)tpos[q] * d, Ls, d, h, l);
                         th[q] = h;
                         tl[q] = l;
                     }
                     __syncthreads();
-                    // V: the tight entry of rank need2-1 in (dff, position) order
+                    // V: the tight entry of rank need2-1 in (dff, index) order
                     for (uint32_t q = t; q < nt; q += kThreads) {
                         uint32_t rk = 0;
                         for (uint32_t o = 0; o < nt; o++)
@@ -568,7 +905,7 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
                     uint32_t n_take = 0;
                     for (uint32_t q = t; q < nt; q += kThreads) {
                         const float diff = __fadd_rn(__fsub_rn(th[q], hv), __fsub_rn(tl[q], lv));
-                        uint32_t cls = diff < -win ? 1u : 0u;
+                        const uint32_t cls = diff < -win ? 1u : 0u;
                         if (diff >= -win && diff <= win) {
                             const uint32_t slot = atomicAdd(&s_na, 1u);
                             tamb[slot] = q;
@@ -583,11 +920,8 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
                     if (need3 >= na) {
                         for (uint32_t q = t; q < na; q += kThreads) tcls[tamb[q]] = 1u;
                     } else if (need3 > 0) {
-                        for (uint32_t q = t; q < na; q += kThreads) {
-                            const uint32_t pq = tpos[tamb[q]];
-                            const uint32_t row = idx_in ? __ldcg(&idx_in[pq]) : pq;
-                            td[q] = (unsigned long long)__double_as_longlong(dist64(a.x + (size_t)row * d, Ls, d));
-                        }
+                        for (uint32_t q = t; q < na; q += kThreads)
+                            td[q] = (unsigned long long)__double_as_longlong(dist64(a.x + (size_t)tpos[tamb[q]] * d, Ls, d));
                         __syncthreads();
                         for (uint32_t q = t; q < na; q += kThreads) {
                             const unsigned long long kq = td[q];
@@ -597,29 +931,22 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
                             tcls[tamb[q]] = rk < need3 ? 1u : 0u;
                         }
                     }
-                    __syncthreads();
-                    for (uint32_t q = t; q < nb; q += kThreads) {
-                        const uint32_t k = __ldcg(&a.band_k32[q]);
-                        const uint32_t pq = __ldcg(&a.band_pos[q]);
-                        bool take = k < tin;
-                        if (!take && k <= tout)
-                            for (uint32_t o = 0; o < nt; o++)
-                                if (tpos[o] == pq) take = tcls[o] != 0;
-                        if (take) {
-                            if (pq < s0) band_before++;
-                            else if (pq < s1) a.status[pq] = 1;
-                        }
-                    }
+                    lo = max(in_key, tin);
+                    tout = tt;
+                    ntt = nt;
                 }
                 __syncthreads();
+                if (!slow) {                       // taken band points before the slice
+                    band_before = cert_before;
+                    for (uint32_t q = t; q < nt; q += kThreads) band_before += tcls[q] != 0 && tpos[q] < s0;
+                }
             }
             if (slow) {
                 // wide band (e.g. many equal distances): float64 for every band entry, spread
                 // over all CTAs, then one CTA selects while the rest wait
                 for (uint32_t q = c * kThreads + t; q < nb; q += G * kThreads) {
                     const uint32_t pq = __ldcg(&a.band_pos[q]);
-                    const uint32_t row = idx_in ? __ldcg(&idx_in[pq]) : pq;
-                    a.band_key[q] = (uint64_t)__double_as_longlong(dist64(a.x + (size_t)row * d, Ls, d));
+                    a.band_key[q] = (uint64_t)__double_as_longlong(dist64(a.x + (size_t)pq * d, Ls, d));
                 }
                 if (!grid_sync(ctl, a.flags, gen)) return;
                 uint64_t K = 0;
@@ -634,155 +961,94 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
                 if (!grid_sync(ctl, a.flags, gen)) return;
                 K = __ldcg(&ctl->sel_key);
                 Pp = __ldcg(&ctl->sel_pos);
-                band_before = 0;
                 for (uint32_t q = t; q < nb; q += kThreads) {
                     const uint64_t kq = __ldcg(&a.band_key[q]);
                     const uint32_t pq = __ldcg(&a.band_pos[q]);
                     if (kq < K || (kq == K && pq <= Pp)) {
                         if (pq < s0) band_before++;
-                        else if (pq < s1) a.status[pq] = 1;
+                        else if (pq < s1) a.key[pq] = kTaken;
                     }
                 }
+                lo = in_key;
+                tout = 0;
+                ntt = 0;
             }
         } else if (need > 0) {
-            // need >= nb: the whole band is taken (need > nb contradicts the bound; flagged)
-            for (uint32_t q = t; q < nb; q += kThreads) {
-                const uint32_t pq = __ldcg(&a.band_pos[q]);
-                if (pq < s0) band_before++;
-                else if (pq < s1) a.status[pq] = 1;
-            }
+            lo = out_key + 1u;      // need >= nb: the whole band is taken (need > nb is flagged)
+            for (uint32_t q = t; q < nb; q += kThreads) band_before += __ldcg(&a.band_pos[q]) < s0;
         }
-        band_before = block_sum(band_before);       // its barrier also orders the status writes
-        uint32_t sel_base = in_before + band_before;
-        uint32_t uns_base = s0 - sel_base;
+        const Rule R{lo, tout, ntt, tpos, tcls};
+        band_before = block_sum(band_before);       // its barriers also publish the kTaken marks
+        // take the subcluster: ids in ascending order to the segment, the rest stay listed;
+        // a taken point is marked removed and leaves the live count of its d buckets
+        // (with landmark-only CTAs they do that bookkeeping in the next round's phase A)
+        const bool ksh = kc && !slow;             // wide-band marks are in global memory only
+        n_live -= compact_list(lin, s0, n_live, seg_out + in_before + band_before, a.lidx + (size_t)(par ^ 1) * n + s0,
+                               [&](uint32_t qi, uint32_t id) { return taken(R, ksh ? skey[qi] : __ldcg(&a.key[id]), id); },
+                               [&](uint32_t id) {
+                                   if (Gl == 0) {
+                                       a.key[id] = kGone;
+                                       drop_buckets<D>(a.x, d, id, a.bcs, nbk);
+                                   }
+                               });
 
-        float mn[DM];
+        // next landmark.  Bucket live counts are upper bounds (this round's removals are
+        // not counted yet), and a point counts as left only if it is neither marked removed
+        // nor taken by this round's rule (a key read before or after its owner marks it
+        // gives the same answer).  After a wide band its kTaken marks are published first.
+        if (slow && !grid_sync(ctl, a.flags, gen)) return;
+        const Rule &RL = R;
+        for (int j = lm_first; j >= 0 && j < d; j += lm_step) {
+            const uint4 *bj = a.bcs + (size_t)j * nbk;
+            const uint32_t *oj = a.ord + (size_t)j * a.ord_ld;
+            uint32_t b = __ldcg(&ctl->lptr[j]);       // the buckets before b hold no point left
+            uint32_t mnb = kGone;
+            while (b < nbk) {
+                // the first bucket from b on with a live count
+                const uint32_t bb = b + (uint32_t)t;
+                const uint4 e = bb < nbk ? __ldcg(&bj[bb]) : make_uint4(0u, 0u, 0u, 0u);
+                uint32_t fb = warp_min(e.x > 0 ? bb : kGone);
+                if (lane == 0) red_a[w] = fb;
+                __syncthreads();
+                fb = red_a[0];
 #pragma unroll
-        for (int j = 0; j < DM; j++) mn[j] = __int_as_float(kInfBits);
-        if (!(D > 0 && D <= 64)) {
-            for (int j = t; j < d; j += kThreads) gmin[j] = kInfBits;
-            __syncthreads();
-        }
-        // stable compaction, QT tiles of kThreads items per scan: item (q, t) of a chunk
-        // is preceded by the earlier tiles, by the earlier warps of its tile and by the
-        // lower lanes of its warp
-        for (uint32_t cb = s0; cb < s1; cb += QT * kThreads) {
-            uint32_t tk = 0, vl = 0;                 // bit q: item (q, t) taken / valid
-            uint32_t ids[QT];
-#pragma unroll
-            for (int q = 0; q < QT; q++) {
-                const uint32_t i = cb + q * kThreads + t;
-                const bool v = i < s1;
-                const uint8_t st = v ? a.status[i] : 0;
-                ids[q] = v ? (idx_in ? __ldcg(&idx_in[i]) : i) : 0u;
-                vl |= (uint32_t)v << q;
-                tk |= (uint32_t)(st == 1) << q;
-            }
-#pragma unroll
-            for (int q = 0; q < QT; q++) {
-                const uint32_t bt = __ballot_sync(0xffffffffu, (tk >> q) & 1u);
-                const uint32_t bv = __ballot_sync(0xffffffffu, (vl >> q) & 1u);
-                if (lane == 0) {
-                    off_t[q * W + w] = __popc(bt);
-                    off_u[q * W + w] = __popc(bv & ~bt);
+                for (int q = 1; q < W; q++) fb = min(fb, red_a[q]);
+                if (bb == fb) {
+                    s_st = e.y;
+                    s_en = e.z;
                 }
-            }
-            __syncthreads();
-            if (w == 0) {                           // exclusive scan of the QT*W counts in order
-                constexpr int PER = QT * W / 32;
-                uint32_t at[PER], au[PER], st_ = 0, su = 0;
-#pragma unroll
-                for (int e = 0; e < PER; e++) {
-                    at[e] = off_t[lane * PER + e];
-                    au[e] = off_u[lane * PER + e];
-                    st_ += at[e];
-                    su += au[e];
+                __syncthreads();
+                if (fb == kGone) {
+                    b += kThreads;
+                    continue;
                 }
-                uint32_t it = warp_incl_scan(st_), iu = warp_incl_scan(su);
-                uint32_t et = it - st_, eu = iu - su;
-#pragma unroll
-                for (int e = 0; e < PER; e++) {
-                    off_t[lane * PER + e] = et;
-                    off_u[lane * PER + e] = eu;
-                    et += at[e];
-                    eu += au[e];
+                // the smallest value among its entries left
+                const uint32_t st = s_st, en = s_en;
+                uint32_t lm = kGone;
+                for (uint32_t q = st + t; q < en; q += kThreads) {
+                    const uint32_t id = __ldcg(&oj[q]);
+                    const uint32_t k = __ldcg(&a.key[id]);
+                    const uint32_t xv = __float_as_uint(__ldg(&a.x[(size_t)id * d + j]));
+                    if (k != kGone && !taken(RL, k, id)) lm = min(lm, xv);
                 }
-                if (lane == 31) {
-                    s_tot[0] = it;
-                    s_tot[1] = iu;
+                lm = warp_min(lm);
+                if (lane == 0) red_b[w] = lm;
+                __syncthreads();
+                lm = red_b[0];
+#pragma unroll
+                for (int q = 1; q < W; q++) lm = min(lm, red_b[q]);
+                __syncthreads();
+                if (lm != kGone) {
+                    mnb = lm;
+                    b = fb;
+                    break;
                 }
+                b = fb + 1;                            // every entry of fb is gone
             }
-            __syncthreads();
-            uint32_t urows[QT];
-            int nu = 0;
-#pragma unroll
-            for (int q = 0; q < QT; q++) {
-                const uint32_t bt = __ballot_sync(0xffffffffu, (tk >> q) & 1u);
-                const uint32_t bv = __ballot_sync(0xffffffffu, (vl >> q) & 1u);
-                if ((vl >> q) & 1u) {
-                    if ((tk >> q) & 1u) {
-                        seg_out[sel_base + off_t[q * W + w] + __popc(bt & lt_mask)] = ids[q];
-                    } else {
-                        idx_out[uns_base + off_u[q * W + w] + __popc(bv & ~bt & lt_mask)] = ids[q];
-                        urows[nu++] = ids[q];
-                    }
-                }
+            if (t == 0) {
+                ctl->lptr[j] = b;
+                ctl->Lbits[par ^ 1][j] = mnb == kGone ? kInfBits : mnb;
             }
-            // minima of the rows that stay, B rows in flight at a time
-            if (D > 0 && D <= 64) {
-                for (int q0 = 0; q0 < nu; q0 += B) {
-                    float rv[B][DM];
-#pragma unroll
-                    for (int q = 0; q < B; q++) {
-                        const uint32_t id = q0 + q < nu ? urows[q0 + q] : urows[q0];
-                        const float *row = a.x + (size_t)id * d;
-                        if (DM % 4 == 0) {
-                            const float4 *r4 = reinterpret_cast<const float4 *>(row);
-#pragma unroll
-                            for (int j4 = 0; j4 < DM / 4; j4++) {
-                                const float4 v = __ldg(&r4[j4]);
-                                rv[q][4 * j4 + 0] = v.x;
-                                rv[q][4 * j4 + 1] = v.y;
-                                rv[q][4 * j4 + 2] = v.z;
-                                rv[q][4 * j4 + 3] = v.w;
-                            }
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < DM; j++) rv[q][j] = __ldg(&row[j]);
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < B; q++)
-#pragma unroll
-                        for (int j = 0; j < DM; j++) mn[j] = fminf(mn[j], rv[q][j]);
-                }
-            } else {
-                for (int q = 0; q < nu; q++) {
-                    const float *row = a.x + (size_t)urows[q] * d;
-                    for (int j = 0; j < d; j++) atomicMin(&gmin[j], __float_as_uint(__ldg(&row[j])));
-                }
-            }
-            sel_base += s_tot[0];
-            uns_base += s_tot[1];
-            __syncthreads();
-        }
-        if (D > 0 && D <= 64) {
-#pragma unroll
-            for (int j = 0; j < DM; j++) {
-                float v = mn[j];
-                for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-                if (lane == 0) wmin[w][j] = v;
-            }
-            __syncthreads();
-            for (int j = t; j < d; j += kThreads) {
-                float v = wmin[0][j];
-                for (int q = 1; q < W; q++) v = fminf(v, wmin[q][j]);
-                if (__float_as_uint(v) < kInfBits) atomicMin(&ctl->Lbits[par ^ 1][j], __float_as_uint(v));
-            }
-        } else {
-            __syncthreads();
-            for (int j = t; j < d; j += kThreads)
-                if (gmin[j] < kInfBits) atomicMin(&ctl->Lbits[par ^ 1][j], gmin[j]);
         }
         if (!grid_sync(ctl, a.flags, gen)) return;
     }
@@ -821,6 +1087,8 @@ cudaError_t peel_launch(const PeelBuffers &b, int64_t n, int d, int64_t N, int s
     // minimum of every attribute is exactly 0)
     cudaError_t e = cudaMemsetAsync(b.ctl, 0, sizeof(PeelCtl), st);
     if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(b.bcnt, 0, (size_t)d * b.nbuckets * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
     const size_t smem = kPeelDynWords * sizeof(uint32_t);
     e = cudaFuncSetAttribute(k_peel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -830,7 +1098,7 @@ cudaError_t peel_launch(const PeelBuffers &b, int64_t n, int d, int64_t N, int s
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t grid = (int64_t)sm_count * std::min(per_sm, 4);
     if (grid > kMaxPeelGrid) grid = kMaxPeelGrid;
-    const int64_t want = (n + 63) / 64;             // at least ~64 points per CTA in round 0
+    const int64_t want = (n + 63) / 64;             // at least ~64 points per CTA
     if (grid > want) grid = std::max<int64_t>(1, want);
     PeelArgs a;
     a.x = b.x;
@@ -838,10 +1106,13 @@ cudaError_t peel_launch(const PeelBuffers &b, int64_t n, int d, int64_t N, int s
     a.n = n;
     a.N = N;
     a.S = S;
-    a.idx0 = b.idx[0];
-    a.idx1 = b.idx[1];
     a.key = b.key;
-    a.status = b.status;
+    a.ord = b.ord;
+    a.bcnt = b.bcnt;
+    a.bcs = b.bcs;
+    a.lidx = b.lidx;
+    a.ord_ld = b.ord_ld;
+    a.nbk = b.nbuckets;
     a.band_key = b.band_key;
     a.band_k32 = b.band_k32;
     a.band_pos = b.band_pos;
@@ -876,6 +1147,13 @@ cudaError_t peel_launch(const PeelBuffers &b, int64_t n, int d, int64_t N, int s
 }
 
 }  // namespace
+
+uint32_t peel_buckets(int64_t n)
+{
+    uint32_t nb = 4096;
+    while (nb < 65536u && (int64_t)nb * 16 < n) nb <<= 1;
+    return nb;
+}
 
 cudaError_t launch_peel(const PeelBuffers &b, int64_t n, int d, int64_t N, int sm_count,
                         cudaStream_t st, KTimer *kt)

@@ -14,7 +14,6 @@ namespace pscl {
 constexpr int kMaxD = 1024;          // attributes per point
 constexpr int kMaxK = 4096;          // centers of one Lloyd run
 constexpr int kHistBins = 2048;      // 11-bit radix digits of the peel's key select
-constexpr int kBlkItems = 1024;      // points per block in the peel's classify/compact
 constexpr int kFixShift = 32;        // fixed-point scale 2^32 of the centroid sums
 
 constexpr int kMaxPeelGrid = 2048;   // CTAs of the persistent peel launch
@@ -23,7 +22,8 @@ constexpr int kMaxPeelGrid = 2048;   // CTAs of the persistent peel launch
 struct PeelCtl {
     uint32_t hist[2][2][kHistBins];  // [round parity][digit level][bin]
     uint32_t ghist[2][kHistBins];    // [round parity][bin]: second digit inside the guessed first
-    uint32_t Lbits[2][kMaxD];        // landmark of this / next round (float bits, min by atomicMin)
+    uint32_t Lbits[2][kMaxD];        // landmark of this / next round (float bits)
+    uint32_t lptr[kMaxD];            // per attribute: buckets in front of it hold no remaining point
     uint32_t cnt_in[kMaxPeelGrid];   // per CTA: points certainly taken this round
     uint32_t band_cnt[2];            // band entries of this / next round
     uint32_t bar_count;              // grid barrier: arrivals since the launch
@@ -93,18 +93,24 @@ size_t scale_part_floats(int64_t n, int d, int sm_count);
 // peel.cu
 struct PeelBuffers {
     const float *x;                  // n x d scaled points
-    uint32_t *idx[2];                // remaining point indices (ping-pong)
-    uint32_t *key;                   // float32 distance keys of the remaining points
-    uint8_t *status;                 // 0 out, 1 taken, 2 band (per remaining point)
+    uint32_t *key;                   // n: float32 distance key of each point (removed: all ones)
+    uint32_t *ord;                   // d x ord_ld: point ids of each attribute in bucket order
+    uint32_t *bcnt;                  // d x nbuckets: bucket counts, then scatter cursors
+    uint4 *bcs;                      // d x nbuckets: (points left, first entry, end entry, 0)
+    uint32_t *lidx;                  // 2 x n: per CTA slice, the ids of its points left
+    int64_t ord_ld;                  // n rounded up to a multiple of 4
+    uint32_t nbuckets;               // power of two, 4096 .. 65536
     uint64_t *band_key;              // float64 distance bits of band points (wide bands)
     uint32_t *band_k32;              // float32 keys of band points
-    uint32_t *band_pos;              // their positions among the remaining points
+    uint32_t *band_pos;              // their point ids
     float *landmarks;                // all landmarks (S x d), for inspection
     uint32_t *perm;                  // n: subcluster-packed original indices
     float *xseg;                     // n x d: subcluster-packed points
     PeelCtl *ctl;
     uint32_t *flags;
 };
+// Buckets of the per-attribute orders the peel builds for n points.
+uint32_t peel_buckets(int64_t n);
 cudaError_t launch_peel(const PeelBuffers &b, int64_t n, int d, int64_t N, int sm_count,
                         cudaStream_t st, KTimer *kt);
 
