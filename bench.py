@@ -329,19 +329,131 @@ def main_arm(args, w: synth.Workload):
         dist.destroy_process_group()
 
 
+def main_uneven(args):
+    """The uneven batch: 2048 independent instances, sizes log-uniform in [256, 65536],
+    d = 32, k = max(8, size / 256), 25 Lloyd iterations, every instance min-max scaled on
+    its own; one graph-recorded run of all instances per step, work-unit shape from the
+    autotuner.  Printed as its own line (not the default workload)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1412_1947_gb300 import binding as B
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    iters, seed = 25, 777
+    prec = B.PRECISIONS[args.prec]
+    parts, ks = synth.uneven_batch()
+    sizes = np.array([len(p) for p in parts], np.int64)
+    keff = np.minimum(np.array(ks, np.int64), sizes)
+    raw = np.ascontiguousarray(np.concatenate(parts), np.float32)
+    evals = int((sizes * keff).sum()) * iters
+    x_dev = torch.from_numpy(raw).to(dev)
+    ctx = B.pscl_ctx_create(0, 0, stream.cuda_stream)
+    b = B.Batch(x_dev, sizes, ks, ctx=ctx)
+    unit_rows, rpt, _ = b.tune(2, prec)
+    for _ in range(args.warmup):
+        b.run(iters, seed, prec)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clk = ClockSampler(0)
+    clk.start()
+    for i in range(args.steps):
+        starts[i].record(stream)
+        b.run(iters, seed, prec)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    step_ms = [s_.elapsed_time(e) for s_, e in zip(starts, ends)]
+    mean_ms = statistics.mean(step_ms)
+    _, _, sse = b.result(labels=False)
+    # the Lloyd iterations alone (unrecorded run, events around them)
+    b.option(B.PSCL_OPT_GRAPH, 0)
+    b.run(iters, seed, prec)
+    lloyd_ms = b.lloyd_ms()
+    # the plain form: one launch pair per instance and iteration
+    plain = None
+    if not args.no_plain:
+        b.option(B.PSCL_OPT_PLAIN_LLOYD, 1)
+        b.run(iters, seed, B.PSCL_PREC_FP32)
+        pl_ms = b.lloyd_ms()
+        _, _, sse_p = b.result(labels=False)
+        plain = {"form": "plain float32, one launch pair per instance per iteration", "lloyd_ms": pl_ms,
+                 "value": evals / (pl_ms * 1e-3), "sse_equal": bool(np.array_equal(sse_p, sse))}
+        b.option(B.PSCL_OPT_PLAIN_LLOYD, 0)
+    b.option(B.PSCL_OPT_GRAPH, 1)
+    # end to end: pinned host points in, per-instance SSE out, every step
+    host = torch.from_numpy(raw).pin_memory()
+    e2e_s = []
+    for i in range(args.steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.load(host)
+        b.run(iters, seed, prec)
+        _, _, _ = b.result(labels=False)
+        if i:
+            e2e_s.append(time.perf_counter() - t0)
+    e2e_mean = statistics.mean(e2e_s)
+    d = raw.shape[1]
+    flops = evals * 3 * d
+    roof = {"kernel": "Lloyd iterations (k_lloyd_assign + finalize)", "bound": "alu",
+            "achieved": flops / (lloyd_ms * 1e-3) / 1e12, "peak": FP32_ALU_PEAK / 1e12, "unit": "TFLOP/s",
+            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz", "traffic": None}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    line = {"metric": METRIC, "value": evals / (mean_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else args.prec + "+f32", "data": "synthetic",
+            "config": {"workload": "uneven2048_d32_k8to256_it25", "instances": len(sizes), "rows": int(sizes.sum()),
+                       "d": d, "iters": iters, "l2": "inputs (3 GB) larger than L2",
+                       "tuned": {"unit_rows": unit_rows, "rows_per_thread": "1" if rpt else "default"}},
+            "lloyd_ms": lloyd_ms, "lloyd_only_value": evals / (lloyd_ms * 1e-3), "sse_sum": float(sse.sum()),
+            "e2e": {"value": evals / e2e_mean, "unit": UNIT, "h2d_bytes_per_step": int(raw.nbytes),
+                    "d2h_bytes_per_step": int(8 * len(sizes))},
+            "gpu_launches": None, "roofline": roof, "plain_fp32": plain, "clocks": clocks}
+    if not args.no_cpu:
+        # the oracle, single-threaded, on the first instances up to ~1e8 distance evaluations
+        budget, ev_s, t_s, used = 1e8, 0, 0.0, 0
+        for i, (p, k) in enumerate(zip(parts, ks)):
+            e = len(p) * min(k, len(p)) * iters
+            if ev_s and ev_s + e > budget:
+                break
+            xs, _, _ = oracle.scale(p)
+            t0 = time.perf_counter()
+            oracle.lloyd_seeded(xs, k, iters, seed, 0, i)
+            t_s += time.perf_counter() - t0
+            ev_s += e
+            used += 1
+        line["cpu_baseline"] = {"value": ev_s / t_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"the first {used} instances ({ev_s:.3g} distance evaluations)"}
+    b.close()
+    B.pscl_ctx_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="medium", choices=["small", "medium", "large"])
+    ap.add_argument("--workload", default="medium", choices=["small", "medium", "large", "uneven"])
     ap.add_argument("--oracle-n", type=int, default=1 << 17)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16", "tf32x3", "bf16x3"],
                     help="arithmetic of the Lloyd assignment (tf32/bf16: tensor cores + float32 near-tie recheck)")
     args = ap.parse_args()
+    if args.workload == "uneven":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the uneven batch has no reference arm; "
+                              "its oracle is timed in the cpu_baseline of the same line"}))
+        else:
+            main_uneven(args)
+        return
     w = {"small": synth.SMALL, "medium": synth.MEDIUM, "large": synth.LARGE}[args.workload]
     if args.impl == "reference":
         reference_arm(args, w)

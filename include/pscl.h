@@ -85,7 +85,14 @@ typedef enum {
     PSCL_OPT_GRAPH = 4,
     /* 1: time every kernel launch of later unrecorded runs with CUDA events on the
      *    context's stream (pscl_get_kernel_times).  Default 0. */
-    PSCL_OPT_KERNEL_TIMING = 5
+    PSCL_OPT_KERNEL_TIMING = 5,
+    /* Batches only (pscl_batch_set_option): rows per work unit of the Lloyd launches,
+     *    32..1024 (rounded up to a multiple of 32), 0 = the planner's default.  A tuning
+     *    choice: results do not depend on it. */
+    PSCL_OPT_UNIT_ROWS = 6,
+    /* Batches only: 1 = one row per thread in the float32 assignment kernel, 0 = its
+     *    default (up to 4 rows kept in registers).  Results do not depend on it. */
+    PSCL_OPT_ROWS_PER_THREAD = 7
 } pscl_option;
 
 /* The library's kernels, for pscl_get_kernel_times. */
@@ -224,6 +231,61 @@ int pscl_get_phase_ms(pscl_job *job, float *ms5);
  * Errors: PSCL_EINVAL, PSCL_ECUDA (see pscl_last_error()). */
 int pscl_assign_sse_noalloc(const float *points, int64_t n, int32_t d, const float *centers,
                             int32_t k, int32_t *labels, double *sse, void *stream);
+
+/* ---------------------------------------------------------------- uneven batches
+ * Many independent clustering instances of uneven sizes, each with its own k: the
+ * first-level Lloyd runs of Algorithm 1 step 4 (§II), given directly instead of produced
+ * by the peel.  Every instance is min-max scaled on its own (Algorithm 1 step 1, same
+ * formula as pscl_scale_features) and then clustered by Lloyd (§I) from the seeded
+ * initial centers of segment = its index, stage 0 (the seeding of pscl_subcluster).
+ * All instances advance together: each launch covers work units of every instance, and a
+ * run is recorded once into a CUDA graph (PSCL_OPT_GRAPH, on by default for batches) and
+ * replayed.  The paper has no batch of independent problems; it is the serving form of
+ * its first level.
+ *
+ * points: sum(sizes) x d float32, row-major, instance after instance (host memory, or
+ *         16-byte aligned device memory of the context's device with on_device = 1; a
+ *         device buffer is read, not copied, by every run and must outlive the batch).
+ * sizes, k: n_inst entries each; sizes >= 1, 1 <= k <= 4096; instance i gets
+ *         k_eff = min(k[i], sizes[i]) centers.  sum(sizes) <= 2^31 - 1.
+ * Errors: PSCL_EINVAL (bad argument), PSCL_ENOMEM (budget or device memory),
+ *         PSCL_ECUDA.  The library owns every device allocation of the batch. */
+typedef struct pscl_batch pscl_batch;
+int pscl_batch_create(pscl_ctx *ctx, const void *points, int on_device, int32_t d, int32_t n_inst,
+                      const int64_t *sizes, const int32_t *k, pscl_batch **out);
+/* New points of the same shape for later runs (host memory is copied on the context's
+ * stream; a device buffer is used in place, as for pscl_batch_create). */
+int pscl_batch_load(pscl_batch *b, const void *points, int on_device);
+/* Options: PSCL_OPT_TRACE_LABELS, PSCL_OPT_GRAPH, PSCL_OPT_PLAIN_LLOYD (one launch pair
+ * per instance and iteration, for comparison), PSCL_OPT_UNIT_ROWS,
+ * PSCL_OPT_ROWS_PER_THREAD; others return PSCL_EINVAL. */
+int pscl_batch_set_option(pscl_batch *b, int option, int64_t value);
+/* Autotuner: times `iters` Lloyd iterations of this batch (unrecorded, after one warm-up
+ * run) for every work-unit size in {128, 256, 512, 1024} rows and both rows-per-thread
+ * settings, keeps the fastest and applies it; the choice is remembered for later batches
+ * of the same (device, d, largest k, log2 of the rows, prec).  Writes the choice and
+ * whether it came from that memory (any output may be NULL).  Results never depend on it. */
+int pscl_batch_tune(pscl_batch *b, int32_t iters, int prec, int64_t *unit_rows, int32_t *rows_per_thread,
+                    int32_t *cached);
+/* Queues scale + seeded init + `iters` Lloyd iterations + per-instance SSE on the
+ * context's stream and returns; prec as for pscl_subcluster. */
+int pscl_batch_run(pscl_batch *b, int32_t iters, uint64_t seed, int prec);
+/* Waits for the batch's queued work; PSCL_EINVAL if an input value is not finite. */
+int pscl_batch_sync(pscl_batch *b);
+/* Results of the last run (waits first; any output may be NULL):
+ *   centers: sum(k_eff) x d float32, instance after instance, in scaled coordinates;
+ *   labels:  sum(sizes) int32, the nearest final center of every point (index within its
+ *            instance, lowest on ties);
+ *   sse:     n_inst doubles, per instance the sum over its scaled points of the squared
+ *            distance to the nearest final center. */
+int pscl_batch_get(pscl_batch *b, float *centers, int32_t *labels, double *sse);
+/* The scaled points, sum(sizes) x d float32. */
+int pscl_batch_get_scaled(pscl_batch *b, float *out);
+/* iters x sum(sizes) labels of every iteration (needs PSCL_OPT_TRACE_LABELS). */
+int pscl_batch_get_label_trace(pscl_batch *b, int32_t *out);
+/* Device time of the Lloyd iterations of the last unrecorded run, in milliseconds. */
+int pscl_batch_lloyd_ms(pscl_batch *b, float *ms);
+int pscl_batch_destroy(pscl_batch *b);
 
 #ifdef __cplusplus
 }

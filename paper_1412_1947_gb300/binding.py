@@ -21,7 +21,7 @@ PSCL_PREC_FP32, PSCL_PREC_TF32, PSCL_PREC_BF16, PSCL_PREC_TF32X3, PSCL_PREC_BF16
 PRECISIONS = {"fp32": PSCL_PREC_FP32, "tf32": PSCL_PREC_TF32, "bf16": PSCL_PREC_BF16,
               "tf32x3": PSCL_PREC_TF32X3, "bf16x3": PSCL_PREC_BF16X3}
 PSCL_OPT_PLAIN_LLOYD, PSCL_OPT_TRACE_LABELS, PSCL_OPT_INIT_FIRST_K, PSCL_OPT_GRAPH = 1, 2, 3, 4
-PSCL_OPT_KERNEL_TIMING = 5
+PSCL_OPT_KERNEL_TIMING, PSCL_OPT_UNIT_ROWS, PSCL_OPT_ROWS_PER_THREAD = 5, 6, 7
 
 # entry point -> (restype, argtypes); the list is the C ABI of include/pscl.h
 _P, _I, _I32, _I64, _U64, _SZ = C.c_void_p, C.c_int, C.c_int32, C.c_int64, C.c_uint64, C.c_size_t
@@ -49,6 +49,17 @@ SIGNATURES = {
     "pscl_get_kernel_times": (_I, [_P, _P, _P]),
     "pscl_get_recheck_stats": (_I, [_P, _P, _P]),
     "pscl_assign_sse_noalloc": (_I, [_P, _I64, _I32, _P, _I32, _P, _P, _P]),
+    "pscl_batch_create": (_I, [_P, _P, _I, _I32, _I32, _P, _P, _P]),
+    "pscl_batch_load": (_I, [_P, _P, _I]),
+    "pscl_batch_set_option": (_I, [_P, _I, _I64]),
+    "pscl_batch_tune": (_I, [_P, _I32, _I, _P, _P, _P]),
+    "pscl_batch_run": (_I, [_P, _I32, _U64, _I]),
+    "pscl_batch_sync": (_I, [_P]),
+    "pscl_batch_get": (_I, [_P, _P, _P, _P]),
+    "pscl_batch_get_scaled": (_I, [_P, _P]),
+    "pscl_batch_get_label_trace": (_I, [_P, _P]),
+    "pscl_batch_lloyd_ms": (_I, [_P, _P]),
+    "pscl_batch_destroy": (_I, [_P]),
 }
 KERNELS = ["scale_minmax", "scale_apply", "peel", "gather", "lloyd_init", "lloyd_assign", "lloyd_finalize",
            "final_sse"]
@@ -231,7 +242,129 @@ def pscl_assign_sse_noalloc(points, centers, labels, sse, stream=None):
                                        labels.data_ptr(), sse.data_ptr(), stream))
 
 
+def pscl_batch_create(ctx, points, sizes, k):
+    """points: rows x d (numpy float32, or a torch CUDA tensor), sizes / k per instance."""
+    p, dev, rows, d, keep = _points(points)
+    sz = np.ascontiguousarray(sizes, np.int64)
+    kk = np.ascontiguousarray(k, np.int32)
+    if sz.shape != kk.shape or int(sz.sum()) != rows:
+        raise ValueError("sizes and k need one entry per instance and sizes must add up to the rows")
+    h = C.c_void_p()
+    _chk(lib().pscl_batch_create(ctx, p, dev, d, len(sz), _ptr(sz), _ptr(kk), C.byref(h)))
+    return h, keep
+
+
+def pscl_batch_load(b, points):
+    p, dev, _, _, keep = _points(points)
+    _chk(lib().pscl_batch_load(b, p, dev))
+    return keep
+
+
+def pscl_batch_set_option(b, option, value):
+    _chk(lib().pscl_batch_set_option(b, option, int(value)))
+
+
+def pscl_batch_tune(b, iters, prec=PSCL_PREC_FP32):
+    u, r, c = C.c_int64(), C.c_int32(), C.c_int32()
+    _chk(lib().pscl_batch_tune(b, iters, prec, C.byref(u), C.byref(r), C.byref(c)))
+    return u.value, r.value, bool(c.value)
+
+
+def pscl_batch_run(b, iters, seed, prec=PSCL_PREC_FP32):
+    _chk(lib().pscl_batch_run(b, iters, seed, prec))
+
+
+def pscl_batch_sync(b):
+    _chk(lib().pscl_batch_sync(b))
+
+
+def pscl_batch_get(b, P, rows, n_inst, d, labels=True):
+    c = np.empty((P, d), np.float32)
+    lab = np.empty(rows, np.int32) if labels else None
+    sse = np.empty(n_inst, np.float64)
+    _chk(lib().pscl_batch_get(b, _ptr(c), _ptr(lab), _ptr(sse)))
+    return c, lab, sse
+
+
+def pscl_batch_get_scaled(b, rows, d):
+    out = np.empty((rows, d), np.float32)
+    _chk(lib().pscl_batch_get_scaled(b, _ptr(out)))
+    return out
+
+
+def pscl_batch_get_label_trace(b, iters, rows):
+    out = np.empty(iters * rows, np.int32)
+    _chk(lib().pscl_batch_get_label_trace(b, _ptr(out)))
+    return out.reshape(iters, rows)
+
+
+def pscl_batch_lloyd_ms(b):
+    ms = C.c_float()
+    _chk(lib().pscl_batch_lloyd_ms(b, C.byref(ms)))
+    return ms.value
+
+
+def pscl_batch_destroy(b):
+    _chk(lib().pscl_batch_destroy(b))
+
+
 # ---------------------------------------------------------------- convenience
+class Batch:
+    """Independent clustering instances of uneven sizes (a light owner of the handles)."""
+
+    def __init__(self, points, sizes, k, device=0, hbm_budget_bytes=0, stream=None, ctx=None):
+        self._own_ctx = ctx is None
+        self.ctx = pscl_ctx_create(device, hbm_budget_bytes, stream) if ctx is None else ctx
+        self.h, self._keep = pscl_batch_create(self.ctx, points, sizes, k)
+        self.sizes = np.asarray(sizes, np.int64)
+        self.k = np.minimum(np.asarray(k, np.int64), self.sizes)
+        self.rows, self.d = int(points.shape[0]), int(points.shape[1])
+        self.iters = 0
+
+    def option(self, opt, value=1):
+        pscl_batch_set_option(self.h, opt, value)
+        return self
+
+    def load(self, points):
+        self._keep = pscl_batch_load(self.h, points)
+
+    def tune(self, iters=3, prec=PSCL_PREC_FP32):
+        return pscl_batch_tune(self.h, iters, prec)
+
+    def run(self, iters, seed, prec=PSCL_PREC_FP32):
+        pscl_batch_run(self.h, iters, seed, prec)
+        self.iters = iters
+
+    def sync(self):
+        pscl_batch_sync(self.h)
+
+    def result(self, labels=True):
+        return pscl_batch_get(self.h, int(self.k.sum()), self.rows, len(self.sizes), self.d, labels)
+
+    def scaled(self):
+        return pscl_batch_get_scaled(self.h, self.rows, self.d)
+
+    def trace(self):
+        return pscl_batch_get_label_trace(self.h, self.iters, self.rows)
+
+    def lloyd_ms(self):
+        return pscl_batch_lloyd_ms(self.h)
+
+    def close(self):
+        if self.h is not None:
+            pscl_batch_destroy(self.h)
+            self.h = None
+        if self._own_ctx and self.ctx is not None:
+            pscl_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
 class Job:
     """One clustering problem on one device (a light owner of the C handles)."""
 

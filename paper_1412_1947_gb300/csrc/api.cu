@@ -55,6 +55,12 @@ struct Alloc {
     size_t bytes;
 };
 
+// Anything that owns device allocations charged to a context's budget.
+struct Owner {
+    pscl_ctx *ctx = nullptr;
+    std::vector<Alloc> allocs;
+};
+
 // One Lloyd launch plan: tables on the device and their host copies.
 struct LloydPlan {
     int n_seg = 0, n_units = 0, kmax = 0, d = 0;
@@ -62,7 +68,10 @@ struct LloydPlan {
     std::vector<int64_t> seg_start;
     std::vector<int32_t> seg_size, cen_off, k_eff, unit_seg, unit_start, unit_count, seg_unit0;
     int64_t *d_seg_start = nullptr;
-    int32_t *d_i32 = nullptr;       // seg_size | cen_off | k_eff | unit_seg | unit_start | unit_count
+    int32_t *d_i32 = nullptr;       // seg_size | cen_off | k_eff | unit_seg | unit_start | unit_count | seg_unit0
+    const int32_t *d_unit0() const { return d_i32 + 3 * n_seg + 3 * n_units; }
+    int32_t *d_split = nullptr;     // CTA splits of the units for 1..4 CTAs per SM
+    int split_off[5] = {};
     SegTable table() const
     {
         SegTable t;
@@ -75,15 +84,15 @@ struct LloydPlan {
         t.unit_count = d_i32 + 3 * n_seg + 2 * n_units;
         t.n_seg = n_seg;
         t.n_units = n_units;
+        t.split = d_split;
+        for (int m = 0; m < 5; m++) t.split_off[m] = split_off[m];
         return t;
     }
 };
 
-struct pscl_job {
-    pscl_ctx *ctx = nullptr;
+struct pscl_job : Owner {
     int64_t n = 0;
     int d = 0;
-    std::vector<Alloc> allocs;
     int state = 0;                    // 0 loaded, 1 scaled, 2 subclustered, 3 clustered
     // options
     int plain = 0, trace = 0, first_k = 0, graph = 0, ktiming = 0;
@@ -135,7 +144,7 @@ struct pscl_job {
 };
 
 // ------------------------------------------------------------------ memory
-static int job_alloc(pscl_job *j, void **p, size_t bytes)
+static int job_alloc(Owner *j, void **p, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
     bytes = (bytes + 255) & ~(size_t)255;
@@ -154,7 +163,7 @@ static int job_alloc(pscl_job *j, void **p, size_t bytes)
     return PSCL_OK;
 }
 
-static void job_free(pscl_job *j, void *p)
+static void job_free(Owner *j, void *p)
 {
     if (!p) return;
     for (size_t i = 0; i < j->allocs.size(); i++) {
@@ -168,7 +177,7 @@ static void job_free(pscl_job *j, void *p)
 }
 
 template <class T>
-static int A(pscl_job *j, T **p, size_t count)
+static int A(Owner *j, T **p, size_t count)
 {
     void *v = nullptr;
     int rc = job_alloc(j, &v, count * sizeof(T));
@@ -336,9 +345,11 @@ extern "C" int pscl_job_destroy(pscl_job *j)
 
 // ------------------------------------------------------------------ planning
 // Work units: every set is cut into ceil(m / target) near-equal pieces (multiples of 32
-// rows), target chosen so that a launch has a few units per SM.
-static int build_lloyd_plan(pscl_job *j, LloydPlan &p, const std::vector<int64_t> &starts,
-                            const std::vector<int32_t> &sizes, const std::vector<int32_t> &keff)
+// rows), target chosen so that a launch has a few units per SM (or given: unit_rows, at
+// most 1024 rows, the shared-accumulator bound of the assignment kernel).
+static int build_lloyd_plan(Owner *j, LloydPlan &p, const std::vector<int64_t> &starts,
+                            const std::vector<int32_t> &sizes, const std::vector<int32_t> &keff,
+                            int64_t unit_rows = 0)
 {
     p.n_seg = (int)sizes.size();
     p.seg_start = starts;
@@ -355,8 +366,8 @@ static int build_lloyd_plan(pscl_job *j, LloydPlan &p, const std::vector<int64_t
     }
     p.P = P;
     p.rows = rows;
-    int64_t target = rows / ((int64_t)j->ctx->sm_count * 4);
-    target = std::max<int64_t>(128, std::min<int64_t>(1024, target));
+    int64_t target = unit_rows > 0 ? unit_rows : rows / ((int64_t)j->ctx->sm_count * 4);
+    target = std::max<int64_t>(unit_rows > 0 ? 32 : 128, std::min<int64_t>(1024, target));
     p.unit_seg.clear();
     p.unit_start.clear();
     p.unit_count.clear();
@@ -379,17 +390,41 @@ static int build_lloyd_plan(pscl_job *j, LloydPlan &p, const std::vector<int64_t
     p.d_seg_start = nullptr;
     p.d_i32 = nullptr;
     TRY(A(j, &p.d_seg_start, p.n_seg));
-    TRY(A(j, &p.d_i32, 3 * (size_t)p.n_seg + 3 * (size_t)p.n_units));
+    TRY(A(j, &p.d_i32, 4 * (size_t)p.n_seg + 3 * (size_t)p.n_units + 1));
     std::vector<int32_t> packed;
-    packed.reserve(3 * p.n_seg + 3 * p.n_units);
+    packed.reserve(4 * p.n_seg + 3 * p.n_units + 1);
     packed.insert(packed.end(), p.seg_size.begin(), p.seg_size.end());
     packed.insert(packed.end(), p.cen_off.begin(), p.cen_off.end());
     packed.insert(packed.end(), p.k_eff.begin(), p.k_eff.end());
     packed.insert(packed.end(), p.unit_seg.begin(), p.unit_seg.end());
     packed.insert(packed.end(), p.unit_start.begin(), p.unit_start.end());
     packed.insert(packed.end(), p.unit_count.begin(), p.unit_count.end());
+    packed.insert(packed.end(), p.seg_unit0.begin(), p.seg_unit0.end());
     CU(cudaMemcpy(p.d_seg_start, p.seg_start.data(), p.n_seg * sizeof(int64_t), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(p.d_i32, packed.data(), packed.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    // Contiguous unit ranges of near-equal weight for persistent launches of G = m * SMs
+    // CTAs (rows, plus a set-up allowance wherever a range has to start a new set).
+    const int sm = j->ctx->sm_count;
+    std::vector<int64_t> wpre(p.n_units + 1, 0);
+    for (int u = 0; u < p.n_units; u++) {
+        const bool first = u == 0 || p.unit_seg[u] != p.unit_seg[u - 1];
+        wpre[u + 1] = wpre[u] + p.unit_count[u] + (first ? 256 : 0);
+    }
+    std::vector<int32_t> split;
+    for (int m = 1; m <= 4; m++) {
+        const int G = m * sm;
+        p.split_off[m] = (int)split.size();
+        int u = 0;
+        for (int c = 0; c <= G; c++) {
+            const int64_t target = wpre[p.n_units] * c / G;
+            while (u < p.n_units && wpre[u] < target) u++;
+            split.push_back(c == G ? p.n_units : u);
+        }
+    }
+    job_free(j, p.d_split);
+    p.d_split = nullptr;
+    TRY(A(j, &p.d_split, split.size()));
+    CU(cudaMemcpy(p.d_split, split.data(), split.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     return PSCL_OK;
 }
 
@@ -815,5 +850,394 @@ extern "C" int pscl_get_phase_ms(pscl_job *j, float *ms)
     if (!ms) return fail(PSCL_EINVAL, "ms is NULL");
     if (!j->ev_ok) return fail(PSCL_ESTATE, "no timed run (phase times need an unrecorded pscl_run or the three calls)");
     for (int i = 0; i < 5; i++) CU(cudaEventElapsedTime(&ms[i], j->ev[i], j->ev[i + 1]));
+    return PSCL_OK;
+}
+
+// ------------------------------------------------------------------ uneven batch
+// Independent point sets, each min-max scaled on its own and clustered by its own seeded
+// Lloyd run; every launch covers all sets (work units of at most 1024 rows of one set),
+// and a run is recorded once into a CUDA graph.
+struct pscl_batch : Owner {
+    int d = 0, n_inst = 0;
+    int64_t rows = 0;
+    std::vector<int64_t> starts;
+    std::vector<int32_t> sizes, keff;
+    const float *dev_in = nullptr;
+    float *raw = nullptr, *x = nullptr, *part = nullptr;
+    double *mn = nullptr, *mx = nullptr;
+    LloydPlan plan;
+    float *centers = nullptr;
+    unsigned long long *acc = nullptr;
+    int32_t *cnt = nullptr, *labels = nullptr, *out_labels = nullptr, *trace = nullptr;
+    int64_t trace_len = 0;
+    double *unit_sse = nullptr, *seg_sse = nullptr;
+    uint32_t *flags = nullptr;
+    int64_t unit_rows = 0;            // 0: the planner's default
+    int rpt = 0;                      // rows per thread of the float32 kernel, 0 = default
+    int trace_on = 0, graph = 1, plain = 0;
+    int iters = 0;
+    KTimer kt;
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t gkey[6] = {};
+    cudaEvent_t ev[2] = {};
+};
+
+static void batch_drop_graph(pscl_batch *b)
+{
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+}
+
+// (Re)build the work-unit plan and everything sized by it.
+static int batch_plan(pscl_batch *b)
+{
+    batch_drop_graph(b);
+    TRY(build_lloyd_plan(b, b->plan, b->starts, b->sizes, b->keff, b->unit_rows));
+    job_free(b, b->part);
+    job_free(b, b->unit_sse);
+    b->part = nullptr;
+    b->unit_sse = nullptr;
+    TRY(A(b, &b->part, 2 * (size_t)b->plan.n_units * b->d));
+    TRY(A(b, &b->unit_sse, b->plan.n_units));
+    return PSCL_OK;
+}
+
+extern "C" int pscl_batch_create(pscl_ctx *c, const void *points, int on_device, int32_t d, int32_t n_inst,
+                                 const int64_t *sizes, const int32_t *k, pscl_batch **out)
+{
+    if (!c || !out || !points || !sizes || !k) return fail(PSCL_EINVAL, "a required pointer is NULL");
+    if (d < 1 || d > kMaxD) return fail(PSCL_EINVAL, "d=%d outside 1..%d", d, kMaxD);
+    if (n_inst < 1) return fail(PSCL_EINVAL, "n_inst=%d < 1", n_inst);
+    int64_t rows = 0;
+    for (int i = 0; i < n_inst; i++) {
+        if (sizes[i] < 1 || sizes[i] > (int64_t)INT32_MAX)
+            return fail(PSCL_EINVAL, "instance %d: size %lld outside 1..2^31-1", i, (long long)sizes[i]);
+        if (k[i] < 1 || k[i] > kMaxK) return fail(PSCL_EINVAL, "instance %d: k=%d outside 1..%d", i, k[i], kMaxK);
+        rows += sizes[i];
+    }
+    if (rows > (int64_t)INT32_MAX) return fail(PSCL_EINVAL, "%lld rows in all exceed 2^31-1", (long long)rows);
+    CU(cudaSetDevice(c->device));
+    pscl_batch *b = new pscl_batch();
+    b->ctx = c;
+    b->d = d;
+    b->n_inst = n_inst;
+    b->rows = rows;
+    b->starts.resize(n_inst);
+    b->sizes.resize(n_inst);
+    b->keff.resize(n_inst);
+    int64_t P = 0, off = 0;
+    for (int i = 0; i < n_inst; i++) {
+        b->starts[i] = off;
+        b->sizes[i] = (int32_t)sizes[i];
+        b->keff[i] = (int32_t)std::min<int64_t>(k[i], sizes[i]);
+        off += sizes[i];
+        P += b->keff[i];
+    }
+    int rc = PSCL_OK;
+    if (on_device) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, points) != cudaSuccess || at.type != cudaMemoryTypeDevice ||
+            at.device != c->device || ((uintptr_t)points & 15) != 0) {
+            cudaGetLastError();
+            rc = fail(PSCL_EINVAL, "points_on_device=1 but the pointer is not 16-byte aligned device memory of device %d",
+                      c->device);
+        }
+        b->dev_in = static_cast<const float *>(points);
+    } else {
+        rc = A(b, &b->raw, (size_t)rows * d);
+        if (!rc && cudaMemcpyAsync(b->raw, points, (size_t)rows * d * sizeof(float), cudaMemcpyHostToDevice,
+                                   c->stream) != cudaSuccess)
+            rc = fail(PSCL_ECUDA, "upload of the points failed");
+        b->dev_in = b->raw;
+    }
+    if (!rc) rc = A(b, &b->x, (size_t)rows * d);
+    if (!rc) rc = A(b, &b->mn, (size_t)n_inst * d);
+    if (!rc) rc = A(b, &b->mx, (size_t)n_inst * d);
+    if (!rc) rc = A(b, &b->centers, (size_t)P * d);
+    if (!rc) rc = A(b, &b->acc, (size_t)P * d);
+    if (!rc) rc = A(b, &b->cnt, 2 * (size_t)P);
+    if (!rc) rc = A(b, &b->labels, rows);
+    if (!rc) rc = A(b, &b->out_labels, rows);
+    if (!rc) rc = A(b, &b->seg_sse, n_inst);
+    if (!rc) rc = A(b, &b->flags, kFlagWords);
+    if (!rc) rc = batch_plan(b);
+    for (int i = 0; i < 2 && !rc; i++)
+        if (cudaEventCreate(&b->ev[i]) != cudaSuccess) rc = fail(PSCL_ECUDA, "cudaEventCreate failed");
+    if (rc) {
+        std::string msg = g_err;
+        pscl_batch_destroy(b);
+        g_err = msg;
+        return rc;
+    }
+    *out = b;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_batch_load(pscl_batch *b, const void *points, int on_device)
+{
+    if (!b || !points) return fail(PSCL_EINVAL, "batch or points is NULL");
+    CU(cudaSetDevice(b->ctx->device));
+    if (on_device) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, points) != cudaSuccess || at.type != cudaMemoryTypeDevice ||
+            at.device != b->ctx->device || ((uintptr_t)points & 15) != 0) {
+            cudaGetLastError();
+            return fail(PSCL_EINVAL, "points_on_device=1 but the pointer is not 16-byte aligned device memory of device %d",
+                        b->ctx->device);
+        }
+        if (b->dev_in != points) batch_drop_graph(b);
+        b->dev_in = static_cast<const float *>(points);
+        return PSCL_OK;
+    }
+    if (!b->raw) TRY(A(b, &b->raw, (size_t)b->rows * b->d));
+    if (b->dev_in != b->raw) batch_drop_graph(b);
+    CU(cudaMemcpyAsync(b->raw, points, (size_t)b->rows * b->d * sizeof(float), cudaMemcpyHostToDevice, b->ctx->stream));
+    b->dev_in = b->raw;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_batch_destroy(pscl_batch *b)
+{
+    if (!b) return fail(PSCL_EINVAL, "batch is NULL");
+    cudaSetDevice(b->ctx->device);
+    cudaStreamSynchronize(b->ctx->stream);
+    batch_drop_graph(b);
+    for (auto &a : b->allocs) {
+        cudaFree(a.p);
+        b->ctx->in_use -= a.bytes;
+    }
+    for (int i = 0; i < 2; i++)
+        if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+    delete b;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_batch_set_option(pscl_batch *b, int opt, int64_t v)
+{
+    if (!b) return fail(PSCL_EINVAL, "batch is NULL");
+    switch (opt) {
+    case PSCL_OPT_TRACE_LABELS: b->trace_on = v != 0; break;
+    case PSCL_OPT_GRAPH: b->graph = v != 0; break;
+    case PSCL_OPT_PLAIN_LLOYD: b->plain = v != 0; break;
+    case PSCL_OPT_UNIT_ROWS:
+        if (v < 0 || v > 1024) return fail(PSCL_EINVAL, "unit rows %lld outside 0..1024", (long long)v);
+        b->unit_rows = v;
+        return batch_plan(b);
+    case PSCL_OPT_ROWS_PER_THREAD:
+        if (v != 0 && v != 1) return fail(PSCL_EINVAL, "rows per thread must be 0 (default) or 1");
+        b->rpt = (int)v;
+        break;
+    default: return fail(PSCL_EINVAL, "option %d does not apply to a batch", opt);
+    }
+    batch_drop_graph(b);
+    return PSCL_OK;
+}
+
+// Scale, seeded init (stage 0, segment = instance), `iters` iterations, per-instance SSE.
+static int batch_enqueue(pscl_batch *b, int iters, uint64_t seed, int prec, bool events)
+{
+    cudaStream_t st = b->ctx->stream;
+    const SegTable t = b->plan.table();
+    const int32_t *u0 = b->plan.d_unit0();
+    CU(cudaMemsetAsync(b->flags, 0, kFlagWords * sizeof(uint32_t), st));
+    CU(launch_seg_scale(b->dev_in, b->x, t, u0, b->d, b->part, b->mn, b->mx, b->flags, st, &b->kt));
+    LloydBuffers lb{};
+    lb.pts = b->x;
+    lb.centers = b->centers;
+    lb.acc = b->acc;
+    lb.count = b->cnt;
+    lb.labels = b->labels;
+    lb.trace = b->trace_on ? b->trace : nullptr;
+    lb.rows = b->rows;
+    const int64_t P = b->plan.P;
+    CU(launch_lloyd_init(lb, t, b->d, P, seed, 0u, 0, b->plan.kmax, st, &b->kt));
+    if (events) CU(cudaEventRecord(b->ev[0], st));
+    if (!b->plain) {
+        for (int it = 0; it < iters; it++) {
+            lb.count = b->cnt + (size_t)(it & 1) * P;
+            CU(launch_lloyd_iter(lb, b->cnt + (size_t)((it + 1) & 1) * P, t, b->d, it, 0, b->plan.n_units, 0, P,
+                                 b->plan.kmax, prec, b->flags, b->ctx->sm_count, st, &b->kt, b->rpt));
+        }
+    } else {                           // one launch pair per instance and iteration
+        const LloydPlan &p = b->plan;
+        for (int s = 0; s < p.n_seg; s++) {
+            for (int it = 0; it < iters; it++) {
+                lb.count = b->cnt + (size_t)(it & 1) * P;
+                CU(launch_lloyd_iter(lb, b->cnt + (size_t)((it + 1) & 1) * P, t, b->d, it, p.seg_unit0[s],
+                                     p.seg_unit0[s + 1], p.cen_off[s], (int64_t)p.cen_off[s] + p.k_eff[s], p.k_eff[s],
+                                     prec, b->flags, b->ctx->sm_count, st, &b->kt, b->rpt));
+            }
+        }
+    }
+    if (events) CU(cudaEventRecord(b->ev[1], st));
+    CU(launch_seg_sse(b->x, t, u0, b->d, b->centers, b->plan.kmax, b->out_labels, b->unit_sse, b->seg_sse, st,
+                      &b->kt));
+    return PSCL_OK;
+}
+
+extern "C" int pscl_batch_run(pscl_batch *b, int32_t iters, uint64_t seed, int prec)
+{
+    if (!b) return fail(PSCL_EINVAL, "batch is NULL");
+    if (iters < 0) return fail(PSCL_EINVAL, "iters < 0");
+    TRY(check_prec(prec));
+    CU(cudaSetDevice(b->ctx->device));
+    int64_t tl = b->trace_on ? (int64_t)iters * b->rows : 0;
+    if (tl != b->trace_len) {
+        batch_drop_graph(b);
+        job_free(b, b->trace);
+        b->trace = nullptr;
+        b->trace_len = tl;
+        if (tl) TRY(A(b, &b->trace, tl));
+    }
+    b->iters = iters;
+    b->kt.reset();
+    if (!b->graph) return batch_enqueue(b, iters, seed, prec, true);
+    const uint64_t key[6] = {(uint64_t)iters, seed, (uint64_t)prec, (uint64_t)(b->trace_on | b->plain << 1),
+                             (uint64_t)b->unit_rows, (uint64_t)b->rpt};
+    if (b->gexec && memcmp(key, b->gkey, sizeof key) != 0) batch_drop_graph(b);
+    cudaStream_t st = b->ctx->stream;
+    if (!b->gexec) {
+        cudaGraph_t g = nullptr;
+        CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int rc = batch_enqueue(b, iters, seed, prec, false);
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(PSCL_ECUDA, "stream capture failed: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            b->gexec = nullptr;
+            return fail(PSCL_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+        }
+        memcpy(b->gkey, key, sizeof key);
+    }
+    CU(cudaGraphLaunch(b->gexec, st));
+    return PSCL_OK;
+}
+
+extern "C" int pscl_batch_sync(pscl_batch *b)
+{
+    if (!b) return fail(PSCL_EINVAL, "batch is NULL");
+    CU(cudaSetDevice(b->ctx->device));
+    CU(cudaStreamSynchronize(b->ctx->stream));
+    uint32_t h[kFlagWords];
+    CU(cudaMemcpy(h, b->flags, sizeof h, cudaMemcpyDeviceToHost));
+    if (h[0]) return fail(PSCL_EINVAL, "the input holds a value that is not finite");
+    if (h[1] & 4u) return fail(PSCL_ETIMEOUT, "a bounded device-side wait gave up (tensor-core commit)");
+    return PSCL_OK;
+}
+
+extern "C" int pscl_batch_get(pscl_batch *b, float *centers, int32_t *labels, double *sse)
+{
+    TRY(pscl_batch_sync(b));
+    if (centers) CU(cudaMemcpy(centers, b->centers, (size_t)b->plan.P * b->d * sizeof(float), cudaMemcpyDeviceToHost));
+    if (labels) CU(cudaMemcpy(labels, b->out_labels, (size_t)b->rows * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (sse) CU(cudaMemcpy(sse, b->seg_sse, (size_t)b->n_inst * sizeof(double), cudaMemcpyDeviceToHost));
+    return PSCL_OK;
+}
+
+extern "C" int pscl_batch_get_scaled(pscl_batch *b, float *out)
+{
+    TRY(pscl_batch_sync(b));
+    if (!out) return fail(PSCL_EINVAL, "out is NULL");
+    CU(cudaMemcpy(out, b->x, (size_t)b->rows * b->d * sizeof(float), cudaMemcpyDeviceToHost));
+    return PSCL_OK;
+}
+
+extern "C" int pscl_batch_get_label_trace(pscl_batch *b, int32_t *out)
+{
+    TRY(pscl_batch_sync(b));
+    if (!out) return fail(PSCL_EINVAL, "out is NULL");
+    if (!b->trace_len) return fail(PSCL_ESTATE, "no label trace was recorded (PSCL_OPT_TRACE_LABELS)");
+    CU(cudaMemcpy(out, b->trace, (size_t)b->trace_len * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    return PSCL_OK;
+}
+
+extern "C" int pscl_batch_lloyd_ms(pscl_batch *b, float *ms)
+{
+    TRY(pscl_batch_sync(b));
+    if (!ms) return fail(PSCL_EINVAL, "ms is NULL");
+    if (b->graph) return fail(PSCL_ESTATE, "Lloyd time is kept only for runs outside a graph (PSCL_OPT_GRAPH 0)");
+    CU(cudaEventElapsedTime(ms, b->ev[0], b->ev[1]));
+    return PSCL_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+// Work-unit size and rows per thread of the assignment kernel, chosen by timing a few
+// Lloyd iterations of the batch itself for every candidate.  Neither changes any result
+// (the sums are exact integers), only the time.  Choices are remembered per (device, d,
+// largest k, log2 of the rows, precision) for the life of the process.
+struct TuneKey {
+    int device, d, kmax, lg_rows, prec;
+    bool operator==(const TuneKey &o) const
+    {
+        return device == o.device && d == o.d && kmax == o.kmax && lg_rows == o.lg_rows && prec == o.prec;
+    }
+};
+struct TuneChoice {
+    TuneKey key;
+    int64_t unit_rows;
+    int rpt;
+};
+static std::vector<TuneChoice> g_tuned;
+
+extern "C" int pscl_batch_tune(pscl_batch *b, int32_t iters, int prec, int64_t *unit_rows, int32_t *rows_per_thread,
+                               int32_t *cached)
+{
+    if (!b) return fail(PSCL_EINVAL, "batch is NULL");
+    if (iters < 1) return fail(PSCL_EINVAL, "iters < 1");
+    TRY(check_prec(prec));
+    CU(cudaSetDevice(b->ctx->device));
+    int lg = 0;
+    while ((int64_t)1 << (lg + 1) <= b->rows) lg++;
+    const TuneKey key{b->ctx->device, b->d, b->plan.kmax, lg, prec};
+    int hit = 0;
+    for (auto &c : g_tuned) {
+        if (c.key == key) {
+            b->unit_rows = c.unit_rows;
+            b->rpt = c.rpt;
+            hit = 1;
+            break;
+        }
+    }
+    if (!hit) {
+        const int save_graph = b->graph, save_trace = b->trace_on;
+        b->graph = 0;
+        b->trace_on = 0;
+        static const int64_t units[] = {128, 256, 512, 1024};
+        float best = 0.0f;
+        int64_t best_u = 0;
+        int best_r = 0;
+        for (int64_t u : units) {
+            for (int r = 0; r < 2; r++) {
+                b->unit_rows = u;
+                b->rpt = r;
+                TRY(batch_plan(b));
+                TRY(pscl_batch_run(b, 1, 0, prec));           // warm-up
+                TRY(pscl_batch_run(b, iters, 0, prec));
+                float ms = 0.0f;
+                TRY(pscl_batch_lloyd_ms(b, &ms));
+                if (best_u == 0 || ms < best) {
+                    best = ms;
+                    best_u = u;
+                    best_r = r;
+                }
+            }
+        }
+        b->graph = save_graph;
+        b->trace_on = save_trace;
+        b->unit_rows = best_u;
+        b->rpt = best_r;
+        g_tuned.push_back({key, best_u, best_r});
+    }
+    TRY(batch_plan(b));
+    if (unit_rows) *unit_rows = b->unit_rows;
+    if (rows_per_thread) *rows_per_thread = b->rpt;
+    if (cached) *cached = hit;
     return PSCL_OK;
 }

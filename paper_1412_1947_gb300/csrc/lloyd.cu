@@ -389,13 +389,6 @@ k_final_sse(const float *__restrict__ x, int64_t n, int d, const float *__restri
     *ticket = 0;
 }
 
-// rows kept in registers per thread: 64 floats of rows at most
-template <int D>
-__host__ __device__ constexpr int kRowsPerThread()
-{
-    return D <= 0 ? 1 : (D >= 64 ? 1 : 64 / D > 4 ? 4 : 64 / D);
-}
-
 int center_chunk(int d, int k)
 {
     int c = kCenterChunkBytes / (d * 4);
@@ -403,9 +396,98 @@ int center_chunk(int d, int k)
     return c >= k ? k : c;
 }
 
+// Per work unit of independent sets: the nearest center of every row among its set's
+// centers (float32 direct form, lowest index on ties) and the sum of those squared
+// distances in double (per thread in row order, then a fixed tree over the block).
 template <int D>
-cudaError_t assign_dispatch(const LloydBuffers &b, const SegTable &t, int d, int iter, int unit_lo,
-                            int unit_hi, int kmax, cudaStream_t st, KTimer *kt)
+__global__ void __launch_bounds__(kThreads)
+k_seg_sse(const float *__restrict__ pts, SegTable t, int d, const float *__restrict__ centers, int chunk_k,
+          int32_t *labels, double *unit_sse)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *sc = reinterpret_cast<float *>(smem);
+    const int u = blockIdx.x;
+    const int s = t.unit_seg[u];
+    const int k = t.k_eff[s];
+    const int64_t c0 = t.cen_off[s];
+    const int64_t row0 = t.seg_start[s] + t.unit_start[u];
+    const int rows = t.unit_count[u];
+    const int dd = D > 0 ? D : d;
+    double part = 0.0;
+    for (int p0 = 0; p0 < rows; p0 += kThreads) {
+        const int p = p0 + threadIdx.x;
+        const bool live = p < rows;
+        const float *xr = pts + (row0 + (live ? p : 0)) * dd;
+        float xv[D > 0 ? D : 1];
+        if (D > 0) {
+#pragma unroll
+            for (int j = 0; j < (D > 0 ? D : 1); j++) xv[j] = __ldg(&xr[j]);
+        }
+        const float *xp = D > 0 ? xv : xr;
+        float best = __int_as_float(0x7f800000);
+        int bj = 0;
+        for (int cb = 0; cb < k; cb += chunk_k) {
+            const int ce = min(k, cb + chunk_k);
+            __syncthreads();
+            for (int e = threadIdx.x; e < (ce - cb) * dd; e += kThreads) sc[e] = centers[(c0 + cb) * dd + e];
+            __syncthreads();
+            if (live) {
+                for (int j = cb; j < ce; j++) {
+                    const float v = dist_direct<D>(xp, sc + (size_t)(j - cb) * dd, dd);
+                    if (v < best) { best = v; bj = j; }
+                }
+            }
+        }
+        if (live) {
+            labels[row0 + p] = bj;
+            part = __dadd_rn(part, (double)best);
+        }
+    }
+    for (int o = 16; o; o >>= 1) part = __dadd_rn(part, __shfl_down_sync(0xffffffffu, part, o));
+    __shared__ double ws[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = ws[0];
+        for (int w = 1; w < kThreads / 32; w++) b = __dadd_rn(b, ws[w]);
+        unit_sse[u] = b;
+    }
+}
+
+// SSE of every set: its units' sums in unit order.
+__global__ void k_seg_sse_fold(const double *unit_sse, const int32_t *seg_unit0, int n_seg, double *seg_sse)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_seg) return;
+    double v = 0.0;
+    for (int u = seg_unit0[s]; u < seg_unit0[s + 1]; u++) v = __dadd_rn(v, unit_sse[u]);
+    seg_sse[s] = v;
+}
+
+template <int D>
+cudaError_t seg_sse_dispatch(const float *pts, const SegTable &t, int d, const float *centers, int kmax,
+                             int32_t *labels, double *unit_sse, cudaStream_t st, KTimer *kt)
+{
+    const int chunk = center_chunk(d, kmax);
+    const size_t smem = (size_t)chunk * d * 4;
+    auto kern = k_seg_sse<D>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kt->begin(st);
+    kern<<<t.n_units, kThreads, smem, st>>>(pts, t, d, centers, chunk, labels, unit_sse);
+    kt->end(PSCL_K_FINAL_SSE, st);
+    return cudaGetLastError();
+}
+
+// rows kept in registers per thread: 64 floats of rows at most
+template <int D>
+__host__ __device__ constexpr int kRowsPerThread()
+{
+    return D <= 0 ? 1 : (D >= 64 ? 1 : 64 / D > 4 ? 4 : 64 / D);
+}
+
+template <int D, int R>
+cudaError_t assign_launch(const LloydBuffers &b, const SegTable &t, int d, int iter, int unit_lo,
+                          int unit_hi, int kmax, cudaStream_t st, KTimer *kt)
 {
     const int chunk = center_chunk(d, kmax);
     const size_t acc_bytes = (size_t)kmax * d * 8 + (size_t)kmax * 4;
@@ -415,14 +497,14 @@ cudaError_t assign_dispatch(const LloydBuffers &b, const SegTable &t, int d, int
     const int grid = unit_hi - unit_lo;
     if (grid <= 0) return cudaSuccess;
     if (smem_acc) {
-        auto kern = k_lloyd_assign<D, kRowsPerThread<D>(), true>;
+        auto kern = k_lloyd_assign<D, R, true>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kt->begin(st);
         kern<<<grid, kThreads, smem, st>>>(b.pts, t, d, b.centers, b.acc, b.count, b.labels, b.trace,
                                            (int64_t)iter * b.rows, unit_lo, chunk);
         kt->end(PSCL_K_LLOYD_ASSIGN, st);
     } else {
-        auto kern = k_lloyd_assign<D, kRowsPerThread<D>(), false>;
+        auto kern = k_lloyd_assign<D, R, false>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kt->begin(st);
         kern<<<grid, kThreads, smem, st>>>(b.pts, t, d, b.centers, b.acc, b.count, b.labels, b.trace,
@@ -430,6 +512,17 @@ cudaError_t assign_dispatch(const LloydBuffers &b, const SegTable &t, int d, int
         kt->end(PSCL_K_LLOYD_ASSIGN, st);
     }
     return cudaGetLastError();
+}
+
+// rows_per_thread: 0 = kRowsPerThread<D>(), 1 = one row per thread (a tuning choice; the
+// result is the same)
+template <int D>
+cudaError_t assign_dispatch(const LloydBuffers &b, const SegTable &t, int d, int iter, int unit_lo,
+                            int unit_hi, int kmax, int rows_per_thread, cudaStream_t st, KTimer *kt)
+{
+    if (rows_per_thread == 1 && kRowsPerThread<D>() > 1)
+        return assign_launch<D, 1>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt);
+    return assign_launch<D, kRowsPerThread<D>()>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt);
 }
 
 template <int D>
@@ -478,19 +571,19 @@ cudaError_t launch_lloyd_init(const LloydBuffers &b, const SegTable &t, int d, i
 cudaError_t launch_lloyd_iter(const LloydBuffers &b, int32_t *count_next, const SegTable &t, int d,
                               int iter, int unit_lo, int unit_hi, int64_t cen_lo, int64_t cen_hi,
                               int kmax, int prec, uint32_t *flags, int sm_count, cudaStream_t st,
-                              KTimer *kt)
+                              KTimer *kt, int rows_per_thread)
 {
     cudaError_t e;
     if (prec != PSCL_PREC_FP32 && tc_supported(d, kmax, prec)) {
-        e = launch_lloyd_assign_tc(b, t, d, iter, unit_lo, unit_hi, kmax, prec, flags, st, kt);
+        e = launch_lloyd_assign_tc(b, t, d, iter, unit_lo, unit_hi, kmax, prec, flags, sm_count, st, kt);
     } else switch (d) {
-    case 2: e = assign_dispatch<2>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt); break;
-    case 4: e = assign_dispatch<4>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt); break;
-    case 8: e = assign_dispatch<8>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt); break;
-    case 16: e = assign_dispatch<16>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt); break;
-    case 32: e = assign_dispatch<32>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt); break;
-    case 64: e = assign_dispatch<64>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt); break;
-    default: e = assign_dispatch<0>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt); break;
+    case 2: e = assign_dispatch<2>(b, t, d, iter, unit_lo, unit_hi, kmax, rows_per_thread, st, kt); break;
+    case 4: e = assign_dispatch<4>(b, t, d, iter, unit_lo, unit_hi, kmax, rows_per_thread, st, kt); break;
+    case 8: e = assign_dispatch<8>(b, t, d, iter, unit_lo, unit_hi, kmax, rows_per_thread, st, kt); break;
+    case 16: e = assign_dispatch<16>(b, t, d, iter, unit_lo, unit_hi, kmax, rows_per_thread, st, kt); break;
+    case 32: e = assign_dispatch<32>(b, t, d, iter, unit_lo, unit_hi, kmax, rows_per_thread, st, kt); break;
+    case 64: e = assign_dispatch<64>(b, t, d, iter, unit_lo, unit_hi, kmax, rows_per_thread, st, kt); break;
+    default: e = assign_dispatch<0>(b, t, d, iter, unit_lo, unit_hi, kmax, rows_per_thread, st, kt); break;
     }
     if (e != cudaSuccess) return e;
     int64_t work = (cen_hi - cen_lo) * d;
@@ -500,6 +593,25 @@ cudaError_t launch_lloyd_iter(const LloydBuffers &b, int32_t *count_next, const 
     kt->begin(st);
     k_lloyd_finalize<<<(int)g, 256, 0, st>>>(b.centers, b.acc, b.count, count_next, cen_lo, cen_hi, d);
     kt->end(PSCL_K_LLOYD_FINALIZE, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_sse(const float *pts, const SegTable &t, const int32_t *seg_unit0, int d,
+                           const float *centers, int kmax, int32_t *labels, double *unit_sse, double *seg_sse,
+                           cudaStream_t st, KTimer *kt)
+{
+    cudaError_t e;
+    switch (d) {
+    case 2: e = seg_sse_dispatch<2>(pts, t, d, centers, kmax, labels, unit_sse, st, kt); break;
+    case 4: e = seg_sse_dispatch<4>(pts, t, d, centers, kmax, labels, unit_sse, st, kt); break;
+    case 8: e = seg_sse_dispatch<8>(pts, t, d, centers, kmax, labels, unit_sse, st, kt); break;
+    case 16: e = seg_sse_dispatch<16>(pts, t, d, centers, kmax, labels, unit_sse, st, kt); break;
+    case 32: e = seg_sse_dispatch<32>(pts, t, d, centers, kmax, labels, unit_sse, st, kt); break;
+    case 64: e = seg_sse_dispatch<64>(pts, t, d, centers, kmax, labels, unit_sse, st, kt); break;
+    default: e = seg_sse_dispatch<0>(pts, t, d, centers, kmax, labels, unit_sse, st, kt); break;
+    }
+    if (e != cudaSuccess) return e;
+    k_seg_sse_fold<<<(t.n_seg + 255) / 256, 256, 0, st>>>(unit_sse, seg_unit0, t.n_seg, seg_sse);
     return cudaGetLastError();
 }
 

@@ -30,6 +30,8 @@
 // The centroid sums are the same exact fixed-point sums as in the float32 path.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "pscl_internal.cuh"
 
 namespace pscl {
@@ -205,17 +207,42 @@ __device__ __forceinline__ void issue_mma(uint32_t dcol, uint32_t a_smem, uint32
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_smem));
 }
 
-__device__ __forceinline__ uint32_t tmem_cols(int np)
+__device__ __host__ __forceinline__ uint32_t tmem_cols(int np)
 {
     return np <= 32 ? 32u : (np <= 64 ? 64u : (np <= 128 ? 128u : 256u));
 }
 
-// One assignment step over work units [unit_lo, unit_lo + gridDim.x) with k <= 256.
+// The sums of a run are kept as two 32-bit halves of the 32.32 fixed-point value, q >> 16
+// (<= 2^16 for coordinates in [0, 1]) and q & 0xFFFF, so 32768 rows can be added before
+// either half could wrap; they are folded into the 64-bit global sums that often.
+constexpr int kFoldTiles = 32768 / kTileRows;
+
+__device__ __forceinline__ void flush_sums(uint32_t *shi, uint32_t *slo, int32_t *scnt, int k, int64_t c0,
+                                           unsigned long long *acc, int32_t *count, int dd)
+{
+    for (int e = threadIdx.x; e < k * dd; e += kTcThreads) {
+        const unsigned long long v = ((unsigned long long)shi[e] << 16) + slo[e];
+        if (v) atomicAdd(&acc[c0 * dd + e], v);
+        shi[e] = 0u;
+        slo[e] = 0u;
+    }
+    for (int j = threadIdx.x; j < k; j += kTcThreads) {
+        const int v = scnt[j];
+        if (v) atomicAdd(&count[c0 + j], v);
+        scnt[j] = 0;
+    }
+}
+
+// One assignment step.  CTA c serves the units [split[c], split[c+1]) (a persistent
+// launch over all units) or the single unit unit_lo + c (split == NULL).  Its units form
+// runs of consecutive units of one set; per run the set's operand B, reference point and
+// sums are set up once and its rows stream through the tensor cores in 128-row tiles,
+// two deep when two TMEM regions of ncols columns fit (nbuf = 2), else one at a time.
 template <int D, int MODE>
 __global__ void __launch_bounds__(kTcThreads)
-k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const float *__restrict__ centers,
-                  unsigned long long *acc, int32_t *count, int32_t *labels, int32_t *trace, int64_t trace_off,
-                  int unit_lo, uint32_t *flags)
+k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *split, int unit_lo,
+                  const float *__restrict__ centers, unsigned long long *acc, int32_t *count, int32_t *labels,
+                  int32_t *trace, int64_t trace_off, int kmax, int nbuf, uint32_t ncols, uint32_t *flags)
 {
     using L = TcLayout<D, MODE>;
     using O = Op<MODE>;
@@ -223,283 +250,352 @@ k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const float *__rest
     __shared__ uint64_t mbar[2];
     __shared__ uint32_t tmem_slot;
     __shared__ float s_ref[D];
+    __shared__ float s_part[kTcThreads];
     __shared__ float s_cmax2;
     __shared__ int s_fail;
+    __shared__ uint32_t s_stat[2];
 
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int u = unit_lo + blockIdx.x;
-    const int s = t.unit_seg[u];
-    const int k = t.k_eff[s];
-    const int np = (k + 15) & ~15;                                 // MMA N
-    const int64_t c0 = t.cen_off[s];
-    const int64_t row0 = t.seg_start[s] + t.unit_start[u];
-    const int rows = t.unit_count[u];
-    const int ntiles = (rows + kTileRows - 1) / kTileRows;
-    const uint32_t ncols = tmem_cols(np);                          // per TMEM region
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ub = split ? split[blockIdx.x] : unit_lo + (int)blockIdx.x;
+    const int ue = split ? split[blockIdx.x + 1] : ub + 1;
+    const int npmax = (kmax + 15) & ~15;
 
-    // [A0 | A1 | B | float32 centers | high sums | low sums | counts]
+    // [A buffers | B | high sums | low sums | counts]
     unsigned char *sa0 = smem;
-    unsigned char *sb = sa0 + 2 * L::kABytes;
-    float *sc = reinterpret_cast<float *>(sb + (((uint32_t)(np / 8) * L::kGroup + 127) & ~127u));
-    uint32_t *shi = reinterpret_cast<uint32_t *>(sc + (size_t)k * D);
-    uint32_t *slo = shi + (size_t)k * D;
-    int32_t *scnt = reinterpret_cast<int32_t *>(slo + (size_t)k * D);
+    unsigned char *sb = sa0 + (size_t)nbuf * L::kABytes;
+    uint32_t *shi = reinterpret_cast<uint32_t *>(sb + (((uint32_t)(npmax / 8) * L::kGroup + 127) & ~127u));
+    uint32_t *slo = shi + (size_t)kmax * D;
+    int32_t *scnt = reinterpret_cast<int32_t *>(slo + (size_t)kmax * D);
 
-    // ---- set-up: accumulators, centers, reference point, B operand, TMEM, mbarriers
-    for (int e = tid; e < k * D; e += kTcThreads) {
-        shi[e] = 0u;
-        slo[e] = 0u;
-        sc[e] = centers[c0 * D + e];
-    }
-    for (int j = tid; j < k; j += kTcThreads) scnt[j] = 0;
     if (tid == 0) {
         s_fail = 0;
-        s_cmax2 = 0.0f;
+        s_stat[0] = 0u;
+        s_stat[1] = 0u;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();
-    for (int a = tid; a < D; a += kTcThreads) {              // reference: mean of the centers
-        float m = 0.0f;
-        for (int j = 0; j < k; j++) m = __fadd_rn(m, sc[j * D + a]);
-        s_ref[a] = __fdiv_rn(m, (float)k);
+    for (int e = tid; e < kmax * D; e += kTcThreads) {
+        shi[e] = 0u;
+        slo[e] = 0u;
     }
-    if (warp == 0) {
+    for (int j = tid; j < kmax; j += kTcThreads) scnt[j] = 0;
+    if (warp == 0 && ub < ue) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_u32(&tmem_slot)), "r"(2 * ncols));
+                     ::"r"(smem_u32(&tmem_slot)), "r"((uint32_t)nbuf * ncols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     __syncthreads();
-    for (int j = tid; j < np; j += kTcThreads) {
-        float H[D], Lo[D], n2 = 0.0f;
-#pragma unroll
-        for (int a = 0; a < D; a++) {
-            const float cc = j < k ? __fsub_rn(sc[j * D + a], s_ref[a]) : 0.0f;
-            n2 = __fmaf_rn(cc, cc, n2);
-            const float m2 = -2.0f * cc;                          // exact
-            H[a] = O::rnd(m2);
-            Lo[a] = O::rnd(__fsub_rn(m2, H[a]));
-        }
-        float np_[O::kNormParts];
-        {
-            float rem = n2;
-#pragma unroll
-            for (int q = 0; q < O::kNormParts; q++) {
-                np_[q] = j < k ? O::rnd(rem) : 0.0f;
-                rem = __fsub_rn(rem, np_[q]);
-            }
-        }
-        put_row<D, MODE>(sb, j, [&](int e) -> float {
-            if (e < D) return H[e];
-            if (O::kTerms == 3) {
-                if (e < 2 * D) return Lo[e - D];
-                if (e < 3 * D) return H[e - 2 * D];
-            }
-            const int q = e - O::kTerms * D;
-            return q < O::kNormParts ? np_[q] : 0.0f;
-        });
-        if (j < k) atomicMax(reinterpret_cast<int *>(&s_cmax2), __float_as_int(n2));   // non-negative floats
-    }
-    __syncthreads();
+    if (ub >= ue) return;
     const uint32_t tmem = tmem_slot;
-    const uint32_t idesc = O::idesc(np);
-    const float cmax = sqrtf(s_cmax2);
-    // error bound of v_j (factor 2 margin): products (eta_p each, the -2 counted), float32
-    // accumulation over K terms (2^-22 of the magnitude sum per term, allowing for
-    // non-IEEE accumulation), centring (2^-24 per operand), norm parts and their sum
-    const float alpha = 2.0f * (2.0f * O::eta_p() + 2.0f * (float)L::kK * 0x1p-22f + 0x1p-22f);
-    const float beta = 2.0f * ((float)L::kK * 0x1p-22f + (float)(D + 4) * 0x1p-24f + 0x1p-22f);
-
-    // write tile `tile`'s A operand into buffer `buf` (threads = rows)
-    auto stage = [&](int tile, int buf) {
-        const int p = tile * kTileRows + tid;
-        const bool live = p < rows;
-        const float *xr = pts + (row0 + (live ? p : 0)) * D;
-        float h[D], l[D];
-#pragma unroll
-        for (int a = 0; a < D; a++) {
-            const float xc = live ? __fsub_rn(__ldg(&xr[a]), s_ref[a]) : 0.0f;
-            h[a] = O::rnd(xc);
-            l[a] = O::rnd(__fsub_rn(xc, h[a]));
-        }
-        put_row<D, MODE>(sa0 + buf * L::kABytes, tid, [&](int e) { return a_elem<D, MODE>(e, h, l, live); });
-    };
-    // issue the MMAs of the tile staged in buffer `buf`, committed to mbar[buf]
-    auto issue = [=](int buf) {
-        issue_mma<D, MODE>(tmem + (uint32_t)buf * ncols, smem_u32(sa0 + buf * L::kABytes), smem_u32(sb), idesc,
-                           smem_u32(&mbar[buf]));
-    };
-
-    if (ntiles > 0) {
-        stage(0, 0);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) issue(0);
-    }
     uint32_t uses[2] = {0u, 0u};
-    int issued = ntiles > 0 ? 1 : 0;
-    for (int i = 0; i < ntiles; i++) {
-        const int buf = i & 1;
-        // stage and issue the next tile while this one is in flight
-        if (i + 1 < ntiles) {
-            stage(i + 1, buf ^ 1);
+    uint32_t issued[2] = {0u, 0u};
+    uint32_t n_tie = 0, n_live = 0;
+
+    for (int u = ub; u < ue;) {
+        const int s = t.unit_seg[u];
+        int ur = u + 1;
+        while (ur < ue && t.unit_seg[ur] == s) ur++;
+        const int k = t.k_eff[s];
+        const int np = (k + 15) & ~15;                             // MMA N
+        const int64_t c0 = t.cen_off[s];
+        const int64_t row0 = t.seg_start[s] + t.unit_start[u];
+        const int R = t.unit_start[ur - 1] + t.unit_count[ur - 1] - t.unit_start[u];
+        u = ur;
+
+        // ---- set-up of the run: reference point (mean of the centers), operand B, cmax
+        {
+            constexpr int G = kTcThreads / D;
+            const int a = tid % D, g = tid / D;
+            float m = 0.0f;
+            if (g < G)
+                for (int j = g; j < k; j += G) m = __fadd_rn(m, __ldg(&centers[(c0 + j) * D + a]));
+            s_part[tid] = m;
+            if (tid == 0) s_cmax2 = 0.0f;
+            __syncthreads();
+            if (tid < D) {
+                float tot = 0.0f;
+                for (int q = 0; q < G; q++) tot = __fadd_rn(tot, s_part[q * D + tid]);
+                s_ref[tid] = __fdiv_rn(tot, (float)k);
+            }
+            __syncthreads();
+        }
+        for (int j = tid; j < np; j += kTcThreads) {
+            float H[D], Lo[D], n2 = 0.0f;
+#pragma unroll
+            for (int a = 0; a < D; a++) {
+                const float cc = j < k ? __fsub_rn(__ldg(&centers[(c0 + j) * D + a]), s_ref[a]) : 0.0f;
+                n2 = __fmaf_rn(cc, cc, n2);
+                const float m2 = -2.0f * cc;                          // exact
+                H[a] = O::rnd(m2);
+                Lo[a] = O::rnd(__fsub_rn(m2, H[a]));
+            }
+            float np_[O::kNormParts];
+            {
+                float rem = n2;
+#pragma unroll
+                for (int q = 0; q < O::kNormParts; q++) {
+                    np_[q] = j < k ? O::rnd(rem) : 0.0f;
+                    rem = __fsub_rn(rem, np_[q]);
+                }
+            }
+            put_row<D, MODE>(sb, j, [&](int e) -> float {
+                if (e < D) return H[e];
+                if (O::kTerms == 3) {
+                    if (e < 2 * D) return Lo[e - D];
+                    if (e < 3 * D) return H[e - 2 * D];
+                }
+                const int q = e - O::kTerms * D;
+                return q < O::kNormParts ? np_[q] : 0.0f;
+            });
+            if (j < k) atomicMax(reinterpret_cast<int *>(&s_cmax2), __float_as_int(n2));   // non-negative floats
+        }
+        __syncthreads();
+        const uint32_t idesc = O::idesc(np);
+        const float cmax = sqrtf(s_cmax2);
+        // error bound of v_j (factor 2 margin): products (eta_p each, the -2 counted), float32
+        // accumulation over K terms (2^-22 of the magnitude sum per term, allowing for
+        // non-IEEE accumulation), centring (2^-24 per operand), norm parts and their sum
+        const float alpha = 2.0f * (2.0f * O::eta_p() + 2.0f * (float)L::kK * 0x1p-22f + 0x1p-22f);
+        const float beta = 2.0f * ((float)L::kK * 0x1p-22f + (float)(D + 4) * 0x1p-24f + 0x1p-22f);
+        const int ntiles = (R + kTileRows - 1) / kTileRows;
+
+        // write tile `tile`'s A operand into buffer `buf` (threads = rows)
+        auto stage = [&](int tile, int buf) {
+            const int p = tile * kTileRows + tid;
+            const bool live = p < R;
+            const float4 *x4 = reinterpret_cast<const float4 *>(pts + (row0 + (live ? p : 0)) * D);
+            float h[D], l[D];
+#pragma unroll
+            for (int a4 = 0; a4 < D / 4; a4++) {
+                const float4 v = __ldg(&x4[a4]);
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int a = 4 * a4 + q;
+                    const float xc = live ? __fsub_rn(vv[q], s_ref[a]) : 0.0f;
+                    h[a] = O::rnd(xc);
+                    l[a] = O::rnd(__fsub_rn(xc, h[a]));
+                }
+            }
+            put_row<D, MODE>(sa0 + buf * L::kABytes, tid, [&](int e) { return a_elem<D, MODE>(e, h, l, live); });
+        };
+        auto issue = [&](int buf) {
+            issue_mma<D, MODE>(tmem + (uint32_t)buf * ncols, smem_u32(sa0 + buf * L::kABytes), smem_u32(sb), idesc,
+                               smem_u32(&mbar[buf]));
+        };
+        auto stage_issue = [&](int tile, int buf) -> bool {
+            stage(tile, buf);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
-            if (s_fail) break;
-            if (tid == 0) issue(buf ^ 1);
-            issued++;
-        }
-        if (!mbar_wait(smem_u32(&mbar[buf]), uses[buf] & 1u)) s_fail = 1;
-        uses[buf]++;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (s_fail) break;
+            if (s_fail) return false;
+            if (tid == 0) issue(buf);
+            issued[buf]++;
+            return true;
+        };
 
-        // ---- epilogue: this thread's row is TMEM lane tid of region `buf`
-        const int p = i * kTileRows + tid;
-        const bool live = p < rows;
-        const float *xr = pts + (row0 + (live ? p : 0)) * D;
-        float xv[D], xn2 = 0.0f;
+        bool ok = ntiles == 0 || stage_issue(0, 0);
+        for (int i = 0; ok && i < ntiles; i++) {
+            const int buf = nbuf == 2 ? (i & 1) : 0;
+            // two deep: the next tile's MMAs run while this tile's epilogue does
+            if (nbuf == 2 && i + 1 < ntiles && !stage_issue(i + 1, buf ^ 1)) break;
+            if (!mbar_wait(smem_u32(&mbar[buf]), uses[buf] & 1u)) s_fail = 1;
+            uses[buf]++;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            __syncthreads();
+            if (s_fail) break;
+
+            // ---- epilogue: this thread's row is TMEM lane tid of region `buf`
+            const int p = i * kTileRows + tid;
+            const bool live = p < R;
+            const float4 *x4 = reinterpret_cast<const float4 *>(pts + (row0 + (live ? p : 0)) * D);
+            float xv[D], xn2 = 0.0f;
 #pragma unroll
-        for (int a = 0; a < D; a++) {
-            xv[a] = __ldg(&xr[a]);
-            const float xc = __fsub_rn(xv[a], s_ref[a]);
-            xn2 = __fmaf_rn(xc, xc, xn2);
-        }
-        const uint32_t trow = tmem + (uint32_t)buf * ncols + ((uint32_t)(warp * 32) << 16);
-        float best = __int_as_float(0x7f800000), second = best;
-        int bj = 0;
-        for (int cb = 0; cb < k; cb += 32) {
-            float v[32];
-            tmem_ld32(trow + (uint32_t)cb, v);
-#pragma unroll
-            for (int q = 0; q < 32; q++) {
-                const int j = cb + q;
-                if (j < k) {
-                    if (v[q] < best) {
-                        second = best;
-                        best = v[q];
-                        bj = j;
-                    } else if (v[q] < second) {
-                        second = v[q];
-                    }
-                }
+            for (int a4 = 0; a4 < D / 4; a4++) {
+                const float4 v = __ldg(&x4[a4]);
+                xv[4 * a4 + 0] = v.x;
+                xv[4 * a4 + 1] = v.y;
+                xv[4 * a4 + 2] = v.z;
+                xv[4 * a4 + 3] = v.w;
             }
-        }
-        // E bounds the error of every v_j; the float32 direct sums have their own error
-        // (<= (d+3) 2^-24 of a distance, at most (||x~|| + cmax)^2), added so that no center
-        // left out could win the float32 direct comparison
-        const float xn = sqrtf(xn2);
-        const float E = alpha * xn * cmax + beta * cmax * cmax +
-                        (float)(2 * (D + 3)) * 0x1p-24f * (xn + cmax) * (xn + cmax) + 0x1p-100f;
-        const bool tie = live && second - best <= 2.0f * E;
-        if (__any_sync(0xffffffffu, tie)) {
-            // re-score every center within 2E of the best with the float32 direct sum
-            float bd = __int_as_float(0x7f800000);
-            int bjj = bj;
+#pragma unroll
+            for (int a = 0; a < D; a++) {
+                const float xc = __fsub_rn(xv[a], s_ref[a]);
+                xn2 = __fmaf_rn(xc, xc, xn2);
+            }
+            const uint32_t trow = tmem + (uint32_t)buf * ncols + ((uint32_t)(warp * 32) << 16);
+            // best and second best, two independent chains (even / odd columns)
+            float b0 = __int_as_float(0x7f800000), s0 = b0, b1 = b0, s1 = b0;
+            int j0 = 0, j1 = 1;
             for (int cb = 0; cb < k; cb += 32) {
                 float v[32];
                 tmem_ld32(trow + (uint32_t)cb, v);
-                if (tie) {
 #pragma unroll
-                    for (int q = 0; q < 32; q++) {
-                        const int j = cb + q;
-                        if (j < k && v[q] <= best + 2.0f * E) {
-                            float dd = 0.0f;
+                for (int q = 0; q < 32; q += 2) {
+                    const float va = cb + q < k ? v[q] : __int_as_float(0x7f800000);
+                    const float vb = cb + q + 1 < k ? v[q + 1] : __int_as_float(0x7f800000);
+                    s0 = fminf(s0, fmaxf(b0, va));
+                    if (va < b0) { b0 = va; j0 = cb + q; }
+                    s1 = fminf(s1, fmaxf(b1, vb));
+                    if (vb < b1) { b1 = vb; j1 = cb + q + 1; }
+                }
+            }
+            float best, second;
+            int bj;
+            if (b1 < b0 || (b1 == b0 && j1 < j0)) {
+                best = b1; bj = j1; second = fminf(s1, b0);
+            } else {
+                best = b0; bj = j0; second = fminf(s0, b1);
+            }
+            // E bounds the error of every v_j; the float32 direct sums have their own error
+            // (<= (d+3) 2^-24 of a distance, at most (||x~|| + cmax)^2), added so that no center
+            // left out could win the float32 direct comparison
+            const float xn = sqrtf(xn2);
+            const float E = alpha * xn * cmax + beta * cmax * cmax +
+                            (float)(2 * (D + 3)) * 0x1p-24f * (xn + cmax) * (xn + cmax) + 0x1p-100f;
+            const bool tie = live && second - best <= 2.0f * E;
+            if (__any_sync(0xffffffffu, tie)) {
+                // re-score every center within 2E of the best with the float32 direct sum
+                float bd = __int_as_float(0x7f800000);
+                int bjj = bj;
+                for (int cb = 0; cb < k; cb += 32) {
+                    float v[32];
+                    tmem_ld32(trow + (uint32_t)cb, v);
+                    if (tie) {
 #pragma unroll
-                            for (int a = 0; a < D; a++) {
-                                const float tq = __fsub_rn(xv[a], sc[j * D + a]);
-                                dd = __fmaf_rn(tq, tq, dd);
-                            }
-                            if (dd < bd) {
-                                bd = dd;
-                                bjj = j;
+                        for (int q = 0; q < 32; q++) {
+                            const int j = cb + q;
+                            if (j < k && v[q] <= best + 2.0f * E) {
+                                const float *cj = centers + (c0 + j) * D;
+                                float dd = 0.0f;
+#pragma unroll
+                                for (int a = 0; a < D; a++) {
+                                    const float tq = __fsub_rn(xv[a], __ldg(&cj[a]));
+                                    dd = __fmaf_rn(tq, tq, dd);
+                                }
+                                if (dd < bd) {
+                                    bd = dd;
+                                    bjj = j;
+                                }
                             }
                         }
                     }
                 }
+                if (tie) bj = bjj;
             }
-            if (tie) bj = bjj;
-        }
-        {   // statistics: rows re-scored in float32 / rows assigned here
-            const uint32_t nt = __popc(__ballot_sync(0xffffffffu, tie));
-            const uint32_t nl = __popc(__ballot_sync(0xffffffffu, live));
-            if ((tid & 31) == 0) {
-                if (nt) atomicAdd(&flags[2], nt);
-                atomicAdd(&flags[3], nl);
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        if (live) {
-            const int64_t row = row0 + p;
-            labels[row] = bj;
-            if (trace) trace[trace_off + row] = bj;
-            atomicAdd(&scnt[bj], 1);
-            const size_t e0 = (size_t)bj * D;
+            n_tie += tie;
+            n_live += live;
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            if (live) {
+                const int64_t row = row0 + p;
+                labels[row] = bj;
+                if (trace) trace[trace_off + row] = bj;
+                atomicAdd(&scnt[bj], 1);
+                const size_t e0 = (size_t)bj * D;
 #pragma unroll
-            for (int a = 0; a < D; a++) {
-                const unsigned long long q = to_fix(xv[a]);
-                atomicAdd(&shi[e0 + a], (uint32_t)(q >> 11));
-                atomicAdd(&slo[e0 + a], (uint32_t)(q & 0x7FFu));
+                for (int a = 0; a < D; a++) {
+                    const unsigned long long q = to_fix(xv[a]);
+                    atomicAdd(&shi[e0 + a], (uint32_t)(q >> 16));
+                    atomicAdd(&slo[e0 + a], (uint32_t)(q & 0xFFFFu));
+                }
             }
+            if ((i + 1) % kFoldTiles == 0 && i + 1 < ntiles) {
+                __syncthreads();
+                flush_sums(shi, slo, scnt, k, c0, acc, count, D);
+            }
+            // one deep: the next tile after this epilogue released TMEM and the A buffer
+            if (nbuf == 1 && i + 1 < ntiles) {
+                __syncthreads();
+                if (!stage_issue(i + 1, 0)) break;
+            }
+        }
+        __syncthreads();
+        flush_sums(shi, slo, scnt, k, c0, acc, count, D);
+        if (s_fail) break;
+    }
+    {   // statistics: rows re-scored in float32 / rows assigned here
+        const uint32_t nt = __reduce_add_sync(0xffffffffu, n_tie);
+        const uint32_t nl = __reduce_add_sync(0xffffffffu, n_live);
+        if (lane == 0) {
+            atomicAdd(&s_stat[0], nt);
+            atomicAdd(&s_stat[1], nl);
         }
     }
     __syncthreads();
+    if (tid == 0) {
+        if (s_stat[0]) atomicAdd(&flags[2], s_stat[0]);
+        if (s_stat[1]) atomicAdd(&flags[3], s_stat[1]);
+    }
     if (s_fail) {
         // a commit never arrived: report, and give the MMAs still in flight a bounded
         // grace period before the tensor memory is released
         if (tid == 0) atomicOr(&flags[1], 4u);
         for (int b = 0; b < 2; b++)
-            if ((int)uses[b] < (issued + 1 - b) / 2) mbar_wait(smem_u32(&mbar[b]), uses[b] & 1u);
-    }
-    for (int e = tid; e < k * D; e += kTcThreads) {
-        const unsigned long long v = ((unsigned long long)shi[e] << 11) + slo[e];
-        if (v) atomicAdd(&acc[c0 * D + e], v);
-    }
-    for (int j = tid; j < k; j += kTcThreads) {
-        const int v = scnt[j];
-        if (v) atomicAdd(&count[c0 + j], v);
+            if (uses[b] < issued[b]) mbar_wait(smem_u32(&mbar[b]), uses[b] & 1u);
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * ncols));
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)nbuf * ncols));
 }
 
 template <int D, int MODE>
-size_t tc_smem_bytes(int kmax)
+size_t tc_smem_bytes(int kmax, int nbuf)
 {
     using L = TcLayout<D, MODE>;
     const int np = (kmax + 15) & ~15;
     const size_t b = ((size_t)(np / 8) * L::kGroup + 127) & ~(size_t)127;
-    return 2 * (size_t)L::kABytes + b + (size_t)kmax * D * 4 * 3 + (size_t)kmax * 4 + 1024;
+    return (size_t)nbuf * L::kABytes + b + (size_t)kmax * D * 4 * 2 + (size_t)kmax * 4 + 1024;
 }
+
+__host__ __forceinline__ int tc_nbuf(int kmax) { return tmem_cols((kmax + 15) & ~15) <= 128 ? 2 : 1; }
 
 template <int D, int MODE>
 cudaError_t tc_dispatch(const LloydBuffers &b, const SegTable &t, int iter, int unit_lo, int unit_hi, int kmax,
-                        uint32_t *flags, cudaStream_t st, KTimer *kt)
+                        uint32_t *flags, int sm_count, cudaStream_t st, KTimer *kt)
 {
-    const size_t smem = tc_smem_bytes<D, MODE>(kmax);
+    const int nbuf = tc_nbuf(kmax);
+    const uint32_t ncols = tmem_cols((kmax + 15) & ~15);
+    const size_t smem = tc_smem_bytes<D, MODE>(kmax, nbuf);
     auto kern = k_lloyd_assign_tc<D, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    const int32_t *split = nullptr;
+    int grid = unit_hi - unit_lo;
+    if (t.split && unit_lo == 0 && unit_hi == t.n_units) {
+        // persistent: as many CTAs per SM as shared memory, registers and the 512 TMEM
+        // columns allow (<= 4), counted here (the occupancy query answers 1 for this kernel)
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, kern);
+        if (e != cudaSuccess) return e;
+        int dev = 0, smem_sm = 0, reserved = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + reserved);
+        const int by_regs = 65536 / (((fa.numRegs + 7) & ~7) * kTcThreads);
+        const int by_tmem = (int)(512 / ((uint32_t)nbuf * ncols));
+        const int m = std::max(1, std::min(std::min(by_smem, by_regs), std::min(by_tmem, 4)));
+        split = t.split + t.split_off[m];
+        grid = m * sm_count;
+    }
     kt->begin(st);
-    kern<<<unit_hi - unit_lo, kTcThreads, smem, st>>>(b.pts, t, b.centers, b.acc, b.count, b.labels, b.trace,
-                                                      (int64_t)iter * b.rows, unit_lo, flags);
+    kern<<<grid, kTcThreads, smem, st>>>(b.pts, t, split, unit_lo, b.centers, b.acc, b.count, b.labels, b.trace,
+                                         (int64_t)iter * b.rows, kmax, nbuf, ncols, flags);
     kt->end(PSCL_K_LLOYD_ASSIGN, st);
     return cudaGetLastError();
 }
 
 template <int MODE>
 cudaError_t tc_by_d(const LloydBuffers &b, const SegTable &t, int d, int iter, int unit_lo, int unit_hi, int kmax,
-                    uint32_t *flags, cudaStream_t st, KTimer *kt)
+                    uint32_t *flags, int sm_count, cudaStream_t st, KTimer *kt)
 {
     switch (d) {
-    case 4: return tc_dispatch<4, MODE>(b, t, iter, unit_lo, unit_hi, kmax, flags, st, kt);
-    case 8: return tc_dispatch<8, MODE>(b, t, iter, unit_lo, unit_hi, kmax, flags, st, kt);
-    case 16: return tc_dispatch<16, MODE>(b, t, iter, unit_lo, unit_hi, kmax, flags, st, kt);
-    case 32: return tc_dispatch<32, MODE>(b, t, iter, unit_lo, unit_hi, kmax, flags, st, kt);
-    case 64: return tc_dispatch<64, MODE>(b, t, iter, unit_lo, unit_hi, kmax, flags, st, kt);
+    case 4: return tc_dispatch<4, MODE>(b, t, iter, unit_lo, unit_hi, kmax, flags, sm_count, st, kt);
+    case 8: return tc_dispatch<8, MODE>(b, t, iter, unit_lo, unit_hi, kmax, flags, sm_count, st, kt);
+    case 16: return tc_dispatch<16, MODE>(b, t, iter, unit_lo, unit_hi, kmax, flags, sm_count, st, kt);
+    case 32: return tc_dispatch<32, MODE>(b, t, iter, unit_lo, unit_hi, kmax, flags, sm_count, st, kt);
+    case 64: return tc_dispatch<64, MODE>(b, t, iter, unit_lo, unit_hi, kmax, flags, sm_count, st, kt);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -508,11 +604,11 @@ template <int MODE>
 size_t smem_by_d(int d, int kmax)
 {
     switch (d) {
-    case 4: return tc_smem_bytes<4, MODE>(kmax);
-    case 8: return tc_smem_bytes<8, MODE>(kmax);
-    case 16: return tc_smem_bytes<16, MODE>(kmax);
-    case 32: return tc_smem_bytes<32, MODE>(kmax);
-    case 64: return tc_smem_bytes<64, MODE>(kmax);
+    case 4: return tc_smem_bytes<4, MODE>(kmax, tc_nbuf(kmax));
+    case 8: return tc_smem_bytes<8, MODE>(kmax, tc_nbuf(kmax));
+    case 16: return tc_smem_bytes<16, MODE>(kmax, tc_nbuf(kmax));
+    case 32: return tc_smem_bytes<32, MODE>(kmax, tc_nbuf(kmax));
+    case 64: return tc_smem_bytes<64, MODE>(kmax, tc_nbuf(kmax));
     default: return ~(size_t)0;
     }
 }
@@ -546,14 +642,15 @@ bool tc_supported(int d, int kmax, int prec)
 }
 
 cudaError_t launch_lloyd_assign_tc(const LloydBuffers &b, const SegTable &t, int d, int iter, int unit_lo,
-                                   int unit_hi, int kmax, int prec, uint32_t *flags, cudaStream_t st, KTimer *kt)
+                                   int unit_hi, int kmax, int prec, uint32_t *flags, int sm_count, cudaStream_t st,
+                                   KTimer *kt)
 {
     if (unit_hi <= unit_lo) return cudaSuccess;
     switch (mode_of(prec)) {
-    case kModeBf16: return tc_by_d<kModeBf16>(b, t, d, iter, unit_lo, unit_hi, kmax, flags, st, kt);
-    case kModeTf32x3: return tc_by_d<kModeTf32x3>(b, t, d, iter, unit_lo, unit_hi, kmax, flags, st, kt);
-    case kModeBf16x3: return tc_by_d<kModeBf16x3>(b, t, d, iter, unit_lo, unit_hi, kmax, flags, st, kt);
-    default: return tc_by_d<kModeTf32>(b, t, d, iter, unit_lo, unit_hi, kmax, flags, st, kt);
+    case kModeBf16: return tc_by_d<kModeBf16>(b, t, d, iter, unit_lo, unit_hi, kmax, flags, sm_count, st, kt);
+    case kModeTf32x3: return tc_by_d<kModeTf32x3>(b, t, d, iter, unit_lo, unit_hi, kmax, flags, sm_count, st, kt);
+    case kModeBf16x3: return tc_by_d<kModeBf16x3>(b, t, d, iter, unit_lo, unit_hi, kmax, flags, sm_count, st, kt);
+    default: return tc_by_d<kModeTf32>(b, t, d, iter, unit_lo, unit_hi, kmax, flags, sm_count, st, kt);
     }
 }
 

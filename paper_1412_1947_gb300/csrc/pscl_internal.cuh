@@ -52,6 +52,10 @@ struct SegTable {
     const int32_t *unit_count;
     int n_seg;
     int n_units;
+    // Persistent launches over all units with m CTAs per SM (m = 1..4): CTA c serves the
+    // units [split[split_off[m] + c], split[split_off[m] + c + 1]) (NULL: no split).
+    const int32_t *split;
+    int split_off[5];
 };
 
 // Launch bookkeeping: every launcher counts its launches per pscl_kernel tag and, when
@@ -89,6 +93,10 @@ cudaError_t launch_scale(const float *raw, float *x, int64_t n, int d, float *pa
                          uint32_t *ticket, double *mn, double *mx, uint32_t *flags, int sm_count,
                          cudaStream_t st, KTimer *kt);
 size_t scale_part_floats(int64_t n, int d, int sm_count);
+// Independent sets: every set min-max scaled on its own (part: 2 x n_units x d floats,
+// mn / mx: n_seg x d).
+cudaError_t launch_seg_scale(const float *raw, float *x, const SegTable &t, const int32_t *seg_unit0, int d,
+                             float *part, double *mn, double *mx, uint32_t *flags, cudaStream_t st, KTimer *kt);
 
 // peel.cu
 struct PeelBuffers {
@@ -131,13 +139,18 @@ cudaError_t launch_lloyd_init(const LloydBuffers &b, const SegTable &t, int d, i
 cudaError_t launch_lloyd_iter(const LloydBuffers &b, int32_t *count_next, const SegTable &t,
                               int d, int iter, int unit_lo, int unit_hi, int64_t cen_lo,
                               int64_t cen_hi, int kmax, int prec, uint32_t *flags, int sm_count,
-                              cudaStream_t st, KTimer *kt);
+                              cudaStream_t st, KTimer *kt, int rows_per_thread = 0);
+// Independent sets: nearest center of every row within its set, per-set sums of the
+// squared distances (unit_sse: n_units doubles, seg_sse: n_seg doubles).
+cudaError_t launch_seg_sse(const float *pts, const SegTable &t, const int32_t *seg_unit0, int d,
+                           const float *centers, int kmax, int32_t *labels, double *unit_sse, double *seg_sse,
+                           cudaStream_t st, KTimer *kt);
 
 // lloyd_tc.cu
 bool tc_supported(int d, int kmax, int prec);
-cudaError_t launch_lloyd_assign_tc(const LloydBuffers &b, const SegTable &t, int d, int iter,
-                                   int unit_lo, int unit_hi, int kmax, int prec, uint32_t *flags,
-                                   cudaStream_t st, KTimer *kt);
+cudaError_t launch_lloyd_assign_tc(const LloydBuffers &b, const SegTable &t, int d, int iter, int unit_lo,
+                                   int unit_hi, int kmax, int prec, uint32_t *flags, int sm_count, cudaStream_t st,
+                                   KTimer *kt);
 cudaError_t launch_final_sse(const float *x, int64_t n, int d, const float *centers, int k,
                              int32_t *labels, double *blk_sse, double *sse, uint32_t *ticket,
                              int sm_count, cudaStream_t st, KTimer *kt);

@@ -106,7 +106,91 @@ __global__ void k_scale_apply(const float *__restrict__ raw, float *__restrict__
     }
 }
 
+// Independent sets (SegTable units): per unit, the column minima and maxima of its rows.
+// With d <= blockDim.x, thread t reads attribute t % d of rows t / d, t / d + lanes, ...
+__global__ void k_unit_minmax(const float *__restrict__ raw, SegTable t, int d, float *part, uint32_t *flags)
+{
+    extern __shared__ float sm[];                 // 2 * blockDim.x
+    const int u = blockIdx.x;
+    const int64_t row0 = t.seg_start[t.unit_seg[u]] + t.unit_start[u];
+    const int rows = t.unit_count[u];
+    const int lanes = d <= (int)blockDim.x ? (int)blockDim.x / d : 1;
+    bool bad = false;
+    for (int j0 = 0; j0 < d; j0 += (int)blockDim.x) {
+        const int j = j0 + (d <= (int)blockDim.x ? (int)threadIdx.x % d : (int)threadIdx.x);
+        const int r0 = d <= (int)blockDim.x ? (int)threadIdx.x / d : 0;
+        float lo = __int_as_float(kInfBits), hi = -__int_as_float(kInfBits);
+        if (j < d && r0 < lanes) {
+            for (int r = r0; r < rows; r += lanes) {
+                const float v = raw[(row0 + r) * d + j];
+                bad |= !isfinite(v);
+                lo = fminf(lo, v);
+                hi = fmaxf(hi, v);
+            }
+        }
+        sm[threadIdx.x] = lo;
+        sm[blockDim.x + threadIdx.x] = hi;
+        __syncthreads();
+        if (j < d && r0 == 0) {
+            for (int q = 1; q < lanes; q++) {
+                lo = fminf(lo, sm[q * d + threadIdx.x]);
+                hi = fmaxf(hi, sm[blockDim.x + q * d + threadIdx.x]);
+            }
+            part[(size_t)u * d + j] = lo;
+            part[((size_t)t.n_units + u) * d + j] = hi;
+        }
+        __syncthreads();
+    }
+    if (bad) atomicOr(&flags[0], 1u);
+}
+
+// Per set: fold its units' partials (exact in any order) into mn / mx.
+__global__ void k_seg_minmax_fold(const float *part, SegTable t, const int32_t *seg_unit0, int d, double *mn,
+                                  double *mx)
+{
+    const int s = blockIdx.x;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        float lo = __int_as_float(kInfBits), hi = -__int_as_float(kInfBits);
+        for (int u = seg_unit0[s]; u < seg_unit0[s + 1]; u++) {
+            lo = fminf(lo, part[(size_t)u * d + j]);
+            hi = fmaxf(hi, part[((size_t)t.n_units + u) * d + j]);
+        }
+        mn[(size_t)s * d + j] = (double)lo;
+        mx[(size_t)s * d + j] = (double)hi;
+    }
+}
+
+// Per unit: its rows scaled with its set's minimum and range, the same formula as above.
+__global__ void k_unit_scale(const float *__restrict__ raw, float *__restrict__ x, SegTable t, int d,
+                             const double *__restrict__ mn, const double *__restrict__ mx)
+{
+    const int u = blockIdx.x;
+    const int s = t.unit_seg[u];
+    const int64_t row0 = t.seg_start[s] + t.unit_start[u];
+    const int64_t e0 = row0 * d, e1 = (row0 + t.unit_count[u]) * d;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int a = (int)((e - e0) % d);
+        const double lo = mn[(size_t)s * d + a];
+        const double range = __dsub_rn(mx[(size_t)s * d + a], lo);
+        x[e] = range > 0.0 ? __double2float_rn(__dmul_rn(__dsub_rn((double)raw[e], lo), __drcp_rn(range))) : 0.0f;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_seg_scale(const float *raw, float *x, const SegTable &t, const int32_t *seg_unit0, int d,
+                             float *part, double *mn, double *mx, uint32_t *flags, cudaStream_t st, KTimer *kt)
+{
+    const int thr = d < 256 ? ((d + 31) / 32) * 32 : 256;
+    kt->begin(st);
+    k_unit_minmax<<<t.n_units, 256, 2 * 256 * sizeof(float), st>>>(raw, t, d, part, flags);
+    k_seg_minmax_fold<<<t.n_seg, thr, 0, st>>>(part, t, seg_unit0, d, mn, mx);
+    kt->end(PSCL_K_SCALE_MINMAX, st);
+    kt->begin(st);
+    k_unit_scale<<<t.n_units, 256, 0, st>>>(raw, x, t, d, mn, mx);
+    kt->end(PSCL_K_SCALE_APPLY, st);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_scale(const float *raw, float *x, int64_t n, int d, float *part,
                          uint32_t *ticket, double *mn, double *mx, uint32_t *flags, int sm_count,

@@ -105,3 +105,70 @@ def compare(g: GpuRun, o, *, check_labels=True):
             exempt = len(diff)
     return {"local_center_err": le, "final_center_err": fe, "sse_rel": rel,
             "replayed_ties": int(o.n_forced), "label_ties": exempt}
+
+
+# ---------------------------------------------------------------- uneven batches
+@dataclass
+class BatchRun:
+    scaled: np.ndarray
+    centers: np.ndarray          # sum(k_eff) x d
+    labels: np.ndarray
+    sse: np.ndarray              # per instance
+    trace: np.ndarray | None     # iters x rows
+
+
+def run_gpu_batch(parts, ks, iters, seed, *, trace=True, prec=B.PSCL_PREC_FP32, graph=True,
+                  unit_rows=0, rows_per_thread=0, tune=False, device_points=False):
+    raw = np.ascontiguousarray(np.concatenate(parts), np.float32)
+    sizes = [len(p) for p in parts]
+    pts = raw
+    if device_points:
+        import torch
+        pts = torch.from_numpy(raw).cuda()
+    with B.Batch(pts, sizes, ks) as b:
+        b.option(B.PSCL_OPT_GRAPH, graph)
+        if trace:
+            b.option(B.PSCL_OPT_TRACE_LABELS)
+        if unit_rows:
+            b.option(B.PSCL_OPT_UNIT_ROWS, unit_rows)
+        if rows_per_thread:
+            b.option(B.PSCL_OPT_ROWS_PER_THREAD, rows_per_thread)
+        if tune:
+            b.tune(2, prec)
+        b.run(iters, seed, prec)
+        c, lab, sse = b.result()
+        tr = b.trace() if trace and iters else None
+        return BatchRun(b.scaled(), c, lab, sse, tr)
+
+
+def compare_batch(g: BatchRun, parts, ks, iters, seed):
+    """Each instance against the oracle: scaling, seeded init (stage 0, segment = index),
+    Lloyd replayed on the CUDA path's labels, final nearest centers and SSE."""
+    row = cen = 0
+    worst = {"center_err": 0.0, "sse_rel": 0.0, "replayed_ties": 0, "label_ties": 0}
+    for i, (p, k) in enumerate(zip(parts, ks)):
+        m = len(p)
+        ke = min(k, m)
+        xs, _, _ = oracle.scale(p)
+        assert np.array_equal(g.scaled[row:row + m], xs), f"instance {i}: scaled points differ"
+        init = xs[oracle.init_indices(seed, 0, i, m, ke)]
+        force = None if g.trace is None else g.trace[:, row:row + m]
+        c, _, _, _, nf, nb = oracle.lloyd(xs, init, iters, force=force, tie_tol=TIE_TOL)
+        assert nb == 0, f"instance {i}: {nb} label disagreements outside the near-tie band"
+        ce = center_err(g.centers[cen:cen + ke], c)
+        assert ce <= CENTER_TOL, f"instance {i}: centers off by {ce:.3e}"
+        lab, best, second = oracle.assign(xs, c)
+        sse = float(best.sum())
+        rel = abs(g.sse[i] - sse) / max(abs(sse), 1e-300)
+        assert rel <= SSE_TOL, f"instance {i}: SSE {g.sse[i]!r} vs oracle {sse!r}"
+        diff = np.flatnonzero(g.labels[row:row + m] != lab)
+        if len(diff):
+            tie = second[diff] - best[diff] <= TIE_TOL * np.maximum(1.0, best[diff])
+            assert tie.all(), f"instance {i}: {int((~tie).sum())} final labels differ outside the near-tie band"
+        worst["center_err"] = max(worst["center_err"], ce)
+        worst["sse_rel"] = max(worst["sse_rel"], rel)
+        worst["replayed_ties"] += nf
+        worst["label_ties"] += len(diff)
+        row += m
+        cen += ke
+    return worst

@@ -47,11 +47,12 @@ def test_tensor_core_labels_equal_float32(name, prec, n, d, N, lk, fk, T):
 
 
 def test_tensor_core_falls_back_where_shared_memory_is_short():
-    # 200 centers of 64 attributes do not fit the tensor-core kernel's shared memory:
-    # those sets take the float32 kernel (same labels), the small final set the tensor cores
+    # 256 centers of 64 attributes (operands + exact sums) do not fit the tensor-core
+    # kernel's shared memory: those sets take the float32 kernel (same labels), the small
+    # final set the tensor cores
     raw = synth.mixture(9000, 64, 10, seed=2099)
-    ref = run_gpu(raw, 3000, 200, 64, 3, seed=3, trace=False)
-    got = run_gpu(raw, 3000, 200, 64, 3, seed=3, trace=False, prec=B.PSCL_PREC_TF32)
+    ref = run_gpu(raw, 3000, 256, 64, 3, seed=3, trace=False)
+    got = run_gpu(raw, 3000, 256, 64, 3, seed=3, trace=False, prec=B.PSCL_PREC_TF32)
     np.testing.assert_array_equal(got.labels, ref.labels)
     np.testing.assert_array_equal(got.final_centers, ref.final_centers)
     assert got.assigned == got.local_centers.shape[0] * 3
