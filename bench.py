@@ -434,19 +434,110 @@ def main_uneven(args):
     print(json.dumps(line), flush=True)
 
 
+def main_serving(args):
+    """The job server under load: a stream of two-level jobs of mixed shapes (n log-uniform
+    in [1e4, 1e6], d in {8, 32, 128}, final k log-uniform in [8, 1024], N = n/64, 25
+    iterations), points generated on the device; one saturated pass (all jobs submitted at
+    once) gives the peak jobs/s, then Poisson arrivals at 0.5x and 0.8x of it give the
+    latency percentiles.  Printed as its own line (not the default workload)."""
+    import random
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_1412_1947_gb300 import binding as B
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    jobs = synth.serving_stream(args.serve_jobs, synth.BASE_SEED + 4)
+    pts = [synth.mixture_device(j["n"], j["d"], j["blobs"], j["seed"], dev) for j in jobs]
+    torch.cuda.synchronize()
+    budget = 150 << 30
+    srv = B.Server(slots=args.serve_slots, hbm_budget_bytes=budget)
+
+    def run_pass(rate):
+        """Submits every job (all at once when rate is None, else Poisson arrivals at
+        `rate` jobs/s); returns (wall seconds, latencies ms, results)."""
+        tickets = [None] * len(jobs)
+        rnd = random.Random(11)
+        t0 = time.perf_counter()
+
+        def submitter():
+            for i, (j, x) in enumerate(zip(jobs, pts)):
+                if rate:
+                    time.sleep(rnd.expovariate(rate))
+                tickets[i] = srv.submit(x, j["N"], j["local_k"], j["final_k"], j["iters"], j["seed"])
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        lat, res = [], []
+        for t in tickets:
+            srv.wait(t)
+            c, _, sse, times = srv.fetch(t)
+            lat.append(float(times[2]))
+            res.append((c, sse))
+        return time.perf_counter() - t0, lat, res
+
+    run_pass(None)                                    # warm-up (allocator pool, kernels)
+    wall, lat_sat, res = run_pass(None)
+    peak = len(jobs) / wall
+    st = srv.stats()
+    passes = {}
+    for f in (0.5, 0.8):
+        w, lat, _ = run_pass(f * peak)
+        lat = sorted(lat)
+        passes[f"{f}x"] = {"offered_jobs_per_s": f * peak, "jobs_per_s": len(jobs) / w,
+                           "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
+    srv.close()
+    # a sample of the jobs again, each alone: the served results must be the same
+    same = 0
+    sample = list(range(0, len(jobs), max(1, len(jobs) // 10)))
+    for i in sample:
+        j = jobs[i]
+        with B.Job(pts[i]) as jb:
+            jb.run(j["N"], j["local_k"], j["final_k"], j["iters"], j["seed"])
+            c, _, sse = jb.result(labels=False)
+        same += int(np.array_equal(c, res[i][0]) and sse == res[i][1])
+    ls = sorted(lat_sat)
+    evals = sum((j["n"] * j["local_k"] + -(-j["n"] // j["N"]) * j["local_k"] * j["final_k"]) * j["iters"]
+                for j in jobs)
+    line = {"metric": "serving jobs/s", "value": peak, "unit": "jobs/s", "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (generated on the device)",
+            "config": {"workload": f"serving{len(jobs)}_n1e4to1e6_d8-32-128_k8to1024", "jobs": len(jobs),
+                       "slots": args.serve_slots, "hbm_budget_bytes": budget, "iters": 25,
+                       "note": "n scaled down 10x from the 1e4..1e7 stream; FP32 storage only"},
+            "saturated": {"jobs_per_s": peak, "p50_ms": ls[len(ls) // 2],
+                          "p99_ms": ls[min(len(ls) - 1, int(0.99 * len(ls)))],
+                          "dist_evals_per_s": evals / wall, "max_running": st["max_running"],
+                          "peak_bytes": st["peak_bytes"]},
+            "poisson": passes, "alone_equal": f"{same}/{len(sample)}"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="medium", choices=["small", "medium", "large", "uneven"])
+    ap.add_argument("--workload", default="medium", choices=["small", "medium", "large", "uneven", "serving"])
+    ap.add_argument("--serve-jobs", type=int, default=200)
+    ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--oracle-n", type=int, default=1 << 17)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16", "tf32x3", "bf16x3"],
                     help="arithmetic of the Lloyd assignment (tf32/bf16: tensor cores + float32 near-tie recheck)")
     args = ap.parse_args()
+    if args.workload == "serving":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the job server has no reference arm"}))
+        else:
+            main_serving(args)
+        return
     if args.workload == "uneven":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the uneven batch has no reference arm; "

@@ -232,6 +232,61 @@ int pscl_get_phase_ms(pscl_job *job, float *ms5);
 int pscl_assign_sse_noalloc(const float *points, int64_t n, int32_t d, const float *centers,
                             int32_t k, int32_t *labels, double *sse, void *stream);
 
+/* Device bytes a job of this shape holds once pscl_run has planned it (every allocation
+ * of pscl_job_create, pscl_subcluster and pscl_cluster, as counted against the budget):
+ * the admission figure of the server below.  No device work. */
+int pscl_job_footprint(pscl_ctx *ctx, int64_t n, int32_t d, int64_t N, int32_t local_k, int32_t final_k,
+                       int32_t iters, int points_on_device, int trace, size_t *bytes);
+
+/* ---------------------------------------------------------------- serving
+ * A request loop for whole two-level jobs (scale + pscl_subcluster + pscl_cluster) of
+ * mixed shapes, with continuous batching: a native scheduler thread admits queued jobs
+ * onto `slots` execution slots (one CUDA stream each) as slots and device memory free up,
+ * so jobs that arrive while others run start at once and their kernels overlap on the
+ * device.  Admission: a job starts when a slot is free and its pscl_job_footprint fits
+ * the budget left; jobs start in arrival order, except that a later job that fits may
+ * start ahead of an earlier one that does not, until that one has been passed over 32
+ * times.  Each result equals the result of the same job run alone (every kernel is
+ * deterministic).  The paper has no serving layer; this is the form its method takes
+ * behind a service. */
+typedef struct pscl_server pscl_server;
+typedef struct {
+    const void *points;   /* n x d float32, row-major; must stay valid until the job is done */
+    int32_t on_device;    /* 1: 16-byte aligned device memory of the server's device (read in
+                             place); 0: host memory, copied when the job is admitted */
+    int32_t dtype;        /* PSCL_F32 */
+    int64_t n;
+    int32_t d;
+    int64_t N;            /* subcluster size */
+    int32_t local_k, final_k, iters;
+    uint64_t seed;
+    int32_t prec;         /* pscl_prec of both Lloyd stages */
+    int32_t want_labels;  /* 1: keep the n labels of the final clustering for pscl_fetch */
+} pscl_job_desc;
+typedef enum { PSCL_JOB_QUEUED = 0, PSCL_JOB_RUNNING = 1, PSCL_JOB_DONE = 2, PSCL_JOB_FAILED = 3 } pscl_job_state;
+/* slots: 1..64 jobs on the device at once; hbm_budget_bytes: admission budget (0 = 90% of
+ * the device memory free now).  The server's contexts live on ctx's device. */
+int pscl_server_create(pscl_ctx *ctx, int32_t slots, size_t hbm_budget_bytes, pscl_server **out);
+/* Queues a job and returns at once with its ticket.  PSCL_EINVAL for a bad shape,
+ * PSCL_ENOMEM if its footprint exceeds the whole budget (it could never start), PSCL_EBUSY
+ * if 2^20 jobs are already queued; never blocks on the device. */
+int pscl_submit(pscl_server *s, const pscl_job_desc *desc, uint64_t *ticket);
+/* The ticket's pscl_job_state. */
+int pscl_poll(pscl_server *s, uint64_t ticket, int32_t *state);
+/* Waits until the job is done or failed; timeout_us < 0 waits without limit, otherwise
+ * PSCL_ETIMEOUT when the time is up (the job keeps going). */
+int pscl_wait(pscl_server *s, uint64_t ticket, int64_t timeout_us);
+/* Results of a finished job, then the ticket is released (any output may be NULL):
+ * centers final_k x d float32 (scaled coordinates), labels n int32 (needs want_labels),
+ * sse, times_ms[3] = {queued, admitted to done, submitted to done} on the host clock.
+ * A failed job returns its error code.  PSCL_ESTATE if the job has not finished. */
+int pscl_fetch(pscl_server *s, uint64_t ticket, float *centers, int32_t *labels, double *sse, double *times_ms);
+/* out[8]: completed, failed, queued, running, bytes in use, peak bytes in use, most jobs
+ * running at once, budget. */
+int pscl_server_stats(pscl_server *s, int64_t *out);
+/* Fails the queued jobs, waits for the running ones, releases everything. */
+int pscl_server_destroy(pscl_server *s);
+
 /* ---------------------------------------------------------------- uneven batches
  * Many independent clustering instances of uneven sizes, each with its own k: the
  * first-level Lloyd runs of Algorithm 1 step 4 (§II), given directly instead of produced

@@ -49,6 +49,14 @@ SIGNATURES = {
     "pscl_get_kernel_times": (_I, [_P, _P, _P]),
     "pscl_get_recheck_stats": (_I, [_P, _P, _P]),
     "pscl_assign_sse_noalloc": (_I, [_P, _I64, _I32, _P, _I32, _P, _P, _P]),
+    "pscl_job_footprint": (_I, [_P, _I64, _I32, _I64, _I32, _I32, _I32, _I, _I, _P]),
+    "pscl_server_create": (_I, [_P, _I32, _SZ, _P]),
+    "pscl_submit": (_I, [_P, _P, _P]),
+    "pscl_poll": (_I, [_P, _U64, _P]),
+    "pscl_wait": (_I, [_P, _U64, _I64]),
+    "pscl_fetch": (_I, [_P, _U64, _P, _P, _P, _P]),
+    "pscl_server_stats": (_I, [_P, _P]),
+    "pscl_server_destroy": (_I, [_P]),
     "pscl_batch_create": (_I, [_P, _P, _I, _I32, _I32, _P, _P, _P]),
     "pscl_batch_load": (_I, [_P, _P, _I]),
     "pscl_batch_set_option": (_I, [_P, _I, _I64]),
@@ -61,6 +69,16 @@ SIGNATURES = {
     "pscl_batch_lloyd_ms": (_I, [_P, _P]),
     "pscl_batch_destroy": (_I, [_P]),
 }
+PSCL_JOB_QUEUED, PSCL_JOB_RUNNING, PSCL_JOB_DONE, PSCL_JOB_FAILED = 0, 1, 2, 3
+
+
+class JobDesc(C.Structure):
+    """pscl_job_desc"""
+    _fields_ = [("points", C.c_void_p), ("on_device", C.c_int32), ("dtype", C.c_int32), ("n", C.c_int64),
+                ("d", C.c_int32), ("N", C.c_int64), ("local_k", C.c_int32), ("final_k", C.c_int32),
+                ("iters", C.c_int32), ("seed", C.c_uint64), ("prec", C.c_int32), ("want_labels", C.c_int32)]
+
+
 KERNELS = ["scale_minmax", "scale_apply", "peel", "gather", "lloyd_init", "lloyd_assign", "lloyd_finalize",
            "final_sse"]
 
@@ -242,6 +260,57 @@ def pscl_assign_sse_noalloc(points, centers, labels, sse, stream=None):
                                        labels.data_ptr(), sse.data_ptr(), stream))
 
 
+def pscl_job_footprint(ctx, n, d, N, local_k, final_k, iters, on_device=True, trace=False):
+    b = C.c_size_t()
+    _chk(lib().pscl_job_footprint(ctx, n, d, N, local_k, final_k, iters, int(on_device), int(trace), C.byref(b)))
+    return b.value
+
+
+def pscl_server_create(ctx, slots, hbm_budget_bytes=0):
+    h = C.c_void_p()
+    _chk(lib().pscl_server_create(ctx, slots, hbm_budget_bytes, C.byref(h)))
+    return h
+
+
+def pscl_submit(server, points, N, local_k, final_k, iters, seed, prec=PSCL_PREC_FP32, want_labels=False):
+    """Queues a job; returns (ticket, keep-alive of the points)."""
+    p, dev, n, d, keep = _points(points)
+    desc = JobDesc(p, dev, PSCL_F32, n, d, N, local_k, final_k, iters, seed, prec, int(want_labels))
+    t = C.c_uint64()
+    _chk(lib().pscl_submit(server, C.byref(desc), C.byref(t)))
+    return t.value, keep
+
+
+def pscl_poll(server, ticket):
+    st = C.c_int32()
+    _chk(lib().pscl_poll(server, ticket, C.byref(st)))
+    return st.value
+
+
+def pscl_wait(server, ticket, timeout_us=-1):
+    _chk(lib().pscl_wait(server, ticket, timeout_us))
+
+
+def pscl_fetch(server, ticket, final_k, d, n=None):
+    c = np.empty((final_k, d), np.float32)
+    lab = None if n is None else np.empty(n, np.int32)
+    sse = C.c_double()
+    times = np.empty(3, np.float64)
+    _chk(lib().pscl_fetch(server, ticket, _ptr(c), _ptr(lab), C.byref(sse), _ptr(times)))
+    return c, lab, sse.value, times
+
+
+def pscl_server_stats(server):
+    out = np.empty(8, np.int64)
+    _chk(lib().pscl_server_stats(server, _ptr(out)))
+    keys = ["completed", "failed", "queued", "running", "bytes_in_use", "peak_bytes", "max_running", "budget"]
+    return dict(zip(keys, (int(v) for v in out)))
+
+
+def pscl_server_destroy(server):
+    _chk(lib().pscl_server_destroy(server))
+
+
 def pscl_batch_create(ctx, points, sizes, k):
     """points: rows x d (numpy float32, or a torch CUDA tensor), sizes / k per instance."""
     p, dev, rows, d, keep = _points(points)
@@ -309,6 +378,51 @@ def pscl_batch_destroy(b):
 
 
 # ---------------------------------------------------------------- convenience
+class Server:
+    """Continuous-batching job server (a light owner of the handles)."""
+
+    def __init__(self, slots=4, hbm_budget_bytes=0, device=0, ctx=None):
+        self._own_ctx = ctx is None
+        self.ctx = pscl_ctx_create(device) if ctx is None else ctx
+        self.h = pscl_server_create(self.ctx, slots, hbm_budget_bytes)
+        self._jobs = {}
+
+    def submit(self, points, N, local_k, final_k, iters, seed, prec=PSCL_PREC_FP32, want_labels=False):
+        t, keep = pscl_submit(self.h, points, N, local_k, final_k, iters, seed, prec, want_labels)
+        self._jobs[t] = (keep, final_k, int(points.shape[1]), int(points.shape[0]) if want_labels else None)
+        return t
+
+    def poll(self, ticket):
+        return pscl_poll(self.h, ticket)
+
+    def wait(self, ticket, timeout_us=-1):
+        pscl_wait(self.h, ticket, timeout_us)
+
+    def fetch(self, ticket):
+        _, fk, d, n = self._jobs.pop(ticket)
+        return pscl_fetch(self.h, ticket, fk, d, n)
+
+    def stats(self):
+        return pscl_server_stats(self.h)
+
+    def footprint(self, n, d, N, local_k, final_k, iters, on_device=True):
+        return pscl_job_footprint(self.ctx, n, d, N, local_k, final_k, iters, on_device)
+
+    def close(self):
+        if self.h is not None:
+            pscl_server_destroy(self.h)
+            self.h = None
+        if self._own_ctx and self.ctx is not None:
+            pscl_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
 class Batch:
     """Independent clustering instances of uneven sizes (a light owner of the handles)."""
 

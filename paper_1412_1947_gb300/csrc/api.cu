@@ -141,6 +141,9 @@ struct pscl_job : Owner {
     // recorded pipeline
     cudaGraphExec_t gexec = nullptr;
     uint64_t gkey[8] = {};
+    // serving: the peel goes to a stream shared by all jobs (cooperative launches one at a time)
+    cudaStream_t coop = nullptr;
+    cudaEvent_t coop_ev[2] = {};
 };
 
 // ------------------------------------------------------------------ memory
@@ -152,11 +155,12 @@ static int job_alloc(Owner *j, void **p, size_t bytes)
     if (c->budget && c->in_use + bytes > c->budget)
         return fail(PSCL_ENOMEM, "device-memory budget exceeded: %zu in use + %zu requested > %zu",
                     c->in_use, bytes, c->budget);
-    cudaError_t e = cudaMalloc(p, bytes);
+    // stream-ordered: neither allocating nor freeing waits for other streams' work
+    cudaError_t e = cudaMallocAsync(p, bytes, c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(e == cudaErrorMemoryAllocation ? PSCL_ENOMEM : PSCL_ECUDA,
-                    "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+                    "cudaMallocAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
     }
     j->allocs.push_back({*p, bytes});
     c->in_use += bytes;
@@ -168,7 +172,7 @@ static void job_free(Owner *j, void *p)
     if (!p) return;
     for (size_t i = 0; i < j->allocs.size(); i++) {
         if (j->allocs[i].p == p) {
-            cudaFree(p);
+            cudaFreeAsync(p, j->ctx->stream);
             j->ctx->in_use -= j->allocs[i].bytes;
             j->allocs.erase(j->allocs.begin() + i);
             return;
@@ -211,6 +215,14 @@ extern "C" int pscl_ctx_create(pscl_ctx **out, int device, size_t budget, void *
     c->device = device;
     c->budget = budget;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    {   // keep freed pool memory for the next job instead of returning it at every sync
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        cudaGetLastError();
+    }
     if (stream) {
         c->stream = static_cast<cudaStream_t>(stream);
     } else {
@@ -329,11 +341,13 @@ extern "C" int pscl_job_destroy(pscl_job *j)
     cudaStreamSynchronize(j->ctx->stream);
     drop_graph(j);
     for (auto &a : j->allocs) {
-        cudaFree(a.p);
+        cudaFreeAsync(a.p, j->ctx->stream);
         j->ctx->in_use -= a.bytes;
     }
     for (int i = 0; i < 6; i++)
         if (j->ev[i]) cudaEventDestroy(j->ev[i]);
+    for (int i = 0; i < 2; i++)
+        if (j->coop_ev[i]) cudaEventDestroy(j->coop_ev[i]);
     if (j->kt.ev) {
         for (int i = 0; i < 2 * j->kt.cap; i++) cudaEventDestroy(j->kt.ev[i]);
         delete[] j->kt.ev;
@@ -344,6 +358,19 @@ extern "C" int pscl_job_destroy(pscl_job *j)
 }
 
 // ------------------------------------------------------------------ planning
+static int64_t unit_target(int64_t rows, int sm_count, int64_t unit_rows)
+{
+    const int64_t target = unit_rows > 0 ? unit_rows : rows / ((int64_t)sm_count * 4);
+    return std::max<int64_t>(unit_rows > 0 ? 32 : 128, std::min<int64_t>(1024, target));
+}
+
+// rows per unit of a set of m rows (a multiple of 32)
+static int64_t unit_size(int64_t m, int64_t target)
+{
+    const int64_t nu = (m + target - 1) / target;
+    return ((m + nu - 1) / nu + 31) / 32 * 32;
+}
+
 // Work units: every set is cut into ceil(m / target) near-equal pieces (multiples of 32
 // rows), target chosen so that a launch has a few units per SM (or given: unit_rows, at
 // most 1024 rows, the shared-accumulator bound of the assignment kernel).
@@ -366,17 +393,15 @@ static int build_lloyd_plan(Owner *j, LloydPlan &p, const std::vector<int64_t> &
     }
     p.P = P;
     p.rows = rows;
-    int64_t target = unit_rows > 0 ? unit_rows : rows / ((int64_t)j->ctx->sm_count * 4);
-    target = std::max<int64_t>(unit_rows > 0 ? 32 : 128, std::min<int64_t>(1024, target));
+    const int64_t target = unit_target(rows, j->ctx->sm_count, unit_rows);
     p.unit_seg.clear();
     p.unit_start.clear();
     p.unit_count.clear();
     p.seg_unit0.assign(p.n_seg + 1, 0);
     for (int s = 0; s < p.n_seg; s++) {
         p.seg_unit0[s] = (int32_t)p.unit_seg.size();
-        int64_t m = sizes[s];
-        int64_t nu = (m + target - 1) / target;
-        int64_t us = ((m + nu - 1) / nu + 31) / 32 * 32;
+        const int64_t m = sizes[s];
+        const int64_t us = unit_size(m, target);
         for (int64_t r = 0; r < m; r += us) {
             p.unit_seg.push_back(s);
             p.unit_start.push_back((int32_t)r);
@@ -400,8 +425,9 @@ static int build_lloyd_plan(Owner *j, LloydPlan &p, const std::vector<int64_t> &
     packed.insert(packed.end(), p.unit_start.begin(), p.unit_start.end());
     packed.insert(packed.end(), p.unit_count.begin(), p.unit_count.end());
     packed.insert(packed.end(), p.seg_unit0.begin(), p.seg_unit0.end());
-    CU(cudaMemcpy(p.d_seg_start, p.seg_start.data(), p.n_seg * sizeof(int64_t), cudaMemcpyHostToDevice));
-    CU(cudaMemcpy(p.d_i32, packed.data(), packed.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    cudaStream_t st = j->ctx->stream;
+    CU(cudaMemcpyAsync(p.d_seg_start, p.seg_start.data(), p.n_seg * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(p.d_i32, packed.data(), packed.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     // Contiguous unit ranges of near-equal weight for persistent launches of G = m * SMs
     // CTAs (rows, plus a set-up allowance wherever a range has to start a new set).
     const int sm = j->ctx->sm_count;
@@ -424,7 +450,8 @@ static int build_lloyd_plan(Owner *j, LloydPlan &p, const std::vector<int64_t> &
     job_free(j, p.d_split);
     p.d_split = nullptr;
     TRY(A(j, &p.d_split, split.size()));
-    CU(cudaMemcpy(p.d_split, split.data(), split.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CU(cudaMemcpyAsync(p.d_split, split.data(), split.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    // (pageable sources: cudaMemcpyAsync returns once it has staged them)
     return PSCL_OK;
 }
 
@@ -555,6 +582,67 @@ static int plan_cluster(pscl_job *j, int32_t final_k, int32_t iters, uint64_t se
     return PSCL_OK;
 }
 
+// ------------------------------------------------------------------ footprint
+static size_t r256(size_t b) { return ((b ? b : 16) + 255) & ~(size_t)255; }
+
+// Device bytes a job of this shape holds after pscl_run: every allocation of
+// pscl_job_create, plan_subcluster and plan_cluster, each rounded as job_alloc rounds it.
+static size_t job_footprint(int64_t n, int d, int64_t N, int local_k, int final_k, int iters, bool host_input,
+                            bool trace, int sm)
+{
+    size_t b = r256((size_t)n * d * 4) + 2 * r256((size_t)d * 8) + r256(scale_part_floats(n, d, sm) * 4) +
+               r256(8 * 4) + r256(sizeof(PeelCtl)) + r256(kFlagWords * 4);
+    if (host_input) b += r256((size_t)n * d * 4);
+    const int64_t ord_ld = (n + 3) & ~(int64_t)3;
+    const size_t nbk = peel_buckets(n);
+    b += r256((size_t)n * 4) + r256((size_t)d * ord_ld * 4) + r256((size_t)d * nbk * 4) + r256((size_t)d * nbk * 16) +
+         r256(2 * (size_t)n * 4) + r256((size_t)n * 8) + 2 * r256((size_t)n * 4) + r256((size_t)n * 4) +
+         r256((size_t)n * d * 4) + r256((size_t)n * 4);
+    const int64_t S = (n + N - 1) / N;
+    b += r256((size_t)S * d * 4);
+    const int64_t tl = unit_target(n, sm, 0);
+    int64_t units = 0, P = 0;
+    for (int64_t s = 0; s < S; s++) {
+        const int64_t m = std::min<int64_t>(N, n - s * N);
+        units += (m + unit_size(m, tl) - 1) / unit_size(m, tl);
+        P += std::min<int64_t>(local_k, m);
+    }
+    const size_t split = (size_t)10 * sm + 4;
+    b += r256((size_t)S * 8) + r256((4 * (size_t)S + 3 * (size_t)units + 1) * 4) + r256(split * 4);
+    b += r256((size_t)P * d * 4) + r256((size_t)P * d * 8) + r256(2 * (size_t)P * 4);
+    if (trace) b += r256((size_t)iters * n * 4);
+    const int64_t tf = unit_target(P, sm, 0);
+    const int64_t uf = (P + unit_size(P, tf) - 1) / unit_size(P, tf);
+    b += r256(8) + r256((4 + 3 * (size_t)uf + 1) * 4) + r256(split * 4);
+    b += r256((size_t)final_k * d * 4) + r256((size_t)final_k * d * 8) + r256(2 * (size_t)final_k * 4) +
+         r256((size_t)P * 4);
+    b += r256((size_t)n * 4) + r256((size_t)sse_grid(n, sm) * 8) + r256(8);
+    if (trace) b += r256((size_t)iters * P * 4);
+    return b;
+}
+
+cudaStream_t pscl::ctx_stream(const pscl_ctx *c) { return c->stream; }
+int pscl::ctx_device(const pscl_ctx *c) { return c->device; }
+
+int pscl::job_set_coop_stream(pscl_job *j, cudaStream_t s)
+{
+    for (int i = 0; i < 2; i++)
+        if (!j->coop_ev[i]) CU(cudaEventCreateWithFlags(&j->coop_ev[i], cudaEventDisableTiming));
+    j->coop = s;
+    drop_graph(j);
+    return PSCL_OK;
+}
+
+extern "C" int pscl_job_footprint(pscl_ctx *c, int64_t n, int32_t d, int64_t N, int32_t local_k, int32_t final_k,
+                                  int32_t iters, int points_on_device, int trace, size_t *bytes)
+{
+    if (!c || !bytes) return fail(PSCL_EINVAL, "ctx or bytes is NULL");
+    if (n < 1 || d < 1 || N < 1 || local_k < 1 || final_k < 1 || iters < 0)
+        return fail(PSCL_EINVAL, "shape out of range");
+    *bytes = job_footprint(n, d, N, local_k, final_k, iters, !points_on_device, trace != 0, c->sm_count);
+    return PSCL_OK;
+}
+
 // ------------------------------------------------------------------ enqueue (launches only)
 static int run_lloyd(pscl_job *j, const LloydPlan &p, const float *pts, float *centers,
                      unsigned long long *acc, int32_t *cnt2, int32_t *labels, int32_t *trace,
@@ -604,7 +692,15 @@ static int enqueue_scale(pscl_job *j, bool events)
 static int enqueue_subcluster(pscl_job *j, bool events)
 {
     cudaStream_t st = j->ctx->stream;
-    CU(launch_peel(j->pb, j->n, j->d, j->N, j->ctx->sm_count, st, &j->kt));
+    if (j->coop) {
+        CU(cudaEventRecord(j->coop_ev[0], st));
+        CU(cudaStreamWaitEvent(j->coop, j->coop_ev[0], 0));
+        CU(launch_peel(j->pb, j->n, j->d, j->N, j->ctx->sm_count, j->coop, &j->kt));
+        CU(cudaEventRecord(j->coop_ev[1], j->coop));
+        CU(cudaStreamWaitEvent(st, j->coop_ev[1], 0));
+    } else {
+        CU(launch_peel(j->pb, j->n, j->d, j->N, j->ctx->sm_count, st, &j->kt));
+    }
     if (events) CU(cudaEventRecord(j->ev[2], st));
     TRY(run_lloyd(j, j->lp, j->pb.xseg, j->cl, j->acc_l, j->cnt_l, j->lab_l, j->trace_l, j->iters, j->seed, 0u,
                   j->plain != 0, j->prec));
@@ -1005,7 +1101,7 @@ extern "C" int pscl_batch_destroy(pscl_batch *b)
     cudaStreamSynchronize(b->ctx->stream);
     batch_drop_graph(b);
     for (auto &a : b->allocs) {
-        cudaFree(a.p);
+        cudaFreeAsync(a.p, b->ctx->stream);
         b->ctx->in_use -= a.bytes;
     }
     for (int i = 0; i < 2; i++)

@@ -119,6 +119,12 @@ struct PeelBuffers {
 };
 // Buckets of the per-attribute orders the peel builds for n points.
 uint32_t peel_buckets(int64_t n);
+// api.cu: route a job's peel through stream s (ordered with the job's own stream);
+// a context's stream and device.
+int job_set_coop_stream(pscl_job *j, cudaStream_t s);
+cudaStream_t ctx_stream(const pscl_ctx *c);
+int ctx_device(const pscl_ctx *c);
+
 cudaError_t launch_peel(const PeelBuffers &b, int64_t n, int d, int64_t N, int sm_count,
                         cudaStream_t st, KTimer *kt);
 

@@ -125,3 +125,37 @@ def uneven_batch(count: int = 2048, d: int = 32, lo: int = 256, hi: int = 65536,
         pts.append(mixture(int(m), d, k, seed=seed * 7919 + i + 1))
         ks.append(k)
     return pts, ks
+
+
+def mixture_device(n: int, d: int, blobs: int, seed: int, device, sigma_range=(0.2, 1.0)):
+    """The mixture recipe drawn on a CUDA device with a seeded torch generator (the job
+    server's workload, where a host upload per job would dominate).  Not bit-identical to
+    mixture() with the same seed: a different bit source."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    means = torch.rand((blobs, d), generator=g, device=device, dtype=torch.float64) * 10.0
+    sig = sigma_range[0] + (sigma_range[1] - sigma_range[0]) * torch.rand(blobs, generator=g, device=device,
+                                                                         dtype=torch.float64)
+    which = torch.randint(0, blobs, (n,), generator=g, device=device)
+    z = torch.randn((n, d), generator=g, device=device, dtype=torch.float64)
+    return (means[which] + z * sig[which][:, None]).to(torch.float32).contiguous()
+
+
+def serving_stream(count: int, seed: int, n_range=(1e4, 1e6), dims=(8, 32, 128), k_range=(8, 1024)):
+    """Job shapes of the serving workload: n and final k log-uniform, d uniform on dims,
+    N = ceil(n / 64), local k = min(N, max(8, ceil(N / 256), ceil(2 final_k / S))) so that
+    the pooled local centers number at least 2 final_k; 25 iterations."""
+    g = rng(seed)
+    jobs = []
+    for i in range(count):
+        n = int(math.exp(g.uniform(math.log(n_range[0]), math.log(n_range[1]))))
+        d = int(g.choice(dims))
+        fk = int(math.exp(g.uniform(math.log(k_range[0]), math.log(k_range[1]))))
+        N = -(-n // 64)
+        S = -(-n // N)
+        lk = min(N, max(8, -(-N // 256), -(-2 * fk // S)))
+        fk = min(fk, S * lk)
+        jobs.append({"n": n, "d": d, "N": N, "local_k": lk, "final_k": fk, "iters": 25, "seed": seed * 7 + i,
+                     "blobs": max(2, fk)})
+    return jobs

@@ -1,0 +1,131 @@
+"""The job server: admission by device footprint, overlap of jobs on the device, and
+results equal to the same jobs run alone."""
+import math
+import time
+
+import numpy as np
+import pytest
+
+from paper_1412_1947_gb300 import binding as B
+from paper_1412_1947_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def serving_params(n, final_k):
+    """N = ceil(n / 64) and the local k of the serving recipe (pooled count >= 2 final_k)."""
+    N = -(-n // 64)
+    S = -(-n // N)
+    local_k = min(N, max(8, -(-N // 256), -(-2 * final_k // S)))
+    return N, local_k
+
+
+def make_jobs(count, seed):
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for i in range(count):
+        n = int(math.exp(rng.uniform(math.log(4000), math.log(60000))))
+        d = int(rng.choice([8, 16, 32]))
+        fk = int(math.exp(rng.uniform(math.log(4), math.log(64))))
+        N, lk = serving_params(n, fk)
+        pts = synth.mixture(n, d, max(2, fk), seed=seed * 100 + i)
+        jobs.append(dict(points=pts, N=N, local_k=lk, final_k=fk, iters=6, seed=1000 + i))
+    return jobs
+
+
+def run_alone(job):
+    with B.Job(job["points"]) as j:
+        j.run(job["N"], job["local_k"], job["final_k"], job["iters"], job["seed"])
+        return j.result()
+
+
+@pytest.mark.parametrize("n,d,N,lk,fk,T,host", [(10000, 8, 157, 8, 8, 3, True), (50000, 32, 782, 12, 40, 2, False),
+                                                 (4096, 4, 256, 16, 3, 20, False)])
+def test_footprint_is_the_allocated_bytes(n, d, N, lk, fk, T, host):
+    import torch
+    pts = synth.mixture(n, d, 5, seed=n)
+    src = pts if host else torch.from_numpy(pts).cuda()
+    ctx = B.pscl_ctx_create(0)
+    try:
+        j = B.Job(src, ctx=ctx)
+        j.run(N, lk, fk, T, 1)
+        j.result(labels=False)
+        assert B.pscl_ctx_bytes_in_use(ctx) == B.pscl_job_footprint(ctx, n, d, N, lk, fk, T, on_device=not host)
+        j.close()
+        assert B.pscl_ctx_bytes_in_use(ctx) == 0
+    finally:
+        B.pscl_ctx_destroy(ctx)
+
+
+def test_jobs_in_the_mix_equal_jobs_alone():
+    import torch
+    jobs = make_jobs(10, seed=41)
+    alone = [run_alone(jb) for jb in jobs]
+    dev = [torch.from_numpy(jb["points"]).cuda() for jb in jobs]
+    with B.Server(slots=3) as s:
+        tickets = [s.submit(x, jb["N"], jb["local_k"], jb["final_k"], jb["iters"], jb["seed"], want_labels=True)
+                   for x, jb in zip(dev, jobs)]
+        for t in tickets:
+            s.wait(t)
+        st = s.stats()
+        for t, ref in zip(tickets, alone):
+            c, lab, sse, times = s.fetch(t)
+            np.testing.assert_array_equal(c, ref[0])
+            np.testing.assert_array_equal(lab, ref[1])
+            assert sse == ref[2]
+            assert times[2] >= times[1] >= 0.0
+    assert st["completed"] == len(jobs) and st["failed"] == 0
+    assert st["max_running"] >= 2, st          # jobs were on the device together
+    assert st["peak_bytes"] <= st["budget"]
+
+
+def test_admission_keeps_to_the_budget():
+    import torch
+    jobs = make_jobs(6, seed=77)
+    dev = [torch.from_numpy(jb["points"]).cuda() for jb in jobs]
+    ctx = B.pscl_ctx_create(0)
+    fps = [B.pscl_job_footprint(ctx, len(jb["points"]), jb["points"].shape[1], jb["N"], jb["local_k"],
+                                jb["final_k"], jb["iters"]) for jb in jobs]
+    budget = max(fps) + min(fps)             # at most two of them at a time, often one
+    with B.Server(slots=4, hbm_budget_bytes=budget, ctx=ctx) as s:
+        ts = [s.submit(x, jb["N"], jb["local_k"], jb["final_k"], jb["iters"], jb["seed"]) for x, jb in zip(dev, jobs)]
+        for t in ts:
+            s.wait(t)
+        st = s.stats()
+        for t, jb in zip(ts, jobs):
+            c, _, sse, _ = s.fetch(t)
+            ref = run_alone(jb)
+            np.testing.assert_array_equal(c, ref[0])
+        assert st["peak_bytes"] <= budget and st["completed"] == len(jobs)
+        # a job larger than the whole budget can never start
+        big = torch.from_numpy(synth.mixture(200000, 32, 8, seed=5)).cuda()
+        with pytest.raises(B.PsclError) as e:
+            s.submit(big, 3125, 8, 8, 3, 1)
+        assert e.value.code == B.PSCL_ENOMEM
+    B.pscl_ctx_destroy(ctx)
+
+
+def test_wait_times_out_and_arrivals_overlap():
+    import torch
+    big = torch.from_numpy(synth.mixture(1 << 20, 16, 64, seed=9)).cuda()
+    small = [torch.from_numpy(jb["points"]).cuda() for jb in make_jobs(4, seed=90)]
+    with B.Server(slots=3) as s:
+        t0 = s.submit(big, 16384, 16, 64, 25, 3)
+        with pytest.raises(B.PsclError) as e:
+            s.wait(t0, 1)
+        assert e.value.code == B.PSCL_ETIMEOUT
+        assert s.poll(t0) in (B.PSCL_JOB_QUEUED, B.PSCL_JOB_RUNNING)
+        # jobs that arrive while the big one runs start and finish without waiting for it
+        later = []
+        for x in small:
+            time.sleep(0.002)
+            later.append(s.submit(x, 500, 8, 8, 3, 7))
+        for t in later:
+            s.wait(t)
+        done_small = [s.poll(t) for t in later]
+        s.wait(t0)
+        assert all(v == B.PSCL_JOB_DONE for v in done_small)
+        _, _, _, tb = s.fetch(t0)
+        for t in later:
+            _, _, _, ts = s.fetch(t)
+            assert ts[0] < tb[2]               # admitted before the big job was done
