@@ -583,6 +583,7 @@ cudaError_t launch_lloyd_iter(const LloydBuffers &b, int32_t *count_next, const 
     case 16: e = assign_dispatch<16>(b, t, d, iter, unit_lo, unit_hi, kmax, rows_per_thread, st, kt); break;
     case 32: e = assign_dispatch<32>(b, t, d, iter, unit_lo, unit_hi, kmax, rows_per_thread, st, kt); break;
     case 64: e = assign_dispatch<64>(b, t, d, iter, unit_lo, unit_hi, kmax, rows_per_thread, st, kt); break;
+    case 128: e = assign_dispatch<128>(b, t, d, iter, unit_lo, unit_hi, kmax, rows_per_thread, st, kt); break;
     default: e = assign_dispatch<0>(b, t, d, iter, unit_lo, unit_hi, kmax, rows_per_thread, st, kt); break;
     }
     if (e != cudaSuccess) return e;
@@ -608,6 +609,7 @@ cudaError_t launch_seg_sse(const float *pts, const SegTable &t, const int32_t *s
     case 16: e = seg_sse_dispatch<16>(pts, t, d, centers, kmax, labels, unit_sse, st, kt); break;
     case 32: e = seg_sse_dispatch<32>(pts, t, d, centers, kmax, labels, unit_sse, st, kt); break;
     case 64: e = seg_sse_dispatch<64>(pts, t, d, centers, kmax, labels, unit_sse, st, kt); break;
+    case 128: e = seg_sse_dispatch<128>(pts, t, d, centers, kmax, labels, unit_sse, st, kt); break;
     default: e = seg_sse_dispatch<0>(pts, t, d, centers, kmax, labels, unit_sse, st, kt); break;
     }
     if (e != cudaSuccess) return e;
@@ -626,6 +628,7 @@ cudaError_t launch_final_sse(const float *x, int64_t n, int d, const float *cent
     case 16: return sse_dispatch<16>(x, n, d, centers, k, labels, blk_sse, sse, ticket, sm_count, st, kt);
     case 32: return sse_dispatch<32>(x, n, d, centers, k, labels, blk_sse, sse, ticket, sm_count, st, kt);
     case 64: return sse_dispatch<64>(x, n, d, centers, k, labels, blk_sse, sse, ticket, sm_count, st, kt);
+    case 128: return sse_dispatch<128>(x, n, d, centers, k, labels, blk_sse, sse, ticket, sm_count, st, kt);
     default: return sse_dispatch<0>(x, n, d, centers, k, labels, blk_sse, sse, ticket, sm_count, st, kt);
     }
 }

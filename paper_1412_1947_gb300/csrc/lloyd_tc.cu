@@ -41,6 +41,7 @@ constexpr int kTcThreads = 128;           // one thread per TMEM lane / tile row
 constexpr int kTileRows = 128;            // MMA M
 constexpr unsigned kWaitLimit = 1u << 26; // bounded mbarrier polls
 constexpr float kFix = 4294967296.0f;
+constexpr size_t kTcSmemMax = 200 * 1024; // dynamic shared memory the kernel may use
 
 enum TcMode { kModeTf32 = 0, kModeBf16 = 1, kModeTf32x3 = 2, kModeBf16x3 = 3 };
 
@@ -242,7 +243,7 @@ template <int D, int MODE>
 __global__ void __launch_bounds__(kTcThreads)
 k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *split, int unit_lo,
                   const float *__restrict__ centers, unsigned long long *acc, int32_t *count, int32_t *labels,
-                  int32_t *trace, int64_t trace_off, int kmax, int nbuf, uint32_t ncols, uint32_t *flags)
+                  int32_t *trace, int64_t trace_off, int kmax, int nbuf, uint32_t ncols, int sacc, uint32_t *flags)
 {
     using L = TcLayout<D, MODE>;
     using O = Op<MODE>;
@@ -275,11 +276,13 @@ k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *spli
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int e = tid; e < kmax * D; e += kTcThreads) {
-        shi[e] = 0u;
-        slo[e] = 0u;
+    if (sacc) {
+        for (int e = tid; e < kmax * D; e += kTcThreads) {
+            shi[e] = 0u;
+            slo[e] = 0u;
+        }
+        for (int j = tid; j < kmax; j += kTcThreads) scnt[j] = 0;
     }
-    for (int j = tid; j < kmax; j += kTcThreads) scnt[j] = 0;
     if (warp == 0 && ub < ue) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"(smem_u32(&tmem_slot)), "r"((uint32_t)nbuf * ncols));
@@ -491,16 +494,22 @@ k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *spli
                 const int64_t row = row0 + p;
                 labels[row] = bj;
                 if (trace) trace[trace_off + row] = bj;
-                atomicAdd(&scnt[bj], 1);
-                const size_t e0 = (size_t)bj * D;
+                if (sacc) {
+                    atomicAdd(&scnt[bj], 1);
+                    const size_t e0 = (size_t)bj * D;
 #pragma unroll
-                for (int a = 0; a < D; a++) {
-                    const unsigned long long q = to_fix(xv[a]);
-                    atomicAdd(&shi[e0 + a], (uint32_t)(q >> 16));
-                    atomicAdd(&slo[e0 + a], (uint32_t)(q & 0xFFFFu));
+                    for (int a = 0; a < D; a++) {
+                        const unsigned long long q = to_fix(xv[a]);
+                        atomicAdd(&shi[e0 + a], (uint32_t)(q >> 16));
+                        atomicAdd(&slo[e0 + a], (uint32_t)(q & 0xFFFFu));
+                    }
+                } else {                           // sums too large for shared memory
+                    atomicAdd(&count[c0 + bj], 1);
+#pragma unroll
+                    for (int a = 0; a < D; a++) atomicAdd(&acc[(c0 + bj) * D + a], to_fix(xv[a]));
                 }
             }
-            if ((i + 1) % kFoldTiles == 0 && i + 1 < ntiles) {
+            if (sacc && (i + 1) % kFoldTiles == 0 && i + 1 < ntiles) {
                 __syncthreads();
                 flush_sums(shi, slo, scnt, k, c0, acc, count, D);
             }
@@ -511,7 +520,7 @@ k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *spli
             }
         }
         __syncthreads();
-        flush_sums(shi, slo, scnt, k, c0, acc, count, D);
+        if (sacc) flush_sums(shi, slo, scnt, k, c0, acc, count, D);
         if (s_fail) break;
     }
     {   // statistics: rows re-scored in float32 / rows assigned here
@@ -540,23 +549,32 @@ k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *spli
 }
 
 template <int D, int MODE>
-size_t tc_smem_bytes(int kmax, int nbuf)
+size_t tc_smem_bytes(int kmax, int nbuf, bool sacc)
 {
     using L = TcLayout<D, MODE>;
     const int np = (kmax + 15) & ~15;
     const size_t b = ((size_t)(np / 8) * L::kGroup + 127) & ~(size_t)127;
-    return (size_t)nbuf * L::kABytes + b + (size_t)kmax * D * 4 * 2 + (size_t)kmax * 4 + 1024;
+    return (size_t)nbuf * L::kABytes + b + (sacc ? (size_t)kmax * D * 4 * 2 + (size_t)kmax * 4 : 0) + 1024;
 }
 
-__host__ __forceinline__ int tc_nbuf(int kmax) { return tmem_cols((kmax + 15) & ~15) <= 128 ? 2 : 1; }
+// Two operand buffers and TMEM regions (MMA of the next tile under the epilogue of this
+// one) when two regions fit in 256 columns and two A buffers in shared memory, else one.
+template <int D, int MODE>
+int tc_nbuf(int kmax)
+{
+    if (tmem_cols((kmax + 15) & ~15) > 128) return 1;
+    return tc_smem_bytes<D, MODE>(kmax, 2, false) <= kTcSmemMax ? 2 : 1;
+}
 
 template <int D, int MODE>
 cudaError_t tc_dispatch(const LloydBuffers &b, const SegTable &t, int iter, int unit_lo, int unit_hi, int kmax,
                         uint32_t *flags, int sm_count, cudaStream_t st, KTimer *kt)
 {
-    const int nbuf = tc_nbuf(kmax);
+    const int nbuf = tc_nbuf<D, MODE>(kmax);
     const uint32_t ncols = tmem_cols((kmax + 15) & ~15);
-    const size_t smem = tc_smem_bytes<D, MODE>(kmax, nbuf);
+    // exact sums in shared memory when they fit next to the operands, else global atomics
+    const int sacc = tc_smem_bytes<D, MODE>(kmax, nbuf, true) <= kTcSmemMax;
+    const size_t smem = tc_smem_bytes<D, MODE>(kmax, nbuf, sacc != 0);
     auto kern = k_lloyd_assign_tc<D, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -581,7 +599,7 @@ cudaError_t tc_dispatch(const LloydBuffers &b, const SegTable &t, int iter, int 
     }
     kt->begin(st);
     kern<<<grid, kTcThreads, smem, st>>>(b.pts, t, split, unit_lo, b.centers, b.acc, b.count, b.labels, b.trace,
-                                         (int64_t)iter * b.rows, kmax, nbuf, ncols, flags);
+                                         (int64_t)iter * b.rows, kmax, nbuf, ncols, sacc, flags);
     kt->end(PSCL_K_LLOYD_ASSIGN, st);
     return cudaGetLastError();
 }
@@ -604,11 +622,11 @@ template <int MODE>
 size_t smem_by_d(int d, int kmax)
 {
     switch (d) {
-    case 4: return tc_smem_bytes<4, MODE>(kmax, tc_nbuf(kmax));
-    case 8: return tc_smem_bytes<8, MODE>(kmax, tc_nbuf(kmax));
-    case 16: return tc_smem_bytes<16, MODE>(kmax, tc_nbuf(kmax));
-    case 32: return tc_smem_bytes<32, MODE>(kmax, tc_nbuf(kmax));
-    case 64: return tc_smem_bytes<64, MODE>(kmax, tc_nbuf(kmax));
+    case 4: return tc_smem_bytes<4, MODE>(kmax, 1, false);
+    case 8: return tc_smem_bytes<8, MODE>(kmax, 1, false);
+    case 16: return tc_smem_bytes<16, MODE>(kmax, 1, false);
+    case 32: return tc_smem_bytes<32, MODE>(kmax, 1, false);
+    case 64: return tc_smem_bytes<64, MODE>(kmax, 1, false);
     default: return ~(size_t)0;
     }
 }
@@ -626,8 +644,9 @@ int mode_of(int prec)
 }  // namespace
 
 // The tensor-core assignment serves d in {4, 8, 16, 32, 64}, at most 256 centers per set
-// and sets whose operands, centers and sums fit in 200 KB of shared memory; every other
-// case takes the float32 direct kernel (same labels).
+// and sets whose operands fit in 200 KB of shared memory (the exact sums go to shared
+// memory when they fit too, else straight to the global sums); every other case takes
+// the float32 direct kernel (same labels).
 bool tc_supported(int d, int kmax, int prec)
 {
     if (kmax < 1 || kmax > 256) return false;
@@ -638,7 +657,7 @@ bool tc_supported(int d, int kmax, int prec)
     case kModeBf16x3: need = smem_by_d<kModeBf16x3>(d, kmax); break;
     default: need = smem_by_d<kModeTf32>(d, kmax); break;
     }
-    return need <= 200 * 1024;
+    return need <= kTcSmemMax;
 }
 
 cudaError_t launch_lloyd_assign_tc(const LloydBuffers &b, const SegTable &t, int d, int iter, int unit_lo,

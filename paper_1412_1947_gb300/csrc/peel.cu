@@ -1165,6 +1165,7 @@ cudaError_t launch_peel(const PeelBuffers &b, int64_t n, int d, int64_t N, int s
     case 16: return peel_launch<16>(b, n, d, N, sm_count, st, kt);
     case 32: return peel_launch<32>(b, n, d, N, sm_count, st, kt);
     case 64: return peel_launch<64>(b, n, d, N, sm_count, st, kt);
+    case 128: return peel_launch<128>(b, n, d, N, sm_count, st, kt);
     default: return peel_launch<0>(b, n, d, N, sm_count, st, kt);
     }
 }

@@ -36,26 +36,34 @@ def test_tensor_core_labels_equal_float32(name, prec, n, d, N, lk, fk, T):
     # worst-case operand-rounding bound, re-scored in float32)
     assert ref.rechecked == 0 and ref.assigned == 0
     P = got.local_centers.shape[0]
-    if name.endswith("x3") and d == 64:
-        # three operand blocks of 64 attributes, double buffered, exceed the shared memory
-        # the tensor-core kernel may use: the subclusters take the float32 kernel
-        assert got.assigned in (P * T, 0)
-    else:
-        assert got.assigned == (n + P) * T
+    assert got.assigned == (n + P) * T
     assert got.rechecked < 0.99 * max(got.assigned, 1), (got.rechecked, got.assigned)
     print(f"{name} n={n} d={d} k={lk}: re-scored {got.rechecked} of {got.assigned} rows")
 
 
-def test_tensor_core_falls_back_where_shared_memory_is_short():
-    # 256 centers of 64 attributes (operands + exact sums) do not fit the tensor-core
-    # kernel's shared memory: those sets take the float32 kernel (same labels), the small
-    # final set the tensor cores
-    raw = synth.mixture(9000, 64, 10, seed=2099)
-    ref = run_gpu(raw, 3000, 256, 64, 3, seed=3, trace=False)
-    got = run_gpu(raw, 3000, 256, 64, 3, seed=3, trace=False, prec=B.PSCL_PREC_TF32)
+def test_tensor_core_falls_back_above_256_centers():
+    # more than 256 centers per set exceed one MMA: those sets take the float32 kernel
+    # (same labels), the final set of 64 centers the tensor cores
+    raw = synth.mixture(9000, 32, 10, seed=2099)
+    ref = run_gpu(raw, 3000, 300, 64, 3, seed=3, trace=False)
+    got = run_gpu(raw, 3000, 300, 64, 3, seed=3, trace=False, prec=B.PSCL_PREC_TF32)
     np.testing.assert_array_equal(got.labels, ref.labels)
     np.testing.assert_array_equal(got.final_centers, ref.final_centers)
     assert got.assigned == got.local_centers.shape[0] * 3
+
+
+@pytest.mark.parametrize("name,prec", [("tf32", B.PSCL_PREC_TF32), ("bf16", B.PSCL_PREC_BF16),
+                                       ("bf16x3", B.PSCL_PREC_BF16X3)])
+def test_tensor_core_with_sums_in_global_memory(name, prec):
+    # 256 centers of 64 attributes: operands fit shared memory, the exact sums do not and
+    # go straight to the global sums; labels and centers still equal the float32 path
+    raw = synth.mixture(20000, 64, 40, seed=2100)
+    ref = run_gpu(raw, 5000, 256, 64, 3, seed=3, trace=False)
+    got = run_gpu(raw, 5000, 256, 64, 3, seed=3, trace=False, prec=prec)
+    np.testing.assert_array_equal(got.labels, ref.labels)
+    np.testing.assert_array_equal(got.local_centers, ref.local_centers)
+    np.testing.assert_array_equal(got.final_centers, ref.final_centers)
+    assert got.assigned == (20000 + got.local_centers.shape[0]) * 3
 
 
 @pytest.mark.parametrize("name,prec", PRECS)
