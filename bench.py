@@ -37,6 +37,22 @@ METRIC = "Lloyd dist-evals/s"
 UNIT = "dist-evals/s"
 L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2
 FP32_ALU_PEAK = 152 * 128 * 2 * 2.07e9   # SMs x FP32 lanes x 2 flop (FMA) x max SM clock
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands, by
+# (kernel, workload): 301.5 MB + 207.1 MB for the peel on the 2^20 x 16 workload
+# (profiles/k_peel_n1048576_d16.md).  Drop an entry when its kernel changes.
+NCU_TRAFFIC = {("peel", "n1048576_d16_N4096_k64_f64"): 508.57e6}
+
+
+def replica_max(x: float, dist=None) -> float:
+    """The maximum of x over the ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    if dist.get_backend() == "nccl":
+        t = t.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def workload_evals(w: synth.Workload) -> int:
@@ -214,11 +230,7 @@ def main_arm(args, w: synth.Workload):
         dist.barrier()
     clocks = clk.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    mean_ms = statistics.mean(step_ms)
-    if dist:
-        t = torch.tensor([mean_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        mean_ms = float(t.item())
+    mean_ms = replica_max(statistics.mean(step_ms), dist)
     _, _, sse = job.result(labels=False)
 
     # ---- end to end through the public API with host buffers: H2D of the points from
@@ -240,11 +252,7 @@ def main_arm(args, w: synth.Workload):
         job_e.run(wr.N, wr.local_k, wr.final_k, wr.iters, seed, prec)
         c, _, sse_e = job_e.result(labels=False)
         e2e_s.append(time.perf_counter() - t0)
-    e2e_mean = statistics.mean(e2e_s)
-    if dist:
-        t = torch.tensor([e2e_mean], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_mean = float(t.item())
+    e2e_mean = replica_max(statistics.mean(e2e_s), dist)
     job_e.close()
     B.pscl_ctx_destroy(ctx_e)
 
@@ -299,7 +307,8 @@ def main_arm(args, w: synth.Workload):
         byts = rem * wr.d * 4 if name == "peel" else wr.n * wr.d * 4 * 2
         roof = {"kernel": name, "bound": "hbm", "achieved": byts / (ms * 1e-3) / 1e9,
                 "peak": 6691.5, "unit": "GB/s", "peak_kind": "measured (MEASURED_PEAKS hbm_gbs)",
-                "per_launch_ms": ms / nl, "launches": nl, "traffic": None}
+                "per_launch_ms": ms / nl, "launches": nl, "traffic": NCU_TRAFFIC.get((name, w.name)),
+                "algorithmic_bytes": byts}
     roof["frac"] = roof["achieved"] / roof["peak"]
 
     value = evals * world / (mean_ms * 1e-3)
