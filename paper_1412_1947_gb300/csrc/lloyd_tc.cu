@@ -243,7 +243,8 @@ template <int D, int MODE>
 __global__ void __launch_bounds__(kTcThreads)
 k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *split, int unit_lo,
                   const float *__restrict__ centers, unsigned long long *acc, int32_t *count, int32_t *labels,
-                  int32_t *trace, int64_t trace_off, int kmax, int nbuf, uint32_t ncols, int sacc, uint32_t *flags)
+                  int32_t *trace, int64_t trace_off, int kmax, int nbuf, uint32_t ncols, int sacc, int scent,
+                  uint32_t *flags)
 {
     using L = TcLayout<D, MODE>;
     using O = Op<MODE>;
@@ -261,10 +262,11 @@ k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *spli
     const int ue = split ? split[blockIdx.x + 1] : ub + 1;
     const int npmax = (kmax + 15) & ~15;
 
-    // [A buffers | B | high sums | low sums | counts]
+    // [A buffers | B | float32 centers (scent) | high sums | low sums | counts (sacc)]
     unsigned char *sa0 = smem;
     unsigned char *sb = sa0 + (size_t)nbuf * L::kABytes;
-    uint32_t *shi = reinterpret_cast<uint32_t *>(sb + (((uint32_t)(npmax / 8) * L::kGroup + 127) & ~127u));
+    float *sc = reinterpret_cast<float *>(sb + (((uint32_t)(npmax / 8) * L::kGroup + 127) & ~127u));
+    uint32_t *shi = reinterpret_cast<uint32_t *>(sc + (scent ? (size_t)kmax * D : 0));
     uint32_t *slo = shi + (size_t)kmax * D;
     int32_t *scnt = reinterpret_cast<int32_t *>(slo + (size_t)kmax * D);
 
@@ -306,7 +308,11 @@ k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *spli
         const int R = t.unit_start[ur - 1] + t.unit_count[ur - 1] - t.unit_start[u];
         u = ur;
 
-        // ---- set-up of the run: reference point (mean of the centers), operand B, cmax
+        // ---- set-up of the run: float32 centers (for the near-tie re-scoring), reference
+        // point (mean of the centers), operand B, cmax
+        if (scent)
+            for (int e = tid; e < k * D; e += kTcThreads) sc[e] = __ldg(&centers[c0 * D + e]);
+        const float *cen = scent ? sc : centers + c0 * D;       // this set's centers
         {
             constexpr int G = kTcThreads / D;
             const int a = tid % D, g = tid / D;
@@ -363,6 +369,22 @@ k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *spli
         const float beta = 2.0f * ((float)L::kK * 0x1p-22f + (float)(D + 4) * 0x1p-24f + 0x1p-22f);
         const int ntiles = (R + kTileRows - 1) / kTileRows;
 
+        // rows of the next tile to stage, loaded one tile ahead (D <= 32: registers)
+        constexpr bool kPre = D <= 32;
+        float xp[kPre ? D : 1];
+        auto load_rows = [&](int tile) {
+            if (!kPre || tile >= ntiles) return;
+            const int p = tile * kTileRows + tid;
+            const float4 *x4 = reinterpret_cast<const float4 *>(pts + (row0 + (p < R ? p : 0)) * D);
+#pragma unroll
+            for (int a4 = 0; a4 < (kPre ? D : 4) / 4; a4++) {
+                const float4 v = __ldg(&x4[a4]);
+                xp[4 * a4 + 0] = v.x;
+                xp[4 * a4 + 1] = v.y;
+                xp[4 * a4 + 2] = v.z;
+                xp[4 * a4 + 3] = v.w;
+            }
+        };
         // write tile `tile`'s A operand into buffer `buf` (threads = rows)
         auto stage = [&](int tile, int buf) {
             const int p = tile * kTileRows + tid;
@@ -371,8 +393,17 @@ k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *spli
             float h[D], l[D];
 #pragma unroll
             for (int a4 = 0; a4 < D / 4; a4++) {
-                const float4 v = __ldg(&x4[a4]);
-                const float vv[4] = {v.x, v.y, v.z, v.w};
+                float vv[4];
+                if (kPre) {
+#pragma unroll
+                    for (int q = 0; q < 4; q++) vv[q] = xp[(4 * a4 + q) % (kPre ? D : 1)];
+                } else {
+                    const float4 v = __ldg(&x4[a4]);
+                    vv[0] = v.x;
+                    vv[1] = v.y;
+                    vv[2] = v.z;
+                    vv[3] = v.w;
+                }
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
                     const int a = 4 * a4 + q;
@@ -382,6 +413,7 @@ k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *spli
                 }
             }
             put_row<D, MODE>(sa0 + buf * L::kABytes, tid, [&](int e) { return a_elem<D, MODE>(e, h, l, live); });
+            load_rows(tile + 1);           // in flight while this tile's MMAs and epilogue run
         };
         auto issue = [&](int buf) {
             issue_mma<D, MODE>(tmem + (uint32_t)buf * ncols, smem_u32(sa0 + buf * L::kABytes), smem_u32(sb), idesc,
@@ -398,6 +430,7 @@ k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *spli
             return true;
         };
 
+        load_rows(0);
         bool ok = ntiles == 0 || stage_issue(0, 0);
         for (int i = 0; ok && i < ntiles; i++) {
             const int buf = nbuf == 2 ? (i & 1) : 0;
@@ -428,60 +461,64 @@ k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *spli
                 xn2 = __fmaf_rn(xc, xc, xn2);
             }
             const uint32_t trow = tmem + (uint32_t)buf * ncols + ((uint32_t)(warp * 32) << 16);
-            // best and second best, two independent chains (even / odd columns)
-            float b0 = __int_as_float(0x7f800000), s0 = b0, b1 = b0, s1 = b0;
-            int j0 = 0, j1 = 1;
+            // pass 1: the smallest v_j (four independent chains)
+            const float kInf = __int_as_float(0x7f800000);
+            float m4[4] = {kInf, kInf, kInf, kInf};
             for (int cb = 0; cb < k; cb += 32) {
                 float v[32];
                 tmem_ld32(trow + (uint32_t)cb, v);
 #pragma unroll
-                for (int q = 0; q < 32; q += 2) {
-                    const float va = cb + q < k ? v[q] : __int_as_float(0x7f800000);
-                    const float vb = cb + q + 1 < k ? v[q + 1] : __int_as_float(0x7f800000);
-                    s0 = fminf(s0, fmaxf(b0, va));
-                    if (va < b0) { b0 = va; j0 = cb + q; }
-                    s1 = fminf(s1, fmaxf(b1, vb));
-                    if (vb < b1) { b1 = vb; j1 = cb + q + 1; }
-                }
+                for (int q = 0; q < 32; q++) m4[q & 3] = fminf(m4[q & 3], cb + q < k ? v[q] : kInf);
             }
-            float best, second;
-            int bj;
-            if (b1 < b0 || (b1 == b0 && j1 < j0)) {
-                best = b1; bj = j1; second = fminf(s1, b0);
-            } else {
-                best = b0; bj = j0; second = fminf(s0, b1);
-            }
+            const float best = fminf(fminf(m4[0], m4[1]), fminf(m4[2], m4[3]));
             // E bounds the error of every v_j; the float32 direct sums have their own error
             // (<= (d+3) 2^-24 of a distance, at most (||x~|| + cmax)^2), added so that no center
             // left out could win the float32 direct comparison
             const float xn = sqrtf(xn2);
             const float E = alpha * xn * cmax + beta * cmax * cmax +
                             (float)(2 * (D + 3)) * 0x1p-24f * (xn + cmax) * (xn + cmax) + 0x1p-100f;
-            const bool tie = live && second - best <= 2.0f * E;
+            const float thr = best + 2.0f * E;
+            // pass 2: every center within 2E of the best (the best among them), as a list of
+            // 8-bit indices (k <= 256), in ascending index
+            unsigned long long cl = 0ull;
+            int nc = 0;
+            for (int cb = 0; cb < k; cb += 32) {
+                float v[32];
+                tmem_ld32(trow + (uint32_t)cb, v);
+#pragma unroll
+                for (int q = 0; q < 32; q++) {
+                    if (cb + q < k && v[q] <= thr) {
+                        if (nc < 8) cl |= (unsigned long long)(cb + q) << (8 * nc);
+                        nc++;
+                    }
+                }
+            }
+            int bj = (int)(cl & 0xFFu);
+            const bool tie = live && nc > 1;
             if (__any_sync(0xffffffffu, tie)) {
-                // re-score every center within 2E of the best with the float32 direct sum
-                float bd = __int_as_float(0x7f800000);
+                // near tie: re-score the candidates with the float32 direct sum, lowest index
+                // among equal sums (the float32 path's choice); past 8 candidates, all centers
+                auto direct = [&](int j) {
+                    const float *cj = cen + (size_t)j * D;
+                    float dd = 0.0f;
+#pragma unroll
+                    for (int a = 0; a < D; a++) {
+                        const float tq = __fsub_rn(xv[a], cj[a]);      // shared or global (generic)
+                        dd = __fmaf_rn(tq, tq, dd);
+                    }
+                    return dd;
+                };
+                const int nlist = tie ? (nc <= 8 ? nc : k) : 0;
+                const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)nlist);
+                float bd = kInf;
                 int bjj = bj;
-                for (int cb = 0; cb < k; cb += 32) {
-                    float v[32];
-                    tmem_ld32(trow + (uint32_t)cb, v);
-                    if (tie) {
-#pragma unroll
-                        for (int q = 0; q < 32; q++) {
-                            const int j = cb + q;
-                            if (j < k && v[q] <= best + 2.0f * E) {
-                                const float *cj = centers + (c0 + j) * D;
-                                float dd = 0.0f;
-#pragma unroll
-                                for (int a = 0; a < D; a++) {
-                                    const float tq = __fsub_rn(xv[a], __ldg(&cj[a]));
-                                    dd = __fmaf_rn(tq, tq, dd);
-                                }
-                                if (dd < bd) {
-                                    bd = dd;
-                                    bjj = j;
-                                }
-                            }
+                for (int c = 0; c < nmax; c++) {
+                    if (c < nlist) {
+                        const int j = nc <= 8 ? (int)((cl >> (8 * c)) & 0xFFu) : c;
+                        const float dd = direct(j);
+                        if (dd < bd) {                     // ascending j: strict keeps the lowest
+                            bd = dd;
+                            bjj = j;
                         }
                     }
                 }
@@ -549,12 +586,13 @@ k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *spli
 }
 
 template <int D, int MODE>
-size_t tc_smem_bytes(int kmax, int nbuf, bool sacc)
+size_t tc_smem_bytes(int kmax, int nbuf, bool sacc, bool scent = false)
 {
     using L = TcLayout<D, MODE>;
     const int np = (kmax + 15) & ~15;
     const size_t b = ((size_t)(np / 8) * L::kGroup + 127) & ~(size_t)127;
-    return (size_t)nbuf * L::kABytes + b + (sacc ? (size_t)kmax * D * 4 * 2 + (size_t)kmax * 4 : 0) + 1024;
+    return (size_t)nbuf * L::kABytes + b + (scent ? (size_t)kmax * D * 4 : 0) +
+           (sacc ? (size_t)kmax * D * 4 * 2 + (size_t)kmax * 4 : 0) + 1024;
 }
 
 // Two operand buffers and TMEM regions (MMA of the next tile under the epilogue of this
@@ -572,9 +610,11 @@ cudaError_t tc_dispatch(const LloydBuffers &b, const SegTable &t, int iter, int 
 {
     const int nbuf = tc_nbuf<D, MODE>(kmax);
     const uint32_t ncols = tmem_cols((kmax + 15) & ~15);
-    // exact sums in shared memory when they fit next to the operands, else global atomics
+    // exact sums in shared memory when they fit next to the operands (else global atomics),
+    // then the float32 centers for the re-scoring when they fit too (else read through L1)
     const int sacc = tc_smem_bytes<D, MODE>(kmax, nbuf, true) <= kTcSmemMax;
-    const size_t smem = tc_smem_bytes<D, MODE>(kmax, nbuf, sacc != 0);
+    const int scent = tc_smem_bytes<D, MODE>(kmax, nbuf, sacc != 0, true) <= kTcSmemMax;
+    const size_t smem = tc_smem_bytes<D, MODE>(kmax, nbuf, sacc != 0, scent != 0);
     auto kern = k_lloyd_assign_tc<D, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -599,7 +639,7 @@ cudaError_t tc_dispatch(const LloydBuffers &b, const SegTable &t, int iter, int 
     }
     kt->begin(st);
     kern<<<grid, kTcThreads, smem, st>>>(b.pts, t, split, unit_lo, b.centers, b.acc, b.count, b.labels, b.trace,
-                                         (int64_t)iter * b.rows, kmax, nbuf, ncols, sacc, flags);
+                                         (int64_t)iter * b.rows, kmax, nbuf, ncols, sacc, scent, flags);
     kt->end(PSCL_K_LLOYD_ASSIGN, st);
     return cudaGetLastError();
 }
