@@ -160,6 +160,19 @@ int pscl_scale_features(pscl_job *job);
 int pscl_subcluster(pscl_job *job, int64_t N, int32_t local_k, int32_t iters, uint64_t seed,
                     int prec);
 
+/* Unequal-sized subclustering (Algorithm 2) in place of pscl_subcluster: L and H are the
+ * points made of every attribute's lowest and highest scaled value; the segment from L
+ * to H is cut into m equal pieces whose middles are the landmarks
+ *     l_i = float(L + ((i + 1/2) / m) (H - L)), i = 0..m-1   (double arithmetic);
+ * every point joins its nearest landmark (squared Euclidean distance in float64 as for
+ * pscl_subcluster, the lower landmark index on ties).  The groups that got points are the
+ * subclusters, in landmark order, points in ascending index; then Lloyd runs on each of
+ * them as in pscl_subcluster (local_k, iters, seed, prec; subcluster s = the s-th
+ * non-empty group), and pscl_cluster follows as usual.  m: 1..4096.  Synchronises with
+ * the device once (the group sizes plan the Lloyd launches), so it is not recorded by
+ * PSCL_OPT_GRAPH.  Errors as pscl_subcluster. */
+int pscl_subcluster_unequal(pscl_job *job, int32_t m, int32_t local_k, int32_t iters, uint64_t seed, int prec);
+
 /* Final clustering of the P pooled local centers (§V) into final_k centers with Lloyd
  * (initial centers keyed by (seed, stage 1, 0)), then the nearest final center and the
  * sum of squared errors of every scaled point.

@@ -108,6 +108,20 @@ def peel(x: np.ndarray, N: int, select: bool = False):
     return perm, seg_off[:S + 1].copy(), lm[:S].copy()
 
 
+def group_unequal(x: np.ndarray, m: int):
+    """Algorithm 2's grouping: returns (perm[n], seg_off[S+1], landmarks[m, d], group[n])."""
+    x = np.ascontiguousarray(x, np.float32)
+    n, d = x.shape
+    perm = np.empty(n, np.int64)
+    seg_off = np.empty(m + 1, np.int64)
+    lm = np.empty((m, d), np.float32)
+    g = np.empty(n, np.int32)
+    S = C.c_int64(0)
+    _check(lib().or_group_unequal(_p(x), n, d, m, _p(perm), _p(seg_off), C.byref(S), _p(lm), _p(g)),
+           "group_unequal")
+    return perm, seg_off[:S.value + 1].copy(), lm, g
+
+
 def assign(pts: np.ndarray, centers: np.ndarray):
     pts = np.ascontiguousarray(pts, np.float32)
     c = np.ascontiguousarray(centers, np.float64)
@@ -156,7 +170,7 @@ class _Args(C.Structure):
         ("raw", C.c_void_p), ("n", C.c_int64), ("N", C.c_int64), ("d", C.c_int32),
         ("local_k", C.c_int32), ("final_k", C.c_int32), ("iters", C.c_int32),
         ("seed", C.c_uint64), ("first_k", C.c_int32), ("n_threads", C.c_int32),
-        ("select_peel", C.c_int32), ("force_local", C.c_void_p), ("force_final", C.c_void_p), ("tie_tol", C.c_double),
+        ("select_peel", C.c_int32), ("unequal_m", C.c_int32), ("force_local", C.c_void_p), ("force_final", C.c_void_p), ("tie_tol", C.c_double),
         ("scaled", C.c_void_p), ("perm", C.c_void_p), ("seg_off", C.c_void_p),
         ("landmarks", C.c_void_p), ("local_centers", C.c_void_p), ("local_k_eff", C.c_void_p),
         ("local_labels", C.c_void_p), ("local_sse", C.c_void_p), ("final_centers", C.c_void_p),
@@ -200,11 +214,16 @@ def pooled_count(n: int, N: int, local_k: int) -> tuple[int, int]:
 
 def two_level(raw: np.ndarray, N: int, local_k: int, final_k: int, iters: int, seed: int,
               first_k: bool = False, threads: int = 0, force_local=None, force_final=None,
-              select_peel: bool = False,
+              select_peel: bool = False, unequal_m: int = 0,
               tie_tol: float = 0.0) -> TwoLevel:
+    """unequal_m > 0: Algorithm 2 with that many landmarks instead of the peel (N unused)."""
     raw = np.ascontiguousarray(raw, np.float32)
     n, d = raw.shape
-    S, P = pooled_count(n, N, local_k)
+    if unequal_m > 0:
+        N = 1
+        S, P = unequal_m, min(n, unequal_m * local_k)      # upper bounds, trimmed below
+    else:
+        S, P = pooled_count(n, N, local_k)
     o = dict(
         scaled=np.empty((n, d), np.float32), perm=np.empty(n, np.int64),
         seg_off=np.empty(S + 1, np.int64), landmarks=np.empty((S, d), np.float32),
@@ -222,13 +241,21 @@ def two_level(raw: np.ndarray, N: int, local_k: int, final_k: int, iters: int, s
     a.local_k, a.final_k, a.iters, a.seed = local_k, final_k, iters, seed
     a.first_k, a.n_threads = int(first_k), int(threads)
     a.select_peel = int(select_peel)
+    a.unequal_m = int(unequal_m)
     a.force_local = None if fl is None else fl.ctypes.data
     a.force_final = None if ff is None else ff.ctypes.data
     a.tie_tol = tie_tol
     for k, v in o.items():
         setattr(a, k, v.ctypes.data)
     _check(lib().or_two_level(C.byref(a)), "two_level")
-    if a.n_seg != S or a.n_pooled != P:
+    if unequal_m > 0:
+        S, P = a.n_seg, a.n_pooled
+        o["seg_off"] = o["seg_off"][:S + 1]
+        o["local_centers"] = o["local_centers"][:P]
+        o["local_k_eff"] = o["local_k_eff"][:S]
+        o["local_sse"] = o["local_sse"][:S]
+        o["final_labels_pooled"] = o["final_labels_pooled"][:P]
+    elif a.n_seg != S or a.n_pooled != P:
         raise RuntimeError("oracle subcluster count disagrees with the closed form")
     o["local_sse"] = o["local_sse"][:, :iters]
     o["final_sse_hist"] = o["final_sse_hist"][:iters]

@@ -19,6 +19,9 @@
  *   4. the pooled local centers are clustered once more with Lloyd (§V) to get the
  *      final centers;
  *   5. the sum of squared errors of all scaled points against the final centers.
+ * Step 2 can instead be the unequal-sized subclustering of Algorithm 2: m landmarks
+ * spaced along the segment from the per-attribute minimum L to the per-attribute
+ * maximum H, every point grouped with its nearest landmark.
  *
  * Readings where the paper is silent (each is a choice, stated once here):
  *   - scaling: x' = float( (double(x) - mn) * (1 / (mx - mn)) ), the reciprocal and the
@@ -32,7 +35,13 @@
  *     exactly T iterations, breaks assignment ties by the lower center index and keeps
  *     an empty cluster's previous center;
  *   - the pooled set is the unweighted list of local centers in (subcluster, center)
- *     order.
+ *     order;
+ *   - Algorithm 2 ("divide the line segment between H and L into the required number
+ *     of points"): landmark i of m sits at the middle of the i-th of m equal pieces,
+ *     l_i = float(L + ((i + 1/2) / m) * (H - L)) per attribute in double; a point joins
+ *     the landmark at the smallest squared distance (same summation as the peel),
+ *     the lower landmark index on ties; landmarks nobody joins form no subcluster, and
+ *     the subclusters are numbered in landmark order.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -356,6 +365,78 @@ int or_lloyd_seeded(const float *pts, int64_t m, int32_t d, int32_t k, int32_t T
 }
 
 /* ------------------------------------------------------------------------------ */
+/* Step 2 alternative: unequal-sized subclustering (Algorithm 2).                    */
+/* x: n*d scaled points, m landmarks.  Outputs as or_peel (groups with no point are   */
+/* skipped, so *n_seg <= m); landmarks[m*d] (optional); group[n] (optional): the      */
+/* landmark index of every point.                                                     */
+/* ------------------------------------------------------------------------------ */
+int or_group_unequal(const float *x, int64_t n, int32_t d, int32_t m, int64_t *perm, int64_t *seg_off,
+                     int64_t *n_seg, float *landmarks, int32_t *group)
+{
+    double *lm, *lo, *hi;
+    int64_t *cnt, *next, i;
+    int32_t *g, j, a;
+    int64_t S = 0;
+    if (n < 1 || d < 1 || m < 1) return OR_EINVAL;
+    lm = (double *)malloc((size_t)m * d * sizeof(double));
+    lo = (double *)malloc((size_t)d * sizeof(double));
+    hi = (double *)malloc((size_t)d * sizeof(double));
+    cnt = (int64_t *)calloc((size_t)m, sizeof(int64_t));
+    next = (int64_t *)malloc((size_t)m * sizeof(int64_t));
+    g = group ? group : (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!lm || !lo || !hi || !cnt || !next || !g) {
+        free(lm); free(lo); free(hi); free(cnt); free(next);
+        if (!group) free(g);
+        return OR_ENOMEM;
+    }
+    /* L and H: the lowest and highest value of every attribute */
+    for (a = 0; a < d; a++) {
+        lo[a] = (double)x[a];
+        hi[a] = (double)x[a];
+    }
+    for (i = 1; i < n; i++)
+        for (a = 0; a < d; a++) {
+            double v = (double)x[i * d + a];
+            if (v < lo[a]) lo[a] = v;
+            if (v > hi[a]) hi[a] = v;
+        }
+    /* the landmarks: middles of m equal pieces of the segment from L to H, stored as
+     * float like the points */
+    for (j = 0; j < m; j++) {
+        double t = ((double)j + 0.5) / (double)m;
+        for (a = 0; a < d; a++) {
+            float v = (float)(lo[a] + t * (hi[a] - lo[a]));
+            lm[(int64_t)j * d + a] = (double)v;
+            if (landmarks) landmarks[(int64_t)j * d + a] = v;
+        }
+    }
+    /* every point joins its nearest landmark (lower index on ties) */
+    for (i = 0; i < n; i++) {
+        double best = INFINITY;
+        int32_t bj = 0;
+        for (j = 0; j < m; j++) {
+            double v = sqdist(x + i * d, lm + (int64_t)j * d, d);
+            if (v < best) { best = v; bj = j; }
+        }
+        g[i] = bj;
+        cnt[bj] += 1;
+    }
+    /* subclusters in landmark order, points in ascending index inside each */
+    seg_off[0] = 0;
+    for (j = 0; j < m; j++) {
+        if (cnt[j] == 0) { next[j] = -1; continue; }
+        next[j] = seg_off[S];
+        seg_off[S + 1] = seg_off[S] + cnt[j];
+        S++;
+    }
+    for (i = 0; i < n; i++) perm[next[g[i]]++] = i;
+    *n_seg = S;
+    free(lm); free(lo); free(hi); free(cnt); free(next);
+    if (!group) free(g);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------ */
 /* The whole method.                                                                   */
 /* ------------------------------------------------------------------------------ */
 typedef struct {
@@ -371,6 +452,7 @@ typedef struct {
     int32_t first_k;          /* 1: every Lloyd starts from its first k_eff points */
     int32_t n_threads;        /* threads over subclusters (0 = library default)    */
     int32_t select_peel;      /* 1: or_peel_select instead of or_peel (same result) */
+    int32_t unequal_m;        /* > 0: Algorithm 2 with this many landmarks instead of the peel */
     const int32_t *force_local; /* optional iters*n trace, subcluster-packed order */
     const int32_t *force_final; /* optional iters*P trace                          */
     double tie_tol;
@@ -378,7 +460,7 @@ typedef struct {
     float *scaled;            /* n*d */
     int64_t *perm;            /* n   */
     int64_t *seg_off;         /* S+1 */
-    float *landmarks;         /* S*d (optional) */
+    float *landmarks;         /* S*d, or unequal_m*d (optional) */
     double *local_centers;    /* P*d */
     int32_t *local_k_eff;     /* S */
     int32_t *local_labels;    /* n, subcluster-packed order (optional) */
@@ -411,12 +493,14 @@ int or_two_level(or_two_level_args *A)
     mn = (double *)malloc((size_t)d * sizeof(double));
     mx = (double *)malloc((size_t)d * sizeof(double));
     packed = (float *)malloc((size_t)n * d * sizeof(float));
-    cen_off = (int64_t *)malloc((size_t)(n / A->N + 2) * sizeof(int64_t));
+    cen_off = (int64_t *)malloc((size_t)(n / A->N + 2 + (A->unequal_m > 0 ? A->unequal_m : 0)) * sizeof(int64_t));
     if (!mn || !mx || !packed || !cen_off) { rc = OR_ENOMEM; goto done; }
 
     rc = or_scale(A->raw, n, d, A->scaled, mn, mx);
     if (rc) goto done;
-    if (A->select_peel)
+    if (A->unequal_m > 0)
+        rc = or_group_unequal(A->scaled, n, d, A->unequal_m, A->perm, A->seg_off, &S, A->landmarks, NULL);
+    else if (A->select_peel)
         rc = or_peel_select(A->scaled, n, d, A->N, A->perm, A->seg_off, &S, A->landmarks);
     else
         rc = or_peel(A->scaled, n, d, A->N, A->perm, A->seg_off, &S, A->landmarks);

@@ -36,6 +36,7 @@ SIGNATURES = {
     "pscl_job_destroy": (_I, [_P]),
     "pscl_scale_features": (_I, [_P]),
     "pscl_subcluster": (_I, [_P, _I64, _I32, _I32, _U64, _I]),
+    "pscl_subcluster_unequal": (_I, [_P, _I32, _I32, _I32, _U64, _I]),
     "pscl_cluster": (_I, [_P, _I32, _I32, _U64, _I]),
     "pscl_run": (_I, [_P, _I64, _I32, _I32, _I32, _U64, _I]),
     "pscl_job_sync": (_I, [_P]),
@@ -173,6 +174,10 @@ def pscl_scale_features(job):
 
 def pscl_subcluster(job, N, local_k, iters, seed, prec=PSCL_PREC_FP32):
     _chk(lib().pscl_subcluster(job, N, local_k, iters, seed, prec))
+
+
+def pscl_subcluster_unequal(job, m, local_k, iters, seed, prec=PSCL_PREC_FP32):
+    _chk(lib().pscl_subcluster_unequal(job, m, local_k, iters, seed, prec))
 
 
 def pscl_cluster(job, final_k, iters, seed, prec=PSCL_PREC_FP32):
@@ -503,6 +508,13 @@ class Job:
     def steps(self, N, local_k, final_k, iters, seed, prec=PSCL_PREC_FP32):
         pscl_scale_features(self.h)
         pscl_subcluster(self.h, N, local_k, iters, seed, prec)
+        pscl_cluster(self.h, final_k, iters, seed, prec)
+        self.final_k = final_k
+
+    def steps_unequal(self, m, local_k, final_k, iters, seed, prec=PSCL_PREC_FP32):
+        """Algorithm 2 in place of the peel: m landmarks along the segment from L to H."""
+        pscl_scale_features(self.h)
+        pscl_subcluster_unequal(self.h, m, local_k, iters, seed, prec)
         pscl_cluster(self.h, final_k, iters, seed, prec)
         self.final_k = final_k
 

@@ -141,6 +141,12 @@ struct pscl_job : Owner {
     // recorded pipeline
     cudaGraphExec_t gexec = nullptr;
     uint64_t gkey[8] = {};
+    // Algorithm 2 (unequal-sized subclustering): m landmarks and the grouping's buffers
+    int unequal_m = 0;
+    float *u_lm = nullptr;
+    int32_t *u_group = nullptr;
+    uint32_t *u_cnt = nullptr, *u_total = nullptr;
+    double *u_lo = nullptr, *u_hi = nullptr;
     // serving: the peel goes to a stream shared by all jobs (cooperative launches one at a time)
     cudaStream_t coop = nullptr;
     cudaEvent_t coop_ev[2] = {};
@@ -462,12 +468,46 @@ static int check_prec(int prec)
     return PSCL_OK;
 }
 
+static int alloc_subcluster_buffers(pscl_job *j);
+static int plan_local(pscl_job *j, const std::vector<int64_t> &starts, const std::vector<int32_t> &sizes,
+                      int32_t local_k);
+static int plan_trace(pscl_job *j, int32_t iters);
+
 static int plan_subcluster(pscl_job *j, int64_t N, int32_t local_k, int32_t iters, uint64_t seed, int prec)
 {
     if (N < 1) return fail(PSCL_EINVAL, "N=%lld < 1", (long long)N);
     if (local_k < 1 || local_k > kMaxK) return fail(PSCL_EINVAL, "local_k=%d outside 1..%d", local_k, kMaxK);
     if (iters < 0) return fail(PSCL_EINVAL, "iters < 0");
     TRY(check_prec(prec));
+    TRY(alloc_subcluster_buffers(j));
+    const int64_t n = j->n;
+    const int d = j->d;
+    const bool same = N == j->N && local_k == j->local_k;
+    j->iters = iters;
+    j->seed = seed;
+    j->prec = prec;
+    if (!same) {
+        drop_graph(j);
+        j->N = N;
+        j->local_k = local_k;
+        const int64_t S = (n + N - 1) / N;
+        std::vector<int64_t> starts(S);
+        std::vector<int32_t> sizes(S);
+        for (int64_t s = 0; s < S; s++) {
+            starts[s] = s * N;
+            sizes[s] = (int32_t)std::min<int64_t>(N, n - s * N);
+        }
+        job_free(j, j->pb.landmarks);
+        j->pb.landmarks = nullptr;
+        TRY(A(j, &j->pb.landmarks, (size_t)S * d));
+        TRY(plan_local(j, starts, sizes, local_k));
+    }
+    return plan_trace(j, iters);
+}
+
+// The subcluster buffers every scheme uses (allocated once per job).
+static int alloc_subcluster_buffers(pscl_job *j)
+{
     const int64_t n = j->n;
     const int d = j->d;
     if (!j->peel_alloc) {
@@ -490,42 +530,40 @@ static int plan_subcluster(pscl_job *j, int64_t N, int32_t local_k, int32_t iter
         b.flags = j->flags;
         j->peel_alloc = true;
     }
-    const bool same = N == j->N && local_k == j->local_k;
-    j->iters = iters;
-    j->seed = seed;
-    j->prec = prec;
-    if (!same) {
-        drop_graph(j);
-        j->N = N;
-        j->local_k = local_k;
-        j->S = (n + N - 1) / N;
-        j->seg_off.assign(j->S + 1, 0);
-        std::vector<int64_t> starts(j->S);
-        std::vector<int32_t> sizes(j->S), keff(j->S);
-        for (int64_t s = 0; s < j->S; s++) {
-            j->seg_off[s] = s * N;
-            starts[s] = s * N;
-            sizes[s] = (int32_t)std::min<int64_t>(N, n - s * N);
-            keff[s] = std::min<int32_t>(local_k, sizes[s]);
-        }
-        j->seg_off[j->S] = n;
-        job_free(j, j->pb.landmarks);
-        j->pb.landmarks = nullptr;
-        TRY(A(j, &j->pb.landmarks, (size_t)j->S * d));
-        TRY(build_lloyd_plan(j, j->lp, starts, sizes, keff));
-        j->P = j->lp.P;
-        job_free(j, j->cl);
-        job_free(j, j->acc_l);
-        job_free(j, j->cnt_l);
-        j->cl = nullptr;
-        j->acc_l = nullptr;
-        j->cnt_l = nullptr;
-        TRY(A(j, &j->cl, (size_t)j->P * d));
-        TRY(A(j, &j->acc_l, (size_t)j->P * d));
-        TRY(A(j, &j->cnt_l, 2 * (size_t)j->P));
-        j->final_k = 0;              // the final plan depends on P
+    return PSCL_OK;
+}
+
+// The local Lloyd plan over the subclusters (starts, sizes), their centers and sums.
+static int plan_local(pscl_job *j, const std::vector<int64_t> &starts, const std::vector<int32_t> &sizes,
+                      int32_t local_k)
+{
+    const int d = j->d;
+    j->S = (int64_t)sizes.size();
+    j->seg_off.assign(j->S + 1, 0);
+    std::vector<int32_t> keff(j->S);
+    for (int64_t s = 0; s < j->S; s++) {
+        j->seg_off[s] = starts[s];
+        keff[s] = std::min<int32_t>(local_k, sizes[s]);
     }
-    int64_t tl = j->trace ? (int64_t)iters * n : 0;
+    j->seg_off[j->S] = j->n;
+    TRY(build_lloyd_plan(j, j->lp, starts, sizes, keff));
+    j->P = j->lp.P;
+    job_free(j, j->cl);
+    job_free(j, j->acc_l);
+    job_free(j, j->cnt_l);
+    j->cl = nullptr;
+    j->acc_l = nullptr;
+    j->cnt_l = nullptr;
+    TRY(A(j, &j->cl, (size_t)j->P * d));
+    TRY(A(j, &j->acc_l, (size_t)j->P * d));
+    TRY(A(j, &j->cnt_l, 2 * (size_t)j->P));
+    j->final_k = 0;              // the final plan depends on P
+    return PSCL_OK;
+}
+
+static int plan_trace(pscl_job *j, int32_t iters)
+{
+    int64_t tl = j->trace ? (int64_t)iters * j->n : 0;
     if (tl != j->trace_l_len) {
         job_free(j, j->trace_l);
         j->trace_l = nullptr;
@@ -760,6 +798,72 @@ extern "C" int pscl_subcluster(pscl_job *j, int64_t N, int32_t local_k, int32_t 
     TRY(plan_subcluster(j, N, local_k, iters, seed, prec));
     TRY(enqueue_subcluster(j, true));
     j->state = 2;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_subcluster_unequal(pscl_job *j, int32_t m, int32_t local_k, int32_t iters, uint64_t seed,
+                                       int prec)
+{
+    if (!j) return fail(PSCL_EINVAL, "job is NULL");
+    if (j->state < 1) return fail(PSCL_ESTATE, "pscl_subcluster_unequal needs pscl_scale_features first");
+    if (m < 1 || m > kMaxLandmarks) return fail(PSCL_EINVAL, "m=%d outside 1..%d", m, kMaxLandmarks);
+    if (local_k < 1 || local_k > kMaxK) return fail(PSCL_EINVAL, "local_k=%d outside 1..%d", local_k, kMaxK);
+    if (iters < 0) return fail(PSCL_EINVAL, "iters < 0");
+    TRY(check_prec(prec));
+    CU(cudaSetDevice(j->ctx->device));
+    TRY(alloc_subcluster_buffers(j));
+    const int64_t n = j->n;
+    const int d = j->d;
+    cudaStream_t st = j->ctx->stream;
+    drop_graph(j);
+    if (m != j->unequal_m) {
+        for (void *p : {(void *)j->u_lm, (void *)j->u_group, (void *)j->u_cnt, (void *)j->u_total, (void *)j->u_lo,
+                        (void *)j->u_hi})
+            job_free(j, p);
+        j->u_lm = nullptr;
+        j->u_group = nullptr;
+        j->u_cnt = nullptr;
+        j->u_total = nullptr;
+        j->u_lo = j->u_hi = nullptr;
+        TRY(A(j, &j->u_lm, (size_t)m * d));
+        TRY(A(j, &j->u_group, n));
+        TRY(A(j, &j->u_cnt, group_cnt_words(n, m)));
+        TRY(A(j, &j->u_total, m));
+        TRY(A(j, &j->u_lo, d));
+        TRY(A(j, &j->u_hi, d));
+        j->unequal_m = m;
+    }
+    // L, H of the scaled points, the landmarks, the groups and the grouped order
+    CU(launch_minmax(j->x, n, d, j->part, j->tickets + 2, j->u_lo, j->u_hi, j->flags, j->ctx->sm_count, st, &j->kt));
+    CU(launch_group_unequal(j->x, n, d, j->u_lo, j->u_hi, m, j->u_lm, j->u_group, j->u_cnt, j->u_total, j->pb.perm,
+                            st, &j->kt));
+    CU(launch_gather(j->x, j->pb.perm, n, d, j->pb.xseg, j->ctx->sm_count, st, &j->kt));
+    // the subclusters are the groups that got points: their sizes decide the Lloyd plan
+    std::vector<uint32_t> total(m);
+    CU(cudaMemcpyAsync(total.data(), j->u_total, m * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    std::vector<int64_t> starts;
+    std::vector<int32_t> sizes;
+    int64_t off = 0;
+    for (int i = 0; i < m; i++) {
+        if (!total[i]) continue;
+        starts.push_back(off);
+        sizes.push_back((int32_t)total[i]);
+        off += total[i];
+    }
+    if (off != n) return fail(PSCL_ECUDA, "internal error: the groups hold %lld of %lld points", (long long)off,
+                              (long long)n);
+    j->N = -(int64_t)m;                 // no equal-sized plan is current
+    j->local_k = local_k;
+    j->iters = iters;
+    j->seed = seed;
+    j->prec = prec;
+    TRY(plan_local(j, starts, sizes, local_k));
+    TRY(plan_trace(j, iters));
+    TRY(run_lloyd(j, j->lp, j->pb.xseg, j->cl, j->acc_l, j->cnt_l, j->lab_l, j->trace_l, iters, seed, 0u,
+                  j->plain != 0, prec));
+    j->state = 2;
+    j->ev_ok = false;
     return PSCL_OK;
 }
 

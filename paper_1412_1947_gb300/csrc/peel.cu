@@ -1134,19 +1134,26 @@ cudaError_t peel_launch(const PeelBuffers &b, int64_t n, int d, int64_t N, int s
     e = cudaLaunchKernelEx(&cfg, k_peel<D>, a);
     kt->end(PSCL_K_PEEL, st);
     if (e != cudaSuccess) return e;
-    int64_t work = (d % 4 == 0) ? n * d / 4 : n * d;
-    int64_t g = (work + 255) / 256;
-    if (g > (int64_t)sm_count * 16) g = (int64_t)sm_count * 16;
-    kt->begin(st);
-    if (d % 4 == 0)
-        k_gather_rows<true><<<(int)g, 256, 0, st>>>(b.x, b.perm, n, d, b.xseg);
-    else
-        k_gather_rows<false><<<(int)g, 256, 0, st>>>(b.x, b.perm, n, d, b.xseg);
-    kt->end(PSCL_K_GATHER, st);
-    return cudaGetLastError();
+    return launch_gather(b.x, b.perm, n, d, b.xseg, sm_count, st, kt);
 }
 
 }  // namespace
+
+cudaError_t launch_gather(const float *x, const uint32_t *perm, int64_t n, int d, float *xseg, int sm_count,
+                          cudaStream_t st, KTimer *kt)
+{
+    int64_t work = (d % 4 == 0) ? n * d / 4 : n * d;
+    int64_t g = (work + 255) / 256;
+    if (g > (int64_t)sm_count * 16) g = (int64_t)sm_count * 16;
+    if (g < 1) g = 1;
+    kt->begin(st);
+    if (d % 4 == 0)
+        k_gather_rows<true><<<(int)g, 256, 0, st>>>(x, perm, n, d, xseg);
+    else
+        k_gather_rows<false><<<(int)g, 256, 0, st>>>(x, perm, n, d, xseg);
+    kt->end(PSCL_K_GATHER, st);
+    return cudaGetLastError();
+}
 
 uint32_t peel_buckets(int64_t n)
 {

@@ -93,6 +93,9 @@ cudaError_t launch_scale(const float *raw, float *x, int64_t n, int d, float *pa
                          uint32_t *ticket, double *mn, double *mx, uint32_t *flags, int sm_count,
                          cudaStream_t st, KTimer *kt);
 size_t scale_part_floats(int64_t n, int d, int sm_count);
+// Column minima / maxima of x (n x d) into mn / mx (part, ticket: as for launch_scale).
+cudaError_t launch_minmax(const float *x, int64_t n, int d, float *part, uint32_t *ticket, double *mn, double *mx,
+                          uint32_t *flags, int sm_count, cudaStream_t st, KTimer *kt);
 // Independent sets: every set min-max scaled on its own (part: 2 x n_units x d floats,
 // mn / mx: n_seg x d).
 cudaError_t launch_seg_scale(const float *raw, float *x, const SegTable &t, const int32_t *seg_unit0, int d,
@@ -119,6 +122,19 @@ struct PeelBuffers {
 };
 // Buckets of the per-attribute orders the peel builds for n points.
 uint32_t peel_buckets(int64_t n);
+// Rows of x in the order of perm, packed into xseg (the gather after any subclustering).
+cudaError_t launch_gather(const float *x, const uint32_t *perm, int64_t n, int d, float *xseg, int sm_count,
+                          cudaStream_t st, KTimer *kt);
+
+// group.cu: Algorithm 2.  Landmarks lm (m x d) from lo / hi (the attributes' lowest and
+// highest values), the group of every point, and perm = the points grouped in landmark
+// order (ascending index inside a group); total[m] = each group's size.  cnt holds
+// group_cnt_words(n, m) words.
+constexpr int kMaxLandmarks = 4096;
+size_t group_cnt_words(int64_t n, int m);
+cudaError_t launch_group_unequal(const float *x, int64_t n, int d, const double *lo, const double *hi, int m,
+                                 float *lm, int32_t *group, uint32_t *cnt, uint32_t *total, uint32_t *perm,
+                                 cudaStream_t st, KTimer *kt);
 // api.cu: route a job's peel through stream s (ordered with the job's own stream);
 // a context's stream and device.
 int job_set_coop_stream(pscl_job *j, cudaStream_t s);

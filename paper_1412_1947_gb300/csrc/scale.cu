@@ -192,6 +192,20 @@ cudaError_t launch_seg_scale(const float *raw, float *x, const SegTable &t, cons
     return cudaGetLastError();
 }
 
+cudaError_t launch_minmax(const float *x, int64_t n, int d, float *part, uint32_t *ticket, double *mn, double *mx,
+                          uint32_t *flags, int sm_count, cudaStream_t st, KTimer *kt)
+{
+    int threads = d * (1024 / d);
+    int64_t rows_per_pass = threads / d;
+    int64_t want = (n + rows_per_pass - 1) / rows_per_pass;
+    int grid = (int)(want < (int64_t)sm_count * 4 ? want : (int64_t)sm_count * 4);
+    if (grid < 1) grid = 1;
+    kt->begin(st);
+    k_minmax<<<grid, threads, 2 * threads * sizeof(float), st>>>(x, n, d, part, ticket, mn, mx, flags);
+    kt->end(PSCL_K_SCALE_MINMAX, st);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scale(const float *raw, float *x, int64_t n, int d, float *part,
                          uint32_t *ticket, double *mn, double *mx, uint32_t *flags, int sm_count,
                          cudaStream_t st, KTimer *kt)

@@ -41,7 +41,7 @@ class GpuRun:
 
 
 def run_gpu(raw, N, local_k, final_k, iters, seed, *, trace=True, plain=False, first_k=False,
-            graph=False, prec=B.PSCL_PREC_FP32, runs=1, device_points=False):
+            graph=False, prec=B.PSCL_PREC_FP32, runs=1, device_points=False, unequal_m=0):
     pts = raw
     if device_points:
         import torch
@@ -56,7 +56,9 @@ def run_gpu(raw, N, local_k, final_k, iters, seed, *, trace=True, plain=False, f
         if graph:
             j.option(B.PSCL_OPT_GRAPH)
         for _ in range(runs):
-            if graph:
+            if unequal_m:
+                j.steps_unequal(unequal_m, local_k, final_k, iters, seed, prec)
+            elif graph:
                 j.run(N, local_k, final_k, iters, seed, prec)
             else:
                 j.steps(N, local_k, final_k, iters, seed, prec)
@@ -69,12 +71,12 @@ def run_gpu(raw, N, local_k, final_k, iters, seed, *, trace=True, plain=False, f
         return GpuRun(j.scaled(), perm, seg_off, lc, ke, cnt, fc, lab, sse, tl, tf, rc, asg)
 
 
-def run_oracle(raw, N, local_k, final_k, iters, seed, gpu: GpuRun | None = None, first_k=False):
+def run_oracle(raw, N, local_k, final_k, iters, seed, gpu: GpuRun | None = None, first_k=False, unequal_m=0):
     fl = ff = None
     if gpu is not None and gpu.trace_local is not None:
         fl, ff = gpu.trace_local, gpu.trace_final
     return oracle.two_level(raw, N, local_k, final_k, iters, seed, first_k=first_k,
-                            force_local=fl, force_final=ff, tie_tol=TIE_TOL)
+                            force_local=fl, force_final=ff, tie_tol=TIE_TOL, unequal_m=unequal_m)
 
 
 def center_err(a, ref):

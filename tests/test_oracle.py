@@ -312,3 +312,52 @@ def test_two_level_select_peel_flag_changes_nothing():
     np.testing.assert_array_equal(a.perm, b.perm)
     np.testing.assert_array_equal(a.final_centers, b.final_centers)
     assert a.sse == b.sse
+
+
+# ---------------------------------------------------------------- Algorithm 2 grouping
+def test_unequal_grouping_1d_closed_form():
+    # data spanning [0, 1]: 4 landmarks at 1/8, 3/8, 5/8, 7/8, a point x joins landmark
+    # ceil(4x) - 1 (0 for x = 0); x = 1/4, 1/2, 3/4 lie exactly between two landmarks and
+    # join the lower one
+    xs = np.array([0, 1, 0.25, 0.5, 0.75, 0.1, 0.3, 0.6, 0.9, 0.2499, 0.2501, 0.125, 0.5, 0.75],
+                  np.float32)[:, None]
+    perm, off, lm, g = oracle.group_unequal(xs, 4)
+    np.testing.assert_array_equal(lm[:, 0], np.array([0.125, 0.375, 0.625, 0.875], np.float32))
+    expect = np.maximum(np.ceil(xs[:, 0].astype(np.float64) * 4) - 1, 0).astype(np.int32)
+    np.testing.assert_array_equal(g, expect)
+    # groups in landmark order, ascending index inside each
+    sizes = np.bincount(expect, minlength=4)
+    np.testing.assert_array_equal(np.diff(off), sizes[sizes > 0])
+    for s in range(len(off) - 1):
+        seg = perm[off[s]:off[s + 1]]
+        assert np.all(np.diff(seg) > 0) and len(set(expect[seg])) == 1
+
+
+def test_unequal_landmarks_lie_on_the_segment_from_L_to_H():
+    # L = (0, 3, -2), H = (1, 3, 6): the constant attribute stays 3 on every landmark
+    x = np.array([[0, 3, 6], [1, 3, -2], [0.5, 3, 0], [0.2, 3, 1]], np.float32)
+    _, _, lm, _ = oracle.group_unequal(x, 5)
+    for i in range(5):
+        t = (i + 0.5) / 5
+        np.testing.assert_array_equal(lm[i], np.array([t, 3, -2 + 8 * t], np.float32))
+
+
+def test_unequal_empty_groups_are_skipped_and_m1_is_one_group():
+    rng = np.random.default_rng(4)
+    x = np.concatenate([rng.uniform(0, 0.05, (50, 2)), rng.uniform(0.95, 1.0, (50, 2))]).astype(np.float32)
+    perm, off, _, g = oracle.group_unequal(x, 10)
+    assert len(off) - 1 == len(np.unique(g)) < 10 and np.all(np.diff(off) > 0)
+    assert sorted(perm.tolist()) == list(range(100))
+    perm1, off1, _, g1 = oracle.group_unequal(x, 1)
+    np.testing.assert_array_equal(perm1, np.arange(100))
+    np.testing.assert_array_equal(off1, [0, 100])
+    assert not g1.any()
+
+
+def test_unequal_two_level_uses_the_grouping():
+    raw = synth.mixture(600, 3, 4, outlier_frac=0.05, seed=77)
+    o = oracle.two_level(raw, 0, 4, 3, 5, 9, unequal_m=12)
+    perm, off, _, _ = oracle.group_unequal(o.scaled, 12)
+    np.testing.assert_array_equal(o.perm, perm)
+    np.testing.assert_array_equal(o.seg_off, off)
+    assert o.local_centers.shape[0] == sum(min(4, int(v)) for v in np.diff(off))
