@@ -47,7 +47,9 @@ typedef enum {
     PSCL_ECUDA = 6     /* a CUDA runtime call failed; see pscl_last_error()            */
 } pscl_status;
 
-/* Storage type of the points (only float32 is accepted at present). */
+/* Storage type of the points.  PSCL_BF16: bfloat16 bit patterns (uint16); they are widened
+ * to float32 (exactly) at the start of every run and the scaled values are rounded to
+ * bfloat16 (Algorithm 1 step 1 in the job's storage type), kept in float32. */
 typedef enum { PSCL_F32 = 0, PSCL_BF16 = 1 } pscl_dtype;
 
 /* Arithmetic of the Lloyd assignment step (§I's "nearest center").
@@ -123,11 +125,11 @@ size_t pscl_ctx_bytes_in_use(const pscl_ctx *ctx);
 const char *pscl_last_error(void);
 
 /* Job: one clustering problem.
- *   points            n x d row-major float32, on the host (points_on_device = 0; copied
+ *   points            n x d row-major, float32 or bfloat16 (dtype), on the host (points_on_device = 0; copied
  *                     to the device before the call returns its status) or on the
  *                     context's device (points_on_device = 1; read later, by
  *                     pscl_scale_features).
- * Errors: PSCL_EINVAL (NULL pointer, n < 1, d outside 1..1024, dtype not PSCL_F32),
+ * Errors: PSCL_EINVAL (NULL pointer, n < 1, d outside 1..1024, dtype not PSCL_F32 / PSCL_BF16),
  *         PSCL_ENOMEM (over budget), PSCL_ECUDA. */
 int pscl_job_create(pscl_ctx *ctx, const void *points, int dtype, int64_t n, int32_t d,
                     int points_on_device, pscl_job **out);
@@ -249,7 +251,7 @@ int pscl_assign_sse_noalloc(const float *points, int64_t n, int32_t d, const flo
  * of pscl_job_create, pscl_subcluster and pscl_cluster, as counted against the budget):
  * the admission figure of the server below.  No device work. */
 int pscl_job_footprint(pscl_ctx *ctx, int64_t n, int32_t d, int64_t N, int32_t local_k, int32_t final_k,
-                       int32_t iters, int points_on_device, int trace, size_t *bytes);
+                       int32_t iters, int dtype, int points_on_device, int trace, size_t *bytes);
 
 /* ---------------------------------------------------------------- serving
  * A request loop for whole two-level jobs (scale + pscl_subcluster + pscl_cluster) of
@@ -267,7 +269,7 @@ typedef struct {
     const void *points;   /* n x d float32, row-major; must stay valid until the job is done */
     int32_t on_device;    /* 1: 16-byte aligned device memory of the server's device (read in
                              place); 0: host memory, copied when the job is admitted */
-    int32_t dtype;        /* PSCL_F32 */
+    int32_t dtype;        /* PSCL_F32, or PSCL_BF16 (bfloat16 bit patterns) */
     int64_t n;
     int32_t d;
     int64_t N;            /* subcluster size */

@@ -47,6 +47,8 @@ def lib():
         L.or_init_state.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32]
         L.or_init_indices.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int64, C.c_int32, P]
         L.or_scale.argtypes = [P, C.c_int64, C.c_int32, P, P, P]
+        L.or_group_unequal.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, P, P, P, P, P]
+        L.or_scale_storage.argtypes = [P, C.c_int64, C.c_int32, P, P, P, C.c_int]
         L.or_peel.argtypes = [P, C.c_int64, C.c_int32, C.c_int64, P, P, P, P]
         L.or_peel_select.argtypes = [P, C.c_int64, C.c_int32, C.c_int64, P, P, P, P]
         L.or_assign.argtypes = [P, C.c_int64, C.c_int32, P, C.c_int32, P, P, P]
@@ -82,13 +84,14 @@ def init_indices(seed: int, stage: int, segment: int, m: int, k: int) -> np.ndar
     return out
 
 
-def scale(raw: np.ndarray):
+def scale(raw: np.ndarray, bf16: bool = False):
+    """Min-max scaling; bf16 rounds the scaled values to bfloat16 (kept in float32)."""
     raw = np.ascontiguousarray(raw, np.float32)
     n, d = raw.shape
     out = np.empty_like(raw)
     mn = np.empty(d, np.float64)
     mx = np.empty(d, np.float64)
-    _check(lib().or_scale(_p(raw), n, d, _p(out), _p(mn), _p(mx)), "scale")
+    _check(lib().or_scale_storage(_p(raw), n, d, _p(out), _p(mn), _p(mx), int(bf16)), "scale")
     return out, mn, mx
 
 
@@ -170,7 +173,8 @@ class _Args(C.Structure):
         ("raw", C.c_void_p), ("n", C.c_int64), ("N", C.c_int64), ("d", C.c_int32),
         ("local_k", C.c_int32), ("final_k", C.c_int32), ("iters", C.c_int32),
         ("seed", C.c_uint64), ("first_k", C.c_int32), ("n_threads", C.c_int32),
-        ("select_peel", C.c_int32), ("unequal_m", C.c_int32), ("force_local", C.c_void_p), ("force_final", C.c_void_p), ("tie_tol", C.c_double),
+        ("select_peel", C.c_int32), ("unequal_m", C.c_int32), ("storage_bf16", C.c_int32),
+        ("force_local", C.c_void_p), ("force_final", C.c_void_p), ("tie_tol", C.c_double),
         ("scaled", C.c_void_p), ("perm", C.c_void_p), ("seg_off", C.c_void_p),
         ("landmarks", C.c_void_p), ("local_centers", C.c_void_p), ("local_k_eff", C.c_void_p),
         ("local_labels", C.c_void_p), ("local_sse", C.c_void_p), ("final_centers", C.c_void_p),
@@ -214,7 +218,7 @@ def pooled_count(n: int, N: int, local_k: int) -> tuple[int, int]:
 
 def two_level(raw: np.ndarray, N: int, local_k: int, final_k: int, iters: int, seed: int,
               first_k: bool = False, threads: int = 0, force_local=None, force_final=None,
-              select_peel: bool = False, unequal_m: int = 0,
+              select_peel: bool = False, unequal_m: int = 0, bf16: bool = False,
               tie_tol: float = 0.0) -> TwoLevel:
     """unequal_m > 0: Algorithm 2 with that many landmarks instead of the peel (N unused)."""
     raw = np.ascontiguousarray(raw, np.float32)
@@ -242,6 +246,7 @@ def two_level(raw: np.ndarray, N: int, local_k: int, final_k: int, iters: int, s
     a.first_k, a.n_threads = int(first_k), int(threads)
     a.select_peel = int(select_peel)
     a.unequal_m = int(unequal_m)
+    a.storage_bf16 = int(bf16)
     a.force_local = None if fl is None else fl.ctypes.data
     a.force_final = None if ff is None else ff.ctypes.data
     a.tie_tol = tie_tol

@@ -24,8 +24,9 @@
  * maximum H, every point grouped with its nearest landmark.
  *
  * Readings where the paper is silent (each is a choice, stated once here):
- *   - scaling: x' = float( (double(x) - mn) * (1 / (mx - mn)) ), the reciprocal and the
- *     product in double; a constant attribute scales to 0;
+ *   - scaling: x' = RN_storage( (double(x) - mn) * (1 / (mx - mn)) ), the reciprocal and
+ *     the product in double, rounded once to the job's storage type (float32, or bfloat16
+ *     kept in a float); a constant attribute scales to 0;
  *   - distance: squared Euclidean, summed over attributes j = 0..d-1 in ascending order;
  *   - peel ties: equal distances are taken in ascending point index;
  *   - the landmark is recomputed over the remaining points every round;
@@ -107,7 +108,20 @@ int or_init_indices(uint64_t seed, uint32_t stage, uint32_t segment, int64_t m, 
 /* Step 1: feature scaling (Algorithm 1 step 1; the paper leaves the method open and */
 /* min-max to [0,1] is used).                                                          */
 /* ------------------------------------------------------------------------------ */
-int or_scale(const float *raw, int64_t n, int32_t d, float *out, double *mn, double *mx)
+/* v rounded to nearest (ties to even) with 8 significant bits and bfloat16's exponent
+ * range (subnormal spacing 2^-133), directly from double. */
+static float round_bf16(double v)
+{
+    int e;
+    double m, r;
+    if (v == 0.0 || !isfinite(v)) return (float)v;
+    if (fabs(v) < ldexp(1.0, -126)) return (float)(nearbyint(ldexp(v, 133)) * ldexp(1.0, -133));
+    m = frexp(v, &e);                         /* v = m 2^e, 0.5 <= |m| < 1 */
+    r = nearbyint(ldexp(m, 8));               /* 8 significant bits, ties to even */
+    return (float)ldexp(r, e - 8);
+}
+
+int or_scale_storage(const float *raw, int64_t n, int32_t d, float *out, double *mn, double *mx, int bf16)
 {
     int64_t i;
     int32_t j;
@@ -128,13 +142,18 @@ int or_scale(const float *raw, int64_t n, int32_t d, float *out, double *mn, dou
         for (i = 0; i < n; i++) {
             if (range > 0.0) {
                 double t = (double)raw[i * d + j] - mn[j];
-                out[i * d + j] = (float)(t * inv);
+                out[i * d + j] = bf16 ? round_bf16(t * inv) : (float)(t * inv);
             } else {
                 out[i * d + j] = 0.0f;
             }
         }
     }
     return OR_OK;
+}
+
+int or_scale(const float *raw, int64_t n, int32_t d, float *out, double *mn, double *mx)
+{
+    return or_scale_storage(raw, n, d, out, mn, mx, 0);
 }
 
 /* ------------------------------------------------------------------------------ */
@@ -453,6 +472,7 @@ typedef struct {
     int32_t n_threads;        /* threads over subclusters (0 = library default)    */
     int32_t select_peel;      /* 1: or_peel_select instead of or_peel (same result) */
     int32_t unequal_m;        /* > 0: Algorithm 2 with this many landmarks instead of the peel */
+    int32_t storage_bf16;     /* 1: scaled values rounded to bfloat16 (raw: bfloat16 values) */
     const int32_t *force_local; /* optional iters*n trace, subcluster-packed order */
     const int32_t *force_final; /* optional iters*P trace                          */
     double tie_tol;
@@ -496,7 +516,7 @@ int or_two_level(or_two_level_args *A)
     cen_off = (int64_t *)malloc((size_t)(n / A->N + 2 + (A->unequal_m > 0 ? A->unequal_m : 0)) * sizeof(int64_t));
     if (!mn || !mx || !packed || !cen_off) { rc = OR_ENOMEM; goto done; }
 
-    rc = or_scale(A->raw, n, d, A->scaled, mn, mx);
+    rc = or_scale_storage(A->raw, n, d, A->scaled, mn, mx, A->storage_bf16);
     if (rc) goto done;
     if (A->unequal_m > 0)
         rc = or_group_unequal(A->scaled, n, d, A->unequal_m, A->perm, A->seg_off, &S, A->landmarks, NULL);

@@ -50,7 +50,7 @@ SIGNATURES = {
     "pscl_get_kernel_times": (_I, [_P, _P, _P]),
     "pscl_get_recheck_stats": (_I, [_P, _P, _P]),
     "pscl_assign_sse_noalloc": (_I, [_P, _I64, _I32, _P, _I32, _P, _P, _P]),
-    "pscl_job_footprint": (_I, [_P, _I64, _I32, _I64, _I32, _I32, _I32, _I, _I, _P]),
+    "pscl_job_footprint": (_I, [_P, _I64, _I32, _I64, _I32, _I32, _I32, _I, _I, _I, _P]),
     "pscl_server_create": (_I, [_P, _I32, _SZ, _P]),
     "pscl_submit": (_I, [_P, _P, _P]),
     "pscl_poll": (_I, [_P, _U64, _P]),
@@ -122,14 +122,22 @@ def _ptr(a):
 
 
 def _points(points):
-    """(pointer, on_device, n, d, keep-alive) for a numpy array or a torch CUDA tensor."""
+    """(pointer, on_device, n, d, keep-alive) for a numpy array or a torch tensor:
+    float32, or bfloat16 (torch.bfloat16, or numpy uint16 holding bfloat16 bits)."""
     if isinstance(points, np.ndarray):
-        a = np.ascontiguousarray(points, dtype=np.float32)
+        a = np.ascontiguousarray(points, dtype=np.uint16 if points.dtype == np.uint16 else np.float32)
         return a.ctypes.data, 0, a.shape[0], a.shape[1], a
     t = points
-    if t.dtype.itemsize != 4 or not t.is_contiguous() or t.dim() != 2:
-        raise ValueError("points must be a contiguous 2-D float32 tensor")
+    if t.dtype.itemsize not in (2, 4) or not t.is_contiguous() or t.dim() != 2:
+        raise ValueError("points must be a contiguous 2-D float32 or bfloat16 tensor")
     return t.data_ptr(), 1 if t.is_cuda else 0, t.shape[0], t.shape[1], t
+
+
+def _dtype(points):
+    """PSCL_BF16 for bfloat16 points (torch.bfloat16 or numpy uint16 bits), else PSCL_F32."""
+    if isinstance(points, np.ndarray):
+        return PSCL_BF16 if points.dtype == np.uint16 else PSCL_F32
+    return PSCL_BF16 if points.dtype.itemsize == 2 else PSCL_F32
 
 
 # ---------------------------------------------------------------- C entry points
@@ -147,8 +155,9 @@ def pscl_ctx_bytes_in_use(ctx):
     return lib().pscl_ctx_bytes_in_use(ctx)
 
 
-def pscl_job_create(ctx, points, dtype=PSCL_F32):
+def pscl_job_create(ctx, points, dtype=None):
     p, dev, n, d, keep = _points(points)
+    dtype = _dtype(points) if dtype is None else dtype
     h = C.c_void_p()
     _chk(lib().pscl_job_create(ctx, p, dtype, n, d, dev, C.byref(h)))
     return h, keep
@@ -265,9 +274,10 @@ def pscl_assign_sse_noalloc(points, centers, labels, sse, stream=None):
                                        labels.data_ptr(), sse.data_ptr(), stream))
 
 
-def pscl_job_footprint(ctx, n, d, N, local_k, final_k, iters, on_device=True, trace=False):
+def pscl_job_footprint(ctx, n, d, N, local_k, final_k, iters, on_device=True, trace=False, dtype=PSCL_F32):
     b = C.c_size_t()
-    _chk(lib().pscl_job_footprint(ctx, n, d, N, local_k, final_k, iters, int(on_device), int(trace), C.byref(b)))
+    _chk(lib().pscl_job_footprint(ctx, n, d, N, local_k, final_k, iters, dtype, int(on_device), int(trace),
+                                  C.byref(b)))
     return b.value
 
 
@@ -280,7 +290,7 @@ def pscl_server_create(ctx, slots, hbm_budget_bytes=0):
 def pscl_submit(server, points, N, local_k, final_k, iters, seed, prec=PSCL_PREC_FP32, want_labels=False):
     """Queues a job; returns (ticket, keep-alive of the points)."""
     p, dev, n, d, keep = _points(points)
-    desc = JobDesc(p, dev, PSCL_F32, n, d, N, local_k, final_k, iters, seed, prec, int(want_labels))
+    desc = JobDesc(p, dev, _dtype(points), n, d, N, local_k, final_k, iters, seed, prec, int(want_labels))
     t = C.c_uint64()
     _chk(lib().pscl_submit(server, C.byref(desc), C.byref(t)))
     return t.value, keep

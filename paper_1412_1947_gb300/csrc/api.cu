@@ -98,8 +98,11 @@ struct pscl_job : Owner {
     int plain = 0, trace = 0, first_k = 0, graph = 0, ktiming = 0;
     KTimer kt;                        // launch counts (+ events when timing) of the last run
     // input and scaling
-    const float *dev_in = nullptr;    // caller's device buffer, or raw
-    float *raw = nullptr;             // owned copy of host input
+    int dtype = PSCL_F32;
+    const float *dev_in = nullptr;    // caller's device buffer, or raw (float32 points)
+    float *raw = nullptr;             // owned copy of host input, or the widened bfloat16 input
+    const uint16_t *in16 = nullptr;   // bfloat16 input: the caller's device buffer, or raw16
+    uint16_t *raw16 = nullptr;        // owned copy of bfloat16 host input
     float *x = nullptr;               // scaled points (original order)
     double *mn = nullptr, *mx = nullptr;
     float *part = nullptr;
@@ -261,6 +264,28 @@ extern "C" const char *pscl_last_error(void) { return g_err.c_str(); }
 static int load_points(pscl_job *j, const void *points, int on_device)
 {
     if (!points) return fail(PSCL_EINVAL, "points is NULL");
+    if (j->dtype == PSCL_BF16) {
+        // bfloat16 points: widened to float32 at the start of every run (enqueue_scale)
+        if (!j->raw) TRY(A(j, &j->raw, (size_t)j->n * j->d));
+        if (on_device) {
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, points) != cudaSuccess || at.type != cudaMemoryTypeDevice ||
+                at.device != j->ctx->device) {
+                cudaGetLastError();
+                return fail(PSCL_EINVAL, "points_on_device=1 but the pointer is not device memory of device %d",
+                            j->ctx->device);
+            }
+            j->in16 = static_cast<const uint16_t *>(points);
+        } else {
+            if (!j->raw16) TRY(A(j, &j->raw16, (size_t)j->n * j->d));
+            CU(cudaMemcpyAsync(j->raw16, points, (size_t)j->n * j->d * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                               j->ctx->stream));
+            j->in16 = j->raw16;
+        }
+        j->dev_in = j->raw;
+        j->state = 0;
+        return PSCL_OK;
+    }
     if (on_device) {
         cudaPointerAttributes at{};
         if (cudaPointerGetAttributes(&at, points) != cudaSuccess || at.type != cudaMemoryTypeDevice ||
@@ -285,7 +310,7 @@ extern "C" int pscl_job_create(pscl_ctx *c, const void *points, int dtype, int64
                                int on_device, pscl_job **out)
 {
     if (!c || !out) return fail(PSCL_EINVAL, "ctx or out is NULL");
-    if (dtype != PSCL_F32) return fail(PSCL_EINVAL, "only PSCL_F32 storage is supported");
+    if (dtype != PSCL_F32 && dtype != PSCL_BF16) return fail(PSCL_EINVAL, "dtype %d is not PSCL_F32 or PSCL_BF16", dtype);
     if (n < 1 || n > (int64_t)INT32_MAX) return fail(PSCL_EINVAL, "n=%lld outside 1..2^31-1", (long long)n);
     if (d < 1 || d > kMaxD) return fail(PSCL_EINVAL, "d=%d outside 1..%d", d, kMaxD);
     CU(cudaSetDevice(c->device));
@@ -293,6 +318,7 @@ extern "C" int pscl_job_create(pscl_ctx *c, const void *points, int dtype, int64
     j->ctx = c;
     j->n = n;
     j->d = d;
+    j->dtype = dtype;
     int rc = PSCL_OK;
     if (!rc) rc = A(j, &j->x, (size_t)n * d);
     if (!rc) rc = A(j, &j->mn, d);
@@ -625,12 +651,17 @@ static size_t r256(size_t b) { return ((b ? b : 16) + 255) & ~(size_t)255; }
 
 // Device bytes a job of this shape holds after pscl_run: every allocation of
 // pscl_job_create, plan_subcluster and plan_cluster, each rounded as job_alloc rounds it.
-static size_t job_footprint(int64_t n, int d, int64_t N, int local_k, int final_k, int iters, bool host_input,
-                            bool trace, int sm)
+static size_t job_footprint(int64_t n, int d, int64_t N, int local_k, int final_k, int iters, int dtype,
+                            bool host_input, bool trace, int sm)
 {
     size_t b = r256((size_t)n * d * 4) + 2 * r256((size_t)d * 8) + r256(scale_part_floats(n, d, sm) * 4) +
                r256(8 * 4) + r256(sizeof(PeelCtl)) + r256(kFlagWords * 4);
-    if (host_input) b += r256((size_t)n * d * 4);
+    if (dtype == PSCL_BF16) {
+        b += r256((size_t)n * d * 4);                         // the widened points
+        if (host_input) b += r256((size_t)n * d * 2);         // the bfloat16 copy
+    } else if (host_input) {
+        b += r256((size_t)n * d * 4);
+    }
     const int64_t ord_ld = (n + 3) & ~(int64_t)3;
     const size_t nbk = peel_buckets(n);
     b += r256((size_t)n * 4) + r256((size_t)d * ord_ld * 4) + r256((size_t)d * nbk * 4) + r256((size_t)d * nbk * 16) +
@@ -672,12 +703,13 @@ int pscl::job_set_coop_stream(pscl_job *j, cudaStream_t s)
 }
 
 extern "C" int pscl_job_footprint(pscl_ctx *c, int64_t n, int32_t d, int64_t N, int32_t local_k, int32_t final_k,
-                                  int32_t iters, int points_on_device, int trace, size_t *bytes)
+                                  int32_t iters, int dtype, int points_on_device, int trace, size_t *bytes)
 {
     if (!c || !bytes) return fail(PSCL_EINVAL, "ctx or bytes is NULL");
     if (n < 1 || d < 1 || N < 1 || local_k < 1 || final_k < 1 || iters < 0)
         return fail(PSCL_EINVAL, "shape out of range");
-    *bytes = job_footprint(n, d, N, local_k, final_k, iters, !points_on_device, trace != 0, c->sm_count);
+    if (dtype != PSCL_F32 && dtype != PSCL_BF16) return fail(PSCL_EINVAL, "unknown dtype %d", dtype);
+    *bytes = job_footprint(n, d, N, local_k, final_k, iters, dtype, !points_on_device, trace != 0, c->sm_count);
     return PSCL_OK;
 }
 
@@ -721,8 +753,9 @@ static int enqueue_scale(pscl_job *j, bool events)
     cudaStream_t st = j->ctx->stream;
     if (events) CU(cudaEventRecord(j->ev[0], st));
     CU(cudaMemsetAsync(j->flags, 0, kFlagWords * sizeof(uint32_t), st));   // errors and counters of this run
+    if (j->dtype == PSCL_BF16) CU(launch_widen_bf16(j->in16, j->raw, j->n * j->d, j->ctx->sm_count, st));
     CU(launch_scale(j->dev_in, j->x, j->n, j->d, j->part, j->tickets, j->mn, j->mx, j->flags,
-                    j->ctx->sm_count, st, &j->kt));
+                    j->ctx->sm_count, st, &j->kt, j->dtype == PSCL_BF16));
     if (events) CU(cudaEventRecord(j->ev[1], st));
     return PSCL_OK;
 }
@@ -899,7 +932,8 @@ extern "C" int pscl_run(pscl_job *j, int64_t N, int32_t local_k, int32_t final_k
         return PSCL_OK;
     }
     uint64_t key[8] = {(uint64_t)N, (uint64_t)local_k, (uint64_t)final_k, (uint64_t)iters, seed, (uint64_t)prec,
-                       (uint64_t)(uintptr_t)j->dev_in, (uint64_t)(j->plain | j->trace << 1 | j->first_k << 2)};
+                       (uint64_t)(uintptr_t)j->dev_in ^ (uint64_t)(uintptr_t)j->in16,
+                       (uint64_t)(j->plain | j->trace << 1 | j->first_k << 2)};
     if (j->gexec && memcmp(key, j->gkey, sizeof key) != 0) drop_graph(j);
     if (!j->gexec) {
         cudaGraph_t g = nullptr;

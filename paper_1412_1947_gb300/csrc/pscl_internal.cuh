@@ -89,9 +89,12 @@ struct KTimer {
 // All launchers queue work on `st` and return cudaGetLastError().
 
 // scale.cu
+// bf16: round the scaled values to bfloat16 (kept in float32).
 cudaError_t launch_scale(const float *raw, float *x, int64_t n, int d, float *part,
                          uint32_t *ticket, double *mn, double *mx, uint32_t *flags, int sm_count,
-                         cudaStream_t st, KTimer *kt);
+                         cudaStream_t st, KTimer *kt, int bf16 = 0);
+// bfloat16 points (bit patterns) widened to float32.
+cudaError_t launch_widen_bf16(const uint16_t *in, float *out, int64_t count, int sm_count, cudaStream_t st);
 size_t scale_part_floats(int64_t n, int d, int sm_count);
 // Column minima / maxima of x (n x d) into mn / mx (part, ticket: as for launch_scale).
 cudaError_t launch_minmax(const float *x, int64_t n, int d, float *part, uint32_t *ticket, double *mn, double *mx,

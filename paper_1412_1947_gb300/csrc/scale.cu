@@ -1,11 +1,14 @@
 // Feature scaling (Algorithm 1, step 1): min-max of every attribute to [0, 1].
 //
 //   mn_j = min_i x_ij, mx_j = max_i x_ij              (exact in any order)
-//   x'_ij = float( (double(x_ij) - mn_j) * (1 / (mx_j - mn_j)) )  in double, 0 if mx_j = mn_j
+//   x'_ij = RN( (double(x_ij) - mn_j) * (1 / (mx_j - mn_j)) )  in double, 0 if mx_j = mn_j,
+//           rounded once to the storage type (float32, or bfloat16 kept in a float)
 //
 // Two kernels: a column min/max reduction (per-block partials, the last block to finish
 // folds them) and an element-wise pass.  Both are HBM-bound: 2 reads + 1 write of n*d*4
 // bytes in total.
+#include <cuda_bf16.h>
+
 #include "pscl_internal.cuh"
 
 namespace pscl {
@@ -65,7 +68,20 @@ __global__ void k_minmax(const float *__restrict__ raw, int64_t n, int d, float 
     if (t == 0) *ticket = 0;
 }
 
-template <bool kVec4>
+template <bool kBf16>
+__device__ __forceinline__ float to_storage(double v)
+{
+    return kBf16 ? __bfloat162float(__double2bfloat16(v)) : __double2float_rn(v);
+}
+
+// bfloat16 points widened to float32 (exact).
+__global__ void k_widen_bf16(const uint16_t *__restrict__ in, float *__restrict__ out, int64_t count)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = __uint_as_float((uint32_t)in[e] << 16);
+}
+
+template <bool kVec4, bool kBf16>
 __global__ void k_scale_apply(const float *__restrict__ raw, float *__restrict__ x, int64_t n,
                               int d, const double *__restrict__ mn, const double *__restrict__ mx)
 {
@@ -90,7 +106,7 @@ __global__ void k_scale_apply(const float *__restrict__ raw, float *__restrict__
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 double inv = sinv[a + q];
-                o[q] = inv != 0.0 ? __double2float_rn(__dmul_rn(__dsub_rn((double)o[q], smn[a + q]), inv))
+                o[q] = inv != 0.0 ? to_storage<kBf16>(__dmul_rn(__dsub_rn((double)o[q], smn[a + q]), inv))
                                   : 0.0f;
             }
             x4[e] = make_float4(o[0], o[1], o[2], o[3]);
@@ -100,7 +116,7 @@ __global__ void k_scale_apply(const float *__restrict__ raw, float *__restrict__
              e += (int64_t)gridDim.x * blockDim.x) {
             int a = (int)(e % d);
             double inv = sinv[a];
-            x[e] = inv != 0.0 ? __double2float_rn(__dmul_rn(__dsub_rn((double)raw[e], smn[a]), inv))
+            x[e] = inv != 0.0 ? to_storage<kBf16>(__dmul_rn(__dsub_rn((double)raw[e], smn[a]), inv))
                               : 0.0f;
         }
     }
@@ -206,9 +222,18 @@ cudaError_t launch_minmax(const float *x, int64_t n, int d, float *part, uint32_
     return cudaGetLastError();
 }
 
+cudaError_t launch_widen_bf16(const uint16_t *in, float *out, int64_t count, int sm_count, cudaStream_t st)
+{
+    int64_t g = (count + 255) / 256;
+    if (g > (int64_t)sm_count * 16) g = (int64_t)sm_count * 16;
+    if (g < 1) g = 1;
+    k_widen_bf16<<<(int)g, 256, 0, st>>>(in, out, count);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scale(const float *raw, float *x, int64_t n, int d, float *part,
                          uint32_t *ticket, double *mn, double *mx, uint32_t *flags, int sm_count,
-                         cudaStream_t st, KTimer *kt)
+                         cudaStream_t st, KTimer *kt, int bf16)
 {
     int threads = d * (1024 / d);
     int64_t rows_per_pass = threads / d;
@@ -225,10 +250,14 @@ cudaError_t launch_scale(const float *raw, float *x, int64_t n, int d, float *pa
     if (g2 < 1) g2 = 1;
     size_t smem = 2 * (size_t)d * sizeof(double);
     kt->begin(st);
-    if (vec)
-        k_scale_apply<true><<<(int)g2, 256, smem, st>>>(raw, x, n, d, mn, mx);
+    if (vec && bf16)
+        k_scale_apply<true, true><<<(int)g2, 256, smem, st>>>(raw, x, n, d, mn, mx);
+    else if (vec)
+        k_scale_apply<true, false><<<(int)g2, 256, smem, st>>>(raw, x, n, d, mn, mx);
+    else if (bf16)
+        k_scale_apply<false, true><<<(int)g2, 256, smem, st>>>(raw, x, n, d, mn, mx);
     else
-        k_scale_apply<false><<<(int)g2, 256, smem, st>>>(raw, x, n, d, mn, mx);
+        k_scale_apply<false, false><<<(int)g2, 256, smem, st>>>(raw, x, n, d, mn, mx);
     kt->end(PSCL_K_SCALE_APPLY, st);
     return cudaGetLastError();
 }

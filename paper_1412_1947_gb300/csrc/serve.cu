@@ -247,7 +247,8 @@ extern "C" int pscl_submit(pscl_server *s, const pscl_job_desc *d, uint64_t *tic
         d->local_k > pscl::kMaxK || d->final_k < 1 || d->final_k > pscl::kMaxK || d->iters < 0)
         return set_err(PSCL_EINVAL, "job shape out of range");
     size_t fp = 0;
-    int rc = pscl_job_footprint(s->probe, d->n, d->d, d->N, d->local_k, d->final_k, d->iters, d->on_device, 0, &fp);
+    int rc = pscl_job_footprint(s->probe, d->n, d->d, d->N, d->local_k, d->final_k, d->iters, d->dtype, d->on_device,
+                                0, &fp);
     if (rc) return rc;
     Ticket *t = new Ticket();
     t->desc = *d;

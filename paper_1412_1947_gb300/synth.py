@@ -145,7 +145,8 @@ def mixture_device(n: int, d: int, blobs: int, seed: int, device, sigma_range=(0
 def serving_stream(count: int, seed: int, n_range=(1e4, 1e6), dims=(8, 32, 128), k_range=(8, 1024)):
     """Job shapes of the serving workload: n and final k log-uniform, d uniform on dims,
     N = ceil(n / 64), local k = min(N, max(8, ceil(N / 256), ceil(2 final_k / S))) so that
-    the pooled local centers number at least 2 final_k; 25 iterations."""
+    the pooled local centers number at least 2 final_k; 25 iterations; storage bfloat16 or
+    float32 with probability 1/2 each."""
     g = rng(seed)
     jobs = []
     for i in range(count):
@@ -156,6 +157,7 @@ def serving_stream(count: int, seed: int, n_range=(1e4, 1e6), dims=(8, 32, 128),
         S = -(-n // N)
         lk = min(N, max(8, -(-N // 256), -(-2 * fk // S)))
         fk = min(fk, S * lk)
+        bf16 = bool(g.random() < 0.5)
         jobs.append({"n": n, "d": d, "N": N, "local_k": lk, "final_k": fk, "iters": 25, "seed": seed * 7 + i,
-                     "blobs": max(2, fk)})
+                     "blobs": max(2, fk), "bf16": bf16})
     return jobs

@@ -361,3 +361,21 @@ def test_unequal_two_level_uses_the_grouping():
     np.testing.assert_array_equal(o.perm, perm)
     np.testing.assert_array_equal(o.seg_off, off)
     assert o.local_centers.shape[0] == sum(min(4, int(v)) for v in np.diff(off))
+
+
+# ---------------------------------------------------------------- bfloat16 storage
+def test_bf16_storage_rounds_once_to_nearest_even():
+    # raw [0, 512, 257, 259, 384, 171]: scaled = v / 512 exactly, then 8 significant bits:
+    #   257/512 = 0.5 + 2^-9, halfway between 0.5 and 0.5 + 2^-8 -> 0.5 (even)
+    #   259/512 = 0.5 + 1.5 * 2^-8, halfway -> 0.5 + 2^-7 (even)
+    #   384/512 = 0.75 exact; 171/512 = 0.333984375 exact (0x3EAB)
+    raw = np.array([[0.0], [512.0], [257.0], [259.0], [384.0], [171.0]], np.float32)
+    xs, _, _ = oracle.scale(raw, bf16=True)
+    np.testing.assert_array_equal(xs[:, 0], np.array([0, 1, 0.5, 0.5078125, 0.75, 0.333984375], np.float32))
+    # 1/3 from [0, 3]: 1.0101010101..b x 2^-2, the bit after the 8th is 1 with more set bits
+    # after it -> rounds up to 1.0101011b x 2^-2 = 0.333984375
+    xs2, _, _ = oracle.scale(np.array([[0.0], [3.0], [1.0]], np.float32), bf16=True)
+    assert xs2[2, 0] == np.float32(0.333984375)
+    # float32 storage keeps 24 bits
+    xs3, _, _ = oracle.scale(np.array([[0.0], [3.0], [1.0]], np.float32))
+    assert xs3[2, 0] == np.float32(1.0 / 3.0)
