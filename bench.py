@@ -38,9 +38,9 @@ UNIT = "dist-evals/s"
 L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2
 FP32_ALU_PEAK = 152 * 128 * 2 * 2.07e9   # SMs x FP32 lanes x 2 flop (FMA) x max SM clock
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands, by
-# (kernel, workload): 301.5 MB + 207.1 MB for the peel on the 2^20 x 16 workload
+# (kernel, workload): 296.0 MB + 189.4 MB for the peel on the 2^20 x 16 workload
 # (profiles/k_peel_n1048576_d16.md).  Drop an entry when its kernel changes.
-NCU_TRAFFIC = {("peel", "n1048576_d16_N4096_k64_f64"): 508.57e6}
+NCU_TRAFFIC = {("peel", "n1048576_d16_N4096_k64_f64"): 485.40e6}
 
 
 def replica_max(x: float, dist=None) -> float:
@@ -205,6 +205,7 @@ def main_arm(args, w: synth.Workload):
     ctx = B.pscl_ctx_create(local, 0, stream.cuda_stream)
     job = B.Job(x_dev, ctx=ctx)
     job.option(B.PSCL_OPT_GRAPH)
+    job.option(B.PSCL_OPT_ROWS_PER_THREAD, args.rows_per_thread)
     run = lambda: job.run(wr.N, wr.local_k, wr.final_k, wr.iters, seed, prec)  # noqa: E731
 
     for _ in range(args.warmup):
@@ -239,6 +240,7 @@ def main_arm(args, w: synth.Workload):
     ctx_e = B.pscl_ctx_create(local, 0, stream.cuda_stream)
     job_e = B.Job(host, ctx=ctx_e)
     job_e.option(B.PSCL_OPT_GRAPH)
+    job_e.option(B.PSCL_OPT_ROWS_PER_THREAD, args.rows_per_thread)
     for _ in range(max(1, args.warmup)):
         job_e.load(host)
         job_e.run(wr.N, wr.local_k, wr.final_k, wr.iters, seed, prec)
@@ -259,6 +261,7 @@ def main_arm(args, w: synth.Workload):
     # ---- per-kernel device times (events around every launch, unrecorded runs)
     job_k = B.Job(x_dev, ctx=ctx)
     job_k.option(B.PSCL_OPT_KERNEL_TIMING)
+    job_k.option(B.PSCL_OPT_ROWS_PER_THREAD, args.rows_per_thread)
     kt = None
     for _ in range(2):
         flush.zero_()
@@ -536,6 +539,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="medium", choices=["small", "medium", "large", "uneven", "serving"])
+    ap.add_argument("--rows-per-thread", type=int, default=0, choices=[0, 1, 2],
+                    help="float32 assignment: 0 default, 1 one row per thread, 2 eight rows (d <= 16)")
     ap.add_argument("--serve-jobs", type=int, default=200)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--oracle-n", type=int, default=1 << 17)

@@ -92,8 +92,9 @@ typedef enum {
      *    32..1024 (rounded up to a multiple of 32), 0 = the planner's default.  A tuning
      *    choice: results do not depend on it. */
     PSCL_OPT_UNIT_ROWS = 6,
-    /* Batches only: 1 = one row per thread in the float32 assignment kernel, 0 = its
-     *    default (up to 4 rows kept in registers).  Results do not depend on it. */
+    /* Rows per thread in the float32 assignment kernel: 0 = its default (up to 4 rows
+     *    kept in registers), 1 = one, 2 = eight for d <= 16.  Jobs and batches; results do
+     *    not depend on it. */
     PSCL_OPT_ROWS_PER_THREAD = 7
 } pscl_option;
 
@@ -331,7 +332,7 @@ int pscl_batch_load(pscl_batch *b, const void *points, int on_device);
  * PSCL_OPT_ROWS_PER_THREAD; others return PSCL_EINVAL. */
 int pscl_batch_set_option(pscl_batch *b, int option, int64_t value);
 /* Autotuner: times `iters` Lloyd iterations of this batch (unrecorded, after one warm-up
- * run) for every work-unit size in {128, 256, 512, 1024} rows and both rows-per-thread
+ * run) for every work-unit size in {128, 256, 512, 1024} rows and the three rows-per-thread
  * settings, keeps the fastest and applies it; the choice is remembered for later batches
  * of the same (device, d, largest k, log2 of the rows, prec).  Writes the choice and
  * whether it came from that memory (any output may be NULL).  Results never depend on it. */

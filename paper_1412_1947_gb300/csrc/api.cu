@@ -95,7 +95,7 @@ struct pscl_job : Owner {
     int d = 0;
     int state = 0;                    // 0 loaded, 1 scaled, 2 subclustered, 3 clustered
     // options
-    int plain = 0, trace = 0, first_k = 0, graph = 0, ktiming = 0;
+    int plain = 0, trace = 0, first_k = 0, graph = 0, ktiming = 0, rpt = 0;
     KTimer kt;                        // launch counts (+ events when timing) of the last run
     // input and scaling
     int dtype = PSCL_F32;
@@ -360,6 +360,10 @@ extern "C" int pscl_job_set_option(pscl_job *j, int opt, int64_t v)
     case PSCL_OPT_INIT_FIRST_K: j->first_k = v != 0; break;
     case PSCL_OPT_GRAPH: j->graph = v != 0; break;
     case PSCL_OPT_KERNEL_TIMING: j->ktiming = v != 0; break;
+    case PSCL_OPT_ROWS_PER_THREAD:
+        if (v < 0 || v > 2) return fail(PSCL_EINVAL, "rows per thread must be 0, 1 or 2");
+        j->rpt = (int)v;
+        break;
     default: return fail(PSCL_EINVAL, "unknown option %d", opt);
     }
     drop_graph(j);
@@ -733,7 +737,7 @@ static int run_lloyd(pscl_job *j, const LloydPlan &p, const float *pts, float *c
         for (int it = 0; it < iters; it++) {
             b.count = cnt2 + (size_t)(it & 1) * p.P;
             CU(launch_lloyd_iter(b, cnt2 + (size_t)((it + 1) & 1) * p.P, t, j->d, it, 0, p.n_units, 0, p.P,
-                                 p.kmax, prec, j->flags, j->ctx->sm_count, st, &j->kt));
+                                 p.kmax, prec, j->flags, j->ctx->sm_count, st, &j->kt, j->rpt));
         }
     } else {
         for (int s = 0; s < p.n_seg; s++) {
@@ -741,7 +745,7 @@ static int run_lloyd(pscl_job *j, const LloydPlan &p, const float *pts, float *c
                 b.count = cnt2 + (size_t)(it & 1) * p.P;
                 CU(launch_lloyd_iter(b, cnt2 + (size_t)((it + 1) & 1) * p.P, t, j->d, it, p.seg_unit0[s],
                                      p.seg_unit0[s + 1], p.cen_off[s], (int64_t)p.cen_off[s] + p.k_eff[s],
-                                     p.k_eff[s], prec, j->flags, j->ctx->sm_count, st, &j->kt));
+                                     p.k_eff[s], prec, j->flags, j->ctx->sm_count, st, &j->kt, j->rpt));
             }
         }
     }
@@ -933,7 +937,7 @@ extern "C" int pscl_run(pscl_job *j, int64_t N, int32_t local_k, int32_t final_k
     }
     uint64_t key[8] = {(uint64_t)N, (uint64_t)local_k, (uint64_t)final_k, (uint64_t)iters, seed, (uint64_t)prec,
                        (uint64_t)(uintptr_t)j->dev_in ^ (uint64_t)(uintptr_t)j->in16,
-                       (uint64_t)(j->plain | j->trace << 1 | j->first_k << 2)};
+                       (uint64_t)(j->plain | j->trace << 1 | j->first_k << 2 | j->rpt << 3)};
     if (j->gexec && memcmp(key, j->gkey, sizeof key) != 0) drop_graph(j);
     if (!j->gexec) {
         cudaGraph_t g = nullptr;
@@ -1260,7 +1264,7 @@ extern "C" int pscl_batch_set_option(pscl_batch *b, int opt, int64_t v)
         b->unit_rows = v;
         return batch_plan(b);
     case PSCL_OPT_ROWS_PER_THREAD:
-        if (v != 0 && v != 1) return fail(PSCL_EINVAL, "rows per thread must be 0 (default) or 1");
+        if (v < 0 || v > 2) return fail(PSCL_EINVAL, "rows per thread must be 0, 1 or 2");
         b->rpt = (int)v;
         break;
     default: return fail(PSCL_EINVAL, "option %d does not apply to a batch", opt);
@@ -1448,7 +1452,7 @@ extern "C" int pscl_batch_tune(pscl_batch *b, int32_t iters, int prec, int64_t *
         int64_t best_u = 0;
         int best_r = 0;
         for (int64_t u : units) {
-            for (int r = 0; r < 2; r++) {
+            for (int r = 0; r < 3; r++) {
                 b->unit_rows = u;
                 b->rpt = r;
                 TRY(batch_plan(b));

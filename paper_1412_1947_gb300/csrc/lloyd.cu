@@ -514,14 +514,16 @@ cudaError_t assign_launch(const LloydBuffers &b, const SegTable &t, int d, int i
     return cudaGetLastError();
 }
 
-// rows_per_thread: 0 = kRowsPerThread<D>(), 1 = one row per thread (a tuning choice; the
-// result is the same)
+// rows_per_thread: 0 = kRowsPerThread<D>(), 1 = one row per thread, 2 = eight rows per
+// thread for d <= 16 (tuning choices; the result is the same)
 template <int D>
 cudaError_t assign_dispatch(const LloydBuffers &b, const SegTable &t, int d, int iter, int unit_lo,
                             int unit_hi, int kmax, int rows_per_thread, cudaStream_t st, KTimer *kt)
 {
     if (rows_per_thread == 1 && kRowsPerThread<D>() > 1)
         return assign_launch<D, 1>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt);
+    if (rows_per_thread == 2 && D > 0 && D <= 16)                 // 8 rows: half the center reads
+        return assign_launch<D, (D > 0 && D <= 16 ? 8 : 1)>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt);
     return assign_launch<D, kRowsPerThread<D>()>(b, t, d, iter, unit_lo, unit_hi, kmax, st, kt);
 }
 

@@ -51,7 +51,8 @@ constexpr int kBandBins = 4096;               // one-ulp bins over a band's floa
 constexpr int kTight = 256;                   // band entries near the cut-off, decided exactly
 constexpr int kKeyCache = 4096;               // keys of a slice kept in shared memory, if it fits
 constexpr int kPeelScratch = 2 * kHistBins > kBandBins + 7 * kTight ? 2 * kHistBins : kBandBins + 7 * kTight;
-constexpr int kPeelDynWords = kPeelScratch + kKeyCache;
+constexpr int kBandStage = 4 * 256;           // band entries staged in shared memory (4 per thread)
+constexpr int kPeelDynWords = kPeelScratch + kKeyCache + 2 * kBandStage;
 constexpr int kQT = 8;                        // tiles of kThreads items per compaction scan
 constexpr unsigned kSpinLimit = 1u << 25;      // ~1-2 s of polling per barrier at most
 
@@ -586,6 +587,8 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
     uint32_t *tamb = reinterpret_cast<uint32_t *>(tl + kTight);    // undecided tight entries
     unsigned long long *td = reinterpret_cast<unsigned long long *>(tamb + kTight);
     uint32_t *skey = dyn + kPeelScratch;               // keys by list position (kc)
+    uint32_t *s_bk = skey + kKeyCache;                 // the band's keys and ids (nb <= kBandStage)
+    uint32_t *s_bp = s_bk + kBandStage;
     __shared__ float Ls[D > 0 ? D : kMaxD];
     __shared__ uint32_t s_in_key, s_out_key, s_nt, s_na, s_v, s_t32, s_st, s_en;
     __shared__ uint32_t red_a[W], red_b[W];
@@ -810,6 +813,15 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
         if (!grid_sync(ctl, a.flags, gen)) return;
 
         // ---- D: settle the band, take the subcluster, next landmark
+        // the per-CTA counts, the band's size and its first entries in one round trip
+        const uint32_t nb = __ldcg(&ctl->band_cnt[par]);
+        uint32_t sk[kBandStage / kThreads], sp[kBandStage / kThreads];
+#pragma unroll
+        for (int r = 0; r < kBandStage / kThreads; r++) {
+            const uint32_t q = t + r * kThreads;
+            sk[r] = q < n ? __ldcg(&a.band_k32[q]) : 0u;
+            sp[r] = q < n ? __ldcg(&a.band_pos[q]) : 0u;
+        }
         uint32_t all_in, in_before;
         {
             uint32_t va = 0, vb = 0, e0, e1;
@@ -820,7 +832,20 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
             }
             block_excl_scan2(va, vb, e0, e1, all_in, in_before);
         }
-        const uint32_t nb = __ldcg(&ctl->band_cnt[par]);
+        const bool staged = nb <= (uint32_t)kBandStage;
+        if (staged) {
+#pragma unroll
+            for (int r = 0; r < kBandStage / kThreads; r++) {
+                const uint32_t q = t + r * kThreads;
+                if (q < nb) {
+                    s_bk[q] = sk[r];
+                    s_bp[q] = sp[r];
+                }
+            }
+            __syncthreads();
+        }
+        auto BK = [&](uint32_t q) { return staged ? s_bk[q] : __ldcg(&a.band_k32[q]); };
+        auto BP = [&](uint32_t q) { return staged ? s_bp[q] : __ldcg(&a.band_pos[q]); };
         const uint32_t need = N > all_in ? N - all_in : 0u;
         if ((all_in > N || need > nb) && c == 0 && t == 0) atomicOr(&a.flags[1], 1u);
         uint32_t lo = in_key, tout = 0, ntt = 0;       // the rule (see taken())
@@ -842,7 +867,7 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
                     s_na = 0;
                 }
                 __syncthreads();
-                for (uint32_t q = t; q < nb; q += kThreads) atomicAdd(&hb[__ldcg(&a.band_k32[q]) - in_key], 1u);
+                for (uint32_t q = t; q < nb; q += kThreads) atomicAdd(&hb[BK(q) - in_key], 1u);
                 __syncthreads();
                 {   // the one-ulp bin of the need-th smallest band key
                     constexpr int per = kBandBins / kThreads;
@@ -866,8 +891,8 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
                 band_cutoffs_key(s_t32, s_t32, d, tin, tt);
                 uint32_t n_cert = 0, cert_before = 0;
                 for (uint32_t q = t; q < nb; q += kThreads) {
-                    const uint32_t k = __ldcg(&a.band_k32[q]);
-                    const uint32_t pq = __ldcg(&a.band_pos[q]);
+                    const uint32_t k = BK(q);
+                    const uint32_t pq = BP(q);
                     if (k < tin) {
                         n_cert++;
                         cert_before += pq < s0;
@@ -975,7 +1000,7 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
             }
         } else if (need > 0) {
             lo = out_key + 1u;      // need >= nb: the whole band is taken (need > nb is flagged)
-            for (uint32_t q = t; q < nb; q += kThreads) band_before += __ldcg(&a.band_pos[q]) < s0;
+            for (uint32_t q = t; q < nb; q += kThreads) band_before += BP(q) < s0;
         }
         const Rule R{lo, tout, ntt, tpos, tcls};
         band_before = block_sum(band_before);       // its barriers also publish the kTaken marks
