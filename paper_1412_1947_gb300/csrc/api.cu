@@ -550,6 +550,7 @@ static int alloc_subcluster_buffers(pscl_job *j)
         TRY(A(j, &b.bcnt, (size_t)d * b.nbuckets));
         TRY(A(j, &b.bcs, (size_t)d * b.nbuckets));
         TRY(A(j, &b.lidx, 2 * (size_t)n));
+        TRY(A(j, &b.kpos, n));
         TRY(A(j, &b.band_key, n));
         TRY(A(j, &b.band_pos, n));
         TRY(A(j, &b.band_k32, n));
@@ -669,7 +670,8 @@ static size_t job_footprint(int64_t n, int d, int64_t N, int local_k, int final_
     const int64_t ord_ld = (n + 3) & ~(int64_t)3;
     const size_t nbk = peel_buckets(n);
     b += r256((size_t)n * 4) + r256((size_t)d * ord_ld * 4) + r256((size_t)d * nbk * 4) + r256((size_t)d * nbk * 16) +
-         r256(2 * (size_t)n * 4) + r256((size_t)n * 8) + 2 * r256((size_t)n * 4) + r256((size_t)n * 4) +
+         r256(2 * (size_t)n * 4) + r256((size_t)n * 4) + r256((size_t)n * 8) + 2 * r256((size_t)n * 4) +
+         r256((size_t)n * 4) +
          r256((size_t)n * d * 4) + r256((size_t)n * 4);
     const int64_t S = (n + N - 1) / N;
     b += r256((size_t)S * d * 4);

@@ -551,6 +551,7 @@ struct PeelArgs {
     uint32_t *bcnt;              // d x nbk: bucket counts, then cursors (zeroed before)
     uint4 *bcs;                  // d x nbk: (points left, first entry, end entry, 0)
     uint32_t *lidx;              // 2 x n: per CTA slice, the ids of its points left
+    uint32_t *kpos;              // n: per CTA slice, this round's keys by list position (!kc)
     int64_t ord_ld;
     uint32_t nbk;
     uint64_t *band_key;          // float64 distance bits (wide bands only)
@@ -723,6 +724,7 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
                 if (lv[q]) {
                     a.key[ids[q]] = k;
                     if (kc) skey[base + q * kThreads + t] = k;
+                    else a.kpos[s0 + base + q * kThreads + t] = k;
                 }
                 // the keys of a round crowd into a few bins: one shared atomic per bin and warp
                 const uint32_t b = lv[q] ? (k >> 21) : kGone;
@@ -764,7 +766,7 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
                     const uint32_t qi = q0 + q * kThreads;
-                    k4[q] = qi >= n_live ? kGone : kc ? skey[qi] : __ldcg(&a.key[lin ? __ldcg(&lin[qi]) : s0 + qi]);
+                    k4[q] = qi >= n_live ? kGone : kc ? skey[qi] : __ldcg(&a.kpos[s0 + qi]);
                 }
 #pragma unroll
                 for (int q = 0; q < 4; q++)
@@ -793,7 +795,7 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 const uint32_t qi = q0 + q * kThreads;
-                k4[q] = qi >= n_live ? kGone : kc ? skey[qi] : __ldcg(&a.key[lin ? __ldcg(&lin[qi]) : s0 + qi]);
+                k4[q] = qi >= n_live ? kGone : kc ? skey[qi] : __ldcg(&a.kpos[s0 + qi]);
             }
 #pragma unroll
             for (int q = 0; q < 4; q++) {
@@ -1007,9 +1009,12 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
         // take the subcluster: ids in ascending order to the segment, the rest stay listed;
         // a taken point is marked removed and leaves the live count of its d buckets
         // (with landmark-only CTAs they do that bookkeeping in the next round's phase A)
-        const bool ksh = kc && !slow;             // wide-band marks are in global memory only
         n_live -= compact_list(lin, s0, n_live, seg_out + in_before + band_before, a.lidx + (size_t)(par ^ 1) * n + s0,
-                               [&](uint32_t qi, uint32_t id) { return taken(R, ksh ? skey[qi] : __ldcg(&a.key[id]), id); },
+                               [&](uint32_t qi, uint32_t id) {
+                                   // a wide band marks its taken points in key[] by id
+                                   const uint32_t k = slow ? __ldcg(&a.key[id]) : kc ? skey[qi] : __ldcg(&a.kpos[s0 + qi]);
+                                   return taken(R, k, id);
+                               },
                                [&](uint32_t id) {
                                    if (Gl == 0) {
                                        a.key[id] = kGone;
@@ -1136,6 +1141,7 @@ cudaError_t peel_launch(const PeelBuffers &b, int64_t n, int d, int64_t N, int s
     a.bcnt = b.bcnt;
     a.bcs = b.bcs;
     a.lidx = b.lidx;
+    a.kpos = b.kpos;
     a.ord_ld = b.ord_ld;
     a.nbk = b.nbuckets;
     a.band_key = b.band_key;

@@ -112,6 +112,7 @@ struct PeelBuffers {
     uint32_t *bcnt;                  // d x nbuckets: bucket counts, then scatter cursors
     uint4 *bcs;                      // d x nbuckets: (points left, first entry, end entry, 0)
     uint32_t *lidx;                  // 2 x n: per CTA slice, the ids of its points left
+    uint32_t *kpos;                  // n: per CTA slice, the round's keys by list position
     int64_t ord_ld;                  // n rounded up to a multiple of 4
     uint32_t nbuckets;               // power of two, 4096 .. 65536
     uint64_t *band_key;              // float64 distance bits of band points (wide bands)

@@ -20,3 +20,18 @@ def test_medium_workload_full_size():
                          force_local=g.trace_local, force_final=g.trace_final, tie_tol=TIE_TOL)
     stats = compare(g, o)
     print("full-size parity:", stats)
+
+
+def test_peel_partition_with_slices_beyond_the_key_cache():
+    # 2^21 points: every CTA's slice exceeds the 4096 keys kept in shared memory, so the
+    # round's keys go through the global per-slice array instead
+    import oracle
+    from paper_1412_1947_gb300 import binding as B
+    raw = synth.mixture(1 << 21, 4, 16, outlier_frac=0.01, seed=8800)
+    with B.Job(raw) as j:
+        j.steps(1 << 17, 4, 4, 1, 3)
+        perm, off = j.partition()
+        x = j.scaled()
+    operm, ooff, _ = oracle.peel(x, 1 << 17, select=True)
+    np.testing.assert_array_equal(off, ooff)
+    np.testing.assert_array_equal(perm, operm)
