@@ -382,6 +382,7 @@ def main_uneven(args):
     clocks = clk.stop()
     step_ms = [s_.elapsed_time(e) for s_, e in zip(starts, ends)]
     mean_ms = statistics.mean(step_ms)
+    launches_per_step = b.launches()
     _, _, sse = b.result(labels=False)
     # the Lloyd iterations alone (unrecorded run, events around them)
     b.option(B.PSCL_OPT_GRAPH, 0)
@@ -425,14 +426,15 @@ def main_uneven(args):
             "lloyd_ms": lloyd_ms, "lloyd_only_value": evals / (lloyd_ms * 1e-3), "sse_sum": float(sse.sum()),
             "e2e": {"value": evals / e2e_mean, "unit": UNIT, "h2d_bytes_per_step": int(raw.nbytes),
                     "d2h_bytes_per_step": int(8 * len(sizes))},
-            "gpu_launches": None, "roofline": roof, "plain_fp32": plain, "clocks": clocks}
+            "gpu_launches": int(launches_per_step * args.steps), "roofline": roof, "plain_fp32": plain,
+            "clocks": clocks}
     if not args.no_cpu:
-        # the oracle, single-threaded, on the first instances up to ~1e8 distance evaluations
+        # the oracle, single-threaded, on instances in order while they fit ~1e8 distance evaluations
         budget, ev_s, t_s, used = 1e8, 0, 0.0, 0
         for i, (p, k) in enumerate(zip(parts, ks)):
             e = len(p) * min(k, len(p)) * iters
-            if ev_s and ev_s + e > budget:
-                break
+            if ev_s + e > budget:
+                continue                    # instances that would overrun the sample
             xs, _, _ = oracle.scale(p)
             t0 = time.perf_counter()
             oracle.lloyd_seeded(xs, k, iters, seed, 0, i)
@@ -440,7 +442,8 @@ def main_uneven(args):
             ev_s += e
             used += 1
         line["cpu_baseline"] = {"value": ev_s / t_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"the first {used} instances ({ev_s:.3g} distance evaluations)"}
+                                "sample": f"{used} instances taken in order while within 1e8 distance evaluations "
+                                          f"({ev_s:.3g} in all), scaling + seeded Lloyd each"}
     b.close()
     B.pscl_ctx_destroy(ctx)
     print(json.dumps(line), flush=True)

@@ -354,6 +354,8 @@ int pscl_batch_get(pscl_batch *b, float *centers, int32_t *labels, double *sse);
 int pscl_batch_get_scaled(pscl_batch *b, float *out);
 /* iters x sum(sizes) labels of every iteration (needs PSCL_OPT_TRACE_LABELS). */
 int pscl_batch_get_label_trace(pscl_batch *b, int32_t *out);
+/* Kernel launches of the last run (counted when it was queued or recorded). */
+int pscl_batch_launches(pscl_batch *b, int64_t *launches);
 /* Device time of the Lloyd iterations of the last unrecorded run, in milliseconds. */
 int pscl_batch_lloyd_ms(pscl_batch *b, float *ms);
 int pscl_batch_destroy(pscl_batch *b);

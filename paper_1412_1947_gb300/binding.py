@@ -68,6 +68,7 @@ SIGNATURES = {
     "pscl_batch_get_scaled": (_I, [_P, _P]),
     "pscl_batch_get_label_trace": (_I, [_P, _P]),
     "pscl_batch_lloyd_ms": (_I, [_P, _P]),
+    "pscl_batch_launches": (_I, [_P, _P]),
     "pscl_batch_destroy": (_I, [_P]),
 }
 PSCL_JOB_QUEUED, PSCL_JOB_RUNNING, PSCL_JOB_DONE, PSCL_JOB_FAILED = 0, 1, 2, 3
@@ -388,6 +389,12 @@ def pscl_batch_lloyd_ms(b):
     return ms.value
 
 
+def pscl_batch_launches(b):
+    n = C.c_int64()
+    _chk(lib().pscl_batch_launches(b, C.byref(n)))
+    return n.value
+
+
 def pscl_batch_destroy(b):
     _chk(lib().pscl_batch_destroy(b))
 
@@ -478,6 +485,9 @@ class Batch:
 
     def lloyd_ms(self):
         return pscl_batch_lloyd_ms(self.h)
+
+    def launches(self):
+        return pscl_batch_launches(self.h)
 
     def close(self):
         if self.h is not None:

@@ -1279,6 +1279,7 @@ extern "C" int pscl_batch_set_option(pscl_batch *b, int opt, int64_t v)
 static int batch_enqueue(pscl_batch *b, int iters, uint64_t seed, int prec, bool events)
 {
     cudaStream_t st = b->ctx->stream;
+    b->kt.reset();                     // a recorded run keeps the count of its recording
     const SegTable t = b->plan.table();
     const int32_t *u0 = b->plan.d_unit0();
     CU(cudaMemsetAsync(b->flags, 0, kFlagWords * sizeof(uint32_t), st));
@@ -1332,7 +1333,6 @@ extern "C" int pscl_batch_run(pscl_batch *b, int32_t iters, uint64_t seed, int p
         if (tl) TRY(A(b, &b->trace, tl));
     }
     b->iters = iters;
-    b->kt.reset();
     if (!b->graph) return batch_enqueue(b, iters, seed, prec, true);
     const uint64_t key[6] = {(uint64_t)iters, seed, (uint64_t)prec, (uint64_t)(b->trace_on | b->plain << 1),
                              (uint64_t)b->unit_rows, (uint64_t)b->rpt};
@@ -1395,6 +1395,15 @@ extern "C" int pscl_batch_get_label_trace(pscl_batch *b, int32_t *out)
     if (!out) return fail(PSCL_EINVAL, "out is NULL");
     if (!b->trace_len) return fail(PSCL_ESTATE, "no label trace was recorded (PSCL_OPT_TRACE_LABELS)");
     CU(cudaMemcpy(out, b->trace, (size_t)b->trace_len * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    return PSCL_OK;
+}
+
+extern "C" int pscl_batch_launches(pscl_batch *b, int64_t *launches)
+{
+    if (!b || !launches) return fail(PSCL_EINVAL, "batch or launches is NULL");
+    int64_t t = 0;
+    for (int i = 0; i < PSCL_K_COUNT; i++) t += b->kt.launches[i];
+    *launches = t;
     return PSCL_OK;
 }
 
