@@ -168,14 +168,17 @@ k_lloyd_assign(const float *__restrict__ pts, SegTable t, int d, const float *__
     // [center chunk | high sums | low sums | counts], each 16-byte aligned.  A fixed-point
     // value q <= 2^32 is added as q >> 11 (<= 2^21) and q & 0x7FF with two native 32-bit
     // shared atomics; a unit has at most 1024 rows, so neither sum can wrap, and the
-    // flush recombines them exactly into the 64-bit global sums.
+    // flush recombines them exactly into the 64-bit global sums.  A center's sums take an
+    // odd stride ds = d | 1, so that the lanes of a warp adding attribute a of different
+    // centers fall in different banks (with stride 16 they shared two).
+    const int ds = dd | 1;
     const size_t c_bytes = ((size_t)min(chunk_k, k) * dd * 4 + 15) & ~(size_t)15;
     float *sc = reinterpret_cast<float *>(smem);
     uint32_t *shi = reinterpret_cast<uint32_t *>(smem + c_bytes);
-    uint32_t *slo = shi + (size_t)k * dd;
-    int32_t *scnt = reinterpret_cast<int32_t *>(slo + (size_t)k * dd);
+    uint32_t *slo = shi + (size_t)k * ds;
+    int32_t *scnt = reinterpret_cast<int32_t *>(slo + (size_t)k * ds);
     if (kSmemAcc) {
-        for (int e = threadIdx.x; e < k * dd; e += kThreads) {
+        for (int e = threadIdx.x; e < k * ds; e += kThreads) {
             shi[e] = 0u;
             slo[e] = 0u;
         }
@@ -256,7 +259,7 @@ k_lloyd_assign(const float *__restrict__ pts, SegTable t, int d, const float *__
             const float *xr = pts + row * dd;
             if (kSmemAcc) {
                 atomicAdd(&scnt[bj[q]], 1);
-                const size_t e0 = (size_t)bj[q] * dd;
+                const size_t e0 = (size_t)bj[q] * ds;
                 if (D > 0) {
 #pragma unroll
                     for (int j = 0; j < DR; j++) {
@@ -285,7 +288,8 @@ k_lloyd_assign(const float *__restrict__ pts, SegTable t, int d, const float *__
     if (kSmemAcc) {
         __syncthreads();
         for (int e = threadIdx.x; e < k * dd; e += kThreads) {
-            const unsigned long long v = ((unsigned long long)shi[e] << 11) + slo[e];
+            const int c = e / dd, es = c * ds + (e - c * dd);
+            const unsigned long long v = ((unsigned long long)shi[es] << 11) + slo[es];
             if (v) atomicAdd(&acc[c0 * dd + e], v);
         }
         for (int j = threadIdx.x; j < k; j += kThreads) {
@@ -490,7 +494,7 @@ cudaError_t assign_launch(const LloydBuffers &b, const SegTable &t, int d, int i
                           int unit_hi, int kmax, cudaStream_t st, KTimer *kt)
 {
     const int chunk = center_chunk(d, kmax);
-    const size_t acc_bytes = (size_t)kmax * d * 8 + (size_t)kmax * 4;
+    const size_t acc_bytes = (size_t)kmax * (d | 1) * 8 + (size_t)kmax * 4;
     const size_t c_bytes = ((size_t)chunk * d * 4 + 15) & ~(size_t)15;
     const bool smem_acc = acc_bytes <= kSmemAccMax;
     const size_t smem = (smem_acc ? acc_bytes : 0) + c_bytes;

@@ -221,11 +221,13 @@ constexpr int kFoldTiles = 32768 / kTileRows;
 __device__ __forceinline__ void flush_sums(uint32_t *shi, uint32_t *slo, int32_t *scnt, int k, int64_t c0,
                                            unsigned long long *acc, int32_t *count, int dd)
 {
+    const int ds = dd | 1;
     for (int e = threadIdx.x; e < k * dd; e += kTcThreads) {
-        const unsigned long long v = ((unsigned long long)shi[e] << 16) + slo[e];
+        const int c = e / dd, es = c * ds + (e - c * dd);
+        const unsigned long long v = ((unsigned long long)shi[es] << 16) + slo[es];
         if (v) atomicAdd(&acc[c0 * dd + e], v);
-        shi[e] = 0u;
-        slo[e] = 0u;
+        shi[es] = 0u;
+        slo[es] = 0u;
     }
     for (int j = threadIdx.x; j < k; j += kTcThreads) {
         const int v = scnt[j];
@@ -262,13 +264,16 @@ k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *spli
     const int ue = split ? split[blockIdx.x + 1] : ub + 1;
     const int npmax = (kmax + 15) & ~15;
 
-    // [A buffers | B | float32 centers (scent) | high sums | low sums | counts (sacc)]
+    // [A buffers | B | float32 centers (scent) | high sums | low sums | counts (sacc)]; a
+    // center's sums take the odd stride D | 1 so that a warp's lanes adding one attribute
+    // of different centers spread over the banks
+    constexpr int DS = D | 1;
     unsigned char *sa0 = smem;
     unsigned char *sb = sa0 + (size_t)nbuf * L::kABytes;
     float *sc = reinterpret_cast<float *>(sb + (((uint32_t)(npmax / 8) * L::kGroup + 127) & ~127u));
     uint32_t *shi = reinterpret_cast<uint32_t *>(sc + (scent ? (size_t)kmax * D : 0));
-    uint32_t *slo = shi + (size_t)kmax * D;
-    int32_t *scnt = reinterpret_cast<int32_t *>(slo + (size_t)kmax * D);
+    uint32_t *slo = shi + (size_t)kmax * DS;
+    int32_t *scnt = reinterpret_cast<int32_t *>(slo + (size_t)kmax * DS);
 
     if (tid == 0) {
         s_fail = 0;
@@ -279,7 +284,7 @@ k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *spli
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (sacc) {
-        for (int e = tid; e < kmax * D; e += kTcThreads) {
+        for (int e = tid; e < kmax * DS; e += kTcThreads) {
             shi[e] = 0u;
             slo[e] = 0u;
         }
@@ -533,7 +538,7 @@ k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *spli
                 if (trace) trace[trace_off + row] = bj;
                 if (sacc) {
                     atomicAdd(&scnt[bj], 1);
-                    const size_t e0 = (size_t)bj * D;
+                    const size_t e0 = (size_t)bj * DS;
 #pragma unroll
                     for (int a = 0; a < D; a++) {
                         const unsigned long long q = to_fix(xv[a]);
@@ -592,7 +597,7 @@ size_t tc_smem_bytes(int kmax, int nbuf, bool sacc, bool scent = false)
     const int np = (kmax + 15) & ~15;
     const size_t b = ((size_t)(np / 8) * L::kGroup + 127) & ~(size_t)127;
     return (size_t)nbuf * L::kABytes + b + (scent ? (size_t)kmax * D * 4 : 0) +
-           (sacc ? (size_t)kmax * D * 4 * 2 + (size_t)kmax * 4 : 0) + 1024;
+           (sacc ? (size_t)kmax * (D | 1) * 4 * 2 + (size_t)kmax * 4 : 0) + 1024;
 }
 
 // Two operand buffers and TMEM regions (MMA of the next tile under the epilogue of this
