@@ -232,7 +232,24 @@ k_lloyd_assign(const float *__restrict__ pts, SegTable t, int d, const float *__
                 __syncthreads();
             }
             const float *cbase = one_chunk ? sc + (size_t)cb * dd : sc;
-            for (int j = cb; j < ce; j++) {
+            int j = cb;
+            if constexpr (D > 0) {
+                // two centers per step: two independent sets of chains in flight (3.6 %
+                // faster at d = 64, where a thread keeps one row); the comparisons stay in
+                // center order (lowest index on ties)
+                for (; j + 1 < ce; j += 2) {
+                    const float *cj = cbase + (size_t)(j - cb) * dd;
+                    float v[R], w[R];
+                    dist_rows<DR, R>(xv, cj, v);
+                    dist_rows<DR, R>(xv, cj + dd, w);
+#pragma unroll
+                    for (int q = 0; q < R; q++) {
+                        if (v[q] < best[q]) { best[q] = v[q]; bj[q] = j; }
+                        if (w[q] < best[q]) { best[q] = w[q]; bj[q] = j + 1; }
+                    }
+                }
+            }
+            for (; j < ce; j++) {
                 const float *cj = cbase + (size_t)(j - cb) * dd;
                 float v[R];
                 if (D > 0) {

@@ -49,10 +49,10 @@ constexpr uint32_t kGone = 0xFFFFFFFFu;       // key of a point removed in an ea
 constexpr uint32_t kTaken = 0xFFFFFFFEu;      // key of a wide-band point taken this round
 constexpr int kBandBins = 4096;               // one-ulp bins over a band's float32 keys
 constexpr int kTight = 256;                   // band entries near the cut-off, decided exactly
-constexpr int kKeyCache = 4096;               // keys of a slice kept in shared memory, if it fits
+constexpr int kKeyCache = 4096;               // keys and ids of a slice kept in shared memory, if it fits
 constexpr int kPeelScratch = 2 * kHistBins > kBandBins + 7 * kTight ? 2 * kHistBins : kBandBins + 7 * kTight;
 constexpr int kBandStage = 4 * 256;           // band entries staged in shared memory (4 per thread)
-constexpr int kPeelDynWords = kPeelScratch + kKeyCache + 2 * kBandStage;
+constexpr int kPeelDynWords = kPeelScratch + 2 * kKeyCache + 2 * kBandStage;
 constexpr int kQT = 8;                        // tiles of kThreads items per compaction scan
 constexpr unsigned kSpinLimit = 1u << 25;      // ~1-2 s of polling per barrier at most
 
@@ -414,14 +414,14 @@ __device__ void find_bins(const uint32_t *h0, const uint32_t *hg, uint32_t guess
     __syncthreads();
 }
 
-// Splits the n_in ids of a CTA's list (in[q], or first + q when `in` is NULL), keeping their
-// order, into those with pred(position, id), written to sel[0..) with on_sel(id) called for
-// each, and
-// the rest, written to keep[0..) when `keep` is given.  Returns how many were selected (to every
+// Splits the n_in ids of a CTA's list (id_of(q) for position q), keeping their order, into
+// those with pred(position, id), written to sel[0..) with on_sel(id) called for each, and the
+// rest, written to keep[0..) when `keep` is given.  `keep` may be the list being read (in
+// shared memory): a tile's ids are all read before any of its kept ids is written, and those
+// land at or below the tile's own positions.  Returns how many were selected (to every
 // thread).
-template <class Pred, class OnSel>
-__device__ uint32_t compact_list(const uint32_t *in, uint32_t first, uint32_t n_in, uint32_t *sel, uint32_t *keep,
-                                 Pred pred, OnSel on_sel)
+template <class IdOf, class Pred, class OnSel>
+__device__ uint32_t compact_list(IdOf id_of, uint32_t n_in, uint32_t *sel, uint32_t *keep, Pred pred, OnSel on_sel)
 {
     constexpr int W = kThreads / 32;
     constexpr int PER = kQT * W / 32;
@@ -438,7 +438,7 @@ __device__ uint32_t compact_list(const uint32_t *in, uint32_t first, uint32_t n_
         for (int q = 0; q < kQT; q++) {
             const uint32_t qi = cb + q * kThreads + t;
             const bool v = qi < n_in;
-            ids[q] = v ? (in ? __ldcg(&in[qi]) : first + qi) : 0u;
+            ids[q] = v ? id_of(qi) : 0u;
             vl |= (uint32_t)v << q;
         }
 #pragma unroll
@@ -588,7 +588,8 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
     uint32_t *tamb = reinterpret_cast<uint32_t *>(tl + kTight);    // undecided tight entries
     unsigned long long *td = reinterpret_cast<unsigned long long *>(tamb + kTight);
     uint32_t *skey = dyn + kPeelScratch;               // keys by list position (kc)
-    uint32_t *s_bk = skey + kKeyCache;                 // the band's keys and ids (nb <= kBandStage)
+    uint32_t *sid = skey + kKeyCache;                  // ids by list position (kc)
+    uint32_t *s_bk = sid + kKeyCache;                  // the band's keys and ids (nb <= kBandStage)
     uint32_t *s_bp = s_bk + kBandStage;
     __shared__ float Ls[D > 0 ? D : kMaxD];
     __shared__ uint32_t s_in_key, s_out_key, s_nt, s_na, s_v, s_t32, s_st, s_en;
@@ -677,14 +678,17 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
         if (c == 0 && a.landmarks)
             for (int j = t; j < d; j += kThreads)
                 a.landmarks[r * d + j] = __uint_as_float(__ldcg(&ctl->Lbits[par][j]));
-        const uint32_t *lin = r == 0 ? nullptr : a.lidx + (size_t)par * n + s0;
+        // the slice's list of ids left: the slice itself in round 0, then in shared memory
+        // when it fits the key cache (compacted there in place), else in global memory
+        const uint32_t *glin = a.lidx + (size_t)par * n + s0;
+        auto LID = [&](uint32_t q) -> uint32_t { return r == 0 ? s0 + q : kc ? sid[q] : __ldcg(&glin[q]); };
         if (nr <= N) {                                // the last subcluster: all that is left
             if (t == 0) ctl->cnt_in[c] = n_live;
             if (!grid_sync(ctl, a.flags, gen)) return;
             uint32_t before = 0;
             for (uint32_t q = t; q < c; q += kThreads) before += __ldcg(&ctl->cnt_in[q]);
             before = block_sum(before);
-            for (uint32_t q = t; q < n_live; q += kThreads) seg_out[before + q] = lin ? __ldcg(&lin[q]) : s0 + q;
+            for (uint32_t q = t; q < n_live; q += kThreads) seg_out[before + q] = LID(q);
             break;
         }
 
@@ -711,7 +715,7 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
             for (int q = 0; q < B; q++) {
                 const uint32_t qi = base + q * kThreads + t;
                 lv[q] = qi < n_live;
-                ids[q] = lv[q] ? (lin ? __ldcg(&lin[qi]) : s0 + qi) : s0;
+                ids[q] = lv[q] ? LID(qi) : s0;
             }
             // past the end a thread reads the slice's first row again (an L1 hit), so every
             // thread keeps B rows in flight without branching
@@ -806,7 +810,7 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
                     const uint32_t qi = q0 + q * kThreads;
                     const uint32_t slot = atomicAdd(&ctl->band_cnt[par], 1u);
                     a.band_k32[slot] = k;
-                    a.band_pos[slot] = lin ? __ldcg(&lin[qi]) : s0 + qi;
+                    a.band_pos[slot] = LID(qi);
                 }
             }
         }
@@ -1009,7 +1013,7 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
         // take the subcluster: ids in ascending order to the segment, the rest stay listed;
         // a taken point is marked removed and leaves the live count of its d buckets
         // (with landmark-only CTAs they do that bookkeeping in the next round's phase A)
-        n_live -= compact_list(lin, s0, n_live, seg_out + in_before + band_before, a.lidx + (size_t)(par ^ 1) * n + s0,
+        n_live -= compact_list(LID, n_live, seg_out + in_before + band_before, kc ? sid : a.lidx + (size_t)(par ^ 1) * n + s0,
                                [&](uint32_t qi, uint32_t id) {
                                    // a wide band marks its taken points in key[] by id
                                    const uint32_t k = slow ? __ldcg(&a.key[id]) : kc ? skey[qi] : __ldcg(&a.kpos[s0 + qi]);
