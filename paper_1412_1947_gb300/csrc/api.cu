@@ -63,7 +63,7 @@ struct Owner {
 
 // One Lloyd launch plan: tables on the device and their host copies.
 struct LloydPlan {
-    int n_seg = 0, n_units = 0, kmax = 0, d = 0;
+    int n_seg = 0, n_units = 0, kmax = 0, d = 0, max_unit = 0;
     int64_t rows = 0, P = 0;
     std::vector<int64_t> seg_start;
     std::vector<int32_t> seg_size, cen_off, k_eff, unit_seg, unit_start, unit_count, seg_unit0;
@@ -446,6 +446,7 @@ static int build_lloyd_plan(Owner *j, LloydPlan &p, const std::vector<int64_t> &
     }
     p.n_units = (int)p.unit_seg.size();
     p.seg_unit0[p.n_seg] = p.n_units;
+    p.max_unit = p.unit_count.empty() ? 0 : *std::max_element(p.unit_count.begin(), p.unit_count.end());
     job_free(j, p.d_seg_start);
     job_free(j, p.d_i32);
     p.d_seg_start = nullptr;
@@ -719,6 +720,14 @@ extern "C" int pscl_job_footprint(pscl_ctx *c, int64_t n, int32_t d, int64_t N, 
     return PSCL_OK;
 }
 
+// Rows per thread of the float32 assignment: the option when set, else one row per thread
+// when no unit has more rows than the kernel's 256 threads (small sets, e.g. the pooled
+// local centers: more rows per thread would only score empty slots), else the default.
+static int rows_per_thread(int option, const LloydPlan &p)
+{
+    return option ? option : (p.max_unit <= 256 ? 1 : 0);
+}
+
 // ------------------------------------------------------------------ enqueue (launches only)
 static int run_lloyd(pscl_job *j, const LloydPlan &p, const float *pts, float *centers,
                      unsigned long long *acc, int32_t *cnt2, int32_t *labels, int32_t *trace,
@@ -739,7 +748,7 @@ static int run_lloyd(pscl_job *j, const LloydPlan &p, const float *pts, float *c
         for (int it = 0; it < iters; it++) {
             b.count = cnt2 + (size_t)(it & 1) * p.P;
             CU(launch_lloyd_iter(b, cnt2 + (size_t)((it + 1) & 1) * p.P, t, j->d, it, 0, p.n_units, 0, p.P,
-                                 p.kmax, prec, j->flags, j->ctx->sm_count, st, &j->kt, j->rpt));
+                                 p.kmax, prec, j->flags, j->ctx->sm_count, st, &j->kt, rows_per_thread(j->rpt, p)));
         }
     } else {
         for (int s = 0; s < p.n_seg; s++) {
@@ -747,7 +756,8 @@ static int run_lloyd(pscl_job *j, const LloydPlan &p, const float *pts, float *c
                 b.count = cnt2 + (size_t)(it & 1) * p.P;
                 CU(launch_lloyd_iter(b, cnt2 + (size_t)((it + 1) & 1) * p.P, t, j->d, it, p.seg_unit0[s],
                                      p.seg_unit0[s + 1], p.cen_off[s], (int64_t)p.cen_off[s] + p.k_eff[s],
-                                     p.k_eff[s], prec, j->flags, j->ctx->sm_count, st, &j->kt, j->rpt));
+                                     p.k_eff[s], prec, j->flags, j->ctx->sm_count, st, &j->kt,
+                                     rows_per_thread(j->rpt, p)));
             }
         }
     }
@@ -1299,7 +1309,8 @@ static int batch_enqueue(pscl_batch *b, int iters, uint64_t seed, int prec, bool
         for (int it = 0; it < iters; it++) {
             lb.count = b->cnt + (size_t)(it & 1) * P;
             CU(launch_lloyd_iter(lb, b->cnt + (size_t)((it + 1) & 1) * P, t, b->d, it, 0, b->plan.n_units, 0, P,
-                                 b->plan.kmax, prec, b->flags, b->ctx->sm_count, st, &b->kt, b->rpt));
+                                 b->plan.kmax, prec, b->flags, b->ctx->sm_count, st, &b->kt,
+                                 rows_per_thread(b->rpt, b->plan)));
         }
     } else {                           // one launch pair per instance and iteration
         const LloydPlan &p = b->plan;
@@ -1308,7 +1319,7 @@ static int batch_enqueue(pscl_batch *b, int iters, uint64_t seed, int prec, bool
                 lb.count = b->cnt + (size_t)(it & 1) * P;
                 CU(launch_lloyd_iter(lb, b->cnt + (size_t)((it + 1) & 1) * P, t, b->d, it, p.seg_unit0[s],
                                      p.seg_unit0[s + 1], p.cen_off[s], (int64_t)p.cen_off[s] + p.k_eff[s], p.k_eff[s],
-                                     prec, b->flags, b->ctx->sm_count, st, &b->kt, b->rpt));
+                                     prec, b->flags, b->ctx->sm_count, st, &b->kt, rows_per_thread(b->rpt, p)));
             }
         }
     }

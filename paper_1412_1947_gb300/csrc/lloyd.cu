@@ -317,23 +317,45 @@ k_lloyd_assign(const float *__restrict__ pts, SegTable t, int d, const float *__
 }
 
 // center = exact sum / count (double), rounded once to float; empty clusters keep their
-// center.  Clears the sums and the other parity's counts for the next iteration.
+// center.  Clears the sums and the other parity's counts for the next iteration.  A thread
+// takes EPT consecutive attributes of one center (d % EPT == 0) and forms the count's
+// reciprocal once for them: float64 is the slow pipe of this GPU.  I is the element index
+// type (32-bit whenever the elements fit, which avoids 64-bit division).
+template <int EPT, typename I>
 __global__ void k_lloyd_finalize(float *centers, unsigned long long *acc, const int32_t *count,
                                  int32_t *count_next, int64_t cen_lo, int64_t cen_hi, int d)
 {
-    const int64_t e0 = cen_lo * d, e1 = cen_hi * d;
-    for (int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < e1;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = e / d;
+    const I g0 = (I)(cen_lo * d / EPT), g1 = (I)(cen_hi * d / EPT), dd = (I)d;
+    for (I g = g0 + (I)blockIdx.x * blockDim.x + threadIdx.x; g < g1; g += (I)gridDim.x * blockDim.x) {
+        const I e = g * EPT;
+        const I c = e / dd;
         const int32_t n = count[c];
-        const long long sum = (long long)acc[e];
         if (n > 0) {
-            double mean = __dmul_rn(__dmul_rn((double)sum, 0x1p-32), __drcp_rn((double)n));
-            centers[e] = __double2float_rn(mean);
+            const double r = __drcp_rn((double)n);
+#pragma unroll
+            for (int q = 0; q < EPT; q++) {
+                const long long sum = (long long)acc[e + q];
+                centers[e + q] = __double2float_rn(__dmul_rn(__dmul_rn((double)sum, 0x1p-32), r));
+            }
         }
-        acc[e] = 0ull;
-        if (e - c * d == 0) count_next[c] = 0;
+#pragma unroll
+        for (int q = 0; q < EPT; q++) acc[e + q] = 0ull;
+        if (e - c * dd == 0) count_next[c] = 0;
     }
+}
+
+template <int EPT>
+void finalize_launch(const LloydBuffers &b, int32_t *count_next, int64_t cen_lo, int64_t cen_hi, int d,
+                     int sm_count, cudaStream_t st)
+{
+    const int64_t work = (cen_hi - cen_lo) * d / EPT;
+    int64_t g = (work + 255) / 256;
+    if (g > (int64_t)sm_count * 8) g = (int64_t)sm_count * 8;
+    if (g < 1) g = 1;
+    if (cen_hi * d < ((int64_t)1 << 31))
+        k_lloyd_finalize<EPT, uint32_t><<<(int)g, 256, 0, st>>>(b.centers, b.acc, b.count, count_next, cen_lo, cen_hi, d);
+    else
+        k_lloyd_finalize<EPT, int64_t><<<(int)g, 256, 0, st>>>(b.centers, b.acc, b.count, count_next, cen_lo, cen_hi, d);
 }
 
 // Nearest final center of every scaled point (original order) and the sum of squared
@@ -610,12 +632,10 @@ cudaError_t launch_lloyd_iter(const LloydBuffers &b, int32_t *count_next, const 
     default: e = assign_dispatch<0>(b, t, d, iter, unit_lo, unit_hi, kmax, rows_per_thread, st, kt); break;
     }
     if (e != cudaSuccess) return e;
-    int64_t work = (cen_hi - cen_lo) * d;
-    int64_t g = (work + 255) / 256;
-    if (g > (int64_t)sm_count * 8) g = (int64_t)sm_count * 8;
-    if (g < 1) g = 1;
     kt->begin(st);
-    k_lloyd_finalize<<<(int)g, 256, 0, st>>>(b.centers, b.acc, b.count, count_next, cen_lo, cen_hi, d);
+    if (d % 4 == 0) finalize_launch<4>(b, count_next, cen_lo, cen_hi, d, sm_count, st);
+    else if (d % 2 == 0) finalize_launch<2>(b, count_next, cen_lo, cen_hi, d, sm_count, st);
+    else finalize_launch<1>(b, count_next, cen_lo, cen_hi, d, sm_count, st);
     kt->end(PSCL_K_LLOYD_FINALIZE, st);
     return cudaGetLastError();
 }
