@@ -54,11 +54,13 @@ def lib():
         L.or_assign.argtypes = [P, C.c_int64, C.c_int32, P, C.c_int32, P, P, P]
         L.or_lloyd.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P,
                                C.c_double, P, P]
+        L.or_lloyd_w.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P,
+                                 C.c_double, P, P]
         L.or_lloyd_seeded.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
                                       C.c_uint32, C.c_uint32, C.c_int, P, P, P, P]
         L.or_two_level.argtypes = [P]
         for f in ("or_init_indices", "or_scale", "or_peel", "or_peel_select", "or_assign", "or_lloyd",
-                  "or_lloyd_seeded", "or_two_level"):
+                  "or_lloyd_w", "or_lloyd_seeded", "or_two_level"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -137,8 +139,9 @@ def assign(pts: np.ndarray, centers: np.ndarray):
     return lab, b, s
 
 
-def lloyd(pts: np.ndarray, init_centers: np.ndarray, iters: int, force=None, tie_tol=0.0):
-    """Lloyd from given initial centers.  Returns (centers, labels, sse_hist, counts, n_forced, n_bad)."""
+def lloyd(pts: np.ndarray, init_centers: np.ndarray, iters: int, force=None, tie_tol=0.0, weights=None):
+    """Lloyd from given initial centers.  Returns (centers, labels, sse_hist, counts, n_forced, n_bad).
+    weights: optional non-negative integer weight per point (weighted means, weighted SSE)."""
     pts = np.ascontiguousarray(pts, np.float32)
     c = np.array(init_centers, np.float64, order="C", copy=True)
     m, d = pts.shape
@@ -149,8 +152,9 @@ def lloyd(pts: np.ndarray, init_centers: np.ndarray, iters: int, force=None, tie
     nf = C.c_int64(0)
     nb = C.c_int64(0)
     frc = None if force is None else np.ascontiguousarray(force, np.int32)
-    _check(lib().or_lloyd(_p(pts), m, d, k, iters, _p(c), _p(lab), _p(hist), _p(cnt), _p(frc),
-                          tie_tol, C.byref(nf), C.byref(nb)), "lloyd")
+    w = None if weights is None else np.ascontiguousarray(weights, np.int64)
+    _check(lib().or_lloyd_w(_p(pts), m, d, k, iters, _p(c), _p(lab), _p(hist), _p(cnt), _p(w), _p(frc),
+                            tie_tol, C.byref(nf), C.byref(nb)), "lloyd")
     return c, lab, hist[:iters], cnt, nf.value, nb.value
 
 
@@ -174,6 +178,7 @@ class _Args(C.Structure):
         ("local_k", C.c_int32), ("final_k", C.c_int32), ("iters", C.c_int32),
         ("seed", C.c_uint64), ("first_k", C.c_int32), ("n_threads", C.c_int32),
         ("select_peel", C.c_int32), ("unequal_m", C.c_int32), ("storage_bf16", C.c_int32),
+        ("pool_weighted", C.c_int32),
         ("force_local", C.c_void_p), ("force_final", C.c_void_p), ("tie_tol", C.c_double),
         ("scaled", C.c_void_p), ("perm", C.c_void_p), ("seg_off", C.c_void_p),
         ("landmarks", C.c_void_p), ("local_centers", C.c_void_p), ("local_k_eff", C.c_void_p),
@@ -219,8 +224,9 @@ def pooled_count(n: int, N: int, local_k: int) -> tuple[int, int]:
 def two_level(raw: np.ndarray, N: int, local_k: int, final_k: int, iters: int, seed: int,
               first_k: bool = False, threads: int = 0, force_local=None, force_final=None,
               select_peel: bool = False, unequal_m: int = 0, bf16: bool = False,
-              tie_tol: float = 0.0) -> TwoLevel:
-    """unequal_m > 0: Algorithm 2 with that many landmarks instead of the peel (N unused)."""
+              tie_tol: float = 0.0, pool_weighted: bool = False) -> TwoLevel:
+    """unequal_m > 0: Algorithm 2 with that many landmarks instead of the peel (N unused).
+    pool_weighted: the pooled Lloyd weighs each local center by its cluster's size."""
     raw = np.ascontiguousarray(raw, np.float32)
     n, d = raw.shape
     if unequal_m > 0:
@@ -247,6 +253,7 @@ def two_level(raw: np.ndarray, N: int, local_k: int, final_k: int, iters: int, s
     a.select_peel = int(select_peel)
     a.unequal_m = int(unequal_m)
     a.storage_bf16 = int(bf16)
+    a.pool_weighted = int(pool_weighted)
     a.force_local = None if fl is None else fl.ctypes.data
     a.force_final = None if ff is None else ff.ctypes.data
     a.tie_tol = tie_tol

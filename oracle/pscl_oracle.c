@@ -284,10 +284,14 @@ int or_assign(const float *pts, int64_t m, int32_t d, const double *c, int32_t k
 /*          own choice is not unique within tie_tol (the other choice's distance is  */
 /*          within tie_tol*max(1, best) of the best), the other choice is followed;  */
 /*          any other disagreement is counted in *n_bad.  NULL = plain Lloyd.          */
+/* weights: optional m non-negative point weights (or_lloyd_w): a center moves to    */
+/*          the weighted mean sum(w x) / sum(w) of its points, and sse_hist holds     */
+/*          sum(w * distance).  With integer weights this is Lloyd on the multiset    */
+/*          that holds point p w_p times.  NULL = every weight 1.                     */
 /* ------------------------------------------------------------------------------ */
-int or_lloyd(const float *pts, int64_t m, int32_t d, int32_t k, int32_t T, double *centers,
-             int32_t *labels, double *sse_hist, int64_t *counts, const int32_t *force,
-             double tie_tol, int64_t *n_forced, int64_t *n_bad)
+int or_lloyd_w(const float *pts, int64_t m, int32_t d, int32_t k, int32_t T, double *centers,
+               int32_t *labels, double *sse_hist, int64_t *counts, const int64_t *weights,
+               const int32_t *force, double tie_tol, int64_t *n_forced, int64_t *n_bad)
 {
     double *sum;
     int64_t *cnt, p, forced = 0, bad = 0;
@@ -325,8 +329,14 @@ int or_lloyd(const float *pts, int64_t m, int32_t d, int32_t k, int32_t T, doubl
         memset(cnt, 0, (size_t)k * sizeof(int64_t));
         for (p = 0; p < m; p++) {
             int32_t l = labels[p];
-            cnt[l] += 1;
-            for (a = 0; a < d; a++) sum[(int64_t)l * d + a] = sum[(int64_t)l * d + a] + (double)pts[p * d + a];
+            if (weights) {
+                cnt[l] += weights[p];
+                for (a = 0; a < d; a++)
+                    sum[(int64_t)l * d + a] = sum[(int64_t)l * d + a] + (double)weights[p] * (double)pts[p * d + a];
+            } else {
+                cnt[l] += 1;
+                for (a = 0; a < d; a++) sum[(int64_t)l * d + a] = sum[(int64_t)l * d + a] + (double)pts[p * d + a];
+            }
         }
         for (j = 0; j < k; j++) {
             if (cnt[j] > 0) {
@@ -336,7 +346,10 @@ int or_lloyd(const float *pts, int64_t m, int32_t d, int32_t k, int32_t T, doubl
         }
         if (sse_hist) {
             double s = 0.0;
-            for (p = 0; p < m; p++) s = s + sqdist(pts + p * d, centers + (int64_t)labels[p] * d, d);
+            for (p = 0; p < m; p++) {
+                double v = sqdist(pts + p * d, centers + (int64_t)labels[p] * d, d);
+                s = s + (weights ? (double)weights[p] * v : v);
+            }
             sse_hist[t] = s;
         }
     }
@@ -350,6 +363,13 @@ int or_lloyd(const float *pts, int64_t m, int32_t d, int32_t k, int32_t T, doubl
     free(sum);
     free(cnt);
     return OR_OK;
+}
+
+int or_lloyd(const float *pts, int64_t m, int32_t d, int32_t k, int32_t T, double *centers,
+             int32_t *labels, double *sse_hist, int64_t *counts, const int32_t *force,
+             double tie_tol, int64_t *n_forced, int64_t *n_bad)
+{
+    return or_lloyd_w(pts, m, d, k, T, centers, labels, sse_hist, counts, NULL, force, tie_tol, n_forced, n_bad);
 }
 
 /* Initial centers of one Lloyd run over m points: the k_eff = min(k, m) points picked
@@ -473,6 +493,9 @@ typedef struct {
     int32_t select_peel;      /* 1: or_peel_select instead of or_peel (same result) */
     int32_t unequal_m;        /* > 0: Algorithm 2 with this many landmarks instead of the peel */
     int32_t storage_bf16;     /* 1: scaled values rounded to bfloat16 (raw: bfloat16 values) */
+    int32_t pool_weighted;    /* 1: the pooled Lloyd weighs every local center by its cluster's
+                                 size in the last local iteration (the abstract clusters the
+                                 subclusters' means; the sizes make that the weighted means) */
     const int32_t *force_local; /* optional iters*n trace, subcluster-packed order */
     const int32_t *force_final; /* optional iters*P trace                          */
     double tie_tol;
@@ -508,6 +531,7 @@ int or_two_level(or_two_level_args *A)
     double *mn, *mx;
     float *packed;
     int64_t *cen_off;
+    int64_t *wts = NULL;      /* pooled weights (pool_weighted) */
     int rc;
     if (n < 1 || d < 1 || A->N < 1 || A->local_k < 1 || A->final_k < 1 || T < 0) return OR_EINVAL;
     mn = (double *)malloc((size_t)d * sizeof(double));
@@ -537,6 +561,11 @@ int or_two_level(or_two_level_args *A)
     }
     A->n_pooled = P;
     if (A->final_k > P) { rc = OR_EINVAL; goto done; }
+    /* pooled weights: the local cluster sizes (no iteration, no sizes: every weight 1) */
+    if (A->pool_weighted && T > 0) {
+        wts = (int64_t *)malloc((size_t)P * sizeof(int64_t));
+        if (!wts) { rc = OR_ENOMEM; goto done; }
+    }
 
     /* Step 3: Lloyd on every subcluster (independent, so they may run concurrently). */
     {
@@ -564,7 +593,7 @@ int or_two_level(or_two_level_args *A)
             }
             if (r2 == OR_OK)
                 r2 = or_lloyd(packed + off * d, m, d, ke, T, A->local_centers + cen_off[s] * d, lab,
-                              hist, NULL, frc, A->tie_tol, &forced, &bad);
+                              hist, wts ? wts + cen_off[s] : NULL, frc, A->tie_tol, &forced, &bad);
             if (r2 != OR_OK) err |= 1;
             free(frc);
             if (!A->local_labels) free(lab);
@@ -584,8 +613,8 @@ int or_two_level(or_two_level_args *A)
         for (i = 0; i < P * d; i++) pool[i] = (float)A->local_centers[i];
         rc = init_centers(pool, P, d, A->final_k, A->seed, 1u, 0u, A->first_k, A->final_centers);
         if (rc == OR_OK)
-            rc = or_lloyd(pool, P, d, A->final_k, T, A->final_centers, lab, A->final_sse_hist, NULL,
-                          A->force_final, A->tie_tol, &forced, &bad);
+            rc = or_lloyd_w(pool, P, d, A->final_k, T, A->final_centers, lab, A->final_sse_hist, NULL, wts,
+                            A->force_final, A->tie_tol, &forced, &bad);
         A->n_forced += forced;
         A->n_bad += bad;
         free(pool);
@@ -617,6 +646,7 @@ done:
     free(mx);
     free(packed);
     free(cen_off);
+    free(wts);
     return rc;
 }
 

@@ -379,3 +379,52 @@ def test_bf16_storage_rounds_once_to_nearest_even():
     # float32 storage keeps 24 bits
     xs3, _, _ = oracle.scale(np.array([[0.0], [3.0], [1.0]], np.float32))
     assert xs3[2, 0] == np.float32(1.0 / 3.0)
+
+
+# ----------------------------------------------------------------------------------
+# Count-weighted pooled Lloyd (the abstract: the second level clusters the subclusters'
+# means; weighing each local center by its cluster's size makes those the weighted means).
+# ----------------------------------------------------------------------------------
+def test_weighted_lloyd_with_unit_weights_is_plain_lloyd():
+    x, _, _ = oracle.scale(synth.mixture(600, 4, 6, seed=31))
+    c0 = x[:7].astype(np.float64)
+    a = oracle.lloyd(x, c0, 9)
+    b = oracle.lloyd(x, c0, 9, weights=np.ones(600, np.int64))
+    for u, v in zip(a[:4], b[:4]):
+        np.testing.assert_array_equal(u, v)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_weighted_lloyd_equals_lloyd_on_the_replicated_multiset(seed):
+    # integer weights w_p: Lloyd on the multiset holding point p w_p times (zero: absent)
+    # moves the centers identically, its labels are the weighted run's labels repeated,
+    # and its SSE is the weighted SSE
+    rng = np.random.default_rng(seed)
+    x, _, _ = oracle.scale(synth.mixture(120, 3, 5, seed=40 + seed))
+    w = rng.integers(0, 5, size=120).astype(np.int64)
+    w[:6] = 1 + np.arange(6)                        # the initial centers carry weight
+    c0 = x[:6].astype(np.float64)
+    cw, lw, hw, _, _, _ = oracle.lloyd(x, c0, 12, weights=w)
+    xr = np.repeat(x, w, axis=0)
+    cr, lr, hr, _, _, _ = oracle.lloyd(xr, c0, 12)
+    np.testing.assert_allclose(cw, cr, rtol=0, atol=1e-14)
+    np.testing.assert_array_equal(np.repeat(lw, w), lr)
+    np.testing.assert_allclose(hw, hr, rtol=1e-13, atol=0)
+
+
+def test_pooled_weights_are_the_local_cluster_sizes():
+    # the two-level run with pool_weighted: its final centers are those of plain Lloyd on
+    # the pooled local centers, each repeated as often as its cluster has members in the
+    # last local iteration (first-k init, so both runs start from the same centers)
+    raw = synth.mixture(3000, 3, 8, seed=51)
+    N, lk, fk, T = 400, 12, 6, 8
+    r = oracle.two_level(raw, N, lk, fk, T, seed=0, first_k=True, pool_weighted=True)
+    sizes = np.concatenate([np.bincount(r.local_labels[r.seg_off[s]:r.seg_off[s + 1]], minlength=r.local_k_eff[s])
+                            for s in range(len(r.seg_off) - 1)])
+    assert sizes.sum() == 3000 and len(sizes) == len(r.local_centers)
+    pool = r.local_centers.astype(np.float32)
+    cr, _, _, _, _, _ = oracle.lloyd(np.repeat(pool, sizes, axis=0), pool[:fk].astype(np.float64), T)
+    np.testing.assert_allclose(r.final_centers, cr, rtol=0, atol=1e-14)
+    u = oracle.two_level(raw, N, lk, fk, T, seed=0, first_k=True)
+    np.testing.assert_array_equal(u.local_centers, r.local_centers)       # the first level is unchanged
+    assert np.abs(u.final_centers - r.final_centers).max() > 1e-6        # the weights do act
