@@ -292,6 +292,16 @@ def main_arm(args, w: synth.Workload):
         job_p.close()
         del local_evals
 
+    # ---- count-weighted pooling on the same data: its final SSE against the unweighted one
+    job_w = B.Job(x_dev, ctx=ctx)
+    job_w.option(B.PSCL_OPT_POOL_WEIGHTED)
+    job_w.steps(wr.N, wr.local_k, wr.final_k, wr.iters, seed, B.PRECISIONS[args.prec])
+    _, _, sse_w = job_w.result(labels=False)
+    ph_w = job_w.phase_ms()
+    pool_weighted = {"sse": sse_w, "sse_unweighted": sse, "sse_ratio": sse_w / sse,
+                     "ms_per_job": float(sum(ph_w)), "final_lloyd_ms": float(ph_w[3])}
+    job_w.close()
+
     job.close()
     B.pscl_ctx_destroy(ctx)
 
@@ -332,7 +342,7 @@ def main_arm(args, w: synth.Workload):
             "phase_ms": {"scale": float(phases[0]), "peel": float(phases[1]), "local_lloyd": float(phases[2]),
                          "final_lloyd": float(phases[3]), "sse": float(phases[4])},
             "lloyd_only_value": evals / (float(phases[2] + phases[3]) * 1e-3),
-            "plain_fp32": plain, "clocks": clocks}
+            "plain_fp32": plain, "pool_weighted": pool_weighted, "clocks": clocks}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, args.oracle_n)
     if rank == 0:

@@ -95,7 +95,15 @@ typedef enum {
     /* Rows per thread in the float32 assignment kernel: 0 = its default (up to 4 rows
      *    kept in registers), 1 = one, 2 = eight for d <= 16.  Jobs and batches; results do
      *    not depend on it. */
-    PSCL_OPT_ROWS_PER_THREAD = 7
+    PSCL_OPT_ROWS_PER_THREAD = 7,
+    /* Jobs only, 1: the Lloyd on the pooled local centers weighs each local center by its
+     *    cluster's size (members in the last local iteration): a center moves to the
+     *    size-weighted mean of its pooled points, so the second level clusters the
+     *    subclusters' means as the abstract describes, each standing for its points.
+     *    The local level and the final SSE over all n points are unchanged; the pooled
+     *    Lloyd then runs in float32 (prec ignored) with global 64-bit sums.  Needs
+     *    n < 2^31 (else PSCL_EINVAL).  Default 0 (unweighted). */
+    PSCL_OPT_POOL_WEIGHTED = 8
 } pscl_option;
 
 /* The library's kernels, for pscl_get_kernel_times. */

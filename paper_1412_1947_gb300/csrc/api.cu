@@ -95,7 +95,7 @@ struct pscl_job : Owner {
     int d = 0;
     int state = 0;                    // 0 loaded, 1 scaled, 2 subclustered, 3 clustered
     // options
-    int plain = 0, trace = 0, first_k = 0, graph = 0, ktiming = 0, rpt = 0;
+    int plain = 0, trace = 0, first_k = 0, graph = 0, ktiming = 0, rpt = 0, pool_w = 0;
     KTimer kt;                        // launch counts (+ events when timing) of the last run
     // input and scaling
     int dtype = PSCL_F32;
@@ -363,6 +363,11 @@ extern "C" int pscl_job_set_option(pscl_job *j, int opt, int64_t v)
     case PSCL_OPT_ROWS_PER_THREAD:
         if (v < 0 || v > 2) return fail(PSCL_EINVAL, "rows per thread must be 0, 1 or 2");
         j->rpt = (int)v;
+        break;
+    case PSCL_OPT_POOL_WEIGHTED:
+        // the weights sum to n in an int32 count, and w x to at most n 2^32 in 64 bits
+        if (v != 0 && j->n >= ((int64_t)1 << 31)) return fail(PSCL_EINVAL, "weighted pooling needs n < 2^31");
+        j->pool_w = v != 0;
         break;
     default: return fail(PSCL_EINVAL, "unknown option %d", opt);
     }
@@ -731,7 +736,8 @@ static int rows_per_thread(int option, const LloydPlan &p)
 // ------------------------------------------------------------------ enqueue (launches only)
 static int run_lloyd(pscl_job *j, const LloydPlan &p, const float *pts, float *centers,
                      unsigned long long *acc, int32_t *cnt2, int32_t *labels, int32_t *trace,
-                     int iters, uint64_t seed, uint32_t stage, bool plain, int prec)
+                     int iters, uint64_t seed, uint32_t stage, bool plain, int prec,
+                     const int32_t *weights = nullptr)
 {
     cudaStream_t st = j->ctx->stream;
     const SegTable t = p.table();
@@ -743,6 +749,7 @@ static int run_lloyd(pscl_job *j, const LloydPlan &p, const float *pts, float *c
     b.labels = labels;
     b.trace = trace;
     b.rows = p.rows;
+    b.weights = weights;
     CU(launch_lloyd_init(b, t, j->d, p.P, seed, stage, j->first_k, p.kmax, st, &j->kt));
     if (!plain) {
         for (int it = 0; it < iters; it++) {
@@ -798,8 +805,11 @@ static int enqueue_subcluster(pscl_job *j, bool events)
 static int enqueue_cluster(pscl_job *j, bool events)
 {
     cudaStream_t st = j->ctx->stream;
+    // count-weighted pooling: each local center weighs its cluster's size, the counts of
+    // the last local iteration (left in its parity of the local count buffer)
+    const int32_t *w = j->pool_w && j->iters > 0 ? j->cnt_l + (size_t)((j->iters - 1) & 1) * j->lp.P : nullptr;
     TRY(run_lloyd(j, j->fp, j->cl, j->cf, j->acc_f, j->cnt_f, j->lab_f, j->trace_f, j->fiters, j->fseed, 1u,
-                  false, j->fprec));
+                  false, j->fprec, w));
     if (events) CU(cudaEventRecord(j->ev[4], st));
     CU(launch_final_sse(j->x, j->n, j->d, j->cf, j->final_k, j->labels, j->blk_sse, j->sse, j->tickets + 1,
                         j->ctx->sm_count, st, &j->kt));
@@ -949,7 +959,7 @@ extern "C" int pscl_run(pscl_job *j, int64_t N, int32_t local_k, int32_t final_k
     }
     uint64_t key[8] = {(uint64_t)N, (uint64_t)local_k, (uint64_t)final_k, (uint64_t)iters, seed, (uint64_t)prec,
                        (uint64_t)(uintptr_t)j->dev_in ^ (uint64_t)(uintptr_t)j->in16,
-                       (uint64_t)(j->plain | j->trace << 1 | j->first_k << 2 | j->rpt << 3)};
+                       (uint64_t)(j->plain | j->trace << 1 | j->first_k << 2 | j->rpt << 3 | j->pool_w << 5)};
     if (j->gexec && memcmp(key, j->gkey, sizeof key) != 0) drop_graph(j);
     if (!j->gexec) {
         cudaGraph_t g = nullptr;

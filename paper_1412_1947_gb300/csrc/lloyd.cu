@@ -153,7 +153,7 @@ template <int D, int R, bool kSmemAcc>
 __global__ void __launch_bounds__(kThreads)
 k_lloyd_assign(const float *__restrict__ pts, SegTable t, int d, const float *__restrict__ centers,
                unsigned long long *acc, int32_t *count, int32_t *labels, int32_t *trace,
-               int64_t trace_off, int unit_lo, int chunk_k)
+               int64_t trace_off, int unit_lo, int chunk_k, const int32_t *__restrict__ weights)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int DR = D > 0 ? D : 1;
@@ -292,12 +292,15 @@ k_lloyd_assign(const float *__restrict__ pts, SegTable t, int d, const float *__
                     }
                 }
             } else {
-                atomicAdd(&count[c0 + bj[q]], 1);
+                // weighted rows (global sums only): w x and w; a zero weight adds nothing
+                const unsigned long long w = weights ? (unsigned long long)(uint32_t)weights[row] : 1ull;
+                if (w == 0ull) continue;
+                atomicAdd(&count[c0 + bj[q]], (int)w);
                 if (D > 0) {
 #pragma unroll
-                    for (int j = 0; j < DR; j++) atomicAdd(&acc[(c0 + bj[q]) * dd + j], to_fix(xv[q][j]));
+                    for (int j = 0; j < DR; j++) atomicAdd(&acc[(c0 + bj[q]) * dd + j], to_fix(xv[q][j]) * w);
                 } else {
-                    for (int j = 0; j < dd; j++) atomicAdd(&acc[(c0 + bj[q]) * dd + j], to_fix(__ldg(&xr[j])));
+                    for (int j = 0; j < dd; j++) atomicAdd(&acc[(c0 + bj[q]) * dd + j], to_fix(__ldg(&xr[j])) * w);
                 }
             }
         }
@@ -535,7 +538,7 @@ cudaError_t assign_launch(const LloydBuffers &b, const SegTable &t, int d, int i
     const int chunk = center_chunk(d, kmax);
     const size_t acc_bytes = (size_t)kmax * (d | 1) * 8 + (size_t)kmax * 4;
     const size_t c_bytes = ((size_t)chunk * d * 4 + 15) & ~(size_t)15;
-    const bool smem_acc = acc_bytes <= kSmemAccMax;
+    const bool smem_acc = !b.weights && acc_bytes <= kSmemAccMax;
     const size_t smem = (smem_acc ? acc_bytes : 0) + c_bytes;
     const int grid = unit_hi - unit_lo;
     if (grid <= 0) return cudaSuccess;
@@ -544,14 +547,14 @@ cudaError_t assign_launch(const LloydBuffers &b, const SegTable &t, int d, int i
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kt->begin(st);
         kern<<<grid, kThreads, smem, st>>>(b.pts, t, d, b.centers, b.acc, b.count, b.labels, b.trace,
-                                           (int64_t)iter * b.rows, unit_lo, chunk);
+                                           (int64_t)iter * b.rows, unit_lo, chunk, b.weights);
         kt->end(PSCL_K_LLOYD_ASSIGN, st);
     } else {
         auto kern = k_lloyd_assign<D, R, false>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kt->begin(st);
         kern<<<grid, kThreads, smem, st>>>(b.pts, t, d, b.centers, b.acc, b.count, b.labels, b.trace,
-                                           (int64_t)iter * b.rows, unit_lo, chunk);
+                                           (int64_t)iter * b.rows, unit_lo, chunk, b.weights);
         kt->end(PSCL_K_LLOYD_ASSIGN, st);
     }
     return cudaGetLastError();
@@ -619,7 +622,7 @@ cudaError_t launch_lloyd_iter(const LloydBuffers &b, int32_t *count_next, const 
                               KTimer *kt, int rows_per_thread)
 {
     cudaError_t e;
-    if (prec != PSCL_PREC_FP32 && tc_supported(d, kmax, prec)) {
+    if (prec != PSCL_PREC_FP32 && !b.weights && tc_supported(d, kmax, prec)) {
         e = launch_lloyd_assign_tc(b, t, d, iter, unit_lo, unit_hi, kmax, prec, flags, sm_count, st, kt);
     } else switch (d) {
     case 2: e = assign_dispatch<2>(b, t, d, iter, unit_lo, unit_hi, kmax, rows_per_thread, st, kt); break;

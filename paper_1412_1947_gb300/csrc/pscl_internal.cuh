@@ -157,11 +157,16 @@ struct LloydBuffers {
     int32_t *labels;                 // rows
     int32_t *trace;                  // iters x rows (or NULL)
     int64_t rows;
+    // rows' non-negative integer weights (or NULL: every weight 1).  A weighted row adds
+    // w x to its center's sum and w to its count; such runs use the float32 assignment
+    // with global 64-bit sums (w q needs up to 63 bits).
+    const int32_t *weights = nullptr;
 };
 cudaError_t launch_lloyd_init(const LloydBuffers &b, const SegTable &t, int d, int64_t P,
                               uint64_t seed, uint32_t stage, int first_k, int kmax,
                               cudaStream_t st, KTimer *kt);
-// prec: a pscl_prec; TF32/BF16 use the tensor-core assignment where tc_supported().
+// prec: a pscl_prec; TF32/BF16 use the tensor-core assignment where tc_supported() and the
+// rows are unweighted.
 cudaError_t launch_lloyd_iter(const LloydBuffers &b, int32_t *count_next, const SegTable &t,
                               int d, int iter, int unit_lo, int unit_hi, int64_t cen_lo,
                               int64_t cen_hi, int kmax, int prec, uint32_t *flags, int sm_count,

@@ -41,7 +41,8 @@ class GpuRun:
 
 
 def run_gpu(raw, N, local_k, final_k, iters, seed, *, trace=True, plain=False, first_k=False,
-            graph=False, prec=B.PSCL_PREC_FP32, runs=1, device_points=False, unequal_m=0):
+            graph=False, prec=B.PSCL_PREC_FP32, runs=1, device_points=False, unequal_m=0,
+            pool_weighted=False):
     pts = raw
     if device_points:
         import torch
@@ -55,6 +56,8 @@ def run_gpu(raw, N, local_k, final_k, iters, seed, *, trace=True, plain=False, f
             j.option(B.PSCL_OPT_INIT_FIRST_K)
         if graph:
             j.option(B.PSCL_OPT_GRAPH)
+        if pool_weighted:
+            j.option(B.PSCL_OPT_POOL_WEIGHTED)
         for _ in range(runs):
             if unequal_m:
                 j.steps_unequal(unequal_m, local_k, final_k, iters, seed, prec)
@@ -71,12 +74,14 @@ def run_gpu(raw, N, local_k, final_k, iters, seed, *, trace=True, plain=False, f
         return GpuRun(j.scaled(), perm, seg_off, lc, ke, cnt, fc, lab, sse, tl, tf, rc, asg)
 
 
-def run_oracle(raw, N, local_k, final_k, iters, seed, gpu: GpuRun | None = None, first_k=False, unequal_m=0):
+def run_oracle(raw, N, local_k, final_k, iters, seed, gpu: GpuRun | None = None, first_k=False, unequal_m=0,
+               pool_weighted=False):
     fl = ff = None
     if gpu is not None and gpu.trace_local is not None:
         fl, ff = gpu.trace_local, gpu.trace_final
     return oracle.two_level(raw, N, local_k, final_k, iters, seed, first_k=first_k,
-                            force_local=fl, force_final=ff, tie_tol=TIE_TOL, unequal_m=unequal_m)
+                            force_local=fl, force_final=ff, tie_tol=TIE_TOL, unequal_m=unequal_m,
+                            pool_weighted=pool_weighted)
 
 
 def center_err(a, ref):
