@@ -545,13 +545,101 @@ def main_serving(args):
     print(json.dumps(line), flush=True)
 
 
+# The paper's timing tables (Table 2: one-level vs two-level k-means on 2-D synthetic data of
+# 100k / 250k / 500k points, 500 per cluster; Table 3: the 500k case at compression 5, 10, 15,
+# 20), on a Tesla C2075 GPU against a Xeon E5-1410 CPU, units unlabelled (seconds, presumably).
+PAPER_TABLE2 = {100000: (2.328, 2.78), 250000: (25.6, 4.96), 500000: (156.8, 6.2)}
+PAPER_TABLE3 = {5: 6.2, 10: 5.76, 15: 4.83, 20: None}
+TABLES_N_SUB = 1000          # subcluster size N; compression c gives N / c local centers
+
+
+def main_tables(args):
+    """Tables 2 and 3 re-shaped for this GPU: for n in {100k, 250k, 500k} 2-D points, 500 per
+    blob, k = n / 500: one-level Lloyd on all points (a batch of one instance) against the
+    two-level method at compression c = N / local_k in {5, 10, 15, 20} with N = 1000; 25
+    Lloyd iterations, seeded init, every run graph-recorded and timed with CUDA events on
+    its stream.  Reports times, speedups and each run's SSE over all scaled points; the
+    oracle's times for the 100k case when host timing is on.  Context, not a driver line."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1412_1947_gb300 import binding as B
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    iters, seed = 25, 1947
+    ctx = B.pscl_ctx_create(0, 0, stream.cuda_stream)
+
+    def timed(fn, reps):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b_ = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b_.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b_))
+        return statistics.median(ms)
+
+    rows = []
+    for n in (100000, 250000, 500000):
+        k = n // 500
+        raw = synth.blob_points(n // 500, 500, 2, seed=synth.BASE_SEED + 10 + n // 50000)
+        x_dev = torch.from_numpy(raw).to(dev)
+        one = B.Batch(x_dev, np.array([n], np.int64), [k], ctx=ctx)
+        one_ms = timed(lambda: one.run(iters, seed, B.PSCL_PREC_FP32), args.steps)
+        _, _, sse1 = one.result(labels=False)
+        one.close()
+        row = {"n": n, "k": k, "one_level_ms": one_ms, "one_level_sse": float(sse1[0]),
+               "one_level_evals": n * k * iters, "two_level": []}
+        for c in (5, 10, 15, 20):
+            lk = -(-TABLES_N_SUB // c)
+            job = B.Job(x_dev, ctx=ctx)
+            job.option(B.PSCL_OPT_GRAPH)
+            ms = timed(lambda: job.run(TABLES_N_SUB, lk, k, iters, seed, B.PSCL_PREC_FP32), args.steps)
+            _, _, sse2 = job.result(labels=False)
+            job.close()
+            row["two_level"].append({"compression": c, "N": TABLES_N_SUB, "local_k": lk, "ms": ms,
+                                     "speedup": one_ms / ms, "sse": sse2, "sse_ratio": sse2 / float(sse1[0])})
+        if n == 100000 and not args.no_cpu:
+            xs, _, _ = oracle.scale(raw)
+            t0 = time.perf_counter()
+            oracle.lloyd_seeded(xs, k, iters, seed)
+            t1 = time.perf_counter()
+            oracle.two_level(raw, TABLES_N_SUB, TABLES_N_SUB // 5, k, iters, seed)
+            t2 = time.perf_counter()
+            row["oracle_s"] = {"one_level": t1 - t0, "two_level_c5": t2 - t1,
+                               "cores": os.cpu_count(), "note": "float64 C oracle, OpenMP over subclusters"}
+        rows.append(row)
+        del x_dev
+    B.pscl_ctx_destroy(ctx)
+    r500 = rows[-1]["two_level"][0]
+    line = {"metric": "two-level speedup over one-level Lloyd (500k points, compression 5)", "value": r500["speedup"],
+            "unit": "x", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic (2-D, 500 points per blob)",
+            "config": {"workload": "tables_2d_500perblob", "iters": iters, "N": TABLES_N_SUB,
+                       "compression": "N / local_k"},
+            "rows": rows,
+            "paper": {"table2_s": {str(k_): v for k_, v in PAPER_TABLE2.items()},
+                      "table3_s": {str(k_): v for k_, v in PAPER_TABLE3.items()},
+                      "hardware": "Tesla C2075 (two-level), Xeon E5-1410 (one-level)"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="medium", choices=["small", "medium", "large", "uneven", "serving"])
+    ap.add_argument("--workload", default="medium", choices=["small", "medium", "large", "uneven", "serving", "tables"])
     ap.add_argument("--rows-per-thread", type=int, default=0, choices=[0, 1, 2],
                     help="float32 assignment: 0 default, 1 one row per thread, 2 eight rows (d <= 16)")
     ap.add_argument("--serve-jobs", type=int, default=200)
@@ -567,6 +655,13 @@ def main():
             print(json.dumps({"impl": "reference", "unavailable": "the job server has no reference arm"}))
         else:
             main_serving(args)
+        return
+    if args.workload == "tables":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the tables workload has no reference arm; "
+                              "its oracle times are in the same line"}))
+        else:
+            main_tables(args)
         return
     if args.workload == "uneven":
         if args.impl == "reference":

@@ -14,6 +14,9 @@ benchmarks use:
   uniform in ``sigma_range``; an ``outlier_frac`` share of the points is uniform in
   [-3*sigma_max, 10 + 3*sigma_max]^d.  Drawn in float64 and rounded once to float32.
 * ``uneven_sizes``  -- instance sizes floor(exp(U[ln lo, ln hi])) (log-uniform).
+* ``blob_points``   -- exactly ``per_blob`` points from each of ``blobs`` isotropic
+  Gaussians (means uniform in [0, 10]^d, sigma uniform in ``sigma_range``), in a random
+  order: the shape of the paper's timing data (2-D, 500 points per cluster, Table 2).
 
 Every generator takes an explicit integer seed; numpy's PCG64 is the bit source.
 """
@@ -62,6 +65,18 @@ def mixture(n: int, d: int, blobs: int, *, sigma: float | None = None,
         perm = g.permutation(n)
         out = out[perm]
     return out
+
+
+def blob_points(blobs: int, per_blob: int, d: int, *, sigma_range: tuple[float, float] = (0.2, 1.0),
+                seed: int = BASE_SEED, dtype=np.float32) -> np.ndarray:
+    """blobs * per_blob x d points, exactly per_blob from each blob, shuffled."""
+    g = rng(seed)
+    means = g.uniform(0.0, 10.0, size=(blobs, d))
+    sig = g.uniform(sigma_range[0], sigma_range[1], size=blobs)
+    which = np.repeat(np.arange(blobs), per_blob)
+    z = g.standard_normal(size=(blobs * per_blob, d))
+    pts = (means[which] + z * sig[which][:, None]).astype(dtype)
+    return pts[g.permutation(blobs * per_blob)]
 
 
 def uneven_sizes(count: int, lo: int, hi: int, seed: int) -> np.ndarray:
