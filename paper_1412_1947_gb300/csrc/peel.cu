@@ -54,6 +54,7 @@ constexpr int kPeelScratch = 2 * kHistBins > kBandBins + 7 * kTight ? 2 * kHistB
 constexpr int kBandStage = 4 * 256;           // band entries staged in shared memory (4 per thread)
 constexpr int kPeelDynWords = kPeelScratch + 2 * kKeyCache + 2 * kBandStage;
 constexpr int kQT = 8;                        // tiles of kThreads items per compaction scan
+constexpr int kCB = 16;                       // keys per thread in flight when classifying
 constexpr unsigned kSpinLimit = 1u << 25;      // ~1-2 s of polling per barrier at most
 
 // ------------------------------------------------------------------ block helpers
@@ -306,6 +307,137 @@ __device__ void select_band_global(const uint64_t *bkey, const uint32_t *bpos, u
     __syncthreads();
 }
 
+// The same selection in three passes when the band's keys spread: the smallest and
+// largest key give the bits all keys share; an 11-bit histogram of the next bits finds
+// the digit of the need-th entry; that digit's entries (at most kSelList) are gathered in
+// shared memory and ranked there by (key, position).  Returns false, with nothing
+// decided, when all keys are equal or the digit holds more entries: the caller then runs
+// select_band_global.  scratch: 2048 + 3 kSelList words of shared memory.
+constexpr int kSelBins = 2048;
+constexpr int kSelList = 1024;
+constexpr int kSelBatch = 8;
+__device__ bool select_band_fast(const uint64_t *bkey, const uint32_t *bpos, uint32_t nb, uint32_t need,
+                                 uint32_t *scratch, uint64_t &K, uint32_t &Pp)
+{
+    __shared__ unsigned long long s_mn[kThreads / 32], s_mx[kThreads / 32];
+    __shared__ uint32_t s_bin, s_rank, s_cnt, s_hit;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    uint32_t *h = scratch;
+    uint64_t *lk = reinterpret_cast<uint64_t *>(scratch + kSelBins);      // 8-byte aligned: kSelBins is even
+    uint32_t *lp = scratch + kSelBins + 2 * kSelList;
+    // pass 1: smallest and largest key
+    // every pass keeps kSelBatch loads per thread in flight: one CTA reads the whole band
+    unsigned long long mn = ~0ull, mx = 0ull;
+    for (uint32_t i0 = t; i0 < nb; i0 += kSelBatch * kThreads) {
+        unsigned long long kk[kSelBatch];
+#pragma unroll
+        for (int u = 0; u < kSelBatch; u++) {
+            const uint32_t i = i0 + u * kThreads;
+            kk[u] = i < nb ? __ldcg(&bkey[i]) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kSelBatch; u++) {
+            if (i0 + u * kThreads < nb) {
+                mn = min(mn, kk[u]);
+                mx = max(mx, kk[u]);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) {
+        s_mn[w] = mn;
+        s_mx[w] = mx;
+    }
+    for (int b = t; b < kSelBins; b += kThreads) h[b] = 0;
+    __syncthreads();
+    mn = s_mn[0];
+    mx = s_mx[0];
+#pragma unroll
+    for (int q = 1; q < kThreads / 32; q++) {
+        mn = min(mn, (unsigned long long)s_mn[q]);
+        mx = max(mx, (unsigned long long)s_mx[q]);
+    }
+    if (mn == mx) return false;                          // uniform across the block
+    const int hb = 63 - __clzll((long long)(mn ^ mx));   // highest bit where keys differ
+    const int sh = hb >= 10 ? hb - 10 : 0;               // digit = bits [sh, hb]
+    // pass 2: histogram of the digit (the bits above hb are common to all keys)
+    for (uint32_t i0 = t; i0 < nb; i0 += kSelBatch * kThreads) {
+        unsigned long long kk[kSelBatch];
+#pragma unroll
+        for (int u = 0; u < kSelBatch; u++) {
+            const uint32_t i = i0 + u * kThreads;
+            kk[u] = i < nb ? __ldcg(&bkey[i]) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kSelBatch; u++)
+            if (i0 + u * kThreads < nb) atomicAdd(&h[(uint32_t)(kk[u] >> sh) & (kSelBins - 1)], 1u);
+    }
+    __syncthreads();
+    {
+        constexpr int per = kSelBins / kThreads;
+        uint32_t loc = 0;
+#pragma unroll
+        for (int q = 0; q < per; q++) loc += h[t * per + q];
+        uint32_t tot;
+        const uint32_t before = block_excl_scan(loc, tot);
+        const uint32_t target = need - 1;
+        if (target >= before && target < before + loc) {
+            uint32_t cc = before;
+            for (int q = 0; q < per; q++) {
+                const uint32_t v = h[t * per + q];
+                if (target >= cc && target < cc + v) {
+                    s_bin = (uint32_t)(t * per + q);
+                    s_rank = target - cc;
+                    s_cnt = v;
+                }
+                cc += v;
+            }
+        }
+        if (t == 0) s_hit = 0;
+    }
+    __syncthreads();
+    const uint32_t bin = s_bin, rank = s_rank, cnt = s_cnt;
+    if (cnt > (uint32_t)kSelList) return false;          // uniform across the block
+    // pass 3: the digit's entries, then their rank by (key, position)
+    for (uint32_t i0 = t; i0 < nb; i0 += kSelBatch * kThreads) {
+        unsigned long long kk[kSelBatch];
+#pragma unroll
+        for (int u = 0; u < kSelBatch; u++) {
+            const uint32_t i = i0 + u * kThreads;
+            kk[u] = i < nb ? __ldcg(&bkey[i]) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kSelBatch; u++) {
+            const uint32_t i = i0 + u * kThreads;
+            if (i < nb && ((uint32_t)(kk[u] >> sh) & (kSelBins - 1)) == bin) {
+                const uint32_t slot = atomicAdd(&s_hit, 1u);
+                lk[slot] = kk[u];
+                lp[slot] = __ldcg(&bpos[i]);
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t q = t; q < cnt; q += kThreads) {
+        const uint64_t kq = lk[q];
+        const uint32_t pq = lp[q];
+        uint32_t rk = 0;
+        for (uint32_t o = 0; o < cnt; o++) rk += (lk[o] < kq) || (lk[o] == kq && lp[o] < pq);
+        if (rk == rank) {
+            s_mn[0] = kq;
+            s_hit = pq;
+        }
+    }
+    __syncthreads();
+    K = s_mn[0];
+    Pp = s_hit;
+    __syncthreads();
+    return true;
+}
+
 // Exclusive scans of two values over the block in one pass (blockDim.x == kThreads).
 __device__ void block_excl_scan2(uint32_t v0, uint32_t v1, uint32_t &e0, uint32_t &e1, uint32_t &t0,
                                  uint32_t &t1)
@@ -504,6 +636,30 @@ __device__ __forceinline__ uint32_t bucket_of(float v, uint32_t nb)
 
 // The round's selection: a point with key k is taken if k < lo, if it is a wide-band point
 // marked kTaken, or if lo <= k <= tout and the tight set lists it as taken.
+// Phase C over a slice's keys (key_at(position)): counts those below in_key (certainly
+// taken) and hands those in [in_key, out_key] to to_band(position, key); CB keys per
+// thread are read at once.
+template <int CB, class KeyAt, class ToBand>
+__device__ __forceinline__ uint32_t classify_keys(uint32_t n_live, uint32_t in_key, uint32_t out_key, KeyAt key_at,
+                                                  ToBand to_band)
+{
+    uint32_t n_in = 0;
+    for (uint32_t q0 = threadIdx.x; q0 < n_live; q0 += CB * kThreads) {
+        uint32_t kk[CB];
+#pragma unroll
+        for (int q = 0; q < CB; q++) {
+            const uint32_t qi = q0 + q * kThreads;
+            kk[q] = qi < n_live ? key_at(qi) : kGone;       // past the end: above out_key
+        }
+#pragma unroll
+        for (int q = 0; q < CB; q++) {
+            if (kk[q] < in_key) n_in++;
+            else if (kk[q] <= out_key) to_band(q0 + q * kThreads, kk[q]);
+        }
+    }
+    return n_in;
+}
+
 struct Rule {
     uint32_t lo, tout, nt;
     const uint32_t *tpos, *tcls;
@@ -793,27 +949,15 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
         }
         __syncthreads();
         const uint32_t in_key = s_in_key, out_key = s_out_key;
-        uint32_t n_in = 0;
-        for (uint32_t q0 = t; q0 < n_live; q0 += 4 * kThreads) {
-            uint32_t k4[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const uint32_t qi = q0 + q * kThreads;
-                k4[q] = qi >= n_live ? kGone : kc ? skey[qi] : __ldcg(&a.kpos[s0 + qi]);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const uint32_t k = k4[q];           // past the end: kGone, above out_key
-                if (k < in_key) {
-                    n_in++;
-                } else if (k <= out_key) {
-                    const uint32_t qi = q0 + q * kThreads;
-                    const uint32_t slot = atomicAdd(&ctl->band_cnt[par], 1u);
-                    a.band_k32[slot] = k;
-                    a.band_pos[slot] = LID(qi);
-                }
-            }
-        }
+        auto to_band = [&](uint32_t qi, uint32_t k) {
+            const uint32_t slot = atomicAdd(&ctl->band_cnt[par], 1u);
+            a.band_k32[slot] = k;
+            a.band_pos[slot] = LID(qi);
+        };
+        // keys from shared memory: 4 per thread at a time; from global memory: kCB
+        uint32_t n_in = kc ? classify_keys<4>(n_live, in_key, out_key, [&](uint32_t qi) { return skey[qi]; }, to_band)
+                           : classify_keys<kCB>(n_live, in_key, out_key,
+                                                [&](uint32_t qi) { return __ldcg(&a.kpos[s0 + qi]); }, to_band);
         n_in = block_sum(n_in);
         if (t == 0) ctl->cnt_in[c] = n_in;
         if (!grid_sync(ctl, a.flags, gen)) return;
@@ -865,7 +1009,11 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
             // of them but those within the dff error of the cut-off (in practice only exact
             // ties), which are decided in float64.
             const uint32_t range = out_key - in_key + 1u;
-            slow = range > (uint32_t)kBandBins;
+            // the tight set spans about 2(d+4) of the band's `range` one-ulp keys: when the
+            // band is dense enough that it would hold over twice kTight entries, the fast
+            // path cannot succeed and is skipped (a choice of path, not of result)
+            slow = range > (uint32_t)kBandBins ||
+                   (uint64_t)nb * (uint64_t)(2 * (d + 4)) > (uint64_t)(2 * kTight) * range;
             if (!slow) {
                 for (int b = t; b < kBandBins; b += kThreads) hb[b] = 0;
                 if (t == 0) {
@@ -974,8 +1122,9 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
             }
             if (slow) {
                 // wide band (e.g. many equal distances): float64 for every band entry, spread
-                // over all CTAs, then one CTA selects while the rest wait
-                for (uint32_t q = c * kThreads + t; q < nb; q += G * kThreads) {
+                // evenly over all CTAs (entry q on CTA q mod G: the float64 pipe is the
+                // bound), then one CTA selects while the rest wait
+                for (uint32_t q = t * G + c; q < nb; q += G * kThreads) {
                     const uint32_t pq = __ldcg(&a.band_pos[q]);
                     a.band_key[q] = (uint64_t)__double_as_longlong(dist64(a.x + (size_t)pq * d, Ls, d));
                 }
@@ -983,7 +1132,10 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
                 uint64_t K = 0;
                 uint32_t Pp = 0;
                 if (c == 0) {
-                    select_band_global(a.band_key, a.band_pos, nb, need, K, Pp);
+                    // the band's float64 keys, the fast path's arrays and the key cache are
+                    // no longer needed here: the selection may use that shared memory
+                    if (!select_band_fast(a.band_key, a.band_pos, nb, need, dyn, K, Pp))
+                        select_band_global(a.band_key, a.band_pos, nb, need, K, Pp);
                     if (t == 0) {
                         ctl->sel_key = K;
                         ctl->sel_pos = Pp;
@@ -992,12 +1144,21 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
                 if (!grid_sync(ctl, a.flags, gen)) return;
                 K = __ldcg(&ctl->sel_key);
                 Pp = __ldcg(&ctl->sel_pos);
-                for (uint32_t q = t; q < nb; q += kThreads) {
-                    const uint64_t kq = __ldcg(&a.band_key[q]);
-                    const uint32_t pq = __ldcg(&a.band_pos[q]);
-                    if (kq < K || (kq == K && pq <= Pp)) {
-                        if (pq < s0) band_before++;
-                        else if (pq < s1) a.key[pq] = kTaken;
+                for (uint32_t q0 = t; q0 < nb; q0 += kSelBatch * kThreads) {
+                    uint64_t kq[kSelBatch];
+                    uint32_t pq[kSelBatch];
+#pragma unroll
+                    for (int u = 0; u < kSelBatch; u++) {
+                        const uint32_t q = q0 + u * kThreads;
+                        kq[u] = q < nb ? __ldcg(&a.band_key[q]) : ~0ull;
+                        pq[u] = q < nb ? __ldcg(&a.band_pos[q]) : n;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kSelBatch; u++) {
+                        if (kq[u] < K || (kq[u] == K && pq[u] <= Pp)) {
+                            if (pq[u] < s0) band_before++;
+                            else if (pq[u] < s1) a.key[pq[u]] = kTaken;
+                        }
                     }
                 }
                 lo = in_key;
@@ -1015,8 +1176,10 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
         // (with landmark-only CTAs they do that bookkeeping in the next round's phase A)
         n_live -= compact_list(LID, n_live, seg_out + in_before + band_before, kc ? sid : a.lidx + (size_t)(par ^ 1) * n + s0,
                                [&](uint32_t qi, uint32_t id) {
-                                   // a wide band marks its taken points in key[] by id
-                                   const uint32_t k = slow ? __ldcg(&a.key[id]) : kc ? skey[qi] : __ldcg(&a.kpos[s0 + qi]);
+                                   uint32_t k = kc ? skey[qi] : __ldcg(&a.kpos[s0 + qi]);
+                                   // a wide band marks its taken points in key[] by id: only a
+                                   // key inside the band needs that look-up
+                                   if (slow && k >= in_key && k <= out_key) k = __ldcg(&a.key[id]);
                                    return taken(R, k, id);
                                },
                                [&](uint32_t id) {

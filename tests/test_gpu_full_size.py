@@ -35,3 +35,18 @@ def test_peel_partition_with_slices_beyond_the_key_cache():
     operm, ooff, _ = oracle.peel(x, 1 << 17, select=True)
     np.testing.assert_array_equal(off, ooff)
     np.testing.assert_array_equal(perm, operm)
+
+
+def test_peel_partition_with_dense_float32_keys():
+    # 2^22 points in 64 attributes, subclusters of 2^20: near the cut-off several points
+    # share each float32 key, so the float32 tight set outgrows shared memory and every
+    # round settles its band in float64 across the grid (the wide-band selection)
+    from paper_1412_1947_gb300 import binding as B
+    raw = synth.mixture(1 << 22, 64, 64, seed=8801)
+    with B.Job(raw) as j:
+        j.steps(1 << 20, 2, 2, 1, 3)
+        perm, off = j.partition()
+        x = j.scaled()
+    operm, ooff, _ = oracle.peel(x, 1 << 20, select=True)
+    np.testing.assert_array_equal(off, ooff)
+    np.testing.assert_array_equal(perm, operm)
