@@ -223,7 +223,12 @@ extern "C" int pscl_ctx_create(pscl_ctx **out, int device, size_t budget, void *
     pscl_ctx *c = new pscl_ctx();
     c->device = device;
     c->budget = budget;
-    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        c->sm_count < 1) {
+        delete c;
+        cudaGetLastError();
+        return fail(PSCL_ECUDA, "device %d: no multiprocessor count", device);
+    }
     {   // keep freed pool memory for the next job instead of returning it at every sync
         cudaMemPool_t pool;
         if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {

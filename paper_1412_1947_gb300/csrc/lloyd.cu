@@ -517,7 +517,7 @@ cudaError_t seg_sse_dispatch(const float *pts, const SegTable &t, int d, const f
     const int chunk = center_chunk(d, kmax);
     const size_t smem = (size_t)chunk * d * 4;
     auto kern = k_seg_sse<D>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (const cudaError_t ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return ea;
     kt->begin(st);
     kern<<<t.n_units, kThreads, smem, st>>>(pts, t, d, centers, chunk, labels, unit_sse);
     kt->end(PSCL_K_FINAL_SSE, st);
@@ -544,14 +544,14 @@ cudaError_t assign_launch(const LloydBuffers &b, const SegTable &t, int d, int i
     if (grid <= 0) return cudaSuccess;
     if (smem_acc) {
         auto kern = k_lloyd_assign<D, R, true>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (const cudaError_t ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return ea;
         kt->begin(st);
         kern<<<grid, kThreads, smem, st>>>(b.pts, t, d, b.centers, b.acc, b.count, b.labels, b.trace,
                                            (int64_t)iter * b.rows, unit_lo, chunk, b.weights);
         kt->end(PSCL_K_LLOYD_ASSIGN, st);
     } else {
         auto kern = k_lloyd_assign<D, R, false>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (const cudaError_t ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return ea;
         kt->begin(st);
         kern<<<grid, kThreads, smem, st>>>(b.pts, t, d, b.centers, b.acc, b.count, b.labels, b.trace,
                                            (int64_t)iter * b.rows, unit_lo, chunk, b.weights);
@@ -584,7 +584,7 @@ cudaError_t sse_dispatch(const float *x, int64_t n, int d, const float *centers,
     int grid = (int)(want < (int64_t)sm_count * 8 ? want : (int64_t)sm_count * 8);
     if (grid < 1) grid = 1;
     auto kern = k_final_sse<D>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (const cudaError_t ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return ea;
     kt->begin(st);
     kern<<<grid, kThreads, smem, st>>>(x, n, d, centers, k, chunk, labels, blk_sse, sse, ticket);
     kt->end(PSCL_K_FINAL_SSE, st);
@@ -606,7 +606,7 @@ cudaError_t launch_lloyd_init(const LloydBuffers &b, const SegTable &t, int d, i
     int cap = 1;
     while (cap < 2 * kmax) cap <<= 1;
     size_t smem = ((size_t)kmax + 2 * (size_t)cap) * sizeof(int32_t);
-    cudaFuncSetAttribute(k_lloyd_init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (const cudaError_t ea = cudaFuncSetAttribute(k_lloyd_init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return ea;
     int grid = t.n_seg < 65535 ? t.n_seg : 65535;
     kt->begin(st);
     k_lloyd_init<<<grid, 256, smem, st>>>(b.pts, t, d, b.centers, b.acc, b.count, P, seed, stage, first_k);

@@ -632,9 +632,11 @@ cudaError_t tc_dispatch(const LloydBuffers &b, const SegTable &t, int iter, int 
         e = cudaFuncGetAttributes(&fa, kern);
         if (e != cudaSuccess) return e;
         int dev = 0, smem_sm = 0, reserved = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+            return e;
+        if ((e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess)
+            return e;
         const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + reserved);
         const int by_regs = 65536 / (((fa.numRegs + 7) & ~7) * kTcThreads);
         const int by_tmem = (int)(512 / ((uint32_t)nbuf * ncols));
