@@ -147,3 +147,17 @@ def test_nonfinite_input_is_reported():
         with pytest.raises(B.PsclError) as e:
             j.scaled()
         assert e.value.code == B.PSCL_EINVAL
+
+
+@pytest.mark.parametrize("n,d,N,lk,fk,T", [
+    (1, 3, 1, 1, 1, 3),                 # a single point: constant attributes, one subcluster
+    (50, 1, 10, 3, 2, 5),               # one attribute (the any-d kernels)
+    (300, 4, 1, 1, 5, 3),               # N = 1: every point its own subcluster and center
+    (500, 8, 100, 5, 25, 0),            # no Lloyd iteration: the seeded initial centers
+    (400, 6, 80, 4, 20, 4),             # final k = every pooled center
+])
+def test_degenerate_shapes_match_oracle(n, d, N, lk, fk, T):
+    raw = synth.mixture(n, d, 3, seed=90 + n)
+    g = run_gpu(raw, N, lk, fk, T, seed=3)
+    o = run_oracle(raw, N, lk, fk, T, seed=3, gpu=g)
+    compare(g, o)
