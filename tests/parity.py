@@ -24,7 +24,7 @@ TIE_TOL = 1e-5
 
 
 @dataclass
-class GpuRun:
+class DeviceRun:
     scaled: np.ndarray
     perm: np.ndarray
     seg_off: np.ndarray
@@ -71,10 +71,10 @@ def run_gpu(raw, N, local_k, final_k, iters, seed, *, trace=True, plain=False, f
         tl = j.trace(0, iters) if trace and iters else None
         tf = j.trace(1, iters) if trace and iters else None
         rc, asg = j.recheck_stats()
-        return GpuRun(j.scaled(), perm, seg_off, lc, ke, cnt, fc, lab, sse, tl, tf, rc, asg)
+        return DeviceRun(j.scaled(), perm, seg_off, lc, ke, cnt, fc, lab, sse, tl, tf, rc, asg)
 
 
-def run_oracle(raw, N, local_k, final_k, iters, seed, gpu: GpuRun | None = None, first_k=False, unequal_m=0,
+def run_oracle(raw, N, local_k, final_k, iters, seed, gpu: DeviceRun | None = None, first_k=False, unequal_m=0,
                pool_weighted=False):
     fl = ff = None
     if gpu is not None and gpu.trace_local is not None:
@@ -89,7 +89,7 @@ def center_err(a, ref):
     return float(np.abs(np.asarray(a, np.float64) - ref).max()) / max(1.0, float(np.abs(ref).max()))
 
 
-def compare(g: GpuRun, o, *, check_labels=True):
+def compare(g: DeviceRun, o, *, check_labels=True):
     """Assert parity; returns a dict of the measured differences."""
     assert np.array_equal(g.scaled, o.scaled), "scaled points differ"
     assert np.array_equal(g.seg_off, o.seg_off), "subcluster offsets differ"
