@@ -92,9 +92,10 @@ typedef enum {
      *    32..1024 (rounded up to a multiple of 32), 0 = the planner's default.  A tuning
      *    choice: results do not depend on it. */
     PSCL_OPT_UNIT_ROWS = 6,
-    /* Rows per thread in the float32 assignment kernel: 0 = its default (up to 4 rows
-     *    kept in registers), 1 = one, 2 = eight for d <= 16.  Jobs and batches; results do
-     *    not depend on it. */
+    /* Rows per thread in the float32 assignment kernel: 0 = automatic (one row when no
+     *    work unit of the run has more rows than the kernel's 256 threads, else up to 4
+     *    rows kept in registers), 1 = one, 2 = eight for d <= 16.  Jobs and batches;
+     *    results do not depend on it. */
     PSCL_OPT_ROWS_PER_THREAD = 7,
     /* Jobs only, 1: the Lloyd on the pooled local centers weighs each local center by its
      *    cluster's size (members in the last local iteration): a center moves to the
