@@ -148,14 +148,20 @@ def run_gpu_batch(parts, ks, iters, seed, *, trace=True, prec=B.PSCL_PREC_FP32, 
         return BatchRun(b.scaled(), c, lab, sse, tr)
 
 
-def compare_batch(g: BatchRun, parts, ks, iters, seed):
-    """Each instance against the oracle: scaling, seeded init (stage 0, segment = index),
-    Lloyd replayed on the CUDA path's labels, final nearest centers and SSE."""
+def compare_batch(g: BatchRun, parts, ks, iters, seed, only=None):
+    """Each instance (or those listed in `only`) against the oracle: scaling, seeded init
+    (stage 0, segment = index), Lloyd replayed on the CUDA path's labels, final nearest
+    centers and SSE."""
     row = cen = 0
     worst = {"center_err": 0.0, "sse_rel": 0.0, "replayed_ties": 0, "label_ties": 0}
+    keep = None if only is None else set(int(i) for i in only)
     for i, (p, k) in enumerate(zip(parts, ks)):
         m = len(p)
         ke = min(k, m)
+        if keep is not None and i not in keep:
+            row += m
+            cen += ke
+            continue
         xs, _, _ = oracle.scale(p)
         assert np.array_equal(g.scaled[row:row + m], xs), f"instance {i}: scaled points differ"
         init = xs[oracle.init_indices(seed, 0, i, m, ke)]

@@ -50,3 +50,17 @@ def test_peel_partition_with_dense_float32_keys():
     operm, ooff, _ = oracle.peel(x, 1 << 20, select=True)
     np.testing.assert_array_equal(off, ooff)
     np.testing.assert_array_equal(perm, operm)
+
+
+def test_uneven_batch_full_size_sampled():
+    # the 2048-instance uneven batch as the bench runs it (graph-recorded, one launch per
+    # iteration over every instance), 3 iterations with label traces; a seeded sample of
+    # instances, the smallest and the largest among them, against the oracle
+    from tests.parity import compare_batch, run_gpu_batch
+    parts, ks = synth.uneven_batch()
+    g = run_gpu_batch(parts, ks, 3, seed=777)
+    sizes = np.array([len(p) for p in parts])
+    rng = np.random.default_rng(5)
+    pick = set(rng.choice(len(parts), 10, replace=False).tolist()) | {int(sizes.argmin()), int(sizes.argmax())}
+    stats = compare_batch(g, parts, ks, 3, seed=777, only=sorted(pick))
+    print("uneven batch, sampled instances:", stats)
