@@ -64,3 +64,60 @@ def test_uneven_batch_full_size_sampled():
     pick = set(rng.choice(len(parts), 10, replace=False).tolist()) | {int(sizes.argmin()), int(sizes.argmax())}
     stats = compare_batch(g, parts, ks, 3, seed=777, only=sorted(pick))
     print("uneven batch, sampled instances:", stats)
+
+
+def _delta64(rows, L):
+    # the peel's distance exactly as defined: float64, attributes summed in ascending order,
+    # one rounding per operation
+    acc = np.zeros(len(rows), np.float64)
+    for j in range(rows.shape[1]):
+        t = rows[:, j].astype(np.float64) - L[j]
+        acc = acc + t * t
+    return acc
+
+
+def test_large_workload_full_size_properties():
+    # 2^24 points in 64 attributes, subclusters of 65536, 256 local centers, final k = 1024,
+    # 25 iterations, run as bench.py runs it; too large for the oracle end to end, so
+    # properties that fix the result: a complete partition into equal subclusters, the
+    # selection property of sampled rounds with exact float64 distances, and the final
+    # labels of a sample equal to the float64 nearest center (near ties excepted)
+    from paper_1412_1947_gb300 import binding as B
+    w = synth.LARGE
+    raw = w.points()
+    with B.Job(raw) as j:
+        j.option(B.PSCL_OPT_GRAPH)
+        j.run(w.N, w.local_k, w.final_k, w.iters, 11)
+        perm, off = j.partition()
+        x = j.scaled()
+        fc, lab, sse = j.result()
+    del raw
+    n, N = w.n, w.N
+    assert np.array_equal(off, np.arange(0, n + 1, N))
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    for r in (1, 100, 254):
+        seg = perm[r * N:(r + 1) * N]
+        later = perm[(r + 1) * N:]
+        L = np.minimum(x[seg].min(0), np.min([x[later[i:i + (1 << 20)]].min(0)
+                                              for i in range(0, len(later), 1 << 20)], axis=0)).astype(np.float64)
+        ds = _delta64(x[seg], L)
+        worst = max(zip(ds.tolist(), seg.tolist()))
+        for i in range(0, len(later), 1 << 20):
+            chunk = later[i:i + (1 << 20)]
+            dl = _delta64(x[chunk], L)
+            k = int(np.argmin(dl))
+            best = min(zip(dl[dl == dl[k]].tolist(), chunk[dl == dl[k]].tolist()))
+            assert worst < best, (r, worst, best)
+    rng = np.random.default_rng(3)
+    pick = rng.choice(n, 50000, replace=False)
+    xs = x[pick].astype(np.float64)
+    c = fc.astype(np.float64)
+    dist = (xs ** 2).sum(1)[:, None] - 2.0 * xs @ c.T + (c ** 2).sum(1)[None, :]
+    two = np.argpartition(dist, 1, axis=1)[:, :2]
+    rows = np.arange(len(pick))[:, None]
+    two = np.take_along_axis(two, np.argsort(dist[rows, two], axis=1, kind="stable"), axis=1)
+    b1 = dist[rows[:, 0], two[:, 0]]
+    b2 = dist[rows[:, 0], two[:, 1]]
+    bad = lab[pick] != two[:, 0]
+    assert np.all(b2[bad] - b1[bad] <= 1e-5 * np.maximum(1.0, b1[bad]) + 1e-9), int(bad.sum())
+    assert np.isfinite(sse) and sse > 0
