@@ -129,3 +129,36 @@ def test_wait_times_out_and_arrivals_overlap():
         for t in later:
             _, _, _, ts = s.fetch(t)
             assert ts[0] < tb[2]               # admitted before the big job was done
+
+
+def test_served_jobs_match_the_oracle():
+    # a seeded sample of the serving recipe (n and final k log-uniform, d in {8, 32, 128},
+    # half of the jobs stored in bfloat16, 25 iterations) served together; each job equals
+    # the same job run alone, and that run (with its label traces) matches the oracle
+    import torch
+    from tests.parity import TIE_TOL, compare, run_gpu
+    import oracle
+    from tests.test_gpu_bf16 import to_bf16
+    jobs = synth.serving_stream(12, seed=321, n_range=(1e4, 6e4), k_range=(8, 128))
+    pts = []
+    for jb in jobs:
+        x = synth.mixture(jb["n"], jb["d"], jb["blobs"], seed=jb["seed"])
+        pts.append(to_bf16(x) if jb["bf16"] else (x, x))
+    dev = [torch.from_numpy(v).cuda().to(torch.bfloat16) if jb["bf16"] else torch.from_numpy(v).cuda()
+           for (b, v), jb in zip(pts, jobs)]
+    with B.Server(slots=4) as s:
+        ts = [s.submit(x, jb["N"], jb["local_k"], jb["final_k"], jb["iters"], jb["seed"], want_labels=True)
+              for x, jb in zip(dev, jobs)]
+        for t in ts:
+            s.wait(t)
+        served = [s.fetch(t) for t in ts]
+    assert sum(jb["bf16"] for jb in jobs) not in (0, len(jobs))
+    for (bits, vals), jb, (c, lab, sse, _) in zip(pts, jobs, served):
+        g = run_gpu(bits if jb["bf16"] else vals, jb["N"], jb["local_k"], jb["final_k"], jb["iters"], jb["seed"])
+        np.testing.assert_array_equal(c, g.final_centers)
+        np.testing.assert_array_equal(lab, g.labels)
+        assert sse == g.sse
+        o = oracle.two_level(vals, jb["N"], jb["local_k"], jb["final_k"], jb["iters"], jb["seed"],
+                             bf16=jb["bf16"], force_local=g.trace_local, force_final=g.trace_final,
+                             tie_tol=TIE_TOL)
+        compare(g, o)
