@@ -124,6 +124,8 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle baseline
 def oracle_sample(w: synth.Workload, n_sample: int):
+    # enough subclusters that the pooled local centers can seed final_k of them
+    n_sample = max(n_sample, -(-w.final_k // w.local_k) * w.N)
     return synth.Workload(w.name + f"_sample{n_sample}", n=n_sample, d=w.d, blobs=w.blobs, N=w.N,
                           local_k=w.local_k, final_k=w.final_k, iters=w.iters, sigma=w.sigma,
                           outlier_frac=w.outlier_frac, seed=w.seed)
@@ -143,8 +145,8 @@ def cpu_baseline(w: synth.Workload, n_sample: int, reps: int = 1):
     secs = min(run_oracle_once(ws, raw, threads) for _ in range(reps))
     ev = workload_evals(ws)
     return {"value": ev / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"the whole two-level job (scale, peel, Lloyd, final Lloyd, SSE) on n={n_sample} "
-                      f"points of the same recipe ({-(-n_sample // w.N)} subclusters of {w.N}), "
+            "sample": f"the whole two-level job (scale, peel, Lloyd, final Lloyd, SSE) on n={ws.n} "
+                      f"points of the same recipe ({-(-ws.n // w.N)} subclusters of {w.N}), "
                       f"{secs:.2f} s, float64 C oracle, OpenMP over subclusters"}
 
 
@@ -165,9 +167,9 @@ def reference_arm(args, w: synth.Workload):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_of(w, {"sample_n": n_sample}),
+            "data": "synthetic", "config": config_of(w, {"sample_n": ws.n}),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"n={n_sample} points of the same recipe per step"},
+                             "sample": f"n={ws.n} points of the same recipe per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -726,6 +726,132 @@ __host__ __device__ constexpr int kPeelBatch()
     return D <= 0 ? 1 : (D >= 64 ? 1 : (64 / D > 4 ? 4 : 64 / D));
 }
 
+// Phase A reads a row with P = min(D/4, 32) lanes, one float4 each (F per lane when D > 128),
+// so that one warp load covers 32/P whole rows instead of one 16-byte piece of 32 rows: the
+// L1 then looks up 8 lines per load at D = 16 instead of 32.  Each lane sums its part of P
+// rows (fused, ascending attributes) and a butterfly over the P lanes leaves every lane the
+// whole sum of one row.  Every squared difference passes through at most D/P + log2 P
+// roundings, fewer than the d of the recursive sum that the phase-C error bound allows.
+template <int D>
+__host__ __device__ constexpr bool kCoopRows()
+{
+    return D >= 8 && D % 4 == 0;
+}
+
+template <int D>
+__host__ __device__ constexpr int kCoopLanes()
+{
+    return D / 4 < 32 ? D / 4 : 32;
+}
+
+// 32-row warp chunks a thread keeps in flight: about 16 float4 loads per lane
+template <int D>
+__host__ __device__ constexpr int kCoopBatch()
+{
+    return 16 / (D / 4) >= 4 ? 4 : (16 / (D / 4) >= 1 ? 16 / (D / 4) : 1);
+}
+
+// Phase A with P lanes per row (see kCoopRows): every live point's float32 key, stored by id
+// and by list position (shared memory when kc) and counted in the first histogram and, when
+// a bin was guessed, in the second.  Out of line, so that the register allocation of the
+// kernel's other phases does not carry its loads in flight.
+template <int D>
+__device__ __noinline__ void coop_keys(const float *__restrict__ x, const float *Ls, uint32_t n_live, uint32_t s0,
+                                       bool round0, bool kc, const uint32_t *sid, const uint32_t *glin, uint32_t *key,
+                                       uint32_t *skey, uint32_t *kpos, uint32_t *sh, uint32_t *gh, uint32_t guess)
+{
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const bool have_guess = guess != kGone;
+    auto LID = [&](uint32_t q) -> uint32_t { return round0 ? s0 + q : kc ? sid[q] : __ldcg(&glin[q]); };
+    auto key_out = [&](bool live, uint32_t pos, uint32_t id, uint32_t k) {
+        if (live) {
+            key[id] = k;
+            if (kc) skey[pos] = k;
+            else kpos[s0 + pos] = k;
+        }
+        const uint32_t b = live ? (k >> 21) : kGone;
+        const uint32_t peers = __match_any_sync(0xffffffffu, b);
+        if (live && lane == __ffs(peers) - 1) atomicAdd(&sh[b], (uint32_t)__popc(peers));
+        if (have_guess) {
+            const uint32_t g2 = live && (k >> 21) == guess ? (k >> 10) & (kHistBins - 1) : kGone;
+            const uint32_t pg = __match_any_sync(0xffffffffu, g2);
+            if (g2 != kGone && lane == __ffs(pg) - 1) atomicAdd(&gh[g2], (uint32_t)__popc(pg));
+        }
+    };
+    constexpr int P = kCoopLanes<D>();                 // lanes per row
+    constexpr int F = D / (4 * P);                     // float4 per lane and row
+    constexpr int RW = 32 / P;                         // rows per warp load
+    constexpr int BC = kCoopBatch<D>();
+    static_assert((P & (P - 1)) == 0 && P >= 2, "lanes per row: a power of two");
+    const int g = lane / P, sl = lane % P;
+    float4 Lq[F];
+#pragma unroll
+    for (int f = 0; f < F; f++) {
+        const int j = 4 * (sl + P * f);
+        Lq[f] = make_float4(Ls[j], Ls[j + 1], Ls[j + 2], Ls[j + 3]);
+    }
+#pragma unroll 1
+    for (uint32_t base = 0; base < n_live; base += BC * kThreads) {
+        // chunk q of this warp: list positions cb + [0, 32); lane i fetches the id of
+        // position cb + i, and row u of its group is position cb + u*RW + g.  Past the
+        // end the id is the slice's first row (read again, an L1 hit).
+        uint32_t myid[BC];
+#pragma unroll
+        for (int q = 0; q < BC; q++) {
+            const uint32_t pos = base + q * kThreads + w * 32 + lane;
+            myid[q] = pos < n_live ? LID(pos) : s0;
+        }
+        float4 v[BC][P][F];
+#pragma unroll
+        for (int q = 0; q < BC; q++)
+#pragma unroll
+            for (int u = 0; u < P; u++) {
+                const uint32_t id = __shfl_sync(0xffffffffu, myid[q], u * RW + g);
+                const float4 *r4 = reinterpret_cast<const float4 *>(x + (size_t)id * D) + sl;
+#pragma unroll
+                for (int f = 0; f < F; f++) v[q][u][f] = __ldg(r4 + P * f);
+            }
+#pragma unroll
+        for (int q = 0; q < BC; q++) {
+            float ps[P];
+#pragma unroll
+            for (int u = 0; u < P; u++) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int f = 0; f < F; f++) {
+                    const float t0 = __fsub_rn(v[q][u][f].x, Lq[f].x);
+                    acc = __fmaf_rn(t0, t0, acc);
+                    const float t1 = __fsub_rn(v[q][u][f].y, Lq[f].y);
+                    acc = __fmaf_rn(t1, t1, acc);
+                    const float t2 = __fsub_rn(v[q][u][f].z, Lq[f].z);
+                    acc = __fmaf_rn(t2, t2, acc);
+                    const float t3 = __fsub_rn(v[q][u][f].w, Lq[f].w);
+                    acc = __fmaf_rn(t3, t3, acc);
+                }
+                ps[u] = acc;
+            }
+            // butterfly: after the round with mask m a lane keeps the half of rows
+            // whose index has its lane bit m; at the end ps[0] is row sl's sum
+            constexpr int LP = P >= 32 ? 5 : P >= 16 ? 4 : P >= 8 ? 3 : P >= 4 ? 2 : 1;
+#pragma unroll
+            for (int lv = 1; lv <= LP; lv++) {
+                const int m = P >> lv;
+                const bool up = (sl & m) != 0;
+#pragma unroll
+                for (int i = 0; i < m; i++) {
+                    const float keep = up ? ps[i + m] : ps[i];
+                    const float send = up ? ps[i] : ps[i + m];
+                    ps[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, m));
+                }
+            }
+            const uint32_t src = (uint32_t)(sl * RW + g);
+            const uint32_t pos = base + q * kThreads + w * 32 + src;
+            const uint32_t id = __shfl_sync(0xffffffffu, myid[q], src);
+            key_out(pos < n_live, pos, id, __float_as_uint(ps[0]));
+        }
+    }
+}
+
 template <int D>
 __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
 {
@@ -864,6 +990,26 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
             }
         }
         __syncthreads();
+        // the key of one point of the round, stored for phases B-D and counted
+        auto key_out = [&](bool live, uint32_t pos, uint32_t id, uint32_t k) {
+            if (live) {
+                a.key[id] = k;
+                if (kc) skey[pos] = k;
+                else a.kpos[s0 + pos] = k;
+            }
+            // the keys of a round crowd into a few bins: one shared atomic per bin and warp
+            const uint32_t b = live ? (k >> 21) : kGone;
+            const uint32_t peers = __match_any_sync(0xffffffffu, b);
+            if (live && lane == __ffs(peers) - 1) atomicAdd(&sh[b], (uint32_t)__popc(peers));
+            if (have_guess) {
+                const uint32_t g2 = live && (k >> 21) == guess ? (k >> 10) & (kHistBins - 1) : kGone;
+                const uint32_t pg = __match_any_sync(0xffffffffu, g2);
+                if (g2 != kGone && lane == __ffs(pg) - 1) atomicAdd(&gh[g2], (uint32_t)__popc(pg));
+            }
+        };
+        if constexpr (kCoopRows<D>()) {
+            coop_keys<D>(a.x, Ls, n_live, s0, r == 0, kc, sid, glin, a.key, skey, a.kpos, sh, gh, guess);
+        } else
         for (uint32_t base = 0; base < n_live; base += B * kThreads) {
             bool lv[B];
             uint32_t ids[B];
@@ -879,23 +1025,7 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
 #pragma unroll
             for (int q = 0; q < B; q++) dl[q] = dist32<D>(a.x + (size_t)ids[q] * d, Ls, d);
 #pragma unroll
-            for (int q = 0; q < B; q++) {
-                const uint32_t k = __float_as_uint(dl[q]);
-                if (lv[q]) {
-                    a.key[ids[q]] = k;
-                    if (kc) skey[base + q * kThreads + t] = k;
-                    else a.kpos[s0 + base + q * kThreads + t] = k;
-                }
-                // the keys of a round crowd into a few bins: one shared atomic per bin and warp
-                const uint32_t b = lv[q] ? (k >> 21) : kGone;
-                const uint32_t peers = __match_any_sync(0xffffffffu, b);
-                if (lv[q] && lane == __ffs(peers) - 1) atomicAdd(&sh[b], (uint32_t)__popc(peers));
-                if (have_guess) {
-                    const uint32_t g2 = lv[q] && (k >> 21) == guess ? (k >> 10) & (kHistBins - 1) : kGone;
-                    const uint32_t pg = __match_any_sync(0xffffffffu, g2);
-                    if (g2 != kGone && lane == __ffs(pg) - 1) atomicAdd(&gh[g2], (uint32_t)__popc(pg));
-                }
-            }
+            for (int q = 0; q < B; q++) key_out(lv[q], base + q * kThreads + t, ids[q], __float_as_uint(dl[q]));
         }
         __syncthreads();
         {
