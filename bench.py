@@ -38,9 +38,9 @@ UNIT = "dist-evals/s"
 L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2
 FP32_ALU_PEAK = 152 * 128 * 2 * 2.07e9   # SMs x FP32 lanes x 2 flop (FMA) x max SM clock
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands, by
-# (kernel, workload): 296.0 MB + 189.4 MB for the peel on the 2^20 x 16 workload
+# (kernel, workload): 296.5 MB + 180.3 MB for the peel on the 2^20 x 16 workload
 # (profiles/k_peel_n1048576_d16.md).  Drop an entry when its kernel changes.
-NCU_TRAFFIC = {("peel", "n1048576_d16_N4096_k64_f64"): 464.50e6}
+NCU_TRAFFIC = {("peel", "n1048576_d16_N4096_k64_f64"): 476.76e6}
 
 
 def replica_max(x: float, dist=None) -> float:
