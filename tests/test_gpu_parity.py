@@ -38,6 +38,46 @@ def test_scaling_bit_exact(n, d, outl):
     np.testing.assert_array_equal(got, exp)
 
 
+def _hard_columns(n, seed):
+    """Attributes that drive the scaling's float-float filter to its edges: sixty decades of
+    magnitude of both signs, a minimum repeated by 30 % of the rows, a range of 1e30 (1/range
+    below 2^-60, subnormal scaled values), a range of 1e-19 (1/range above 2^60), values a few
+    ulps from mid-range power-of-two results, a constant, and a plain uniform attribute."""
+    rng = np.random.default_rng(seed)
+    cols = [
+        rng.uniform(-1, 1, n) * 10.0 ** rng.integers(-30, 30, n),
+        np.where(rng.random(n) < 0.3, -5.0, rng.uniform(-5, 1e-6, n)),
+        np.concatenate([[0.0, 1e30], rng.uniform(0, 1e-8, n - 2)]),
+        rng.uniform(0, 1e-19, n),
+        np.concatenate([[0.0, 3.0], 1.5 + rng.integers(-64, 64, n - 2) * 2.0 ** -23,]),
+        np.full(n, 2.5),
+        rng.uniform(-3, 7, n),
+    ]
+    return np.stack(cols, axis=1).astype(np.float32)
+
+
+@pytest.mark.parametrize("d", [7, 8])
+def test_scaling_hard_attributes_bit_exact(d):
+    """float32 and bfloat16 storage, vectorised (d % 4 == 0) and scalar passes: every scaled
+    value bit for bit equal to the float64 definition."""
+    from tests.test_gpu_bf16 import to_bf16
+    n = 200_003
+    raw = _hard_columns(n, 41 + d)
+    raw = np.concatenate([raw, raw[:, : d - raw.shape[1]]], axis=1) if d > raw.shape[1] else raw[:, :d]
+    raw = np.ascontiguousarray(raw)
+    with B.Job(raw) as j:
+        B.pscl_scale_features(j.h)
+        got = j.scaled()
+    exp, _, _ = oracle.scale(raw)
+    np.testing.assert_array_equal(got.view(np.uint32), exp.view(np.uint32))
+    bits, vals = to_bf16(raw)
+    with B.Job(bits) as j:
+        B.pscl_scale_features(j.h)
+        got = j.scaled()
+    exp, _, _ = oracle.scale(vals, bf16=True)
+    np.testing.assert_array_equal(got.view(np.uint32), exp.view(np.uint32))
+
+
 def test_small_workload_parity():
     w = synth.SMALL
     raw = w.points()
