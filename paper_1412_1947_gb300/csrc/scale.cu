@@ -21,6 +21,48 @@ namespace {
 
 constexpr uint32_t kInfBits = 0x7f800000u;
 
+// The last block of a reduction folds the gridDim.x per-block partials (exact in any
+// order): with d <= blockDim.x, thread t folds attribute t mod d over blocks t / d,
+// + blockDim.x / d, ..., then the threads of each attribute meet in shared memory (sm holds
+// 2 blockDim.x floats); wider points fold one attribute per thread.
+__device__ void fold_partials(const float *part, int d, float *sm, double *mn, double *mx)
+{
+    const int t = threadIdx.x, nb = (int)gridDim.x;
+    if (d > (int)blockDim.x) {
+        for (int a = t; a < d; a += blockDim.x) {
+            float l = __int_as_float(kInfBits), h = -__int_as_float(kInfBits);
+            for (int b = 0; b < nb; b++) {
+                l = fminf(l, __ldcg(&part[(size_t)b * d + a]));
+                h = fmaxf(h, __ldcg(&part[(size_t)(nb + b) * d + a]));
+            }
+            mn[a] = (double)l;
+            mx[a] = (double)h;
+        }
+        return;
+    }
+    const int lanes = (int)blockDim.x / d;
+    float l = __int_as_float(kInfBits), h = -__int_as_float(kInfBits);
+    if (t < lanes * d) {
+        const int a = t % d;
+        for (int b = t / d; b < nb; b += lanes) {
+            l = fminf(l, __ldcg(&part[(size_t)b * d + a]));
+            h = fmaxf(h, __ldcg(&part[(size_t)(nb + b) * d + a]));
+        }
+    }
+    __syncthreads();                              // sm's earlier contents are no longer read
+    sm[t] = l;
+    sm[blockDim.x + t] = h;
+    __syncthreads();
+    if (t < d) {
+        for (int k = 1; k < lanes; k++) {
+            l = fminf(l, sm[k * d + t]);
+            h = fmaxf(h, sm[blockDim.x + k * d + t]);
+        }
+        mn[t] = (double)l;
+        mx[t] = (double)h;
+    }
+}
+
 // Block layout: blockDim.x = d * rows_per_pass, so thread t always sees attribute t % d.
 __global__ void k_minmax(const float *__restrict__ raw, int64_t n, int d, float *part,
                          uint32_t *ticket, double *mn, double *mx, uint32_t *flags)
@@ -61,15 +103,7 @@ __global__ void k_minmax(const float *__restrict__ raw, int64_t n, int d, float 
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int a = t; a < d; a += blockDim.x) {
-        float l = __int_as_float(kInfBits), h = -__int_as_float(kInfBits);
-        for (unsigned b = 0; b < gridDim.x; b++) {
-            l = fminf(l, __ldcg(&part[(size_t)b * d + a]));
-            h = fmaxf(h, __ldcg(&part[(size_t)(gridDim.x + b) * d + a]));
-        }
-        mn[a] = (double)l;
-        mx[a] = (double)h;
-    }
+    fold_partials(part, d, sm, mn, mx);
     if (t == 0) *ticket = 0;
 }
 
@@ -133,15 +167,7 @@ __global__ void k_minmax4(const float4 *__restrict__ raw4, int64_t n, int d, flo
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int a = t; a < d; a += blockDim.x) {
-        float l = __int_as_float(kInfBits), h = -__int_as_float(kInfBits);
-        for (unsigned b = 0; b < gridDim.x; b++) {
-            l = fminf(l, __ldcg(&part[(size_t)b * d + a]));
-            h = fmaxf(h, __ldcg(&part[(size_t)(gridDim.x + b) * d + a]));
-        }
-        mn[a] = (double)l;
-        mx[a] = (double)h;
-    }
+    fold_partials(part, d, sm, mn, mx);
     if (t == 0) *ticket = 0;
 }
 
