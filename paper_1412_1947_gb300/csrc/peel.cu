@@ -8,8 +8,9 @@
 // with equal distances taken in ascending point index.  Computing delta64 for every
 // point would run the peel on the slow float64 pipe, so each round works in float32 and
 // keeps float64 for a thin band around the N-th distance:
-//   A. delta32_i by a float32 FMA chain, kept as its bit pattern (order-preserving for
-//      non-negative floats), and a 2048-bin histogram of key bits 31..21;
+//   A. delta32_i in float32 (FMA chains, a row's pieces summed across the lanes that read
+//      it), kept as its bit pattern (order-preserving for non-negative floats), and a
+//      2048-bin histogram of key bits 31..21;
 //   B. the bin holding the N-th smallest key, and a 2048-bin histogram of bits 20..10 of
 //      the keys inside it: the N-th smallest key lies in a 22-bit prefix [A, B].  The bin
 //      is nearly always the previous round's, whose second histogram phase A already
@@ -164,7 +165,8 @@ __device__ bool grid_sync(PeelCtl *ctl, uint32_t *flags, unsigned &target)
 }
 
 // ------------------------------------------------------------------ distances
-// float32 distance: t = RN(x - L), acc = RN(t*t + acc) (fused), ascending attributes.
+// float32 distance of one row by one thread (the phase-A path for d not a multiple of 4,
+// or below 8): t = RN(x - L), acc = RN(t*t + acc) (fused), ascending attributes.
 template <int D>
 __device__ __forceinline__ float dist32(const float *__restrict__ row, const float *Ls, int d)
 {
