@@ -1,4 +1,6 @@
 """Host-side logic of bench.py that needs no GPU."""
+
+
 def test_oracle_samples_pool_enough_centers():
     """The bench's CPU baseline runs the whole method on a sample of each workload: the
     sample must hold enough subclusters for their local centers to seed final_k."""
