@@ -138,16 +138,32 @@ def run_oracle_once(ws: synth.Workload, raw, threads: int) -> float:
     return time.perf_counter() - t0
 
 
+def cpu_model() -> str:
+    """The host CPU's model name as lscpu reports it, else the machine type."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
 def cpu_baseline(w: synth.Workload, n_sample: int, reps: int = 1):
     threads = os.cpu_count() or 1
     ws = oracle_sample(w, n_sample)
     raw = ws.points()
     secs = min(run_oracle_once(ws, raw, threads) for _ in range(reps))
+    secs1 = run_oracle_once(ws, raw, 1)
     ev = workload_evals(ws)
     return {"value": ev / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"the whole two-level job (scale, peel, Lloyd, final Lloyd, SSE) on n={ws.n} "
                       f"points of the same recipe ({-(-ws.n // w.N)} subclusters of {w.N}), "
-                      f"{secs:.2f} s, float64 C oracle, OpenMP over subclusters"}
+                      f"{secs:.2f} s, float64 C oracle, OpenMP over subclusters",
+            "cpu": cpu_model(),
+            "single_thread": {"value": ev / secs1, "unit": UNIT, "seconds": secs1}}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -169,7 +185,7 @@ def reference_arm(args, w: synth.Workload):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_of(w, {"sample_n": ws.n}),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"n={ws.n} points of the same recipe per step"},
+                             "sample": f"n={ws.n} points of the same recipe per step", "cpu": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
