@@ -104,7 +104,22 @@ typedef enum {
      *    The local level and the final SSE over all n points are unchanged; the pooled
      *    Lloyd then runs in float32 (prec ignored) with global 64-bit sums.  Needs
      *    n < 2^31 (else PSCL_EINVAL).  Default 0 (unweighted). */
-    PSCL_OPT_POOL_WEIGHTED = 8
+    PSCL_OPT_POOL_WEIGHTED = 8,
+    /* Jobs only: rounds of the peel that one pass of landmark distances may serve, 1..16,
+     *    0 = the default (8).  The landmark changes only after every remaining point holding
+     *    some attribute's minimum has been taken, and until then the next round is the next
+     *    N points of the same order, so one pass settles up to this many rounds at once.  A
+     *    tuning choice: results do not depend on it. */
+    PSCL_OPT_PEEL_ROUNDS = 9,
+    /* Polls of every bounded device-side wait (the peel's grid barriers, the tensor-core
+     *    assignment's commit waits) before it gives up and the job reports PSCL_ETIMEOUT;
+     *    0 = the default (2^25 polls per barrier, about a second or two).  Jobs only. */
+    PSCL_OPT_WAIT_LIMIT = 10,
+    /* Test hook, jobs only: 1 = the peel's first grid barrier waits for one arrival more
+     *    than the grid gives, 2 = the tensor-core assignment waits once on a barrier that
+     *    nothing completes; either wait gives up after PSCL_OPT_WAIT_LIMIT polls and the
+     *    job reports PSCL_ETIMEOUT.  For tests of the give-up path; default 0. */
+    PSCL_OPT_TEST_STALL = 11
 } pscl_option;
 
 /* The library's kernels, for pscl_get_kernel_times. */

@@ -96,6 +96,9 @@ struct pscl_job : Owner {
     int state = 0;                    // 0 loaded, 1 scaled, 2 subclustered, 3 clustered
     // options
     int plain = 0, trace = 0, first_k = 0, graph = 0, ktiming = 0, rpt = 0, pool_w = 0;
+    int peel_rounds = 0;              // rounds per distance pass of the peel (0: default)
+    uint32_t wait_limit = 0;          // polls of a bounded device-side wait (0: default)
+    int test_stall = 0;               // test hook: a wait that cannot complete (1 peel, 2 tensor core)
     KTimer kt;                        // launch counts (+ events when timing) of the last run
     // input and scaling
     int dtype = PSCL_F32;
@@ -369,6 +372,18 @@ extern "C" int pscl_job_set_option(pscl_job *j, int opt, int64_t v)
         if (v < 0 || v > 2) return fail(PSCL_EINVAL, "rows per thread must be 0, 1 or 2");
         j->rpt = (int)v;
         break;
+    case PSCL_OPT_PEEL_ROUNDS:
+        if (v < 0 || v > kMaxEpoch) return fail(PSCL_EINVAL, "peel rounds per pass must be 0..%d", kMaxEpoch);
+        j->peel_rounds = (int)v;
+        break;
+    case PSCL_OPT_WAIT_LIMIT:
+        if (v < 0 || v > 0xFFFFFFFFll) return fail(PSCL_EINVAL, "wait limit must be 0..2^32-1");
+        j->wait_limit = (uint32_t)v;
+        break;
+    case PSCL_OPT_TEST_STALL:
+        if (v < 0 || v > 2) return fail(PSCL_EINVAL, "test stall must be 0, 1 or 2");
+        j->test_stall = (int)v;
+        break;
     case PSCL_OPT_POOL_WEIGHTED:
         // the weights sum to n in an int32 count, and w x to at most n 2^32 in 64 bits
         if (v != 0 && j->n >= ((int64_t)1 << 31)) return fail(PSCL_EINVAL, "weighted pooling needs n < 2^31");
@@ -556,15 +571,20 @@ static int alloc_subcluster_buffers(pscl_job *j)
         b.x = j->x;
         b.ord_ld = (n + 3) & ~(int64_t)3;
         b.nbuckets = peel_buckets(n);
-        TRY(A(j, &b.key, n));
+        TRY(A(j, &b.rnd, n));
+        TRY(A(j, &b.pflag, 2 * (size_t)n));
         TRY(A(j, &b.ord, (size_t)d * b.ord_ld));
         TRY(A(j, &b.bcnt, (size_t)d * b.nbuckets));
         TRY(A(j, &b.bcs, (size_t)d * b.nbuckets));
         TRY(A(j, &b.lidx, 2 * (size_t)n));
-        TRY(A(j, &b.kpos, n));
-        TRY(A(j, &b.band_key, n));
-        TRY(A(j, &b.band_pos, n));
+        TRY(A(j, &b.kpos, 2 * (size_t)n));
         TRY(A(j, &b.band_k32, n));
+        TRY(A(j, &b.band_pos, n));
+        TRY(A(j, &b.gkey, n));
+        TRY(A(j, &b.gpos, n));
+        TRY(A(j, &b.akey, n));
+        TRY(A(j, &b.apos, n));
+        TRY(A(j, &b.pcnt, 256 * (size_t)perm_grid(n, j->ctx->sm_count)));
         TRY(A(j, &b.perm, n));
         TRY(A(j, &b.xseg, (size_t)n * d));
         TRY(A(j, &j->lab_l, n));
@@ -680,9 +700,12 @@ static size_t job_footprint(int64_t n, int d, int64_t N, int local_k, int final_
     }
     const int64_t ord_ld = (n + 3) & ~(int64_t)3;
     const size_t nbk = peel_buckets(n);
-    b += r256((size_t)n * 4) + r256((size_t)d * ord_ld * 4) + r256((size_t)d * nbk * 4) + r256((size_t)d * nbk * 16) +
-         r256(2 * (size_t)n * 4) + r256((size_t)n * 4) + r256((size_t)n * 8) + 2 * r256((size_t)n * 4) +
-         r256((size_t)n * 4) +
+    // rnd, pflag, ord, bcnt, bcs, lidx, kpos, band_k32, band_pos, gkey, gpos, akey, apos, pcnt,
+    // perm, then xseg and the local labels
+    b += r256((size_t)n * 4) + r256(2 * (size_t)n) + r256((size_t)d * ord_ld * 4) + r256((size_t)d * nbk * 4) +
+         r256((size_t)d * nbk * 16) + 2 * r256(2 * (size_t)n * 4) + 2 * r256((size_t)n * 4) +
+         r256((size_t)n * 8) + r256((size_t)n * 4) + r256((size_t)n * 8) + r256((size_t)n * 4) +
+         r256(256 * (size_t)perm_grid(n, sm) * 4) + r256((size_t)n * 4) +
          r256((size_t)n * d * 4) + r256((size_t)n * 4);
     const int64_t S = (n + N - 1) / N;
     b += r256((size_t)S * d * 4);
@@ -791,6 +814,9 @@ static int enqueue_scale(pscl_job *j, bool events)
 static int enqueue_subcluster(pscl_job *j, bool events)
 {
     cudaStream_t st = j->ctx->stream;
+    j->pb.rounds_per_pass = j->peel_rounds;
+    j->pb.wait_limit = j->wait_limit;
+    j->pb.stall_first_barrier = j->test_stall == 1;
     if (j->coop) {
         CU(cudaEventRecord(j->coop_ev[0], st));
         CU(cudaStreamWaitEvent(j->coop, j->coop_ev[0], 0));

@@ -5,38 +5,51 @@
 //
 // Membership is defined by the float64 distance
 //     delta64_i = sum_{j ascending} (double(x_ij) - double(L_j))^2   (one rounding per op)
-// with equal distances taken in ascending point index.  Computing delta64 for every
-// point would run the peel on the slow float64 pipe, so each round works in float32 and
-// keeps float64 for a thin band around the N-th distance:
+// with equal distances taken in ascending point index.
+//
+// Epochs.  L changes only when every remaining point that holds some attribute's minimum
+// has been taken, and while L stays the distances stay: the round after r takes the next N
+// points of the same order.  So one pass of distances serves an epoch of up to K rounds
+// (K = rounds_per_pass, at most kMaxEpoch): with K boundaries at ranks N, 2N, ..., KN of
+// the order by (delta64, index), every point left gets the round of the epoch it falls
+// in, and the epoch commits its rounds up to the first one after which some attribute
+// has no holder of its landmark value left.  The later rounds' assignments are dropped
+// and the next epoch starts from the new landmark (a new pass of distances) or, when all
+// K rounds committed, from the same one (no pass at all).  On the headline workload
+// (2^20 points, 16 attributes, 256 rounds) the landmark changes in 50 rounds.
+//
+// Each pass works in float32 and keeps exact arithmetic for thin bands around the
+// boundaries:
 //   A. delta32_i in float32 (FMA chains, a row's pieces summed across the lanes that read
 //      it), kept as its bit pattern (order-preserving for non-negative floats), and a
-//      2048-bin histogram of key bits 31..21;
-//   B. the bin holding the N-th smallest key, and a 2048-bin histogram of bits 20..10 of
-//      the keys inside it: the N-th smallest key lies in a 22-bit prefix [A, B].  The bin
-//      is nearly always the previous round's, whose second histogram phase A already
-//      built, and then this pass is skipped;
-//   C. |delta32 - delta64| <= eps*delta32 + ea with eps = (d+4)*2^-23, ea = 2^-120, so
-//      the N-th smallest delta64 lies in [A(1-eps)-ea, B(1+eps)+ea]: a point whose upper
-//      bound is below that interval is certainly taken, one whose lower bound is above
-//      it certainly not; the few in between form the band;
-//   D. the (N - #certain) smallest band points by (delta64, index) are taken, settled in
-//      float32, then compensated float32, then float64 for what each step leaves open;
-//      taken points go to subcluster r in ascending index and are marked removed.
+//      2048-bin histogram of key bits 31..21.  Points equal to L in an attribute are
+//      counted per attribute and flagged (the holders);
+//   B. per boundary, the first-digit bin holding its rank, and 2048-bin histograms of
+//      bits 20..10 inside those bins: each boundary's float32 key lies in a 22-bit prefix
+//      [A, B];
+//   C. |delta32 - delta64| <= eps*delta32 + ea with eps = (d+4)*2^-23, ea = 2^-120, so the
+//      boundary's delta64 lies in [A(1-eps)-ea, B(1+eps)+ea]: a point whose bound lies
+//      below that interval is certainly before the boundary, one above it certainly
+//      after; the few in between form the boundary's band (boundaries whose bands overlap
+//      form one group);
+//   D. each group is settled by one CTA: compensated float32 distances of its entries
+//      (within eps_ff of delta64) order all but the entries within that error of a cut,
+//      and those (in practice exact ties) are ranked by float64 and index.
 // The partition is therefore exactly the float64 definition's, whatever float32 does.
 //
-// Points never move: CTA c owns the index slice [c n/G, (c+1) n/G) in every round and keeps
-// the ids of its points left in a list, in ascending order; a removed point gets the key
-// 0xFFFFFFFF.  The next landmark needs no pass over the rows.  Before round 0 a counting
-// sort lists, per attribute, the point ids by value bucket (buckets are monotone in the
-// value) with a live count per bucket that every removal decrements.  The minimum over the
-// points left is the smallest value left in the first bucket that still has a point, and
-// the buckets in front of it never get one back, so one bucket pointer per attribute only
-// moves forward.
+// Points never move: CTA c owns the index slice [c n/G, (c+1) n/G) and keeps the ids of its
+// points left in a list, in ascending order, with their keys by list position.  Every
+// point gets its round in rnd[]; after the launch a stable counting sort by round packs
+// the subclusters (ascending index inside each).  The next landmark needs no pass over
+// the rows: before the first epoch a counting sort lists, per attribute, the point ids by
+// value bucket (buckets are monotone in the value); the minimum over the points left is
+// the smallest value left in the first bucket that still has a point left, and one bucket
+// pointer per attribute only moves forward (the buckets it passes hold no point left, and
+// points never come back), so each bucket emptied by removals is read once more in all.
 //
-// All rounds run in one persistent cooperative launch, the phases separated by grid
-// barriers (three per round).  Every barrier wait is bounded; a CTA that gives up sets the
-// abort flag, every other CTA then leaves at its next wait, and the host sees
-// PSCL_ETIMEOUT.
+// All epochs run in one persistent cooperative launch, the phases separated by grid
+// barriers.  Every barrier wait is bounded; a CTA that gives up sets the abort flag, every
+// other CTA then leaves at its next wait, and the host sees PSCL_ETIMEOUT.
 #include <algorithm>
 
 #include "pscl_internal.cuh"
@@ -45,18 +58,32 @@ namespace pscl {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kW = kThreads / 32;
 constexpr uint32_t kInfBits = 0x7f800000u;
-constexpr uint32_t kGone = 0xFFFFFFFFu;       // key of a point removed in an earlier round
-constexpr uint32_t kTaken = 0xFFFFFFFEu;      // key of a wide-band point taken this round
-constexpr int kBandBins = 4096;               // one-ulp bins over a band's float32 keys
-constexpr int kTight = 256;                   // band entries near the cut-off, decided exactly
+constexpr uint32_t kGone = 0xFFFFFFFFu;       // key past the end of a list
+constexpr uint32_t kNone = 0xFFFFFFFFu;       // round of a point not assigned (yet)
 constexpr int kKeyCache = 4096;               // keys and ids of a slice kept in shared memory, if it fits
-constexpr int kPeelScratch = 2 * kHistBins > kBandBins + 7 * kTight ? 2 * kHistBins : kBandBins + 7 * kTight;
-constexpr int kBandStage = 4 * 256;           // band entries staged in shared memory (4 per thread)
-constexpr int kPeelDynWords = kPeelScratch + 2 * kKeyCache + 2 * kBandStage;
+constexpr int kSelBins = 2048;
+constexpr int kSelList = 1024;
+constexpr int kSelBatch = 8;
+constexpr int kStage = 1024;                  // band entries of one group staged in shared memory
+constexpr int kStageOff = kSelBins + 3 * kSelList;
+constexpr int kScrWords = kStageOff + 3 * kStage;
+static_assert(kScrWords >= kHistBins, "phase A's histogram fits the scratch");
+static_assert(kStageOff % 2 == 0, "staged 64-bit keys are 8-byte aligned");
+constexpr int kPeelDynWords = kScrWords + 2 * kKeyCache + kKeyCache / 4;
 constexpr int kQT = 8;                        // tiles of kThreads items per compaction scan
-constexpr int kCB = 16;                       // keys per thread in flight when classifying
-constexpr unsigned kSpinLimit = 1u << 25;      // ~1-2 s of polling per barrier at most
+constexpr int kCB = 8;                        // keys per thread in flight when classifying
+// State byte of each list position: bit 7 set once the point has held some attribute's
+// landmark value (it then holds it while it is left); bits 0..6 its place in the current
+// epoch: a round 0..kMaxEpoch-1 it is certainly in, kFlBand (in a band), kFlNone.
+constexpr uint8_t kFlHold = 0x80;
+constexpr uint8_t kFlBand = 0x7E;
+constexpr uint8_t kFlNone = 0x7F;
+constexpr uint32_t kPosMask = 0x7FFFFFFFu;    // a band entry's id; bit 31 carries its hold flag
+constexpr int kDefaultRounds = 16;            // rounds per distance pass by default
+constexpr int kSlotsSmem = kScrWords / kHistBins;   // second-digit histograms counted in shared memory
+constexpr unsigned kDefaultSpin = 1u << 25;   // ~1-2 s of polling per barrier at most
 
 // ------------------------------------------------------------------ block helpers
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
@@ -73,17 +100,17 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
 // Exclusive scan over the block (blockDim.x == kThreads); `total` gets the block sum.
 __device__ uint32_t block_excl_scan(uint32_t v, uint32_t &total)
 {
-    __shared__ uint32_t wsum[kThreads / 32];
+    __shared__ uint32_t wsum[kW];
     __shared__ uint32_t wtot;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t inc = warp_incl_scan(v);
     if (lane == 31) wsum[w] = inc;
     __syncthreads();
     if (w == 0) {
-        uint32_t s = lane < kThreads / 32 ? wsum[lane] : 0;
+        uint32_t s = lane < kW ? wsum[lane] : 0;
         uint32_t si = warp_incl_scan(s);
-        if (lane < kThreads / 32) wsum[lane] = si - s;
-        if (lane == kThreads / 32 - 1) wtot = si;
+        if (lane < kW) wsum[lane] = si - s;
+        if (lane == kW - 1) wtot = si;
     }
     __syncthreads();
     uint32_t r = wsum[w] + inc - v;
@@ -99,66 +126,87 @@ __device__ uint32_t block_sum(uint32_t v)
     return tot;
 }
 
-// In a kHistBins-bin histogram (global memory), find the bin holding rank `target` (0-based)
-// and the rank inside that bin.  Called by the whole block; every thread gets the result.
-__device__ void find_bin(const uint32_t *hist, uint32_t target, uint32_t &bin, uint32_t &rank)
+__device__ __forceinline__ uint32_t warp_min(uint32_t v)
 {
-    __shared__ uint32_t sb, sr;
-    constexpr int per = kHistBins / kThreads;     // 8 bins per thread
-    const int t = threadIdx.x;
-    uint32_t loc[per];
-    uint32_t s = 0;
 #pragma unroll
-    for (int q = 0; q < per; q++) {
-        loc[q] = __ldcg(&hist[t * per + q]);
-        s += loc[q];
-    }
-    uint32_t tot;
-    uint32_t before = block_excl_scan(s, tot);
-    if (target >= before && target < before + s) {
-        uint32_t c = before;
-#pragma unroll
-        for (int q = 0; q < per; q++) {
-            if (target >= c && target < c + loc[q]) {
-                sb = (uint32_t)(t * per + q);
-                sr = target - c;
-            }
-            c += loc[q];
-        }
-    }
-    __syncthreads();
-    bin = sb;
-    rank = sr;
-    __syncthreads();
+    for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
 }
 
-// Grid-wide barrier with a bounded wait: a monotonic arrival counter (release on
-// arrival, acquire while polling), so no reset is needed within a launch.  Returns false
-// if the launch is being aborted.
-__device__ bool grid_sync(PeelCtl *ctl, uint32_t *flags, unsigned &target)
+__device__ uint32_t block_min(uint32_t v)
+{
+    __shared__ uint32_t wm[kW];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_min(v);
+    if (lane == 0) wm[w] = v;
+    __syncthreads();
+    v = wm[0];
+#pragma unroll
+    for (int q = 1; q < kW; q++) v = min(v, wm[q]);
+    __syncthreads();
+    return v;
+}
+
+// ------------------------------------------------------------------ grid barriers
+// Thread 0's bounded wait for the arrival counter to reach `target`.  Returns false if the
+// launch is being aborted (or this wait gave up, which aborts it).
+__device__ bool bar_wait(PeelCtl *ctl, uint32_t *flags, unsigned target, unsigned limit)
+{
+    unsigned spins = 0, v;
+    for (;;) {
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ctl->bar_count) : "memory");
+        if ((int)(v - target) >= 0) return true;
+        if ((++spins & 63) == 0) {
+            if (*(volatile unsigned *)&ctl->abort) return false;
+            if (spins > limit) {
+                atomicExch(&ctl->abort, 1u);
+                atomicOr(&flags[1], 2u);               // timed out
+                return false;
+            }
+            __nanosleep(32);
+        }
+    }
+}
+
+// Grid-wide barrier with a bounded wait: a monotonic arrival counter (release on arrival,
+// acquire while polling), so no reset is needed within a launch.  `extra` arrivals more
+// than the grid gives are awaited (a test of the give-up path; 0 otherwise).
+__device__ bool grid_sync(PeelCtl *ctl, uint32_t *flags, unsigned &target, unsigned limit, unsigned extra = 0)
 {
     __shared__ int ok;
     target += gridDim.x;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int good = 1;
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctl->bar_count) : "memory");
-        unsigned spins = 0, v;
-        for (;;) {
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&ctl->bar_count) : "memory");
-            if ((int)(v - target) >= 0) break;
-            if ((++spins & 63) == 0) {
-                if (*(volatile unsigned *)&ctl->abort) { good = 0; break; }
-                if (spins > kSpinLimit) {
-                    atomicExch(&ctl->abort, 1u);
-                    atomicOr(&flags[1], 2u);           // timed out
-                    good = 0;
-                    break;
-                }
-                __nanosleep(32);
-            }
+        ok = bar_wait(ctl, flags, target + extra, limit) ? 1 : 0;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// A grid barrier whose last arriving CTA runs work() (all its threads) before any CTA
+// leaves: every CTA adds one arrival, the last one then runs the work and adds one more.
+template <class Work>
+__device__ bool grid_sync_last(PeelCtl *ctl, uint32_t *flags, unsigned &target, unsigned limit, Work work)
+{
+    __shared__ int ok, last;
+    target += gridDim.x + 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned old;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(&ctl->bar_count) : "memory");
+        last = old == target - 2u;
+    }
+    __syncthreads();
+    if (last) {
+        work();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctl->bar_count) : "memory");
+            ok = *(volatile unsigned *)&ctl->abort ? 0 : 1;
         }
-        ok = good;
+    } else if (threadIdx.x == 0) {
+        ok = bar_wait(ctl, flags, target, limit) ? 1 : 0;
     }
     __syncthreads();
     return ok != 0;
@@ -166,11 +214,13 @@ __device__ bool grid_sync(PeelCtl *ctl, uint32_t *flags, unsigned &target)
 
 // ------------------------------------------------------------------ distances
 // float32 distance of one row by one thread (the phase-A path for d not a multiple of 4,
-// or below 8): t = RN(x - L), acc = RN(t*t + acc) (fused), ascending attributes.
+// or below 8): t = RN(x - L), acc = RN(t*t + acc) (fused), ascending attributes.  `hz` is
+// set when some attribute equals the landmark's.
 template <int D>
-__device__ __forceinline__ float dist32(const float *__restrict__ row, const float *Ls, int d)
+__device__ __forceinline__ float dist32(const float *__restrict__ row, const float *Ls, int d, bool &hz)
 {
     float acc = 0.0f;
+    bool z = false;
     if (D > 0 && (D % 4) == 0) {
         const float4 *r4 = reinterpret_cast<const float4 *>(row);
 #pragma unroll
@@ -184,6 +234,7 @@ __device__ __forceinline__ float dist32(const float *__restrict__ row, const flo
             acc = __fmaf_rn(t2, t2, acc);
             float t3 = __fsub_rn(v.w, Ls[4 * q + 3]);
             acc = __fmaf_rn(t3, t3, acc);
+            z |= (t0 == 0.0f) | (t1 == 0.0f) | (t2 == 0.0f) | (t3 == 0.0f);
         }
     } else {
         const int dd = D > 0 ? D : d;
@@ -191,8 +242,10 @@ __device__ __forceinline__ float dist32(const float *__restrict__ row, const flo
         for (int j = 0; j < dd; j++) {
             float t = __fsub_rn(__ldg(&row[j]), Ls[j]);
             acc = __fmaf_rn(t, t, acc);
+            z |= t == 0.0f;
         }
     }
+    hz = z;
     return acc;
 }
 
@@ -201,7 +254,7 @@ __device__ double dist64(const float *__restrict__ row, const float *Ls, int d)
 {
     double s = 0.0;
     for (int j = 0; j < d; j++) {
-        double diff = __dsub_rn((double)row[j], (double)Ls[j]);
+        double diff = __dsub_rn((double)__ldg(&row[j]), (double)Ls[j]);
         s = __dadd_rn(s, __dmul_rn(diff, diff));
     }
     return s;
@@ -239,14 +292,26 @@ __device__ __forceinline__ float eps_ff(int d)
     return (float)((double)d * d + 8.0 * d + 1.0) * 0x1p-47f;
 }
 
-// Thresholds of phase C from the 22-bit key prefix [A, B] of the N-th smallest key.
-// With eps = (d+4) 2^-23 and ea = 2^-120 the N-th smallest delta64 lies in
-// [A(1-eps) - ea, B(1+eps) + ea]; a point is certainly in if delta32 (1+eps) + ea is below
-// that interval, which holds for delta32 < A(1-2eps) - 2ea, and certainly out if
-// delta32 (1-eps) - ea is above it, which holds for delta32 > B(1+3eps) + 3ea.  Both
-// cut-offs are evaluated in float32 rounded towards the safe side.
-__device__ void band_cutoffs_key(uint32_t lo, uint32_t hi, int d, uint32_t &in_key, uint32_t &out_key)
+// The compensated distance h + l rounded once to float64 (its bit pattern orders like
+// the value), the key a group's entries are ranked by.
+__device__ __forceinline__ uint64_t dff_key(const float *__restrict__ row, const float *Ls, int d)
 {
+    float h, l;
+    dist_ff(row, Ls, d, h, l);
+    double v = __dadd_rn((double)h, (double)l);
+    if (!(v > 0.0)) v = 0.0;
+    return (uint64_t)__double_as_longlong(v);
+}
+
+// Cut-offs of phase C from the 22-bit key prefix [A, B] of a boundary's float32 key.
+// With eps = (d+4) 2^-23 and ea = 2^-120 the boundary's delta64 lies in
+// [A(1-eps) - ea, B(1+eps) + ea]; a point is certainly before it if delta32 (1+eps) + ea
+// is below that interval, which holds for delta32 < A(1-2eps) - 2ea, and certainly after
+// it if delta32 (1-eps) - ea is above it, which holds for delta32 > B(1+3eps) + 3ea.  Both
+// cut-offs are evaluated in float32 rounded towards the safe side.
+__device__ void band_cutoffs(uint32_t b0, uint32_t b1, int d, uint32_t &in_key, uint32_t &out_key)
+{
+    const uint32_t lo = (b0 << 21) | (b1 << 10), hi = lo | 0x3FFu;
     const float A = __uint_as_float(lo), B = __uint_as_float(hi);
     const float eps = (float)(d + 4) * 0x1p-23f;
     const float in_thr = __fsub_rd(__fmul_rd(A, __fsub_rd(1.0f, 2.0f * eps)), 0x1p-119f);
@@ -255,21 +320,20 @@ __device__ void band_cutoffs_key(uint32_t lo, uint32_t hi, int d, uint32_t &in_k
     out_key = __float_as_uint(out_thr);
 }
 
-__device__ void band_cutoffs(uint32_t b0, uint32_t b1, int d, uint32_t &in_key, uint32_t &out_key)
-{
-    const uint32_t lo = (b0 << 21) | (b1 << 10);
-    band_cutoffs_key(lo, lo | 0x3FFu, d, in_key, out_key);
-}
-
-// Single-block radix select (8-bit digits over the 96-bit (key, pos) composite) of the
-// `need`-th smallest band entry in global memory; for bands too large for shared memory.
-__device__ void select_band_global(const uint64_t *bkey, const uint32_t *bpos, uint32_t nb, uint32_t need,
-                                   uint64_t &K, uint32_t &Pp)
+// ------------------------------------------------------------------ exact selection
+// The `need`-th smallest (1-based) of nb entries by (key, position), key_at / pos_at giving
+// entry i.  Single-block radix select with 8-bit digits over the 96-bit composite.
+template <class KeyAt, class PosAt>
+__device__ void select_radix(KeyAt key_at, PosAt pos_at, uint32_t nb, uint32_t need, uint64_t &K, uint32_t &Pp)
 {
     __shared__ uint32_t h[256];
     __shared__ uint64_t pk;
     __shared__ uint32_t pp, rank;
-    if (threadIdx.x == 0) { pk = 0; pp = 0; rank = need - 1; }
+    if (threadIdx.x == 0) {
+        pk = 0;
+        pp = 0;
+        rank = need - 1;
+    }
     __syncthreads();
     for (int pass = 0; pass < 12; pass++) {
         h[threadIdx.x] = 0;
@@ -277,15 +341,15 @@ __device__ void select_band_global(const uint64_t *bkey, const uint32_t *bpos, u
         const uint64_t cpk = pk;
         const uint32_t cpp = pp;
         for (uint32_t i = threadIdx.x; i < nb; i += kThreads) {
-            uint64_t k = __ldcg(&bkey[i]);
-            uint32_t p = __ldcg(&bpos[i]);
+            const uint64_t k = key_at(i);
+            const uint32_t p = pos_at(i);
             bool match;
             uint32_t digit;
             if (pass < 8) {
                 match = pass == 0 || (k >> (64 - 8 * pass)) == (cpk >> (64 - 8 * pass));
                 digit = (uint32_t)(k >> (56 - 8 * pass)) & 0xFFu;
             } else {
-                int q = pass - 8;
+                const int q = pass - 8;
                 match = k == cpk && (q == 0 || (p >> (32 - 8 * q)) == (cpp >> (32 - 8 * q)));
                 digit = (p >> (24 - 8 * q)) & 0xFFu;
             }
@@ -309,33 +373,29 @@ __device__ void select_band_global(const uint64_t *bkey, const uint32_t *bpos, u
     __syncthreads();
 }
 
-// The same selection in three passes when the band's keys spread: the smallest and
-// largest key give the bits all keys share; an 11-bit histogram of the next bits finds
-// the digit of the need-th entry; that digit's entries (at most kSelList) are gathered in
-// shared memory and ranked there by (key, position).  Returns false, with nothing
-// decided, when all keys are equal or the digit holds more entries: the caller then runs
-// select_band_global.  scratch: 2048 + 3 kSelList words of shared memory.
-constexpr int kSelBins = 2048;
-constexpr int kSelList = 1024;
-constexpr int kSelBatch = 8;
-__device__ bool select_band_fast(const uint64_t *bkey, const uint32_t *bpos, uint32_t nb, uint32_t need,
-                                 uint32_t *scratch, uint64_t &K, uint32_t &Pp)
+// The same selection in three passes when the keys spread: the smallest and largest key
+// give the bits all keys share; an 11-bit histogram of the next bits finds the digit of
+// the need-th entry; that digit's entries (at most kSelList) are gathered in shared memory
+// and ranked there by (key, position).  Returns false, with nothing decided, when all keys
+// are equal or the digit holds more entries: the caller then runs select_radix.
+// scratch: kSelBins + 3 kSelList words of shared memory.
+template <class KeyAt, class PosAt>
+__device__ bool select_fast(KeyAt key_at, PosAt pos_at, uint32_t nb, uint32_t need, uint32_t *scratch, uint64_t &K,
+                            uint32_t &Pp)
 {
-    __shared__ unsigned long long s_mn[kThreads / 32], s_mx[kThreads / 32];
+    __shared__ unsigned long long s_mn[kW], s_mx[kW];
     __shared__ uint32_t s_bin, s_rank, s_cnt, s_hit;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     uint32_t *h = scratch;
     uint64_t *lk = reinterpret_cast<uint64_t *>(scratch + kSelBins);      // 8-byte aligned: kSelBins is even
     uint32_t *lp = scratch + kSelBins + 2 * kSelList;
-    // pass 1: smallest and largest key
-    // every pass keeps kSelBatch loads per thread in flight: one CTA reads the whole band
     unsigned long long mn = ~0ull, mx = 0ull;
     for (uint32_t i0 = t; i0 < nb; i0 += kSelBatch * kThreads) {
         unsigned long long kk[kSelBatch];
 #pragma unroll
         for (int u = 0; u < kSelBatch; u++) {
             const uint32_t i = i0 + u * kThreads;
-            kk[u] = i < nb ? __ldcg(&bkey[i]) : 0ull;
+            kk[u] = i < nb ? key_at(i) : 0ull;
         }
 #pragma unroll
         for (int u = 0; u < kSelBatch; u++) {
@@ -359,20 +419,20 @@ __device__ bool select_band_fast(const uint64_t *bkey, const uint32_t *bpos, uin
     mn = s_mn[0];
     mx = s_mx[0];
 #pragma unroll
-    for (int q = 1; q < kThreads / 32; q++) {
+    for (int q = 1; q < kW; q++) {
         mn = min(mn, (unsigned long long)s_mn[q]);
         mx = max(mx, (unsigned long long)s_mx[q]);
     }
+    __syncthreads();
     if (mn == mx) return false;                          // uniform across the block
     const int hb = 63 - __clzll((long long)(mn ^ mx));   // highest bit where keys differ
     const int sh = hb >= 10 ? hb - 10 : 0;               // digit = bits [sh, hb]
-    // pass 2: histogram of the digit (the bits above hb are common to all keys)
     for (uint32_t i0 = t; i0 < nb; i0 += kSelBatch * kThreads) {
         unsigned long long kk[kSelBatch];
 #pragma unroll
         for (int u = 0; u < kSelBatch; u++) {
             const uint32_t i = i0 + u * kThreads;
-            kk[u] = i < nb ? __ldcg(&bkey[i]) : 0ull;
+            kk[u] = i < nb ? key_at(i) : 0ull;
         }
 #pragma unroll
         for (int u = 0; u < kSelBatch; u++)
@@ -404,13 +464,12 @@ __device__ bool select_band_fast(const uint64_t *bkey, const uint32_t *bpos, uin
     __syncthreads();
     const uint32_t bin = s_bin, rank = s_rank, cnt = s_cnt;
     if (cnt > (uint32_t)kSelList) return false;          // uniform across the block
-    // pass 3: the digit's entries, then their rank by (key, position)
     for (uint32_t i0 = t; i0 < nb; i0 += kSelBatch * kThreads) {
         unsigned long long kk[kSelBatch];
 #pragma unroll
         for (int u = 0; u < kSelBatch; u++) {
             const uint32_t i = i0 + u * kThreads;
-            kk[u] = i < nb ? __ldcg(&bkey[i]) : 0ull;
+            kk[u] = i < nb ? key_at(i) : 0ull;
         }
 #pragma unroll
         for (int u = 0; u < kSelBatch; u++) {
@@ -418,7 +477,7 @@ __device__ bool select_band_fast(const uint64_t *bkey, const uint32_t *bpos, uin
             if (i < nb && ((uint32_t)(kk[u] >> sh) & (kSelBins - 1)) == bin) {
                 const uint32_t slot = atomicAdd(&s_hit, 1u);
                 lk[slot] = kk[u];
-                lp[slot] = __ldcg(&bpos[i]);
+                lp[slot] = pos_at(i);
             }
         }
     }
@@ -440,194 +499,14 @@ __device__ bool select_band_fast(const uint64_t *bkey, const uint32_t *bpos, uin
     return true;
 }
 
-// Exclusive scans of two values over the block in one pass (blockDim.x == kThreads).
-__device__ void block_excl_scan2(uint32_t v0, uint32_t v1, uint32_t &e0, uint32_t &e1, uint32_t &t0,
-                                 uint32_t &t1)
+template <class KeyAt, class PosAt>
+__device__ void select_kth(KeyAt key_at, PosAt pos_at, uint32_t nb, uint32_t need, uint32_t *scratch, uint64_t &K,
+                           uint32_t &Pp)
 {
-    constexpr int W = kThreads / 32;
-    __shared__ uint32_t ws0[W], ws1[W], wt[2];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const uint32_t i0 = warp_incl_scan(v0), i1 = warp_incl_scan(v1);
-    if (lane == 31) {
-        ws0[w] = i0;
-        ws1[w] = i1;
-    }
-    __syncthreads();
-    if (w == 0) {
-        const uint32_t a = lane < W ? ws0[lane] : 0u, b = lane < W ? ws1[lane] : 0u;
-        const uint32_t ia = warp_incl_scan(a), ib = warp_incl_scan(b);
-        if (lane < W) {
-            ws0[lane] = ia - a;
-            ws1[lane] = ib - b;
-        }
-        if (lane == W - 1) {
-            wt[0] = ia;
-            wt[1] = ib;
-        }
-    }
-    __syncthreads();
-    e0 = ws0[w] + i0 - v0;
-    e1 = ws1[w] + i1 - v1;
-    t0 = wt[0];
-    t1 = wt[1];
-    __syncthreads();
+    if (!select_fast(key_at, pos_at, nb, need, scratch, K, Pp)) select_radix(key_at, pos_at, nb, need, K, Pp);
 }
 
-__device__ __forceinline__ uint32_t warp_min(uint32_t v)
-{
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// The bin of rank `target` (0-based) of histogram h0 and the rank inside it; when hg (the
-// second-digit histogram inside bin `guess`) is given and `guess` is that bin, also the
-// bin of that rank in hg (hit).  Both histograms are read and scanned in one pass.
-__device__ void find_bins(const uint32_t *h0, const uint32_t *hg, uint32_t guess, uint32_t target,
-                          uint32_t &b0, uint32_t &r0, uint32_t &b1, uint32_t &r1, bool &hit)
-{
-    __shared__ uint32_t sb0, sr0, sb1, sr1;
-    constexpr int per = kHistBins / kThreads;       // 8 bins per thread
-    static_assert(per == 8, "two uint4 loads per thread");
-    const int t = threadIdx.x;
-    uint32_t l0[per], l1[per];
-    {
-        const uint4 *p = reinterpret_cast<const uint4 *>(h0 + t * per);
-        const uint4 u = __ldcg(p), v = __ldcg(p + 1);
-        l0[0] = u.x; l0[1] = u.y; l0[2] = u.z; l0[3] = u.w;
-        l0[4] = v.x; l0[5] = v.y; l0[6] = v.z; l0[7] = v.w;
-    }
-    if (hg) {
-        const uint4 *p = reinterpret_cast<const uint4 *>(hg + t * per);
-        const uint4 u = __ldcg(p), v = __ldcg(p + 1);
-        l1[0] = u.x; l1[1] = u.y; l1[2] = u.z; l1[3] = u.w;
-        l1[4] = v.x; l1[5] = v.y; l1[6] = v.z; l1[7] = v.w;
-    } else {
-#pragma unroll
-        for (int q = 0; q < per; q++) l1[q] = 0;
-    }
-    uint32_t s0 = 0, s1 = 0;
-#pragma unroll
-    for (int q = 0; q < per; q++) {
-        s0 += l0[q];
-        s1 += l1[q];
-    }
-    uint32_t e0, e1, tot0, tot1;
-    block_excl_scan2(s0, s1, e0, e1, tot0, tot1);
-    if (target >= e0 && target < e0 + s0) {
-        uint32_t cc = e0;
-#pragma unroll
-        for (int q = 0; q < per; q++) {
-            if (target >= cc && target < cc + l0[q]) {
-                sb0 = (uint32_t)(t * per + q);
-                sr0 = target - cc;
-            }
-            cc += l0[q];
-        }
-    }
-    __syncthreads();
-    b0 = sb0;
-    r0 = sr0;
-    hit = hg != nullptr && b0 == guess;
-    if (hit) {
-        if (r0 >= e1 && r0 < e1 + s1) {
-            uint32_t cc = e1;
-#pragma unroll
-            for (int q = 0; q < per; q++) {
-                if (r0 >= cc && r0 < cc + l1[q]) {
-                    sb1 = (uint32_t)(t * per + q);
-                    sr1 = r0 - cc;
-                }
-                cc += l1[q];
-            }
-        }
-        __syncthreads();
-        b1 = sb1;
-        r1 = sr1;
-    }
-    __syncthreads();
-}
-
-// Splits the n_in ids of a CTA's list (id_of(q) for position q), keeping their order, into
-// those with pred(position, id), written to sel[0..) with on_sel(id) called for each, and the
-// rest, written to keep[0..) when `keep` is given.  `keep` may be the list being read (in
-// shared memory): a tile's ids are all read before any of its kept ids is written, and those
-// land at or below the tile's own positions.  Returns how many were selected (to every
-// thread).
-template <class IdOf, class Pred, class OnSel>
-__device__ uint32_t compact_list(IdOf id_of, uint32_t n_in, uint32_t *sel, uint32_t *keep, Pred pred, OnSel on_sel)
-{
-    constexpr int W = kThreads / 32;
-    constexpr int PER = kQT * W / 32;
-    static_assert(PER * 32 == kQT * W, "one warp scans the tile counts");
-    __shared__ uint32_t woff_s[kQT * W + 1], woff_k[kQT * W + 1];
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const uint32_t lt = (1u << lane) - 1u;
-    uint32_t done_s = 0, done_k = 0;
-    // item (q, t) of a chunk is preceded by the earlier tiles, the earlier warps of its tile
-    // and the lower lanes of its warp
-    for (uint32_t cb = 0; cb < n_in; cb += kQT * kThreads) {
-        uint32_t ids[kQT], vl = 0, tk = 0;
-#pragma unroll
-        for (int q = 0; q < kQT; q++) {
-            const uint32_t qi = cb + q * kThreads + t;
-            const bool v = qi < n_in;
-            ids[q] = v ? id_of(qi) : 0u;
-            vl |= (uint32_t)v << q;
-        }
-#pragma unroll
-        for (int q = 0; q < kQT; q++) tk |= (uint32_t)(((vl >> q) & 1u) && pred(cb + q * kThreads + t, ids[q])) << q;
-        uint32_t bt[kQT], bv[kQT];
-#pragma unroll
-        for (int q = 0; q < kQT; q++) {
-            bt[q] = __ballot_sync(0xffffffffu, (tk >> q) & 1u);
-            bv[q] = __ballot_sync(0xffffffffu, (vl >> q) & 1u);
-            if (lane == 0) {
-                woff_s[q * W + w] = __popc(bt[q]);
-                woff_k[q * W + w] = __popc(bv[q] & ~bt[q]);
-            }
-        }
-        __syncthreads();
-        if (w == 0) {
-            uint32_t vs[PER], vk[PER], ss = 0, sk = 0;
-#pragma unroll
-            for (int e = 0; e < PER; e++) {
-                vs[e] = woff_s[lane * PER + e];
-                vk[e] = woff_k[lane * PER + e];
-                ss += vs[e];
-                sk += vk[e];
-            }
-            const uint32_t is = warp_incl_scan(ss), ik = warp_incl_scan(sk);
-            uint32_t es = is - ss, ek = ik - sk;
-#pragma unroll
-            for (int e = 0; e < PER; e++) {
-                woff_s[lane * PER + e] = es;
-                woff_k[lane * PER + e] = ek;
-                es += vs[e];
-                ek += vk[e];
-            }
-            if (lane == 31) {
-                woff_s[kQT * W] = is;
-                woff_k[kQT * W] = ik;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < kQT; q++) {
-            if ((tk >> q) & 1u) {
-                sel[done_s + woff_s[q * W + w] + __popc(bt[q] & lt)] = ids[q];
-                on_sel(ids[q]);
-            } else if (((vl >> q) & 1u) && keep) {
-                keep[done_k + woff_k[q * W + w] + __popc(bv[q] & ~bt[q] & lt)] = ids[q];
-            }
-        }
-        done_s += woff_s[kQT * W];
-        done_k += woff_k[kQT * W];
-        __syncthreads();
-    }
-    return done_s;
-}
-
+// ------------------------------------------------------------------ buckets
 // Bucket of a scaled value (in [0, 1]) among nb equal buckets: monotone in the value.
 __device__ __forceinline__ uint32_t bucket_of(float v, uint32_t nb)
 {
@@ -636,89 +515,32 @@ __device__ __forceinline__ uint32_t bucket_of(float v, uint32_t nb)
     return b < nb ? b : nb - 1u;
 }
 
-// The round's selection: a point with key k is taken if k < lo, if it is a wide-band point
-// marked kTaken, or if lo <= k <= tout and the tight set lists it as taken.
-// Phase C over a slice's keys (key_at(position)): counts those below in_key (certainly
-// taken) and hands those in [in_key, out_key] to to_band(position, key); CB keys per
-// thread are read at once.
-template <int CB, class KeyAt, class ToBand>
-__device__ __forceinline__ uint32_t classify_keys(uint32_t n_live, uint32_t in_key, uint32_t out_key, KeyAt key_at,
-                                                  ToBand to_band)
-{
-    uint32_t n_in = 0;
-    for (uint32_t q0 = threadIdx.x; q0 < n_live; q0 += CB * kThreads) {
-        uint32_t kk[CB];
-#pragma unroll
-        for (int q = 0; q < CB; q++) {
-            const uint32_t qi = q0 + q * kThreads;
-            kk[q] = qi < n_live ? key_at(qi) : kGone;       // past the end: above out_key
-        }
-#pragma unroll
-        for (int q = 0; q < CB; q++) {
-            if (kk[q] < in_key) n_in++;
-            else if (kk[q] <= out_key) to_band(q0 + q * kThreads, kk[q]);
-        }
-    }
-    return n_in;
-}
-
-struct Rule {
-    uint32_t lo, tout, nt;
-    const uint32_t *tpos, *tcls;
-};
-
-__device__ __forceinline__ bool taken(const Rule &R, uint32_t k, uint32_t id)
-{
-    if (k < R.lo || k == kTaken) return true;
-    if (k > R.tout) return false;
-    for (uint32_t o = 0; o < R.nt; o++)
-        if (R.tpos[o] == id) return R.tcls[o] != 0;
-    return false;
-}
-
-// A removed point leaves the live count of its bucket in every attribute.
-template <int D>
-__device__ __forceinline__ void drop_buckets(const float *__restrict__ x, int d, uint32_t id, uint4 *bcs, uint32_t nbk)
-{
-    const float *row = x + (size_t)id * d;
-    if (D > 0 && D % 4 == 0) {
-        float v[D > 0 ? D : 1];
-        const float4 *r4 = reinterpret_cast<const float4 *>(row);
-#pragma unroll
-        for (int q = 0; q < D / 4; q++) {
-            const float4 u = __ldg(&r4[q]);
-            v[4 * q + 0] = u.x;
-            v[4 * q + 1] = u.y;
-            v[4 * q + 2] = u.z;
-            v[4 * q + 3] = u.w;
-        }
-#pragma unroll
-        for (int j = 0; j < D; j++) atomicSub(&bcs[(size_t)j * nbk + bucket_of(v[j], nbk)].x, 1u);
-    } else {
-        for (int j = 0; j < d; j++) atomicSub(&bcs[(size_t)j * nbk + bucket_of(__ldg(&row[j]), nbk)].x, 1u);
-    }
-}
-
 // ------------------------------------------------------------------ the kernel
 struct PeelArgs {
     const float *x;
     int d;
     int64_t n, N, S;
-    uint32_t *key;               // n: this round's float32 key per point; kGone once removed
+    uint32_t *rnd;
+    uint8_t *pflag;              // 2 x n: the state byte of each list position
     uint32_t *ord;               // d x ord_ld: point ids by value bucket, per attribute
     uint32_t *bcnt;              // d x nbk: bucket counts, then cursors (zeroed before)
     uint4 *bcs;                  // d x nbk: (points left, first entry, end entry, 0)
-    uint32_t *lidx;              // 2 x n: per CTA slice, the ids of its points left
-    uint32_t *kpos;              // n: per CTA slice, this round's keys by list position (!kc)
+    uint32_t *lidx;              // 2 x n: per CTA slice, the ids of its points left (not kc; two lists)
+    uint32_t *kpos;              // 2 x n: their keys by list position
     int64_t ord_ld;
     uint32_t nbk;
-    uint64_t *band_key;          // float64 distance bits (wide bands only)
-    uint32_t *band_k32;          // float32 keys of the band
-    uint32_t *band_pos;          // point ids of the band
-    uint32_t *perm;
+    uint32_t *band_k32;
+    uint32_t *band_pos;
+    uint64_t *gkey;
+    uint32_t *gpos;
+    uint64_t *akey;
+    uint32_t *apos;
     float *landmarks;            // S x d or NULL
     PeelCtl *ctl;
     uint32_t *flags;             // job flags: [1] |= 1 bound violated, 2 barrier timed out
+    uint32_t kmax;               // rounds per distance pass
+    uint32_t spin;               // polls of a barrier wait before it gives up
+    uint32_t stall;              // test hook: the first barrier awaits one arrival too many
 };
 
 // rows a thread keeps in flight at once (64 floats of rows at most)
@@ -729,11 +551,11 @@ __host__ __device__ constexpr int kPeelBatch()
 }
 
 // Phase A reads a row with P = min(D/4, 32) lanes, one float4 each (F per lane when D > 128),
-// so that one warp load covers 32/P whole rows instead of one 16-byte piece of 32 rows: the
-// L1 then looks up 8 lines per load at D = 16 instead of 32.  Each lane sums its part of P
-// rows (fused, ascending attributes) and a butterfly over the P lanes leaves every lane the
-// whole sum of one row.  Every squared difference passes through at most D/P + log2 P
-// roundings, fewer than the d of the recursive sum that the phase-C error bound allows.
+// so that one warp load covers 32/P whole rows instead of one 16-byte piece of 32 rows.
+// Each lane sums its part of P rows (fused, ascending attributes) and a butterfly over the
+// P lanes leaves every lane the whole sum of one row.  Every squared difference passes
+// through at most D/P + log2 P roundings, fewer than the d of the recursive sum that the
+// phase-C error bound allows.
 template <int D>
 __host__ __device__ constexpr bool kCoopRows()
 {
@@ -753,137 +575,757 @@ __host__ __device__ constexpr int kCoopBatch()
     return 16 / (D / 4) >= 4 ? 4 : (16 / (D / 4) >= 1 ? 16 / (D / 4) : 1);
 }
 
-// Phase A with P lanes per row (see kCoopRows): every live point's float32 key, stored by id
-// and by list position (shared memory when kc) and counted in the first histogram and, when
-// a bin was guessed, in the second.  Out of line, so that the register allocation of the
-// kernel's other phases does not carry its loads in flight.
+// A live point equal to the landmark in some attribute: counted per such attribute and
+// flagged for the epochs' holder bookkeeping.
+__device__ __forceinline__ void note_holder(const float *__restrict__ row, const float *Ls, int d, uint8_t *fl,
+                                            uint32_t *chold)
+{
+    for (int j = 0; j < d; j++)
+        if (__ldg(&row[j]) == Ls[j]) atomicAdd(&chold[j], 1u);
+    *fl |= kFlHold;
+}
+
+// Phase A: every live point's float32 key, stored by list position (shared memory when
+// kc, else kpos: the slice's keys) and counted in the first-digit histogram sh; holders counted per attribute and
+// flagged in their position's state byte (pfl: the slice's, by list position).  Out of line, so that
+// the register allocation of the kernel's other phases does not carry its loads in flight.
 template <int D>
-__device__ __noinline__ void coop_keys(const float *__restrict__ x, const float *Ls, uint32_t n_live, uint32_t s0,
-                                       bool round0, bool kc, const uint32_t *sid, const uint32_t *glin, uint32_t *key,
-                                       uint32_t *skey, uint32_t *kpos, uint32_t *sh, uint32_t *gh, uint32_t guess)
+__device__ __noinline__ void phase_keys(const float *__restrict__ x, const float *Ls, int d, uint32_t n_live,
+                                        uint32_t s0, bool first, bool kc, const uint32_t *sid, const uint32_t *glin,
+                                        uint32_t *skey, uint32_t *kpos, uint32_t *sh, uint8_t *pfl, uint32_t *chold)
 {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const bool have_guess = guess != kGone;
-    auto LID = [&](uint32_t q) -> uint32_t { return round0 ? s0 + q : kc ? sid[q] : __ldcg(&glin[q]); };
-    auto key_out = [&](bool live, uint32_t pos, uint32_t id, uint32_t k) {
+    auto LID = [&](uint32_t q) -> uint32_t { return first ? s0 + q : kc ? sid[q] : __ldcg(&glin[q]); };
+    auto key_out = [&](bool live, uint32_t pos, uint32_t k) {
         if (live) {
-            key[id] = k;
             if (kc) skey[pos] = k;
-            else kpos[s0 + pos] = k;
+            else kpos[pos] = k;
         }
+        // the keys of a pass crowd into a few bins: one shared atomic per bin and warp
         const uint32_t b = live ? (k >> 21) : kGone;
         const uint32_t peers = __match_any_sync(0xffffffffu, b);
         if (live && lane == __ffs(peers) - 1) atomicAdd(&sh[b], (uint32_t)__popc(peers));
-        if (have_guess) {
-            const uint32_t g2 = live && (k >> 21) == guess ? (k >> 10) & (kHistBins - 1) : kGone;
-            const uint32_t pg = __match_any_sync(0xffffffffu, g2);
-            if (g2 != kGone && lane == __ffs(pg) - 1) atomicAdd(&gh[g2], (uint32_t)__popc(pg));
-        }
     };
-    constexpr int P = kCoopLanes<D>();                 // lanes per row
-    constexpr int F = D / (4 * P);                     // float4 per lane and row
-    constexpr int RW = 32 / P;                         // rows per warp load
-    constexpr int BC = kCoopBatch<D>();
-    static_assert((P & (P - 1)) == 0 && P >= 2, "lanes per row: a power of two");
-    const int g = lane / P, sl = lane % P;
-    float4 Lq[F];
+    if constexpr (kCoopRows<D>()) {
+        constexpr int P = kCoopLanes<D>();                 // lanes per row
+        constexpr int F = D / (4 * P);                     // float4 per lane and row
+        constexpr int RW = 32 / P;                         // rows per warp load
+        constexpr int BC = kCoopBatch<D>();
+        static_assert((P & (P - 1)) == 0 && P >= 2, "lanes per row: a power of two");
+        const int g = lane / P, sl = lane % P;
+        float4 Lq[F];
 #pragma unroll
-    for (int f = 0; f < F; f++) {
-        const int j = 4 * (sl + P * f);
-        Lq[f] = make_float4(Ls[j], Ls[j + 1], Ls[j + 2], Ls[j + 3]);
-    }
+        for (int f = 0; f < F; f++) {
+            const int j = 4 * (sl + P * f);
+            Lq[f] = make_float4(Ls[j], Ls[j + 1], Ls[j + 2], Ls[j + 3]);
+        }
 #pragma unroll 1
-    for (uint32_t base = 0; base < n_live; base += BC * kThreads) {
-        // chunk q of this warp: list positions cb + [0, 32); lane i fetches the id of
-        // position cb + i, and row u of its group is position cb + u*RW + g.  Past the
-        // end the id is the slice's first row (read again, an L1 hit).
-        uint32_t myid[BC];
+        for (uint32_t base = 0; base < n_live; base += BC * kThreads) {
+            // chunk q of this warp: list positions cb + [0, 32); lane i fetches the id of
+            // position cb + i, and row u of its group is position cb + u*RW + g.  Past the
+            // end the id is the slice's first row (read again, an L1 hit).
+            uint32_t myid[BC];
 #pragma unroll
-        for (int q = 0; q < BC; q++) {
-            const uint32_t pos = base + q * kThreads + w * 32 + lane;
-            myid[q] = pos < n_live ? LID(pos) : s0;
+            for (int q = 0; q < BC; q++) {
+                const uint32_t pos = base + q * kThreads + w * 32 + lane;
+                myid[q] = pos < n_live ? LID(pos) : s0;
+            }
+            float4 v[BC][P][F];
+#pragma unroll
+            for (int q = 0; q < BC; q++)
+#pragma unroll
+                for (int u = 0; u < P; u++) {
+                    const uint32_t id = __shfl_sync(0xffffffffu, myid[q], u * RW + g);
+                    const float4 *r4 = reinterpret_cast<const float4 *>(x + (size_t)id * D) + sl;
+#pragma unroll
+                    for (int f = 0; f < F; f++) v[q][u][f] = __ldg(r4 + P * f);
+                }
+#pragma unroll
+            for (int q = 0; q < BC; q++) {
+                float ps[P];
+                uint32_t hz = 0;
+#pragma unroll
+                for (int u = 0; u < P; u++) {
+                    float acc = 0.0f;
+                    bool z = false;
+#pragma unroll
+                    for (int f = 0; f < F; f++) {
+                        const float t0 = __fsub_rn(v[q][u][f].x, Lq[f].x);
+                        acc = __fmaf_rn(t0, t0, acc);
+                        const float t1 = __fsub_rn(v[q][u][f].y, Lq[f].y);
+                        acc = __fmaf_rn(t1, t1, acc);
+                        const float t2 = __fsub_rn(v[q][u][f].z, Lq[f].z);
+                        acc = __fmaf_rn(t2, t2, acc);
+                        const float t3 = __fsub_rn(v[q][u][f].w, Lq[f].w);
+                        acc = __fmaf_rn(t3, t3, acc);
+                        z |= (t0 == 0.0f) | (t1 == 0.0f) | (t2 == 0.0f) | (t3 == 0.0f);
+                    }
+                    ps[u] = acc;
+                    hz |= (uint32_t)z << u;
+                }
+                // butterfly: after the round with mask m a lane keeps the half of rows
+                // whose index has its lane bit m; at the end ps[0] is row sl's sum
+                constexpr int LP = P >= 32 ? 5 : P >= 16 ? 4 : P >= 8 ? 3 : P >= 4 ? 2 : 1;
+#pragma unroll
+                for (int lv = 1; lv <= LP; lv++) {
+                    const int m = P >> lv;
+                    const bool up = (sl & m) != 0;
+#pragma unroll
+                    for (int i = 0; i < m; i++) {
+                        const float keep = up ? ps[i + m] : ps[i];
+                        const float send = up ? ps[i] : ps[i + m];
+                        ps[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, m));
+                    }
+                }
+                if (__any_sync(0xffffffffu, hz != 0u)) {
+                    // rare: some row of the chunk holds a landmark value (warp-uniform branch)
+#pragma unroll 1
+                    for (int u = 0; u < P; u++) {
+                        const uint32_t id = __shfl_sync(0xffffffffu, myid[q], u * RW + g);
+                        const uint32_t rpos = base + q * kThreads + w * 32 + u * RW + g;
+                        if (((hz >> u) & 1u) && rpos < n_live) {
+                            const float4 *r4 = reinterpret_cast<const float4 *>(x + (size_t)id * D) + sl;
+                            for (int f = 0; f < F; f++) {
+                                const float4 vv = __ldg(r4 + P * f);
+                                const int j = 4 * (sl + P * f);
+                                if (vv.x == Ls[j + 0]) atomicAdd(&chold[j + 0], 1u);
+                                if (vv.y == Ls[j + 1]) atomicAdd(&chold[j + 1], 1u);
+                                if (vv.z == Ls[j + 2]) atomicAdd(&chold[j + 2], 1u);
+                                if (vv.w == Ls[j + 3]) atomicAdd(&chold[j + 3], 1u);
+                            }
+                            pfl[rpos] |= kFlHold;
+                        }
+                    }
+                }
+                const uint32_t src = (uint32_t)(sl * RW + g);
+                const uint32_t pos = base + q * kThreads + w * 32 + src;
+                key_out(pos < n_live, pos, __float_as_uint(ps[0]));
+            }
         }
-        float4 v[BC][P][F];
+    } else {
+        constexpr int B = kPeelBatch<D>();
+        for (uint32_t base = 0; base < n_live; base += B * kThreads) {
+            bool lv[B];
+            uint32_t ids[B];
 #pragma unroll
-        for (int q = 0; q < BC; q++)
-#pragma unroll
-            for (int u = 0; u < P; u++) {
-                const uint32_t id = __shfl_sync(0xffffffffu, myid[q], u * RW + g);
-                const float4 *r4 = reinterpret_cast<const float4 *>(x + (size_t)id * D) + sl;
-#pragma unroll
-                for (int f = 0; f < F; f++) v[q][u][f] = __ldg(r4 + P * f);
+            for (int q = 0; q < B; q++) {
+                const uint32_t qi = base + q * kThreads + t;
+                lv[q] = qi < n_live;
+                ids[q] = lv[q] ? LID(qi) : s0;
             }
+            // past the end a thread reads the slice's first row again (an L1 hit), so every
+            // thread keeps B rows in flight without branching
+            float dl[B];
+            bool hz[B];
 #pragma unroll
-        for (int q = 0; q < BC; q++) {
-            float ps[P];
+            for (int q = 0; q < B; q++) dl[q] = dist32<D>(x + (size_t)ids[q] * d, Ls, d, hz[q]);
 #pragma unroll
-            for (int u = 0; u < P; u++) {
-                float acc = 0.0f;
-#pragma unroll
-                for (int f = 0; f < F; f++) {
-                    const float t0 = __fsub_rn(v[q][u][f].x, Lq[f].x);
-                    acc = __fmaf_rn(t0, t0, acc);
-                    const float t1 = __fsub_rn(v[q][u][f].y, Lq[f].y);
-                    acc = __fmaf_rn(t1, t1, acc);
-                    const float t2 = __fsub_rn(v[q][u][f].z, Lq[f].z);
-                    acc = __fmaf_rn(t2, t2, acc);
-                    const float t3 = __fsub_rn(v[q][u][f].w, Lq[f].w);
-                    acc = __fmaf_rn(t3, t3, acc);
-                }
-                ps[u] = acc;
+            for (int q = 0; q < B; q++) {
+                if (lv[q] && hz[q]) note_holder(x + (size_t)ids[q] * d, Ls, d, &pfl[base + q * kThreads + t], chold);
+                key_out(lv[q], base + q * kThreads + t, __float_as_uint(dl[q]));
             }
-            // butterfly: after the round with mask m a lane keeps the half of rows
-            // whose index has its lane bit m; at the end ps[0] is row sl's sum
-            constexpr int LP = P >= 32 ? 5 : P >= 16 ? 4 : P >= 8 ? 3 : P >= 4 ? 2 : 1;
-#pragma unroll
-            for (int lv = 1; lv <= LP; lv++) {
-                const int m = P >> lv;
-                const bool up = (sl & m) != 0;
-#pragma unroll
-                for (int i = 0; i < m; i++) {
-                    const float keep = up ? ps[i + m] : ps[i];
-                    const float send = up ? ps[i] : ps[i + m];
-                    ps[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, m));
-                }
-            }
-            const uint32_t src = (uint32_t)(sl * RW + g);
-            const uint32_t pos = base + q * kThreads + w * 32 + src;
-            const uint32_t id = __shfl_sync(0xffffffffu, myid[q], src);
-            key_out(pos < n_live, pos, id, __float_as_uint(ps[0]));
         }
     }
+}
+
+// A holder of some attribute's landmark value assigned to round rr of the epoch: counted
+// per attribute it holds.
+__device__ __forceinline__ void count_holder(const float *__restrict__ x, const float *Ls, int d, uint32_t id,
+                                             uint32_t rr, PeelCtl *ctl)
+{
+    const float *row = x + (size_t)id * d;
+    for (int j = 0; j < d; j++)
+        if (__ldg(&row[j]) == Ls[j]) atomicAdd(&ctl->hcnt[j][rr], 1u);
+}
+
+// Settles group g of the epoch's boundaries (one CTA): every band entry of the group gets
+// its round, exactly by (delta64, index).  Entries are ranked by their compensated
+// distance; at each boundary only the entries within that distance's error of the cut are
+// ranked again by float64.  r0: the epoch's first round; K: its boundaries.
+__device__ __noinline__ void settle_group(const PeelArgs &a, const float *Ls, uint32_t g, uint32_t r0, uint32_t K,
+                                          uint32_t *scr)
+{
+    PeelCtl *ctl = a.ctl;
+    const int d = a.d;
+    const uint32_t N = (uint32_t)a.N;
+    const int t = threadIdx.x;
+    __shared__ uint32_t s_na;
+    __shared__ double s_lo[kMaxEpoch], s_hi[kMaxEpoch];
+    __shared__ uint32_t s_need[kMaxEpoch], s_need3[kMaxEpoch], s_na3[kMaxEpoch], s_p3[kMaxEpoch];
+    __shared__ unsigned long long s_k3[kMaxEpoch];
+    __shared__ uint32_t s_bc[kMaxEpoch];
+    const uint32_t q1 = __ldcg(&ctl->g_q1[g]), q2 = __ldcg(&ctl->g_q2[g]);
+    const uint32_t ne = __ldcg(&ctl->gcnt[g]);
+    // points certainly before the group: certain points of rounds up to q1 and the
+    // entries of the groups before it, whose regions precede the group's
+    uint32_t before = 0, off = 0;
+    for (uint32_t r = 0; r <= q1; r++) before += __ldcg(&ctl->cert[r]);
+    for (uint32_t h = 0; h < g; h++) off += __ldcg(&ctl->gcnt[h]);
+    before += off;
+    const bool staged = ne <= (uint32_t)kStage;
+    uint64_t *stk = reinterpret_cast<uint64_t *>(scr + kStageOff);
+    uint32_t *stp = scr + kStageOff + 2 * kStage;
+    const uint64_t *gk = a.gkey + off;
+    const uint32_t *gp = a.gpos + off;
+    uint64_t *ak = a.akey + off;
+    uint32_t *ap = a.apos + off;
+    if (t < kMaxEpoch) s_bc[t] = 0;
+    if (t == 0 && __ldcg(&ctl->gfill[g]) != ne) atomicOr(&a.flags[1], 1u);
+    if (staged)
+        for (uint32_t e = t; e < ne; e += kThreads) {
+            stk[e] = __ldcg(&gk[e]);
+            stp[e] = __ldcg(&gp[e]);
+        }
+    __syncthreads();
+    auto KA = [&](uint32_t i) -> uint64_t { return staged ? stk[i] : __ldcg(&gk[i]); };
+    // an entry's id (bit 31 of the stored word is its hold flag)
+    auto PA = [&](uint32_t i) -> uint32_t { return (staged ? stp[i] : __ldcg(&gp[i])) & kPosMask; };
+    auto AK = [&](uint32_t i) -> uint64_t { return __ldcg(&ak[i]); };
+    auto AP = [&](uint32_t i) -> uint32_t { return __ldcg(&ap[i]); };
+    const double win_rel = 4.0 * ((double)eps_ff(d) + 0x1p-52);
+    for (uint32_t i = q1; i <= q2; i++) {
+        const uint32_t bi = i - q1;
+        const int64_t need_s = (int64_t)(i + 1) * N - (int64_t)before;
+        uint32_t need = need_s < 0 ? 0u : (need_s > (int64_t)ne ? ne : (uint32_t)need_s);
+        if (t == 0 && (need_s < 0 || need_s > (int64_t)ne)) atomicOr(&a.flags[1], 1u);
+        if (need == 0 || need == ne) {
+            if (t == 0) s_need[bi] = need;
+            __syncthreads();
+            continue;
+        }
+        uint64_t V;
+        uint32_t Pv;
+        select_kth(KA, PA, ne, need, scr, V, Pv);
+        const double v = __longlong_as_double((long long)V);
+        const double win = win_rel * v + 0x1p-110;
+        const double lo = v - win, hi = v + win;
+        if (t == 0) s_na = 0;
+        __syncthreads();
+        uint32_t below = 0;
+        for (uint32_t e = t; e < ne; e += kThreads) {
+            const double ke = __longlong_as_double((long long)KA(e));
+            if (ke < lo) {
+                below++;
+            } else if (ke <= hi) {
+                const uint32_t slot = atomicAdd(&s_na, 1u);
+                ap[slot] = PA(e);
+            }
+        }
+        below = block_sum(below);
+        const uint32_t na = s_na;
+        const uint32_t need3 = need >= below ? need - below : 0u;
+        if (t == 0 && (need < below || need3 > na)) atomicOr(&a.flags[1], 1u);
+        uint64_t K3 = 0;
+        uint32_t P3 = 0;
+        if (need3 > 0 && need3 < na) {
+            // the entries within the error of the cut-off, ranked by float64 and index
+            for (uint32_t e = t; e < na; e += kThreads) {
+                const uint32_t pos = __ldcg(&ap[e]);
+                ak[e] = (uint64_t)__double_as_longlong(dist64(a.x + (size_t)pos * d, Ls, d));
+            }
+            __syncthreads();
+            select_kth(AK, AP, na, need3, scr, K3, P3);
+        }
+        if (t == 0) {
+            s_need[bi] = need;
+            s_lo[bi] = lo;
+            s_hi[bi] = hi;
+            s_need3[bi] = need3;
+            s_na3[bi] = na;
+            s_k3[bi] = K3;
+            s_p3[bi] = P3;
+        }
+        __syncthreads();
+    }
+    // every entry's round: the first boundary of the group plus the boundaries it is after
+    for (uint32_t e = t; e < ne; e += kThreads) {
+        const uint64_t kb = KA(e);
+        const uint32_t raw = staged ? stp[e] : __ldcg(&gp[e]);
+        const uint32_t pos = raw & kPosMask;
+        const double ke = __longlong_as_double((long long)kb);
+        uint32_t after = 0;
+        for (uint32_t bi = 0; bi <= q2 - q1; bi++) {
+            const uint32_t need = s_need[bi];
+            if (need == 0) {
+                after++;
+                continue;
+            }
+            if (need == ne || ke < s_lo[bi]) continue;
+            if (ke > s_hi[bi]) {
+                after++;
+                continue;
+            }
+            const uint32_t n3 = s_need3[bi];
+            if (n3 == 0) {
+                after++;
+            } else if (n3 < s_na3[bi]) {
+                const uint64_t k64 = (uint64_t)__double_as_longlong(dist64(a.x + (size_t)pos * d, Ls, d));
+                if (k64 > s_k3[bi] || (k64 == s_k3[bi] && pos > s_p3[bi])) after++;
+            }
+        }
+        const uint32_t rr = q1 + after;
+        if (rr < K) {
+            a.rnd[pos] = r0 + rr;
+            atomicAdd(&s_bc[rr], 1u);
+            if (raw & ~kPosMask) count_holder(a.x, Ls, d, pos, rr, ctl);
+        }
+    }
+    __syncthreads();
+    if (t < (int)K && s_bc[t]) atomicAdd(&ctl->bnd[t], s_bc[t]);
+}
+
+// The next landmark (attributes j_first, j_first + j_step, ...): in each attribute the
+// smallest value among the points left (rnd >= live_from), found from the bucket order:
+// from the attribute's bucket pointer on, the first non-empty bucket whose entries include
+// a point left holds it; buckets whose entries are all gone are passed for good.
+__device__ __noinline__ void find_landmark(const PeelArgs &a, int j_first, int j_step, uint32_t live_from)
+{
+    PeelCtl *ctl = a.ctl;
+    const int d = a.d;
+    const uint32_t nbk = a.nbk;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    __shared__ uint32_t red_a[kW], red_b[kW];
+    __shared__ uint32_t s_st, s_en;
+    for (int j = j_first; j >= 0 && j < d; j += j_step) {
+        const uint4 *bj = a.bcs + (size_t)j * nbk;
+        const uint32_t *oj = a.ord + (size_t)j * a.ord_ld;
+        uint32_t b = __ldcg(&ctl->lptr[j]);       // the buckets before b hold no point left
+        uint32_t mnb = kGone;
+        while (b < nbk) {
+            // the first non-empty bucket from b on
+            const uint32_t bb = b + (uint32_t)t;
+            const uint4 e = bb < nbk ? __ldcg(&bj[bb]) : make_uint4(0u, 0u, 0u, 0u);
+            uint32_t fb = warp_min(e.x > 0 ? bb : kGone);
+            if (lane == 0) red_a[w] = fb;
+            __syncthreads();
+            fb = red_a[0];
+#pragma unroll
+            for (int q = 1; q < kW; q++) fb = min(fb, red_a[q]);
+            if (bb == fb) {
+                s_st = e.y;
+                s_en = e.z;
+            }
+            __syncthreads();
+            if (fb == kGone) {
+                b += kThreads;
+                continue;
+            }
+            // the smallest value among its entries left
+            const uint32_t st = s_st, en = s_en;
+            uint32_t lm = kGone;
+            for (uint32_t q = st + t; q < en; q += kThreads) {
+                const uint32_t id = __ldcg(&oj[q]);
+                if (__ldcg(&a.rnd[id]) >= live_from)
+                    lm = min(lm, __float_as_uint(__ldg(&a.x[(size_t)id * d + j])));
+            }
+            lm = warp_min(lm);
+            if (lane == 0) red_b[w] = lm;
+            __syncthreads();
+            lm = red_b[0];
+#pragma unroll
+            for (int q = 1; q < kW; q++) lm = min(lm, red_b[q]);
+            __syncthreads();
+            if (lm != kGone) {
+                mnb = lm;
+                b = fb;
+                break;
+            }
+            b = fb + 1;                            // every entry of fb is gone
+        }
+        if (t == 0) {
+            ctl->lptr[j] = b;
+            ctl->Lbits[j] = mnb == kGone ? kInfBits : mnb;
+        }
+    }
+}
+
+// The last CTA of phase B turns each boundary's first-digit bin and rank inside it into
+// its band cut-offs (second digit from the boundary's histogram), and merges boundaries
+// whose bands overlap into groups.  Warp w resolves boundaries w, w + kW, ...: lane i sums
+// second-digit bins [64 i, 64 i + 64) in two halves, a warp scan finds the lane holding
+// the rank, and that lane walks the half holding it (its loads issued together).
+__device__ __noinline__ void resolve_cutoffs(PeelCtl *ctl, uint32_t K, int d, const uint32_t *sb, const uint32_t *sr,
+                                             const uint32_t *sslot, uint32_t nslot)
+{
+    __shared__ uint32_t s_b1[kMaxEpoch];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t < kMaxEpoch) s_b1[t] = 0;
+    __syncthreads();
+    for (uint32_t q = (uint32_t)w; q < K; q += kW) {
+        const uint4 *h4 = reinterpret_cast<const uint4 *>(ctl->h1[sslot[q]] + lane * 64);
+        uint32_t lo = 0, hi = 0;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const uint4 u = __ldcg(h4 + i), v = __ldcg(h4 + 8 + i);
+            lo += u.x + u.y + u.z + u.w;
+            hi += v.x + v.y + v.z + v.w;
+        }
+        const uint32_t ls = lo + hi;
+        const uint32_t ex = warp_incl_scan(ls) - ls;
+        const uint32_t r = sr[q];
+        if (r >= ex && r < ex + ls) {
+            const int half = r >= ex + lo ? 1 : 0;
+            uint4 u[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++) u[i] = __ldcg(h4 + 8 * half + i);
+            uint32_t cc = ex + (half ? lo : 0u), found = 0;
+            bool done = false;
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const uint32_t v4[4] = {u[i].x, u[i].y, u[i].z, u[i].w};
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    if (!done && r < cc + v4[k]) {
+                        found = (uint32_t)(lane * 64 + 32 * half + 4 * i + k);
+                        done = true;
+                    }
+                    cc += v4[k];
+                }
+            }
+            s_b1[q] = found;
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
+        uint32_t ng = 0, gi = 0, go = 0;
+        for (uint32_t q = 0; q < K; q++) {
+            uint32_t ik, ok;
+            band_cutoffs(sb[q], s_b1[q], d, ik, ok);
+            if (ng > 0 && ik <= go) {
+                go = max(go, ok);
+                ctl->g_out[ng - 1] = go;
+                ctl->g_q2[ng - 1] = q;
+            } else {
+                gi = ik;
+                go = ok;
+                ctl->g_in[ng] = gi;
+                ctl->g_out[ng] = go;
+                ctl->g_q1[ng] = q;
+                ctl->g_q2[ng] = q;
+                ng++;
+            }
+        }
+        ctl->n_groups = ng;
+        ctl->n_slots = nslot;
+    }
+}
+
+// The last CTA of phase D finds how many rounds the epoch commits: up to the first round
+// after which some attribute has no holder of its landmark value left (the landmark then
+// changes).  It updates the live holder counts, checks that every round of the epoch got
+// exactly N points, records the epoch's landmarks and publishes k_commit and l_changed.
+__device__ __noinline__ void commit_count(const PeelArgs &a, const float *Ls, uint32_t K, uint32_t r0, bool need_keys)
+{
+    PeelCtl *ctl = a.ctl;
+    const int d = a.d;
+    const uint32_t N = (uint32_t)a.N;
+    const int t = threadIdx.x;
+    // per attribute: the first round after which no holder of L_j is left
+    // (the counts are read all at once, then scanned in registers)
+    uint32_t qs = kNone;
+    for (int j = t; j < d; j += kThreads) {
+        uint32_t hc[kMaxEpoch];
+#pragma unroll
+        for (int r = 0; r < kMaxEpoch; r++) hc[r] = r < (int)K ? __ldcg(&ctl->hcnt[j][r]) : 0u;
+        const uint32_t ch = __ldcg(&ctl->chold[j]);
+        uint32_t acc = 0, qj = kNone;
+#pragma unroll
+        for (int r = 0; r < kMaxEpoch; r++) {
+            acc += hc[r];
+            if (qj == kNone && r < (int)K && acc >= ch) qj = (uint32_t)r;
+        }
+        qs = min(qs, qj);
+    }
+    qs = block_min(qs);
+    const uint32_t kc_ = qs < K ? qs + 1u : K;
+    const bool changed = qs < K;
+    for (int j = t; j < d; j += kThreads) {
+        if (changed) {
+            ctl->chold[j] = 0;
+        } else {
+            uint32_t gone = 0;
+#pragma unroll
+            for (int r = 0; r < kMaxEpoch; r++) gone += r < (int)kc_ ? __ldcg(&ctl->hcnt[j][r]) : 0u;
+            ctl->chold[j] = __ldcg(&ctl->chold[j]) - gone;
+        }
+    }
+    if (t < (int)K && __ldcg(&ctl->cert[t]) + __ldcg(&ctl->bnd[t]) != N) atomicOr(&a.flags[1], 1u);
+    if (changed)
+        for (int b = t; b < kHistBins; b += kThreads) ctl->h0[b] = 0;
+    if (a.landmarks)
+        for (uint32_t e = t; e < kc_ * (uint32_t)d; e += kThreads)
+            a.landmarks[(size_t)(r0 + e / d) * d + e % d] = Ls[e % d];
+    if (t == 0) {
+        ctl->k_commit = kc_;
+        ctl->l_changed = changed ? 1u : 0u;
+        ctl->epochs += 1;
+        ctl->passes += need_keys ? 1u : 0u;
+    }
+}
+
+// A CTA's list of points left, by list position: ids, float32 keys and state bytes; in
+// shared memory when the slice fits the key cache (kc), else in one of two global lists.
+struct ListView {
+    bool first, kc;
+    uint32_t s0;
+    const uint32_t *sid, *skey;
+    uint8_t *sfl;
+    const uint32_t *gid, *gkp;
+    uint8_t *gfl;
+    uint32_t *gid2, *gkp2;       // the other global list (compaction target)
+    uint8_t *gfl2;
+    __device__ __forceinline__ uint32_t id(uint32_t q) const { return first ? s0 + q : kc ? sid[q] : __ldcg(&gid[q]); }
+    __device__ __forceinline__ uint32_t key(uint32_t q) const { return kc ? skey[q] : __ldcg(&gkp[q]); }
+    __device__ __forceinline__ uint8_t *fl() const { return kc ? sfl : gfl; }
+};
+
+// Phase C for one CTA's list: every live key classified against the epoch's groups (see
+// the kernel); certain points get their round in rnd[] and counted in s_cc, band entries
+// are listed (with their hold flag in bit 31 of the id) and counted per group in s_gc.
+__device__ __noinline__ void classify_live(const PeelArgs &a, const ListView &L, uint32_t n_live, const float *Ls,
+                                          uint32_t r0, uint32_t K, uint32_t ng, const uint32_t *s_gin,
+                                          const uint32_t *s_gout, const uint32_t *s_gq2, uint32_t s_glast,
+                                          uint32_t *s_cc, uint32_t *s_gc)
+{
+    PeelCtl *ctl = a.ctl;
+    const int d = a.d;
+    const int t = threadIdx.x, lane = t & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint8_t *pfl = L.fl();
+    // a key's class: kNone (after the epoch, or past the end of the list), its round r < K
+    // (certainly), or kBandTag | g (in group g's band).  The keys, ids and state bytes of
+    // kCB positions are loaded before any is used; the class goes to the state byte and is
+    // counted in shared memory (the points of the epoch are spread over the list, so few
+    // lanes of a warp meet on one counter).
+    constexpr uint32_t kBandTag = 0x100u;
+    for (uint32_t q0 = 0; q0 < n_live; q0 += kCB * kThreads) {
+        uint32_t kk[kCB], cls[kCB], idv[kCB], fl[kCB];
+#pragma unroll
+        for (int u = 0; u < kCB; u++) {
+            const uint32_t qi = q0 + u * kThreads + t;
+            const bool v = qi < n_live;
+            kk[u] = v ? L.key(qi) : kGone;
+            idv[u] = v ? L.id(qi) : 0u;
+            fl[u] = v ? pfl[qi] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kCB; u++) {
+            cls[u] = kNone;
+            if (kk[u] <= s_glast) {
+                uint32_t g = 0, cum = 0;
+                while (g < ng && kk[u] > s_gout[g]) {
+                    cum = s_gq2[g] + 1u;
+                    g++;
+                }
+                if (g < ng && kk[u] >= s_gin[g]) cls[u] = kBandTag | g;
+                else if (cum < K) cls[u] = cum;
+            }
+            // a point outside the epoch keeps its state byte (kFlNone since the last commit)
+            if (cls[u] != kNone)
+                pfl[q0 + u * kThreads + t] = (uint8_t)((fl[u] & kFlHold) | (cls[u] >= kBandTag ? kFlBand : cls[u]));
+        }
+#pragma unroll
+        for (int u = 0; u < kCB; u++) {
+            const bool band = cls[u] != kNone && cls[u] >= kBandTag;
+            const bool cert = cls[u] < kBandTag;
+            const uint32_t bm = __ballot_sync(0xffffffffu, band);
+            if (bm) {
+                uint32_t base = 0;
+                const int leader = __ffs(bm) - 1;
+                if (lane == leader) base = atomicAdd(&ctl->band_cnt, (uint32_t)__popc(bm));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (band) {
+                    const uint32_t slot = base + (uint32_t)__popc(bm & lt);
+                    a.band_k32[slot] = kk[u];
+                    a.band_pos[slot] = idv[u] | ((fl[u] & kFlHold) ? ~kPosMask : 0u);
+                    atomicAdd(&s_gc[cls[u] - kBandTag], 1u);
+                }
+            }
+            if (cert) {
+                a.rnd[idv[u]] = r0 + cls[u];
+                atomicAdd(&s_cc[cls[u]], 1u);
+                if (fl[u] & kFlHold) count_holder(a.x, Ls, d, idv[u], cls[u], ctl);
+            }
+        }
+    }
+}
+
+// Phase E for a list in shared memory (kc), compacted in place: the points whose round
+// lies before live_from leave it; dropped assignments are reset; with the landmark kept,
+// the committed keys leave the first-digit histogram.  Returns the points left.
+__device__ __noinline__ uint32_t compact_shared(const PeelArgs &a, const ListView &L, uint32_t n_live, uint32_t r0,
+                                                uint32_t live_from, bool changed, uint32_t *scr)
+{
+    PeelCtl *ctl = a.ctl;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint8_t *pfl = L.sfl;
+    if (!changed)
+        for (int b = t; b < kHistBins; b += kThreads) scr[b] = 0;
+    __syncthreads();
+    constexpr int PER = kQT * kW / 32;
+    static_assert(PER * 32 == kQT * kW, "one warp scans the tile counts");
+    __shared__ uint32_t woff[kQT * kW + 1];
+    uint32_t *kid = const_cast<uint32_t *>(L.sid), *kkey = const_cast<uint32_t *>(L.skey);
+    uint32_t done = 0;
+    // in place: a tile's ids, keys and state bytes are all read before any kept one
+    // is written, and those land at or below the tile's own positions.  A position's
+    // state byte tells its round in the epoch; only band entries read their round
+    // (settled by another CTA) from rnd[].
+    for (uint32_t cb = 0; cb < n_live; cb += kQT * kThreads) {
+        uint32_t ids[kQT], keys[kQT], fls[kQT], rv[kQT], vl = 0, kp = 0;
+#pragma unroll
+        for (int q = 0; q < kQT; q++) {
+            const uint32_t qi = cb + q * kThreads + t;
+            const bool v = qi < n_live;
+            ids[q] = v ? L.id(qi) : 0u;
+            keys[q] = v ? L.key(qi) : kGone;
+            fls[q] = v ? pfl[qi] : (uint32_t)kFlNone;
+            vl |= (uint32_t)v << q;
+        }
+#pragma unroll
+        for (int q = 0; q < kQT; q++) {
+            const uint32_t st = fls[q] & 0x7Fu;
+            rv[q] = st == kFlBand ? __ldcg(&a.rnd[ids[q]]) : st == kFlNone ? kNone : r0 + st;
+            kp |= (uint32_t)(((vl >> q) & 1u) && rv[q] >= live_from) << q;
+        }
+        uint32_t bk[kQT];
+#pragma unroll
+        for (int q = 0; q < kQT; q++) {
+            bk[q] = __ballot_sync(0xffffffffu, (kp >> q) & 1u);
+            if (lane == 0) woff[q * kW + w] = __popc(bk[q]);
+        }
+        __syncthreads();
+        if (w == 0) {
+            uint32_t vk[PER], sk = 0;
+#pragma unroll
+            for (int e = 0; e < PER; e++) {
+                vk[e] = woff[lane * PER + e];
+                sk += vk[e];
+            }
+            const uint32_t ik = warp_incl_scan(sk);
+            uint32_t ek = ik - sk;
+#pragma unroll
+            for (int e = 0; e < PER; e++) {
+                woff[lane * PER + e] = ek;
+                ek += vk[e];
+            }
+            if (lane == 31) woff[kQT * kW] = ik;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kQT; q++) {
+            const bool valid = (vl >> q) & 1u;
+            const bool keep = (kp >> q) & 1u;
+            if (keep) {
+                const uint32_t o = done + woff[q * kW + w] + __popc(bk[q] & lt);
+                kid[o] = ids[q];
+                kkey[o] = keys[q];
+                pfl[o] = (uint8_t)((fls[q] & kFlHold) | kFlNone);
+                if (rv[q] != kNone) a.rnd[ids[q]] = kNone;       // an assignment dropped
+            } else if (valid && !changed) {
+                // the next epoch keeps these keys: the committed ones leave the histogram
+                atomicAdd(&scr[keys[q] >> 21], 1u);
+            }
+        }
+        done += woff[kQT * kW];
+        __syncthreads();
+    }
+
+    if (!changed) {
+        // the next epoch keeps these keys: the committed ones leave the histogram
+        __syncthreads();
+        for (int b = t; b < kHistBins; b += kThreads)
+            if (scr[b]) atomicSub(&ctl->h0[b], scr[b]);
+    }
+    return done;
+}
+
+// Phase E for a list in global memory: each warp takes chunks of 32 kQT positions and
+// appends the points it keeps to the other list (their order does not matter: the
+// subclusters are packed by a counting sort over rnd afterwards), claiming slots with one
+// shared atomic per 32 positions; no block barrier inside.  Returns the points left.
+__device__ __noinline__ uint32_t compact_global(const PeelArgs &a, const ListView &L, uint32_t n_live, uint32_t r0,
+                                                uint32_t live_from, bool changed, uint32_t *scr)
+{
+    PeelCtl *ctl = a.ctl;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    __shared__ uint32_t s_out;
+    if (!changed)
+        for (int b = t; b < kHistBins; b += kThreads) scr[b] = 0;
+    if (t == 0) s_out = 0;
+    __syncthreads();
+    for (uint32_t cb = (uint32_t)w * 32 * kQT; cb < n_live; cb += kW * 32 * kQT) {
+        uint32_t ids[kQT], keys[kQT], fls[kQT];
+#pragma unroll
+        for (int q = 0; q < kQT; q++) {
+            const uint32_t qi = cb + q * 32 + lane;
+            const bool v = qi < n_live;
+            ids[q] = v ? L.id(qi) : 0u;
+            keys[q] = v ? __ldcg(&L.gkp[qi]) : kGone;
+            fls[q] = v ? L.gfl[qi] : (uint32_t)kFlNone;
+        }
+        uint32_t bk[kQT], rvs[kQT], tot = 0;
+#pragma unroll
+        for (int q = 0; q < kQT; q++) {
+            const bool valid = cb + q * 32 + lane < n_live;
+            const uint32_t st = fls[q] & 0x7Fu;
+            rvs[q] = st == kFlBand ? __ldcg(&a.rnd[ids[q]]) : st == kFlNone ? kNone : r0 + st;
+            bk[q] = __ballot_sync(0xffffffffu, valid && rvs[q] >= live_from);
+            tot += __popc(bk[q]);
+        }
+        // one slot claim per warp and chunk
+        uint32_t ob = 0;
+        if (lane == 0 && tot) ob = atomicAdd(&s_out, tot);
+        ob = __shfl_sync(0xffffffffu, ob, 0);
+#pragma unroll
+        for (int q = 0; q < kQT; q++) {
+            const bool valid = cb + q * 32 + lane < n_live;
+            if ((bk[q] >> lane) & 1u) {
+                const uint32_t o = ob + __popc(bk[q] & lt);
+                L.gid2[o] = ids[q];
+                L.gkp2[o] = keys[q];
+                L.gfl2[o] = (uint8_t)((fls[q] & kFlHold) | kFlNone);
+                if (rvs[q] != kNone) a.rnd[ids[q]] = kNone;          // an assignment dropped
+            } else if (valid && !changed) {
+                atomicAdd(&scr[keys[q] >> 21], 1u);
+            }
+            ob += __popc(bk[q]);
+        }
+    }
+    __syncthreads();
+    if (!changed) {
+        // the next epoch keeps these keys: the committed ones leave the histogram
+        __syncthreads();
+        for (int b = t; b < kHistBins; b += kThreads)
+            if (scr[b]) atomicSub(&ctl->h0[b], scr[b]);
+    }
+    return s_out;
 }
 
 template <int D>
 __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
 {
-    constexpr int B = kPeelBatch<D>();
-    constexpr int W = kThreads / 32;
-    // dynamic shared memory: [first histogram | guessed second-digit histogram] in phase A;
-    // in phase D the band's one-ulp bins and, kept to the end of the round, the tight set
+    // dynamic shared memory: [scratch: phase A's histogram | selection scratch + staged
+    // band entries] [keys by list position | ids by list position] (the latter when kc)
     extern __shared__ __align__(16) uint32_t dyn[];
-    uint32_t *sh = dyn;
-    uint32_t *gh = dyn + kHistBins;
-    uint32_t *hb = dyn;
-    uint32_t *tpos = dyn + kBandBins;
-    uint32_t *tcls = tpos + kTight;                    // 1 taken, 0 not
-    float *th = reinterpret_cast<float *>(tcls + kTight);
-    float *tl = th + kTight;
-    uint32_t *tamb = reinterpret_cast<uint32_t *>(tl + kTight);    // undecided tight entries
-    unsigned long long *td = reinterpret_cast<unsigned long long *>(tamb + kTight);
-    uint32_t *skey = dyn + kPeelScratch;               // keys by list position (kc)
-    uint32_t *sid = skey + kKeyCache;                  // ids by list position (kc)
-    uint32_t *s_bk = sid + kKeyCache;                  // the band's keys and ids (nb <= kBandStage)
-    uint32_t *s_bp = s_bk + kBandStage;
+    uint32_t *scr = dyn;
+    uint32_t *skey = dyn + kScrWords;
+    uint32_t *sid = skey + kKeyCache;
+    uint8_t *sfl = reinterpret_cast<uint8_t *>(sid + kKeyCache);     // state bytes by list position (kc)
     __shared__ float Ls[D > 0 ? D : kMaxD];
-    __shared__ uint32_t s_in_key, s_out_key, s_nt, s_na, s_v, s_t32, s_st, s_en;
-    __shared__ uint32_t red_a[W], red_b[W];
+    __shared__ uint32_t s_b[kMaxEpoch], s_r[kMaxEpoch], s_slot[kMaxEpoch], s_sbin[kMaxEpoch];
+    __shared__ uint32_t s_gin[kMaxEpoch], s_gout[kMaxEpoch], s_gq2[kMaxEpoch];
+    __shared__ uint32_t s_cc[kMaxEpoch], s_gc[kMaxEpoch];
+    __shared__ uint32_t s_nslot, s_glast;
+    __shared__ uint8_t s_map[kHistBins];
     PeelCtl *ctl = a.ctl;
     const int d = a.d;
-    const uint32_t n = (uint32_t)a.n, N = (uint32_t)a.N, nbk = a.nbk;
+    const uint32_t n = (uint32_t)a.n, N = (uint32_t)a.N;
     const int t = threadIdx.x;
-    const int lane = t & 31, w = t >> 5;
     const unsigned G = gridDim.x, c = blockIdx.x;
+    const unsigned lim = a.spin;
     // With 16 CTAs or more, the last Gl CTAs own no points and only build landmarks, which
     // then overlaps with the others' compaction; otherwise every CTA does both.
     const int Gl = G >= 16 ? min(d, (int)(G / 8)) : 0;
@@ -892,12 +1334,20 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
     const uint32_t s1 = c < Gs ? (uint32_t)((uint64_t)(c + 1) * n / Gs) : n;
     const int lm_first = Gl ? (int)c - (int)Gs : (int)(G - 1 - c);
     const int lm_step = Gl ? Gl : (int)G;
-    uint32_t n_live = s1 - s0;           // points of the slice left (ids in lidx after round 0)
-    const bool kc = s1 - s0 <= (uint32_t)kKeyCache;   // the round's keys stay in shared memory
+    uint32_t n_live = s1 - s0;           // points of the slice left
+    const bool kc = s1 - s0 <= (uint32_t)kKeyCache;   // the list and its keys stay in shared memory
+    // slices beyond the key cache alternate between two lists in global memory
+    uint32_t *gid = a.lidx + s0, *gid2 = a.lidx + n + s0;
+    uint32_t *gkp = a.kpos + s0, *gkp2 = a.kpos + n + s0;
+    uint8_t *gfl = a.pflag + s0, *gfl2 = a.pflag + n + s0;
+    uint8_t *pfl = kc ? sfl : gfl;                      // the slice's state bytes by list position
     unsigned gen = 0;
+    if (kc)
+        for (uint32_t q = t; q < s1 - s0; q += kThreads) sfl[q] = kFlNone;
 
-    // ---- before round 0: per attribute, the point ids by value bucket (counting sort)
+    // ---- before the first epoch: per attribute, the point ids by value bucket (counting sort)
     {
+        const uint32_t nbk = a.nbk;
         const uint64_t stride = (uint64_t)G * kThreads;
         const uint32_t si = (uint32_t)(stride / (uint64_t)d), sj = (uint32_t)(stride % (uint64_t)d);
         const uint64_t e0 = (uint64_t)c * kThreads + t;
@@ -915,7 +1365,7 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
                     i++;
                 }
             }
-            if (!grid_sync(ctl, a.flags, gen)) return;
+            if (!grid_sync(ctl, a.flags, gen, lim, pass == 0 ? a.stall : 0u)) return;
             if (pass == 1) break;
             // exclusive scan of each attribute's counts in place: they become the cursors
             for (int jj = (int)c; jj < d; jj += (int)G) {
@@ -950,436 +1400,284 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
                     run += tot;
                 }
             }
-            if (!grid_sync(ctl, a.flags, gen)) return;
+            if (!grid_sync(ctl, a.flags, gen, lim)) return;
         }
     }
 
-    uint32_t guess = kGone;            // first digit of the previous round's N-th key
-    for (int64_t r = 0; r < a.S; r++) {
-        const uint32_t nr = (uint32_t)(a.n - r * a.N);
-        const int par = (int)(r & 1);
-        uint32_t *seg_out = a.perm + r * a.N;
-        if (c == 0 && a.landmarks)
-            for (int j = t; j < d; j += kThreads)
-                a.landmarks[r * d + j] = __uint_as_float(__ldcg(&ctl->Lbits[par][j]));
-        // the slice's list of ids left: the slice itself in round 0, then in shared memory
-        // when it fits the key cache (compacted there in place), else in global memory
-        const uint32_t *glin = a.lidx + (size_t)par * n + s0;
-        auto LID = [&](uint32_t q) -> uint32_t { return r == 0 ? s0 + q : kc ? sid[q] : __ldcg(&glin[q]); };
-        if (nr <= N) {                                // the last subcluster: all that is left
-            if (t == 0) ctl->cnt_in[c] = n_live;
-            if (!grid_sync(ctl, a.flags, gen)) return;
-            uint32_t before = 0;
-            for (uint32_t q = t; q < c; q += kThreads) before += __ldcg(&ctl->cnt_in[q]);
-            before = block_sum(before);
-            for (uint32_t q = t; q < n_live; q += kThreads) seg_out[before + q] = LID(q);
+    bool first = true;           // the first epoch: a slice's list is the slice itself
+    bool need_keys = true;       // the landmark changed: the keys must be computed
+    uint32_t r0 = 0;             // the epoch's first round
+    // boundaries the next epoch tries: all it may after an epoch that kept its landmark,
+    // twice the rounds committed after one whose landmark changed (most such runs are
+    // short, and each boundary's work is lost when the landmark changes before it)
+    uint32_t kcap = a.kmax;
+    for (;;) {
+        const uint32_t nl_tot = n - r0 * N;
+        auto LID = [&](uint32_t q) -> uint32_t { return first ? s0 + q : kc ? sid[q] : __ldcg(&gid[q]); };
+        auto LKEY = [&](uint32_t q) -> uint32_t { return kc ? skey[q] : __ldcg(&gkp[q]); };
+        const ListView LV{first, kc, s0, sid, skey, sfl, gid, gkp, gfl, gid2, gkp2, gfl2};
+        for (int j = t; j < d; j += kThreads) Ls[j] = __uint_as_float(__ldcg(&ctl->Lbits[j]));
+        __syncthreads();
+        if (nl_tot <= N) {                            // the last subcluster: all that is left
+            for (uint32_t q = t; q < n_live; q += kThreads) a.rnd[LID(q)] = r0;
+            if (c == 0 && a.landmarks)
+                for (int j = t; j < d; j += kThreads) a.landmarks[(size_t)r0 * d + j] = Ls[j];
             break;
         }
+        const uint32_t K = min(kcap, (nl_tot + N - 1) / N - 1u);   // boundaries of the epoch
 
-        // ---- A: float32 distances of the points left and the first histogram
-        for (int j = t; j < d; j += kThreads) Ls[j] = __uint_as_float(__ldcg(&ctl->Lbits[par][j]));
-        const bool have_guess = guess != kGone;
-        for (int b = t; b < (have_guess ? 2 : 1) * kHistBins; b += kThreads) dyn[b] = 0;
-        if (c == 0 && t == 0) ctl->band_cnt[par ^ 1] = 0;
-        if (Gl > 0 && c >= Gs && r > 0) {
-            // the previous subcluster's points: marked removed, out of their buckets' counts
-            // (this round's landmark needs both, its other CTAs have rows to read)
-            const uint32_t *prev = a.perm + (r - 1) * a.N;
-            for (uint32_t q = (c - Gs) * kThreads + t; q < N; q += (uint32_t)Gl * kThreads) {
-                const uint32_t id = __ldcg(&prev[q]);
-                a.key[id] = kGone;
-                drop_buckets<D>(a.x, d, id, a.bcs, nbk);
-            }
-        }
-        __syncthreads();
-        // the key of one point of the round, stored for phases B-D and counted
-        auto key_out = [&](bool live, uint32_t pos, uint32_t id, uint32_t k) {
-            if (live) {
-                a.key[id] = k;
-                if (kc) skey[pos] = k;
-                else a.kpos[s0 + pos] = k;
-            }
-            // the keys of a round crowd into a few bins: one shared atomic per bin and warp
-            const uint32_t b = live ? (k >> 21) : kGone;
-            const uint32_t peers = __match_any_sync(0xffffffffu, b);
-            if (live && lane == __ffs(peers) - 1) atomicAdd(&sh[b], (uint32_t)__popc(peers));
-            if (have_guess) {
-                const uint32_t g2 = live && (k >> 21) == guess ? (k >> 10) & (kHistBins - 1) : kGone;
-                const uint32_t pg = __match_any_sync(0xffffffffu, g2);
-                if (g2 != kGone && lane == __ffs(pg) - 1) atomicAdd(&gh[g2], (uint32_t)__popc(pg));
-            }
-        };
-        if constexpr (kCoopRows<D>()) {
-            coop_keys<D>(a.x, Ls, n_live, s0, r == 0, kc, sid, glin, a.key, skey, a.kpos, sh, gh, guess);
-        } else
-        for (uint32_t base = 0; base < n_live; base += B * kThreads) {
-            bool lv[B];
-            uint32_t ids[B];
-#pragma unroll
-            for (int q = 0; q < B; q++) {
-                const uint32_t qi = base + q * kThreads + t;
-                lv[q] = qi < n_live;
-                ids[q] = lv[q] ? LID(qi) : s0;
-            }
-            // past the end a thread reads the slice's first row again (an L1 hit), so every
-            // thread keeps B rows in flight without branching
-            float dl[B];
-#pragma unroll
-            for (int q = 0; q < B; q++) dl[q] = dist32<D>(a.x + (size_t)ids[q] * d, Ls, d);
-#pragma unroll
-            for (int q = 0; q < B; q++) key_out(lv[q], base + q * kThreads + t, ids[q], __float_as_uint(dl[q]));
-        }
-        __syncthreads();
-        {
-            uint32_t *hist0 = ctl->hist[par][0];
+        // ---- A: float32 distances of the points left, the first histogram, the holders
+        if (need_keys) {
+            for (int b = t; b < kHistBins; b += kThreads) scr[b] = 0;
+            __syncthreads();
+            phase_keys<D>(a.x, Ls, d, n_live, s0, first, kc, sid, gid, skey, gkp, scr, pfl,
+                          ctl->chold);
+            __syncthreads();
             for (int b = t; b < kHistBins; b += kThreads)
-                if (sh[b]) atomicAdd(&hist0[b], sh[b]);
-            if (have_guess) {
-                uint32_t *gg = &ctl->ghist[par][0];
-                for (int b = t; b < kHistBins; b += kThreads)
-                    if (gh[b]) atomicAdd(&gg[b], gh[b]);
-            }
+                if (scr[b]) atomicAdd(&ctl->h0[b], scr[b]);
+            if (!grid_sync(ctl, a.flags, gen, lim)) return;
         }
-        if (!grid_sync(ctl, a.flags, gen)) return;
 
-        // ---- B: the bin of the N-th key and the second digit inside it (the second
-        // histogram is only built here when the bin was not guessed)
-        uint32_t b0, rank0, b1 = 0, rank1 = 0;
-        bool hit;
-        find_bins(ctl->hist[par][0], have_guess ? ctl->ghist[par] : nullptr, guess, N - 1u, b0, rank0, b1,
-                  rank1, hit);
-        guess = b0;
-        if (!hit) {
-            uint32_t *hist1 = ctl->hist[par][1];
-            for (int b = t; b < kHistBins; b += kThreads) sh[b] = 0;
+        // ---- B: each boundary's first-digit bin (every CTA), then second-digit histograms
+        {
+            constexpr int per = kHistBins / kThreads;       // 8 bins per thread
+            uint32_t l0[per];
+            const uint4 *p = reinterpret_cast<const uint4 *>(ctl->h0 + t * per);
+            const uint4 u = __ldcg(p), v = __ldcg(p + 1);
+            l0[0] = u.x; l0[1] = u.y; l0[2] = u.z; l0[3] = u.w;
+            l0[4] = v.x; l0[5] = v.y; l0[6] = v.z; l0[7] = v.w;
+            uint32_t s = 0;
+#pragma unroll
+            for (int q = 0; q < per; q++) s += l0[q];
+            uint32_t tot;
+            const uint32_t e0 = block_excl_scan(s, tot);
+            for (uint32_t q = 0; q < K; q++) {
+                const uint32_t target = (q + 1) * N - 1u;
+                if (target >= e0 && target < e0 + s) {
+                    uint32_t cc = e0;
+#pragma unroll
+                    for (int i = 0; i < per; i++) {
+                        if (target >= cc && target < cc + l0[i]) {
+                            s_b[q] = (uint32_t)(t * per + i);
+                            s_r[q] = target - cc;
+                        }
+                        cc += l0[i];
+                    }
+                }
+            }
+            for (int b = t; b < kHistBins; b += kThreads) s_map[b] = 0xFF;
+            __syncthreads();
+            if (t == 0) {
+                uint32_t ns = 0;
+                for (uint32_t q = 0; q < K; q++) {
+                    if (q == 0 || s_b[q] != s_b[q - 1]) s_sbin[ns++] = s_b[q];
+                    s_slot[q] = ns - 1;
+                }
+                s_nslot = ns;
+                if (tot != nl_tot) atomicOr(&a.flags[1], 1u);
+            }
+            __syncthreads();
+            if (t < (int)s_nslot) s_map[s_sbin[t]] = (uint8_t)t;
+            __syncthreads();
+            // in shared memory for the first kSlotsSmem bins (the others straight to global),
+            // then the non-zero bins added to the grid's histograms
+            const uint32_t nss = min(s_nslot, (uint32_t)kSlotsSmem);
+            for (uint32_t b = t; b < nss * kHistBins; b += kThreads) scr[b] = 0;
             __syncthreads();
             for (uint32_t q0 = t; q0 < n_live; q0 += 4 * kThreads) {
                 uint32_t k4[4];
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
                     const uint32_t qi = q0 + q * kThreads;
-                    k4[q] = qi >= n_live ? kGone : kc ? skey[qi] : __ldcg(&a.kpos[s0 + qi]);
+                    k4[q] = qi < n_live ? LKEY(qi) : kGone;
                 }
 #pragma unroll
-                for (int q = 0; q < 4; q++)
-                    if ((k4[q] >> 21) == b0 && k4[q] != kGone) atomicAdd(&sh[(k4[q] >> 10) & (kHistBins - 1)], 1u);
+                for (int q = 0; q < 4; q++) {
+                    const uint32_t sl = k4[q] == kGone ? 0xFFu : s_map[k4[q] >> 21];
+                    const uint32_t sub = (k4[q] >> 10) & (kHistBins - 1);
+                    if (sl < nss) atomicAdd(&scr[sl * kHistBins + sub], 1u);
+                    else if (sl != 0xFFu) atomicAdd(&ctl->h1[sl][sub], 1u);
+                }
             }
             __syncthreads();
-            for (int b = t; b < kHistBins; b += kThreads)
-                if (sh[b]) atomicAdd(&hist1[b], sh[b]);
-            if (!grid_sync(ctl, a.flags, gen)) return;
-            find_bin(hist1, rank0, b1, rank1);
+            for (uint32_t b = t; b < nss * kHistBins; b += kThreads)
+                if (scr[b]) atomicAdd(&ctl->h1[b / kHistBins][b % kHistBins], scr[b]);
         }
+        // the last CTA to arrive turns each boundary's bins into its band cut-offs, and
+        // merges boundaries whose bands overlap into groups
+        if (!grid_sync_last(ctl, a.flags, gen, lim, [&]() { resolve_cutoffs(ctl, K, d, s_b, s_r, s_slot, s_nslot); }))
+            return;
 
-        // ---- C: classify; the band is listed
-        if (t == 0) band_cutoffs(b0, b1, d, s_in_key, s_out_key);
-        {   // clear next round's histograms (last read in the previous round)
-            uint32_t *nh = &ctl->hist[par ^ 1][0][0];
-            for (uint32_t b = c * kThreads + t; b < 2u * kHistBins; b += G * kThreads) nh[b] = 0;
-            uint32_t *ng = &ctl->ghist[par ^ 1][0];
-            for (uint32_t b = c * kThreads + t; b < (uint32_t)kHistBins; b += G * kThreads) ng[b] = 0;
+        // ---- C: classify every point left: certainly in a round of the epoch, in a band, or later
+        const uint32_t ng = __ldcg(&ctl->n_groups);
+        if (t < (int)ng) {
+            s_gin[t] = __ldcg(&ctl->g_in[t]);
+            s_gout[t] = __ldcg(&ctl->g_out[t]);
+            s_gq2[t] = __ldcg(&ctl->g_q2[t]);
+        }
+        if (t < kMaxEpoch) {
+            s_cc[t] = 0;
+            s_gc[t] = 0;
+        }
+        if (t == 0) s_glast = __ldcg(&ctl->g_out[ng - 1]);
+        __syncthreads();
+        classify_live(a, LV, n_live, Ls, r0, K, ng, s_gin, s_gout, s_gq2, s_glast, s_cc, s_gc);
+        __syncthreads();
+        if (t < (int)K && s_cc[t]) atomicAdd(&ctl->cert[t], s_cc[t]);
+        if (t < (int)ng && s_gc[t]) atomicAdd(&ctl->gcnt[t], s_gc[t]);
+        if (!grid_sync(ctl, a.flags, gen, lim)) return;
+
+        // ---- D: the band entries regrouped by group with their compensated distances
+        // (across the grid), then each group's band settled (CTA c takes groups c, c + G, ...)
+        {
+            const uint32_t nlist = __ldcg(&ctl->band_cnt);
+            if (t < (int)ng) {
+                uint32_t off = 0;
+                for (uint32_t h = 0; h < (uint32_t)t; h++) off += __ldcg(&ctl->gcnt[h]);
+                s_cc[t] = off;                       // the group's region in gkey / gpos
+            }
+            __syncthreads();
+            for (uint32_t e = c * kThreads + t; e < nlist; e += G * kThreads) {
+                const uint32_t k = __ldcg(&a.band_k32[e]);
+                const uint32_t pos = __ldcg(&a.band_pos[e]);
+                uint32_t g = 0;
+                while (g + 1 < ng && k > s_gout[g]) g++;
+                const uint64_t dk = dff_key(a.x + (size_t)(pos & kPosMask) * d, Ls, d);
+                const uint32_t slot = s_cc[g] + atomicAdd(&ctl->gfill[g], 1u);
+                a.gkey[slot] = dk;
+                a.gpos[slot] = pos;
+            }
+            if (!grid_sync(ctl, a.flags, gen, lim)) return;
+            for (uint32_t g = c; g < ng; g += G) settle_group(a, Ls, g, r0, K, scr);
+        }
+        // the last CTA to arrive finds how many rounds the epoch commits: up to the first
+        // round after which some attribute has no holder of its landmark value left
+        if (!grid_sync_last(ctl, a.flags, gen, lim, [&]() { commit_count(a, Ls, K, r0, need_keys); }))
+            return;
+
+        // ---- E: commit: the epoch's first k_commit rounds leave the lists; the other
+        // assignments are dropped; the next landmark if it changes
+        uint32_t kcm = __ldcg(&ctl->k_commit);
+        if (kcm < 1u || kcm > K) {                    // cannot happen; keeps the loop finite
+            if (c == 0 && t == 0) atomicOr(&a.flags[1], 1u);
+            kcm = 1u;
+        }
+        const bool changed = __ldcg(&ctl->l_changed) != 0;
+        const uint32_t live_from = r0 + kcm;
+        n_live = kc ? compact_shared(a, LV, n_live, r0, live_from, changed, scr)
+                    : compact_global(a, LV, n_live, r0, live_from, changed, scr);
+        if (!kc) {
+            uint32_t *ti = gid; gid = gid2; gid2 = ti;
+            uint32_t *tk = gkp; gkp = gkp2; gkp2 = tk;
+            uint8_t *tf = gfl; gfl = gfl2; gfl2 = tf;
+            pfl = gfl;
+        }
+        // the epoch's scratch, cleared across the grid for the next one
+        {
+            const uint32_t ns = __ldcg(&ctl->n_slots);
+            uint32_t *h1 = &ctl->h1[0][0];
+            for (uint32_t b = c * kThreads + t; b < ns * (uint32_t)kHistBins; b += G * kThreads) h1[b] = 0;
+            uint32_t *hc = &ctl->hcnt[0][0];
+            for (uint32_t b = c * kThreads + t; b < (uint32_t)d * kMaxEpoch; b += G * kThreads) hc[b] = 0;
+            if (c == 0 && t < kMaxEpoch) {
+                ctl->cert[t] = 0;
+                ctl->bnd[t] = 0;
+                ctl->gcnt[t] = 0;
+                ctl->gfill[t] = 0;
+            }
+            if (c == 0 && t == 0) ctl->band_cnt = 0;
+        }
+        if (changed) find_landmark(a, lm_first, lm_step, live_from);
+        first = false;
+        need_keys = changed;
+        r0 += kcm;
+        kcap = changed ? min(a.kmax, max(2u, 2u * kcm)) : a.kmax;
+        if (!grid_sync(ctl, a.flags, gen, lim)) return;
+    }
+}
+
+// ------------------------------------------------------------------ packing by round
+// Stable counting sort of the points by round (8 bits of it per pass): the subclusters,
+// each in ascending point index.  Chunk c of the items is [c m/G, (c+1) m/G).
+constexpr int kPermThreads = 256;
+
+__global__ void __launch_bounds__(kPermThreads) k_perm_count(const uint32_t *__restrict__ rnd,
+                                                             const uint32_t *__restrict__ src, uint32_t m, int sh,
+                                                             uint32_t *__restrict__ cnt)
+{
+    __shared__ uint32_t h[256];
+    const int t = threadIdx.x;
+    const uint32_t G = gridDim.x, c = blockIdx.x;
+    h[t] = 0;
+    __syncthreads();
+    const uint32_t lo = (uint32_t)((uint64_t)c * m / G), hi = (uint32_t)((uint64_t)(c + 1) * m / G);
+    for (uint32_t i = lo + t; i < hi; i += kPermThreads) {
+        const uint32_t id = src ? __ldg(&src[i]) : i;
+        atomicAdd(&h[(__ldg(&rnd[id]) >> sh) & 255u], 1u);
+    }
+    __syncthreads();
+    cnt[(size_t)t * G + c] = h[t];
+}
+
+// Exclusive scan of the 256 x G counts in place (digit-major): one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_perm_scan(uint32_t *cnt, uint32_t total)
+{
+    __shared__ uint32_t ws[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const uint32_t per = (total + 1023u) / 1024u;
+    const uint32_t b = (uint32_t)t * per, e = min(total, b + per);
+    uint32_t s = 0;
+    for (uint32_t i = b; i < e; i++) s += cnt[i];
+    uint32_t inc = warp_incl_scan(s);
+    if (lane == 31) ws[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t v = ws[lane];
+        ws[lane] = warp_incl_scan(v) - v;
+    }
+    __syncthreads();
+    uint32_t run = ws[w] + inc - s;
+    for (uint32_t i = b; i < e; i++) {
+        const uint32_t v = cnt[i];
+        cnt[i] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(kPermThreads) k_perm_scatter(const uint32_t *__restrict__ rnd,
+                                                               const uint32_t *__restrict__ src, uint32_t m, int sh,
+                                                               const uint32_t *__restrict__ cnt,
+                                                               uint32_t *__restrict__ dst)
+{
+    constexpr int W = kPermThreads / 32;
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wc[W][256];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const uint32_t G = gridDim.x, c = blockIdx.x;
+    const uint32_t lt = (1u << lane) - 1u;
+    base[t] = cnt[(size_t)t * G + c];
+    const uint32_t lo = (uint32_t)((uint64_t)c * m / G), hi = (uint32_t)((uint64_t)(c + 1) * m / G);
+    for (uint32_t i0 = lo; i0 < hi; i0 += kPermThreads) {
+        const uint32_t i = i0 + t;
+        const bool valid = i < hi;
+        const uint32_t id = valid ? (src ? __ldg(&src[i]) : i) : 0u;
+        const uint32_t dg = valid ? (__ldg(&rnd[id]) >> sh) & 255u : 256u;
+        for (int q = t; q < W * 256; q += kPermThreads) (&wc[0][0])[q] = 0;
+        __syncthreads();
+        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        if (valid && (peers & lt) == 0) wc[w][dg] = (uint32_t)__popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t o = base[dg] + (uint32_t)__popc(peers & lt);
+            for (int v = 0; v < w; v++) o += wc[v][dg];
+            dst[o] = id;
         }
         __syncthreads();
-        const uint32_t in_key = s_in_key, out_key = s_out_key;
-        auto to_band = [&](uint32_t qi, uint32_t k) {
-            const uint32_t slot = atomicAdd(&ctl->band_cnt[par], 1u);
-            a.band_k32[slot] = k;
-            a.band_pos[slot] = LID(qi);
-        };
-        // keys from shared memory: 4 per thread at a time; from global memory: kCB
-        uint32_t n_in = kc ? classify_keys<4>(n_live, in_key, out_key, [&](uint32_t qi) { return skey[qi]; }, to_band)
-                           : classify_keys<kCB>(n_live, in_key, out_key,
-                                                [&](uint32_t qi) { return __ldcg(&a.kpos[s0 + qi]); }, to_band);
-        n_in = block_sum(n_in);
-        if (t == 0) ctl->cnt_in[c] = n_in;
-        if (!grid_sync(ctl, a.flags, gen)) return;
-
-        // ---- D: settle the band, take the subcluster, next landmark
-        // the per-CTA counts, the band's size and its first entries in one round trip
-        const uint32_t nb = __ldcg(&ctl->band_cnt[par]);
-        uint32_t sk[kBandStage / kThreads], sp[kBandStage / kThreads];
+        uint32_t add = 0;
 #pragma unroll
-        for (int r = 0; r < kBandStage / kThreads; r++) {
-            const uint32_t q = t + r * kThreads;
-            sk[r] = q < n ? __ldcg(&a.band_k32[q]) : 0u;
-            sp[r] = q < n ? __ldcg(&a.band_pos[q]) : 0u;
-        }
-        uint32_t all_in, in_before;
-        {
-            uint32_t va = 0, vb = 0, e0, e1;
-            for (uint32_t q = t; q < G; q += kThreads) {
-                const uint32_t v = __ldcg(&ctl->cnt_in[q]);
-                va += v;
-                if (q < c) vb += v;
-            }
-            block_excl_scan2(va, vb, e0, e1, all_in, in_before);
-        }
-        const bool staged = nb <= (uint32_t)kBandStage;
-        if (staged) {
-#pragma unroll
-            for (int r = 0; r < kBandStage / kThreads; r++) {
-                const uint32_t q = t + r * kThreads;
-                if (q < nb) {
-                    s_bk[q] = sk[r];
-                    s_bp[q] = sp[r];
-                }
-            }
-            __syncthreads();
-        }
-        auto BK = [&](uint32_t q) { return staged ? s_bk[q] : __ldcg(&a.band_k32[q]); };
-        auto BP = [&](uint32_t q) { return staged ? s_bp[q] : __ldcg(&a.band_pos[q]); };
-        const uint32_t need = N > all_in ? N - all_in : 0u;
-        if ((all_in > N || need > nb) && c == 0 && t == 0) atomicOr(&a.flags[1], 1u);
-        uint32_t lo = in_key, tout = 0, ntt = 0;       // the rule (see taken())
-        uint32_t band_before = 0;
-        bool slow = false;
-        if (need > 0 && need < nb) {
-            // Fast path, in shared memory (every CTA redundantly).  The need-th smallest
-            // float32 key T32 of the band comes from a one-ulp histogram; the float32 error
-            // bound around T32 leaves a tight set of a few entries; their distances in
-            // compensated float32 (dff, within eps_ff of the float64 definition) settle all
-            // of them but those within the dff error of the cut-off (in practice only exact
-            // ties), which are decided in float64.
-            const uint32_t range = out_key - in_key + 1u;
-            // the tight set spans about 2(d+4) of the band's `range` one-ulp keys: when the
-            // band is dense enough that it would hold over twice kTight entries, the fast
-            // path cannot succeed and is skipped (a choice of path, not of result)
-            slow = range > (uint32_t)kBandBins ||
-                   (uint64_t)nb * (uint64_t)(2 * (d + 4)) > (uint64_t)(2 * kTight) * range;
-            if (!slow) {
-                for (int b = t; b < kBandBins; b += kThreads) hb[b] = 0;
-                if (t == 0) {
-                    s_nt = 0;
-                    s_na = 0;
-                }
-                __syncthreads();
-                for (uint32_t q = t; q < nb; q += kThreads) atomicAdd(&hb[BK(q) - in_key], 1u);
-                __syncthreads();
-                {   // the one-ulp bin of the need-th smallest band key
-                    constexpr int per = kBandBins / kThreads;
-                    uint32_t loc = 0;
-#pragma unroll
-                    for (int q = 0; q < per; q++) loc += hb[t * per + q];
-                    uint32_t tot;
-                    const uint32_t before = block_excl_scan(loc, tot);
-                    const uint32_t target = need - 1;
-                    if (target >= before && target < before + loc) {
-                        uint32_t cc = before;
-                        for (int q = 0; q < per; q++) {
-                            const uint32_t h = hb[t * per + q];
-                            if (target >= cc && target < cc + h) s_t32 = in_key + (uint32_t)(t * per + q);
-                            cc += h;
-                        }
-                    }
-                }
-                __syncthreads();
-                uint32_t tin, tt;
-                band_cutoffs_key(s_t32, s_t32, d, tin, tt);
-                uint32_t n_cert = 0, cert_before = 0;
-                for (uint32_t q = t; q < nb; q += kThreads) {
-                    const uint32_t k = BK(q);
-                    const uint32_t pq = BP(q);
-                    if (k < tin) {
-                        n_cert++;
-                        cert_before += pq < s0;
-                    } else if (k <= tt) {
-                        const uint32_t slot = atomicAdd(&s_nt, 1u);
-                        if (slot < (uint32_t)kTight) tpos[slot] = pq;
-                    }
-                }
-                n_cert = block_sum(n_cert);
-                const uint32_t nt = s_nt;
-                slow = nt > (uint32_t)kTight || n_cert > need || need - n_cert > nt;
-                if (!slow) {
-                    const uint32_t need2 = need - n_cert;
-                    for (uint32_t q = t; q < nt; q += kThreads) {
-                        float h, l;
-                        dist_ff(a.x + (size_t)tpos[q] * d, Ls, d, h, l);
-                        th[q] = h;
-                        tl[q] = l;
-                    }
-                    __syncthreads();
-                    // V: the tight entry of rank need2-1 in (dff, index) order
-                    for (uint32_t q = t; q < nt; q += kThreads) {
-                        uint32_t rk = 0;
-                        for (uint32_t o = 0; o < nt; o++)
-                            rk += (uint32_t)((th[o] < th[q]) |
-                                             ((th[o] == th[q]) & ((tl[o] < tl[q]) | ((tl[o] == tl[q]) & (tpos[o] < tpos[q])))));
-                        if (rk == need2 - 1) s_v = q;
-                    }
-                    __syncthreads();
-                    // the need2-th smallest delta64 lies within eps*hv of hv (order statistics
-                    // move by at most the per-entry error); an entry is decided if its own
-                    // error cannot bridge the gap (plus an absolute floor against underflow)
-                    const float hv = th[s_v], lv = tl[s_v];
-                    const float win = 2.0f * eps_ff(d) * hv + 0x1p-120f;
-                    uint32_t n_take = 0;
-                    for (uint32_t q = t; q < nt; q += kThreads) {
-                        const float diff = __fadd_rn(__fsub_rn(th[q], hv), __fsub_rn(tl[q], lv));
-                        const uint32_t cls = diff < -win ? 1u : 0u;
-                        if (diff >= -win && diff <= win) {
-                            const uint32_t slot = atomicAdd(&s_na, 1u);
-                            tamb[slot] = q;
-                        }
-                        n_take += cls;
-                        tcls[q] = cls;
-                    }
-                    n_take = block_sum(n_take);
-                    const uint32_t na = s_na;
-                    const uint32_t need3 = need2 >= n_take ? need2 - n_take : 0u;
-                    if (need3 > na && t == 0) atomicOr(&a.flags[1], 1u);
-                    if (need3 >= na) {
-                        for (uint32_t q = t; q < na; q += kThreads) tcls[tamb[q]] = 1u;
-                    } else if (need3 > 0) {
-                        for (uint32_t q = t; q < na; q += kThreads)
-                            td[q] = (unsigned long long)__double_as_longlong(dist64(a.x + (size_t)tpos[tamb[q]] * d, Ls, d));
-                        __syncthreads();
-                        for (uint32_t q = t; q < na; q += kThreads) {
-                            const unsigned long long kq = td[q];
-                            const uint32_t pq = tpos[tamb[q]];
-                            uint32_t rk = 0;
-                            for (uint32_t o = 0; o < na; o++) rk += (td[o] < kq) || (td[o] == kq && tpos[tamb[o]] < pq);
-                            tcls[tamb[q]] = rk < need3 ? 1u : 0u;
-                        }
-                    }
-                    lo = max(in_key, tin);
-                    tout = tt;
-                    ntt = nt;
-                }
-                __syncthreads();
-                if (!slow) {                       // taken band points before the slice
-                    band_before = cert_before;
-                    for (uint32_t q = t; q < nt; q += kThreads) band_before += tcls[q] != 0 && tpos[q] < s0;
-                }
-            }
-            if (slow) {
-                // wide band (e.g. many equal distances): float64 for every band entry, spread
-                // evenly over all CTAs (entry q on CTA q mod G: the float64 pipe is the
-                // bound), then one CTA selects while the rest wait
-                for (uint32_t q = t * G + c; q < nb; q += G * kThreads) {
-                    const uint32_t pq = __ldcg(&a.band_pos[q]);
-                    a.band_key[q] = (uint64_t)__double_as_longlong(dist64(a.x + (size_t)pq * d, Ls, d));
-                }
-                if (!grid_sync(ctl, a.flags, gen)) return;
-                uint64_t K = 0;
-                uint32_t Pp = 0;
-                if (c == 0) {
-                    // the band's float64 keys, the fast path's arrays and the key cache are
-                    // no longer needed here: the selection may use that shared memory
-                    if (!select_band_fast(a.band_key, a.band_pos, nb, need, dyn, K, Pp))
-                        select_band_global(a.band_key, a.band_pos, nb, need, K, Pp);
-                    if (t == 0) {
-                        ctl->sel_key = K;
-                        ctl->sel_pos = Pp;
-                    }
-                }
-                if (!grid_sync(ctl, a.flags, gen)) return;
-                K = __ldcg(&ctl->sel_key);
-                Pp = __ldcg(&ctl->sel_pos);
-                for (uint32_t q0 = t; q0 < nb; q0 += kSelBatch * kThreads) {
-                    uint64_t kq[kSelBatch];
-                    uint32_t pq[kSelBatch];
-#pragma unroll
-                    for (int u = 0; u < kSelBatch; u++) {
-                        const uint32_t q = q0 + u * kThreads;
-                        kq[u] = q < nb ? __ldcg(&a.band_key[q]) : ~0ull;
-                        pq[u] = q < nb ? __ldcg(&a.band_pos[q]) : n;
-                    }
-#pragma unroll
-                    for (int u = 0; u < kSelBatch; u++) {
-                        if (kq[u] < K || (kq[u] == K && pq[u] <= Pp)) {
-                            if (pq[u] < s0) band_before++;
-                            else if (pq[u] < s1) a.key[pq[u]] = kTaken;
-                        }
-                    }
-                }
-                lo = in_key;
-                tout = 0;
-                ntt = 0;
-            }
-        } else if (need > 0) {
-            lo = out_key + 1u;      // need >= nb: the whole band is taken (need > nb is flagged)
-            for (uint32_t q = t; q < nb; q += kThreads) band_before += BP(q) < s0;
-        }
-        const Rule R{lo, tout, ntt, tpos, tcls};
-        band_before = block_sum(band_before);       // its barriers also publish the kTaken marks
-        // take the subcluster: ids in ascending order to the segment, the rest stay listed;
-        // a taken point is marked removed and leaves the live count of its d buckets
-        // (with landmark-only CTAs they do that bookkeeping in the next round's phase A)
-        n_live -= compact_list(LID, n_live, seg_out + in_before + band_before, kc ? sid : a.lidx + (size_t)(par ^ 1) * n + s0,
-                               [&](uint32_t qi, uint32_t id) {
-                                   uint32_t k = kc ? skey[qi] : __ldcg(&a.kpos[s0 + qi]);
-                                   // a wide band marks its taken points in key[] by id: only a
-                                   // key inside the band needs that look-up
-                                   if (slow && k >= in_key && k <= out_key) k = __ldcg(&a.key[id]);
-                                   return taken(R, k, id);
-                               },
-                               [&](uint32_t id) {
-                                   if (Gl == 0) {
-                                       a.key[id] = kGone;
-                                       drop_buckets<D>(a.x, d, id, a.bcs, nbk);
-                                   }
-                               });
-
-        // next landmark.  Bucket live counts are upper bounds (this round's removals are
-        // not counted yet), and a point counts as left only if it is neither marked removed
-        // nor taken by this round's rule (a key read before or after its owner marks it
-        // gives the same answer).  After a wide band its kTaken marks are published first.
-        if (slow && !grid_sync(ctl, a.flags, gen)) return;
-        const Rule &RL = R;
-        for (int j = lm_first; j >= 0 && j < d; j += lm_step) {
-            const uint4 *bj = a.bcs + (size_t)j * nbk;
-            const uint32_t *oj = a.ord + (size_t)j * a.ord_ld;
-            uint32_t b = __ldcg(&ctl->lptr[j]);       // the buckets before b hold no point left
-            uint32_t mnb = kGone;
-            while (b < nbk) {
-                // the first bucket from b on with a live count
-                const uint32_t bb = b + (uint32_t)t;
-                const uint4 e = bb < nbk ? __ldcg(&bj[bb]) : make_uint4(0u, 0u, 0u, 0u);
-                uint32_t fb = warp_min(e.x > 0 ? bb : kGone);
-                if (lane == 0) red_a[w] = fb;
-                __syncthreads();
-                fb = red_a[0];
-#pragma unroll
-                for (int q = 1; q < W; q++) fb = min(fb, red_a[q]);
-                if (bb == fb) {
-                    s_st = e.y;
-                    s_en = e.z;
-                }
-                __syncthreads();
-                if (fb == kGone) {
-                    b += kThreads;
-                    continue;
-                }
-                // the smallest value among its entries left
-                const uint32_t st = s_st, en = s_en;
-                uint32_t lm = kGone;
-                for (uint32_t q = st + t; q < en; q += kThreads) {
-                    const uint32_t id = __ldcg(&oj[q]);
-                    const uint32_t k = __ldcg(&a.key[id]);
-                    const uint32_t xv = __float_as_uint(__ldg(&a.x[(size_t)id * d + j]));
-                    if (k != kGone && !taken(RL, k, id)) lm = min(lm, xv);
-                }
-                lm = warp_min(lm);
-                if (lane == 0) red_b[w] = lm;
-                __syncthreads();
-                lm = red_b[0];
-#pragma unroll
-                for (int q = 1; q < W; q++) lm = min(lm, red_b[q]);
-                __syncthreads();
-                if (lm != kGone) {
-                    mnb = lm;
-                    b = fb;
-                    break;
-                }
-                b = fb + 1;                            // every entry of fb is gone
-            }
-            if (t == 0) {
-                ctl->lptr[j] = b;
-                ctl->Lbits[par ^ 1][j] = mnb == kGone ? kInfBits : mnb;
-            }
-        }
-        if (!grid_sync(ctl, a.flags, gen)) return;
+        for (int v = 0; v < W; v++) add += wc[v][t];
+        base[t] += add;
+        __syncthreads();
     }
 }
 
@@ -1412,11 +1710,15 @@ cudaError_t peel_launch(const PeelBuffers &b, int64_t n, int d, int64_t N, int s
                         cudaStream_t st, KTimer *kt)
 {
     const int64_t S = (n + N - 1) / N;
-    // all control state starts cleared; round 0's landmark is the origin (the scaled
-    // minimum of every attribute is exactly 0)
+    // all control state starts cleared; the first landmark is the origin (the scaled
+    // minimum of every attribute is exactly 0); no point has a round yet
     cudaError_t e = cudaMemsetAsync(b.ctl, 0, sizeof(PeelCtl), st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(b.bcnt, 0, (size_t)d * b.nbuckets * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(b.rnd, 0xFF, (size_t)n * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(b.pflag, kFlNone, (size_t)n, st);
     if (e != cudaSuccess) return e;
     const size_t smem = kPeelDynWords * sizeof(uint32_t);
     e = cudaFuncSetAttribute(k_peel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1435,7 +1737,8 @@ cudaError_t peel_launch(const PeelBuffers &b, int64_t n, int d, int64_t N, int s
     a.n = n;
     a.N = N;
     a.S = S;
-    a.key = b.key;
+    a.rnd = b.rnd;
+    a.pflag = b.pflag;
     a.ord = b.ord;
     a.bcnt = b.bcnt;
     a.bcs = b.bcs;
@@ -1443,13 +1746,18 @@ cudaError_t peel_launch(const PeelBuffers &b, int64_t n, int d, int64_t N, int s
     a.kpos = b.kpos;
     a.ord_ld = b.ord_ld;
     a.nbk = b.nbuckets;
-    a.band_key = b.band_key;
     a.band_k32 = b.band_k32;
     a.band_pos = b.band_pos;
-    a.perm = b.perm;
+    a.gkey = b.gkey;
+    a.gpos = b.gpos;
+    a.akey = b.akey;
+    a.apos = b.apos;
     a.landmarks = b.landmarks;
     a.ctl = b.ctl;
     a.flags = b.flags;
+    a.kmax = (uint32_t)(b.rounds_per_pass > 0 ? std::min(b.rounds_per_pass, kMaxEpoch) : kDefaultRounds);
+    a.spin = b.wait_limit ? b.wait_limit : kDefaultSpin;
+    a.stall = b.stall_first_barrier ? 1u : 0u;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kThreads);
@@ -1463,6 +1771,23 @@ cudaError_t peel_launch(const PeelBuffers &b, int64_t n, int d, int64_t N, int s
     kt->begin(st);
     e = cudaLaunchKernelEx(&cfg, k_peel<D>, a);
     kt->end(PSCL_K_PEEL, st);
+    if (e != cudaSuccess) return e;
+    // the subclusters packed by round: a stable counting sort, 8 bits of the round per pass
+    int passes = 1;
+    while (passes < 4 && (S - 1) >> (8 * passes)) passes++;
+    const int pg = perm_grid(n, sm_count);
+    const uint32_t m = (uint32_t)n;
+    const uint32_t *src = nullptr;
+    for (int p = 0; p < passes; p++) {
+        uint32_t *dst = ((passes - 1 - p) & 1) ? b.gpos : b.perm;
+        kt->begin(st);
+        k_perm_count<<<pg, kPermThreads, 0, st>>>(b.rnd, src, m, 8 * p, b.pcnt);
+        k_perm_scan<<<1, 1024, 0, st>>>(b.pcnt, (uint32_t)(256 * pg));
+        k_perm_scatter<<<pg, kPermThreads, 0, st>>>(b.rnd, src, m, 8 * p, b.pcnt, dst);
+        kt->end(PSCL_K_GATHER, st);
+        src = dst;
+    }
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_gather(b.x, b.perm, n, d, b.xseg, sm_count, st, kt);
 }
@@ -1490,6 +1815,13 @@ uint32_t peel_buckets(int64_t n)
     uint32_t nb = 4096;
     while (nb < 65536u && (int64_t)nb * 16 < n) nb <<= 1;
     return nb;
+}
+
+int perm_grid(int64_t n, int sm_count)
+{
+    int64_t g = (n + 2047) / 2048;
+    if (g > (int64_t)sm_count * 4) g = (int64_t)sm_count * 4;
+    return (int)std::max<int64_t>(1, g);
 }
 
 cudaError_t launch_peel(const PeelBuffers &b, int64_t n, int d, int64_t N, int sm_count,

@@ -18,18 +18,32 @@ constexpr int kFixShift = 32;        // fixed-point scale 2^32 of the centroid s
 
 constexpr int kMaxPeelGrid = 2048;   // CTAs of the persistent peel launch
 
+// Rounds one peel epoch may select from one set of distances (boundaries per epoch).
+constexpr int kMaxEpoch = 16;
+
 // Device-resident control block of one persistent peel launch (cleared before it).
 struct PeelCtl {
-    uint32_t hist[2][2][kHistBins];  // [round parity][digit level][bin]
-    uint32_t ghist[2][kHistBins];    // [round parity][bin]: second digit inside the guessed first
-    uint32_t Lbits[2][kMaxD];        // landmark of this / next round (float bits)
-    uint32_t lptr[kMaxD];            // per attribute: buckets in front of it hold no remaining point
-    uint32_t cnt_in[kMaxPeelGrid];   // per CTA: points certainly taken this round
-    uint32_t band_cnt[2];            // band entries of this / next round
-    uint32_t bar_count;              // grid barrier: arrivals since the launch
-    uint32_t abort;                  // set when a barrier wait gave up
-    uint32_t sel_pos;                // large-band selection threshold (key, position)
-    unsigned long long sel_key;
+    uint32_t h0[kHistBins];              // first digit (key bits 31..21) of the live keys
+    uint32_t h1[kMaxEpoch][kHistBins];   // second digit (bits 20..10) inside each boundary's bin
+    uint32_t Lbits[kMaxD];               // landmark of the current epoch (float bits)
+    uint32_t lptr[kMaxD];                // per attribute: buckets in front of it hold no remaining point
+    uint32_t chold[kMaxD];               // live points whose attribute j equals L_j
+    uint32_t hcnt[kMaxD][kMaxEpoch];     // of those, the ones assigned to each round of the epoch
+    uint32_t cert[kMaxEpoch];            // points certainly in each round of the epoch
+    uint32_t bnd[kMaxEpoch];             // band points settled into each round of the epoch
+    uint32_t gcnt[kMaxEpoch];            // band entries of each group of boundaries
+    uint32_t gfill[kMaxEpoch];           // of those, regrouped into the group's region so far
+    uint32_t g_in[kMaxEpoch], g_out[kMaxEpoch];   // a group's band: keys in [g_in, g_out]
+    uint32_t g_q1[kMaxEpoch], g_q2[kMaxEpoch];    // a group's first and last boundary
+    uint32_t n_slots;                    // first-digit bins with a second-digit histogram
+    uint32_t n_groups;
+    uint32_t band_cnt;                   // band entries listed this epoch
+    uint32_t k_commit;                   // rounds the epoch commits
+    uint32_t l_changed;                  // the landmark changes after them
+    uint32_t bar_count;                  // grid barrier: arrivals since the launch
+    uint32_t abort;                      // set when a barrier wait gave up
+    uint32_t epochs;                     // statistics: epochs run,
+    uint32_t passes;                     //   distance passes over the points left
 };
 
 // Job flags read by the host at every synchronisation.
@@ -107,25 +121,35 @@ cudaError_t launch_seg_scale(const float *raw, float *x, const SegTable &t, cons
 // peel.cu
 struct PeelBuffers {
     const float *x;                  // n x d scaled points
-    uint32_t *key;                   // n: float32 distance key of each point (removed: all ones)
+    uint32_t *rnd;                   // n: round (subcluster) of each point, all ones while unassigned
+    uint8_t *pflag;                  // 2 x n: per CTA slice, a state byte per list position
     uint32_t *ord;                   // d x ord_ld: point ids of each attribute in bucket order
     uint32_t *bcnt;                  // d x nbuckets: bucket counts, then scatter cursors
     uint4 *bcs;                      // d x nbuckets: (points left, first entry, end entry, 0)
-    uint32_t *lidx;                  // 2 x n: per CTA slice, the ids of its points left
-    uint32_t *kpos;                  // n: per CTA slice, the round's keys by list position
+    uint32_t *lidx;                  // 2 x n: per CTA slice, the ids of its points left (two lists)
+    uint32_t *kpos;                  // 2 x n: per CTA slice, the keys of its points left by list position
     int64_t ord_ld;                  // n rounded up to a multiple of 4
     uint32_t nbuckets;               // power of two, 4096 .. 65536
-    uint64_t *band_key;              // float64 distance bits of band points (wide bands)
-    uint32_t *band_k32;              // float32 keys of band points
-    uint32_t *band_pos;              // their point ids
+    uint32_t *band_k32;              // n: float32 keys of the epoch's band entries
+    uint32_t *band_pos;              // n: their point ids
+    uint64_t *gkey;                  // n: band entries regrouped by group (compensated distances)
+    uint32_t *gpos;                  //    and their ids; the counting sort's second buffer afterwards
+    uint64_t *akey;                  // n: entries near a group's cut-off (float64 distances)
+    uint32_t *apos;                  //    and their ids
+    uint32_t *pcnt;                  // 256 x perm_grid(n): counting-sort counts
     float *landmarks;                // all landmarks (S x d), for inspection
     uint32_t *perm;                  // n: subcluster-packed original indices
     float *xseg;                     // n x d: subcluster-packed points
     PeelCtl *ctl;
     uint32_t *flags;
+    int rounds_per_pass;             // rounds one distance pass may serve (1..kMaxEpoch; 0: default)
+    uint32_t wait_limit;             // polls of a bounded wait before it gives up (0: default)
+    int stall_first_barrier;         // test hook: the first grid barrier waits for one CTA too many
 };
 // Buckets of the per-attribute orders the peel builds for n points.
 uint32_t peel_buckets(int64_t n);
+// CTAs of the counting sort that packs the subclusters after the peel (pcnt: 256 x this).
+int perm_grid(int64_t n, int sm_count);
 // Rows of x in the order of perm, packed into xseg (the gather after any subclustering).
 cudaError_t launch_gather(const float *x, const uint32_t *perm, int64_t n, int d, float *xseg, int sm_count,
                           cudaStream_t st, KTimer *kt);
