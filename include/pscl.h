@@ -132,6 +132,8 @@ typedef enum {
     PSCL_K_LLOYD_ASSIGN,     /* nearest center + fixed-point sums                */
     PSCL_K_LLOYD_FINALIZE,   /* centers = sums / counts                          */
     PSCL_K_FINAL_SSE,        /* nearest final center and SSE of every point      */
+    PSCL_K_LLOYD_SUMS,       /* after a tensor-core assignment: near ties
+                                re-decided in float32, fixed-point sums          */
     PSCL_K_COUNT
 } pscl_kernel;
 

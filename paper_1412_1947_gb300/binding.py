@@ -83,7 +83,7 @@ class JobDesc(C.Structure):
 
 
 KERNELS = ["scale_minmax", "scale_apply", "peel", "gather", "lloyd_init", "lloyd_assign", "lloyd_finalize",
-           "final_sse"]
+           "final_sse", "lloyd_sums"]
 
 _lib = None
 

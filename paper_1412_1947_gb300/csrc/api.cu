@@ -778,6 +778,8 @@ static int run_lloyd(pscl_job *j, const LloydPlan &p, const float *pts, float *c
     b.trace = trace;
     b.rows = p.rows;
     b.weights = weights;
+    b.wait_limit = j->wait_limit;
+    b.tc_stall = j->test_stall == 2;
     CU(launch_lloyd_init(b, t, j->d, p.P, seed, stage, j->first_k, p.kmax, st, &j->kt));
     if (!plain) {
         for (int it = 0; it < iters; it++) {

@@ -106,10 +106,7 @@ __device__ __forceinline__ float dist_direct(const float *x, const float *c, int
     return acc;
 }
 
-__device__ __forceinline__ unsigned long long to_fix(float v)
-{
-    return (unsigned long long)__float2ll_rn(v * kFix);
-}
+__device__ __forceinline__ unsigned long long to_fix(float v) { return fix_of(v); }
 
 // Squared distances of R rows (registers) to one center (shared memory), float32
 // direct form, ascending attributes; the center is read as float4 when D % 4 == 0.
@@ -622,8 +619,9 @@ cudaError_t launch_lloyd_iter(const LloydBuffers &b, int32_t *count_next, const 
                               KTimer *kt, int rows_per_thread)
 {
     cudaError_t e;
-    if (prec != PSCL_PREC_FP32 && !b.weights && tc_supported(d, kmax, prec)) {
-        e = launch_lloyd_assign_tc(b, t, d, iter, unit_lo, unit_hi, kmax, prec, flags, sm_count, st, kt);
+    if (prec != PSCL_PREC_FP32 && !b.weights && t.split && unit_lo == 0 && unit_hi == t.n_units &&
+        tc_supported(d, kmax, prec)) {
+        e = launch_lloyd_assign_tc(b, t, d, iter, kmax, prec, flags, sm_count, st, kt);
     } else switch (d) {
     case 2: e = assign_dispatch<2>(b, t, d, iter, unit_lo, unit_hi, kmax, rows_per_thread, st, kt); break;
     case 4: e = assign_dispatch<4>(b, t, d, iter, unit_lo, unit_hi, kmax, rows_per_thread, st, kt); break;

@@ -1,33 +1,41 @@
-// Lloyd assignment step on the 5th-generation tensor cores (tcgen05, sm_103a).
+// Lloyd assignment step on the 5th-generation tensor cores (tcgen05, sm_103a): the
+// "nearest center" of §I for every point of every set, as a contraction.
 //
-// For a tile of 128 rows x and the k centers c of their set, with every coordinate
+// For a tile of 128 rows x and the k <= 256 centers c of their set, with coordinates
 // centred on a per-set reference point r (x~ = x - r, c~ = c - r; distances unchanged),
 //     v_j = ||c~_j||^2 - 2 x~ . c~_j        (= ||x - c_j||^2 - ||x~||^2)
-// is one MMA over K: A = [x~ terms, 1 ...] (128 x K), B = [-2 c~ terms, n parts] (k x K),
-// with n parts summing to ||c~_j||^2 (split so that they survive the operand rounding).
-// Modes (pscl_prec):
-//   TF32    A = [x~], B = [-2c~]                     (one product per attribute)
-//   BF16    likewise with BF16 operands
-//   TF32X3  x~ = h + l, c~ = H + L split into TF32 parts: A = [h, h, l], B = [-2H, -2L, -2H]
-//           so one MMA sums h.H + h.L + l.H (error ~2^-21 per product instead of ~2^-10)
-//   BF16X3  likewise with BF16 parts (error ~2^-17 per product)
-// The accumulator is float32 in tensor memory.  Each of the 128 threads owns one row (one
-// TMEM lane), reads its k accumulators with tcgen05.ld and keeps the best and second best.
+// is accumulated in float32 in tensor memory.  Operand modes (pscl_prec):
+//   TF32 / BF16       A = [x~ | 1 ...], B = [-2c~ | n parts]  (one product per attribute)
+//   TF32X3 / BF16X3   x~ = h + l and -2c~ = H + L split into two parts of the type; the MMAs
+//                     add h.H + h.L + l.H (error ~2^-21 / 2^-17 per product instead of
+//                     ~2^-10 / 2^-8)
+// where the n parts sum to ||c~_j||^2 (split so that they survive the operand rounding).
 //
-// Near ties: |v_j - exact| <= E = alpha ||x~|| cmax + beta cmax^2 (operand rounding,
-// float32 accumulation over K terms, centring and norm errors; cmax = max_j ||c~_j||), plus
-// the float32 error of a direct distance.  Every center within 2E of the best is re-scored
-// with the float32 direct sum (x_i - c_ji)^2 -- the PSCL_PREC_FP32 arithmetic -- and the
-// smallest, lowest index on ties, wins.  No center outside that set can win the float32
-// direct comparison, so the labels equal those of the float32 direct path in every mode.
+// Near ties.  |v_j - exact| <= E = alpha ||x~|| cmax + beta cmax^2 (operand rounding,
+// float32 accumulation, centring and norm errors; cmax = max_j ||c~_j||), plus the float32
+// error of a direct distance.  A row whose second-best v lies within 2E of its best could
+// be won by another center in the float32 direct comparison of the PSCL_PREC_FP32 path;
+// such a row is marked (bit 31 of its label) and re-decided by k_tc_sums with the float32
+// direct sum over all centers, lowest index on ties.  Every other row's best is the float32
+// direct winner, so the labels equal those of the float32 path in every mode.
 //
-// Operands are written to shared memory by the threads in the canonical K-major layout
-// without swizzle (8-row x 16-byte core matrices; the K-adjacent ones of a row group are
-// contiguous, LBO = 128 bytes; row groups are SBO = K * element bytes apart).  Tiles are
-// pipelined two deep: the operands and MMA of tile i+1 are issued before the epilogue of
-// tile i (two operand buffers, two TMEM regions, two mbarriers).  One thread issues the
-// MMAs and commits them to an mbarrier that every thread waits on with a bounded spin.
-// The centroid sums are the same exact fixed-point sums as in the float32 path.
+// The assignment kernel is persistent (contiguous unit ranges per CTA) and warp-specialised:
+//   * producer warp: one thread streams 128-row tiles of the float32 points into shared
+//     memory with cp.async.bulk.tensor (a tensor map over the packed points, rows of d
+//     floats, boxes of 128 rows x min(d, 32) attributes with the bank swizzle that fits);
+//   * converter warps (128 threads, a row each): centre the row, split it into the mode's
+//     parts and write operand A in the canonical K-major layout (8-row x 16-byte core
+//     matrices, no swizzle), with ||x~|| for the epilogue; at the start of each set they
+//     build operand B from the set's centers;
+//   * MMA warp: one thread issues the tcgen05.mma of a tile into one of two TMEM
+//     accumulators and commits them to mbarriers (operand A free, accumulator full);
+//   * two epilogue warpgroups, one per accumulator: each thread reads its row's k values
+//     with tcgen05.ld and keeps the best and second best; it writes the label.
+// Stages are handed over with mbarriers; every wait is bounded and a wait that runs out
+// aborts the CTA (after its copies and MMAs in flight have drained) and sets flags[1] bit 2.
+// The exact centroid sums are a separate pass (k_tc_sums), so the epilogue does only the
+// minimum.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -37,25 +45,117 @@
 namespace pscl {
 namespace {
 
-constexpr int kTcThreads = 128;           // one thread per TMEM lane / tile row
-constexpr int kTileRows = 128;            // MMA M
-constexpr unsigned kWaitLimit = 1u << 26; // bounded mbarrier polls
-constexpr float kFix = 4294967296.0f;
-constexpr size_t kTcSmemMax = 200 * 1024; // dynamic shared memory the kernel may use
+constexpr int kTileRows = 128;            // MMA M, rows per tile
+constexpr int kCvtWarp0 = 8;              // converter warps 8..11
+constexpr int kProdWarp = 12;
+constexpr int kMmaWarp = 13;
+constexpr int kTcThreads = 14 * 32;
+constexpr int kXStages = 2;               // float32 point tiles in flight
+constexpr int kAStages = 2;               // operand A buffers
+constexpr int kMeta = 8;                  // per-tile metadata ring (tiles in flight < kMeta)
+constexpr unsigned kDefaultWait = 1u << 26;
+constexpr size_t kTcSmemMax = 220 * 1024;
+constexpr uint32_t kTieBit = 0x80000000u; // label of a row left to the float32 re-scoring
 
 enum TcMode { kModeTf32 = 0, kModeBf16 = 1, kModeTf32x3 = 2, kModeBf16x3 = 3 };
 
-__device__ __forceinline__ unsigned long long to_fix(float v)
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// ---------------------------------------------------------------- mbarriers
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count)
 {
-    return (unsigned long long)__float2ll_rn(v * kFix);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count));
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
+__device__ __forceinline__ void mbar_arrive(uint32_t a)
 {
-    return (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, no swizzle.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done)
+                 : "r"(a), "r"(parity)
+                 : "memory");
+    return done != 0;
+}
+
+// Bounded wait for phase `parity` of the mbarrier at a.  Gives up when the CTA is aborting
+// (*abort set) or after `limit` polls, which starts the abort.  Returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, unsigned limit, volatile int *abort)
+{
+    for (unsigned it = 0;; it++) {
+        if (mbar_try(a, parity)) return true;
+        if ((it & 31u) == 31u) {
+            if (*abort) return false;
+            if (it > limit) {
+                *abort = 1;
+                return false;
+            }
+        }
+    }
+}
+
+// The same wait during clean-up: no abort check, only the limit.
+__device__ __forceinline__ void mbar_drain(uint32_t a, uint32_t parity, unsigned limit)
+{
+    for (unsigned it = 0; it <= limit; it++)
+        if (mbar_try(a, parity)) return;
+}
+
+// The converter warps' named barrier (id 1, 128 threads), returning the AND of `ok` over them.
+__device__ __forceinline__ bool cvt_bar_and(bool ok)
+{
+    uint32_t r;
+    asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.red.and.pred q, 1, 128, p;\n"
+                 " selp.u32 %0, 1, 0, q;\n}\n"
+                 : "=r"(r)
+                 : "r"((uint32_t)ok)
+                 : "memory");
+    return r != 0;
+}
+
+// ---------------------------------------------------------------- TMA
+// One box of the tensor map (x = attribute, y = row) into shared memory at dst; the bytes
+// complete a transaction on the mbarrier at mbar.  Coordinates: x is a multiple of 32
+// attributes (128 bytes), so it meets the 16-byte rule of tiled copies.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
+// ---------------------------------------------------------------- tensor memory
+// Columns [c, c + 32) of this warp's lanes, without waiting: tmem_wait() makes them usable.
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __host__ __forceinline__ uint32_t tmem_cols(int np)
+{
+    return np <= 32 ? 32u : (np <= 64 ? 64u : (np <= 128 ? 128u : 256u));
+}
+
+// Shared-memory matrix descriptor: K-major, no swizzle (version bit 46 of sm_100+).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
     return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
@@ -71,15 +171,15 @@ __device__ __forceinline__ float tf32_rna(float x)
 
 __device__ __forceinline__ float bf16_rn(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
+// ---------------------------------------------------------------- operand modes
 template <int MODE>
 struct Op {
     static constexpr bool kBf16 = MODE == kModeBf16 || MODE == kModeBf16x3;
-    static constexpr int kTerms = MODE >= kModeTf32x3 ? 3 : 1;    // operand blocks of D
+    static constexpr bool kSplit = MODE >= kModeTf32x3;
     static constexpr int kBytes = kBf16 ? 2 : 4;
-    static constexpr int kPerChunk = 16 / kBytes;
-    static constexpr int kMmaK = kBf16 ? 16 : 8;
+    static constexpr int kPerChunk = 16 / kBytes;          // elements per 16-byte core-matrix row
+    static constexpr int kMmaK = kBf16 ? 16 : 8;           // K of one MMA instruction
     static constexpr int kNormParts = kBf16 ? 3 : 2;
-    // operand rounding to this mode's type
     static __device__ __forceinline__ float rnd(float x) { return kBf16 ? bf16_rn(x) : tf32_rna(x); }
     // relative error of one product of the rounded / split operands
     static __device__ __forceinline__ float eta_p()
@@ -99,582 +199,803 @@ struct Op {
     }
 };
 
+// Operand rows: [first part (D) | second part (D, split modes) | ones / norm parts (kMmaK)].
 template <int D, int MODE>
 struct TcLayout {
     using O = Op<MODE>;
-    static constexpr int kUsed = O::kTerms * D + O::kNormParts;
-    static constexpr int kK = ((kUsed + O::kMmaK - 1) / O::kMmaK) * O::kMmaK;
-    static constexpr int kChunks = kK / O::kPerChunk;
-    static constexpr uint32_t kGroup = kChunks * 128;                    // bytes per 8-row group
+    static constexpr int kParts = O::kSplit ? 2 : 1;
+    static constexpr int kK = kParts * D + O::kMmaK;          // elements per operand row
+    static constexpr int kChunks = kK / O::kPerChunk;          // 16-byte core-matrix columns
+    static constexpr uint32_t kGroup = kChunks * 128;          // bytes per 8-row group (SBO)
     static constexpr uint32_t kABytes = (kTileRows / 8) * kGroup;
+    static constexpr int kXBoxCols = D < 32 ? D : 32;          // attributes per TMA box
+    static constexpr int kXBoxes = D / kXBoxCols;
+    static constexpr uint32_t kXBoxBytes = kTileRows * kXBoxCols * 4;
+    static constexpr uint32_t kXBytes = kXBoxes * kXBoxBytes;
+    // bank swizzle of the boxes: its span equals the box row (bytes), 16 .. 128
+    static constexpr int kSwzMask = kXBoxCols * 4 == 128 ? 7 : kXBoxCols * 4 == 64 ? 3 : kXBoxCols * 4 == 32 ? 1 : 0;
 };
 
-// Element e of an A row from the split parts of x~ (h, l) of this row.
+// Byte offset of 16-byte chunk c of row r in a point box (rows of kXBoxCols floats) after
+// the TMA bank swizzle: the chunk index is XORed with bits 7.. of the row's byte offset.
 template <int D, int MODE>
-__device__ __forceinline__ float a_elem(int e, const float *h, const float *l, bool live)
+__device__ __forceinline__ uint32_t xbox_off(int r, int c)
 {
-    using O = Op<MODE>;
-    if (e < D) return h[e];
-    if (O::kTerms == 3) {
-        if (e < 2 * D) return h[e - D];
-        if (e < 3 * D) return l[e - 2 * D];
-    }
-    if (e < O::kTerms * D + O::kNormParts) return live ? 1.0f : 0.0f;
-    return 0.0f;
+    using L = TcLayout<D, MODE>;
+    const uint32_t o = (uint32_t)r * (L::kXBoxCols * 4) + (uint32_t)c * 16;
+    return o ^ (((o >> 7) & (uint32_t)L::kSwzMask) << 4);
 }
 
-// Write one row of an operand (K elements from `elem`) as 16-byte chunks.
-template <int D, int MODE, class F>
-__device__ __forceinline__ void put_row(unsigned char *base, int row, F elem)
+// Byte offset of element e of row r in a K-major operand without swizzle.
+template <int D, int MODE>
+__device__ __forceinline__ uint32_t op_off(int r, int e)
 {
     using O = Op<MODE>;
     using L = TcLayout<D, MODE>;
-    unsigned char *rp = base + (size_t)(row >> 3) * L::kGroup + (row & 7) * 16;
-#pragma unroll
-    for (int c = 0; c < L::kChunks; c++) {
-        uint4 w;
-        if (O::kBf16) {
-            uint32_t v[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const __nv_bfloat16 lo = __float2bfloat16_rn(elem(c * 8 + 2 * q));
-                const __nv_bfloat16 hi = __float2bfloat16_rn(elem(c * 8 + 2 * q + 1));
-                v[q] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-            }
-            w = make_uint4(v[0], v[1], v[2], v[3]);
-        } else {
-            w = make_uint4(__float_as_uint(elem(c * 4 + 0)), __float_as_uint(elem(c * 4 + 1)),
-                           __float_as_uint(elem(c * 4 + 2)), __float_as_uint(elem(c * 4 + 3)));
-        }
-        *reinterpret_cast<uint4 *>(rp + c * 128) = w;
-    }
+    return (uint32_t)(r >> 3) * L::kGroup + (uint32_t)(e / O::kPerChunk) * 128 + (uint32_t)(r & 7) * 16 +
+           (uint32_t)(e % O::kPerChunk) * O::kBytes;
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
-{
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int q = 0; q < 32; q++) v[q] = __uint_as_float(r[q]);
-}
-
-// Bounded wait for the mbarrier phase `parity`; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
-{
-    for (unsigned it = 0; it < kWaitLimit; it++) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(mbar), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-// One thread: the K/kMmaK MMAs of a 128-row tile (A at a_smem, B at b_smem, D at TMEM
-// column dcol), then a commit that arrives on the mbarrier at mbar_smem when they finish.
+// Write 4 consecutive elements (e0 % 4 == 0) of row r of an operand.
 template <int D, int MODE>
-__device__ __forceinline__ void issue_mma(uint32_t dcol, uint32_t a_smem, uint32_t b_smem, uint32_t idesc,
-                                          uint32_t mbar_smem)
+__device__ __forceinline__ void put4(unsigned char *base, int r, int e0, float a, float b, float c, float d)
 {
-    using L = TcLayout<D, MODE>;
     using O = Op<MODE>;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-    for (int kb = 0; kb < L::kK / O::kMmaK; kb++) {
-        const uint64_t ad = smem_desc(a_smem + 2 * kb * 128, 128, L::kGroup);
-        const uint64_t bd = smem_desc(b_smem + 2 * kb * 128, 128, L::kGroup);
-        const uint32_t accum = kb > 0;
-        if (O::kBf16) {
-            asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                         ::"r"(dcol), "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
-        } else {
-            asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-                         ::"r"(dcol), "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
-        }
+    unsigned char *p = base + op_off<D, MODE>(r, e0);
+    if (O::kBf16) {
+        const uint32_t lo = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+                            ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+        const uint32_t hi = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(c)) |
+                            ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(d)) << 16);
+        *reinterpret_cast<uint2 *>(p) = make_uint2(lo, hi);
+    } else {
+        *reinterpret_cast<uint4 *>(p) = make_uint4(__float_as_uint(a), __float_as_uint(b), __float_as_uint(c),
+                                                   __float_as_uint(d));
     }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_smem));
 }
 
-__device__ __host__ __forceinline__ uint32_t tmem_cols(int np)
+
+// ---------------------------------------------------------------- the assignment kernel
+// Per-tile data the converters hand to the epilogue (a ring of kMeta entries).
+struct TileMeta {
+    float xn[kTileRows];         // ||x~|| of each row
+    float cmax;                  // max_j ||c~_j|| of the tile's set
+    int k;                       // centers of the set
+    int nvalid;                  // rows of the tile inside its run
+    int pad;
+    long long row0;              // packed row of the tile's first row
+};
+
+struct TcArgs {
+    const float *centers;
+    int32_t *labels;
+    SegTable t;
+    const int32_t *split;        // CTA c serves the units [split[c], split[c + 1])
+    uint32_t *flags;
+    unsigned wait_limit;
+    int stall;                   // test hook: wait once on a barrier nothing completes
+    int npmax;                   // operand B rows (centers rounded up to 16)
+    uint32_t ncols;              // TMEM columns of one accumulator
+};
+
+// A run: consecutive units of one set in a CTA's range, streamed as 128-row tiles.
+struct Run {
+    int s, k;
+    int64_t c0, row0;
+    int R, ntiles;
+};
+
+__device__ __forceinline__ bool next_run(const SegTable &t, int &u, int ue, Run &run)
 {
-    return np <= 32 ? 32u : (np <= 64 ? 64u : (np <= 128 ? 128u : 256u));
+    if (u >= ue) return false;
+    const int s = t.unit_seg[u];
+    int ur = u + 1;
+    while (ur < ue && t.unit_seg[ur] == s) ur++;
+    run.s = s;
+    run.k = t.k_eff[s];
+    run.c0 = t.cen_off[s];
+    run.row0 = t.seg_start[s] + t.unit_start[u];
+    run.R = t.unit_start[ur - 1] + t.unit_count[ur - 1] - t.unit_start[u];
+    run.ntiles = (run.R + kTileRows - 1) / kTileRows;
+    u = ur;
+    return true;
 }
 
-// The sums of a run are kept as two 32-bit halves of the 32.32 fixed-point value, q >> 16
-// (<= 2^16 for coordinates in [0, 1]) and q & 0xFFFF, so 32768 rows can be added before
-// either half could wrap; they are folded into the 64-bit global sums that often.
-constexpr int kFoldTiles = 32768 / kTileRows;
-
-__device__ __forceinline__ void flush_sums(uint32_t *shi, uint32_t *slo, int32_t *scnt, int k, int64_t c0,
-                                           unsigned long long *acc, int32_t *count, int dd)
-{
-    const int ds = dd | 1;
-    for (int e = threadIdx.x; e < k * dd; e += kTcThreads) {
-        const int c = e / dd, es = c * ds + (e - c * dd);
-        const unsigned long long v = ((unsigned long long)shi[es] << 16) + slo[es];
-        if (v) atomicAdd(&acc[c0 * dd + e], v);
-        shi[es] = 0u;
-        slo[es] = 0u;
-    }
-    for (int j = threadIdx.x; j < k; j += kTcThreads) {
-        const int v = scnt[j];
-        if (v) atomicAdd(&count[c0 + j], v);
-        scnt[j] = 0;
-    }
-}
-
-// One assignment step.  CTA c serves the units [split[c], split[c+1]) (a persistent
-// launch over all units) or the single unit unit_lo + c (split == NULL).  Its units form
-// runs of consecutive units of one set; per run the set's operand B, reference point and
-// sums are set up once and its rows stream through the tensor cores in 128-row tiles,
-// two deep when two TMEM regions of ncols columns fit (nbuf = 2), else one at a time.
 template <int D, int MODE>
-__global__ void __launch_bounds__(kTcThreads)
-k_lloyd_assign_tc(const float *__restrict__ pts, SegTable t, const int32_t *split, int unit_lo,
-                  const float *__restrict__ centers, unsigned long long *acc, int32_t *count, int32_t *labels,
-                  int32_t *trace, int64_t trace_off, int kmax, int nbuf, uint32_t ncols, int sacc, int scent,
-                  uint32_t *flags)
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_assign(const __grid_constant__ CUtensorMap xmap, const TcArgs p)
 {
-    using L = TcLayout<D, MODE>;
     using O = Op<MODE>;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t mbar[2];
+    using L = TcLayout<D, MODE>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // [point tiles | operand A buffers | operand B | metadata ring], from a 1024-byte
+    // boundary (the bank swizzle of the point boxes repeats every 8 rows of 128 bytes)
+    unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    unsigned char *sx = smem;
+    unsigned char *sa = sx + kXStages * L::kXBytes;
+    unsigned char *sb = sa + kAStages * L::kABytes;
+    TileMeta *meta = reinterpret_cast<TileMeta *>(sb + (size_t)(p.npmax / 8) * L::kGroup);
+    __shared__ __align__(8) uint64_t bars[2 * kXStages + 2 * kAStages + 4 + 2 * kMeta + 1];
     __shared__ uint32_t tmem_slot;
+    __shared__ int s_abort;
     __shared__ float s_ref[D];
-    __shared__ float s_part[kTcThreads];
+    __shared__ float s_part[128];
     __shared__ float s_cmax2;
-    __shared__ int s_fail;
     __shared__ uint32_t s_stat[2];
+    const uint32_t b0 = smem_u32(bars);
+    auto XFULL = [&](int s) { return b0 + 8u * (uint32_t)s; };
+    auto XEMPTY = [&](int s) { return b0 + 8u * (uint32_t)(kXStages + s); };
+    auto AFULL = [&](int s) { return b0 + 8u * (uint32_t)(2 * kXStages + s); };
+    auto AEMPTY = [&](int s) { return b0 + 8u * (uint32_t)(2 * kXStages + kAStages + s); };
+    auto TFULL = [&](int s) { return b0 + 8u * (uint32_t)(2 * kXStages + 2 * kAStages + s); };
+    auto TEMPTY = [&](int s) { return b0 + 8u * (uint32_t)(2 * kXStages + 2 * kAStages + 2 + s); };
+    auto MFULL = [&](int s) { return b0 + 8u * (uint32_t)(2 * kXStages + 2 * kAStages + 4 + s); };
+    auto MEMPTY = [&](int s) { return b0 + 8u * (uint32_t)(2 * kXStages + 2 * kAStages + 4 + kMeta + s); };
+    const uint32_t STALL = b0 + 8u * (uint32_t)(2 * kXStages + 2 * kAStages + 4 + 2 * kMeta);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ub = split ? split[blockIdx.x] : unit_lo + (int)blockIdx.x;
-    const int ue = split ? split[blockIdx.x + 1] : ub + 1;
-    const int npmax = (kmax + 15) & ~15;
-
-    // [A buffers | B | float32 centers (scent) | high sums | low sums | counts (sacc)]; a
-    // center's sums take the odd stride D | 1 so that a warp's lanes adding one attribute
-    // of different centers spread over the banks
-    constexpr int DS = D | 1;
-    unsigned char *sa0 = smem;
-    unsigned char *sb = sa0 + (size_t)nbuf * L::kABytes;
-    float *sc = reinterpret_cast<float *>(sb + (((uint32_t)(npmax / 8) * L::kGroup + 127) & ~127u));
-    uint32_t *shi = reinterpret_cast<uint32_t *>(sc + (scent ? (size_t)kmax * D : 0));
-    uint32_t *slo = shi + (size_t)kmax * DS;
-    int32_t *scnt = reinterpret_cast<int32_t *>(slo + (size_t)kmax * DS);
+    const int ub = p.split[blockIdx.x], ue = p.split[blockIdx.x + 1];
+    const unsigned lim = p.wait_limit;
+    volatile int *abort = &s_abort;
 
     if (tid == 0) {
-        s_fail = 0;
+        s_abort = 0;
         s_stat[0] = 0u;
         s_stat[1] = 0u;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (sacc) {
-        for (int e = tid; e < kmax * DS; e += kTcThreads) {
-            shi[e] = 0u;
-            slo[e] = 0u;
+        for (int s = 0; s < kXStages; s++) {
+            mbar_init(XFULL(s), 1);
+            mbar_init(XEMPTY(s), 4);
         }
-        for (int j = tid; j < kmax; j += kTcThreads) scnt[j] = 0;
+        for (int s = 0; s < kAStages; s++) {
+            mbar_init(AFULL(s), 4);
+            mbar_init(AEMPTY(s), 1);
+        }
+        for (int s = 0; s < 2; s++) {
+            mbar_init(TFULL(s), 1);
+            mbar_init(TEMPTY(s), 4);
+        }
+        for (int s = 0; s < kMeta; s++) {
+            mbar_init(MFULL(s), 4);
+            mbar_init(MEMPTY(s), 4);
+        }
+        mbar_init(STALL, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0 && ub < ue) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_u32(&tmem_slot)), "r"((uint32_t)nbuf * ncols));
+                     ::"r"(smem_u32(&tmem_slot)), "r"(2u * p.ncols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ub >= ue) return;
+    // test hook: a wait on a barrier that nothing completes runs out before any copy or
+    // MMA is issued, and the CTA leaves through the abort path
+    if (p.stall && tid == 0) mbar_wait(STALL, 0u, lim, abort);
+    __syncthreads();
     const uint32_t tmem = tmem_slot;
-    uint32_t uses[2] = {0u, 0u};
-    uint32_t issued[2] = {0u, 0u};
-    uint32_t n_tie = 0, n_live = 0;
 
-    for (int u = ub; u < ue;) {
-        const int s = t.unit_seg[u];
-        int ur = u + 1;
-        while (ur < ue && t.unit_seg[ur] == s) ur++;
-        const int k = t.k_eff[s];
-        const int np = (k + 15) & ~15;                             // MMA N
-        const int64_t c0 = t.cen_off[s];
-        const int64_t row0 = t.seg_start[s] + t.unit_start[u];
-        const int R = t.unit_start[ur - 1] + t.unit_count[ur - 1] - t.unit_start[u];
-        u = ur;
-
-        // ---- set-up of the run: float32 centers (for the near-tie re-scoring), reference
-        // point (mean of the centers), operand B, cmax
-        if (scent)
-            for (int e = tid; e < k * D; e += kTcThreads) sc[e] = __ldg(&centers[c0 * D + e]);
-        const float *cen = scent ? sc : centers + c0 * D;       // this set's centers
-        {
-            constexpr int G = kTcThreads / D;
-            const int a = tid % D, g = tid / D;
-            float m = 0.0f;
-            if (g < G)
-                for (int j = g; j < k; j += G) m = __fadd_rn(m, __ldg(&centers[(c0 + j) * D + a]));
-            s_part[tid] = m;
-            if (tid == 0) s_cmax2 = 0.0f;
-            __syncthreads();
-            if (tid < D) {
-                float tot = 0.0f;
-                for (int q = 0; q < G; q++) tot = __fadd_rn(tot, s_part[q * D + tid]);
-                s_ref[tid] = __fdiv_rn(tot, (float)k);
+    if (warp == kProdWarp) {
+        // ---- producer: point tiles by TMA
+        uint32_t issued = 0;
+        if (lane == 0 && !*abort) {
+            int u = ub;
+            Run run;
+            uint32_t i = 0;
+            bool ok = true;
+            while (ok && next_run(p.t, u, ue, run)) {
+                for (int tt = 0; tt < run.ntiles; tt++, i++) {
+                    const int s = (int)(i % kXStages);
+                    const uint32_t use = i / kXStages;
+                    if (use > 0 && !mbar_wait(XEMPTY(s), (use - 1) & 1u, lim, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(XFULL(s), L::kXBytes);
+                    for (int bx = 0; bx < L::kXBoxes; bx++)
+                        tma_load_2d(smem_u32(sx + (size_t)s * L::kXBytes + (size_t)bx * L::kXBoxBytes), &xmap,
+                                    bx * L::kXBoxCols, (int)(run.row0 + (int64_t)tt * kTileRows), XFULL(s));
+                    issued = i + 1;
+                }
             }
-            __syncthreads();
+            if (*abort)   // copies still in flight land before the CTA leaves
+                for (uint32_t j = issued > kXStages ? issued - kXStages : 0u; j < issued; j++)
+                    mbar_drain(XFULL((int)(j % kXStages)), (j / kXStages) & 1u, lim);
         }
-        for (int j = tid; j < np; j += kTcThreads) {
-            float H[D], Lo[D], n2 = 0.0f;
+    } else if (warp == kMmaWarp) {
+        // ---- MMA issue: one thread
+        if (lane == 0 && !*abort) {
+            int u = ub;
+            Run run;
+            uint32_t i = 0, issued = 0;
+            bool ok = true;
+            while (ok && next_run(p.t, u, ue, run)) {
+                const int np = (run.k + 15) & ~15;
+                const uint32_t idesc = O::idesc(np);
+                for (int tt = 0; tt < run.ntiles; tt++, i++) {
+                    const int a = (int)(i % kAStages), bfr = (int)(i & 1u);
+                    if (!mbar_wait(AFULL(a), (i / kAStages) & 1u, lim, abort) ||
+                        (i >= 2 && !mbar_wait(TEMPTY(bfr), ((i >> 1) - 1) & 1u, lim, abort))) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t dcol = tmem + (uint32_t)bfr * p.ncols;
+                    const uint32_t abase = smem_u32(sa + (size_t)a * L::kABytes), bbase = smem_u32(sb);
+                    // products: (A part, B part) blocks; the last pairs the ones with the norm parts
+                    constexpr int kGroups = O::kSplit ? 4 : 2;
+                    const int ga[4] = {0, 0, 1, L::kParts};
+                    const int gb[4] = {0, 1, 0, L::kParts};
+                    uint32_t accum = 0;
 #pragma unroll
-            for (int a = 0; a < D; a++) {
-                const float cc = j < k ? __fsub_rn(__ldg(&centers[(c0 + j) * D + a]), s_ref[a]) : 0.0f;
-                n2 = __fmaf_rn(cc, cc, n2);
-                const float m2 = -2.0f * cc;                          // exact
-                H[a] = O::rnd(m2);
-                Lo[a] = O::rnd(__fsub_rn(m2, H[a]));
-            }
-            float np_[O::kNormParts];
-            {
-                float rem = n2;
-#pragma unroll
-                for (int q = 0; q < O::kNormParts; q++) {
-                    np_[q] = j < k ? O::rnd(rem) : 0.0f;
-                    rem = __fsub_rn(rem, np_[q]);
+                    for (int g = 0; g < kGroups; g++) {
+                        const int pa = g == kGroups - 1 ? L::kParts : ga[g];
+                        const int pb = g == kGroups - 1 ? L::kParts : gb[g];
+                        const int nk = g == kGroups - 1 ? 1 : D / O::kMmaK;
+                        for (int kb = 0; kb < nk; kb++) {
+                            const uint32_t ca = (uint32_t)((pa * D) / O::kPerChunk + 2 * kb) * 128u;
+                            const uint32_t cb = (uint32_t)((pb * D) / O::kPerChunk + 2 * kb) * 128u;
+                            const uint64_t ad = smem_desc(abase + ca, 128, L::kGroup);
+                            const uint64_t bd = smem_desc(bbase + cb, 128, L::kGroup);
+                            if (O::kBf16)
+                                asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+                                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n"
+                                             ::"r"(dcol), "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                            else
+                                asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+                                             " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n}\n"
+                                             ::"r"(dcol), "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                            accum = 1;
+                        }
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 ::"r"(AEMPTY(a)));
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 ::"r"(TFULL(bfr)));
+                    issued = i + 1;
                 }
             }
-            put_row<D, MODE>(sb, j, [&](int e) -> float {
-                if (e < D) return H[e];
-                if (O::kTerms == 3) {
-                    if (e < 2 * D) return Lo[e - D];
-                    if (e < 3 * D) return H[e - 2 * D];
-                }
-                const int q = e - O::kTerms * D;
-                return q < O::kNormParts ? np_[q] : 0.0f;
-            });
-            if (j < k) atomicMax(reinterpret_cast<int *>(&s_cmax2), __float_as_int(n2));   // non-negative floats
+            if (*abort)   // MMAs still in flight finish before TMEM is released
+                for (uint32_t j = issued > 2 ? issued - 2 : 0u; j < issued; j++)
+                    mbar_drain(TFULL((int)(j & 1u)), (j >> 1) & 1u, lim);
         }
-        __syncthreads();
-        const uint32_t idesc = O::idesc(np);
-        const float cmax = sqrtf(s_cmax2);
-        // error bound of v_j (factor 2 margin): products (eta_p each, the -2 counted), float32
-        // accumulation over K terms (2^-22 of the magnitude sum per term, allowing for
-        // non-IEEE accumulation), centring (2^-24 per operand), norm parts and their sum
-        const float alpha = 2.0f * (2.0f * O::eta_p() + 2.0f * (float)L::kK * 0x1p-22f + 0x1p-22f);
-        const float beta = 2.0f * ((float)L::kK * 0x1p-22f + (float)(D + 4) * 0x1p-24f + 0x1p-22f);
-        const int ntiles = (R + kTileRows - 1) / kTileRows;
-
-        // rows of the next tile to stage, loaded one tile ahead (D <= 32: registers)
-        constexpr bool kPre = D <= 32;
-        float xp[kPre ? D : 1];
-        auto load_rows = [&](int tile) {
-            if (!kPre || tile >= ntiles) return;
-            const int p = tile * kTileRows + tid;
-            const float4 *x4 = reinterpret_cast<const float4 *>(pts + (row0 + (p < R ? p : 0)) * D);
-#pragma unroll
-            for (int a4 = 0; a4 < (kPre ? D : 4) / 4; a4++) {
-                const float4 v = __ldg(&x4[a4]);
-                xp[4 * a4 + 0] = v.x;
-                xp[4 * a4 + 1] = v.y;
-                xp[4 * a4 + 2] = v.z;
-                xp[4 * a4 + 3] = v.w;
+    } else if (warp >= kCvtWarp0) {
+        // ---- converters: operand B per set, operand A and ||x~|| per tile
+        const int r = tid - kCvtWarp0 * 32;                 // 0..127: the tile row of this thread
+        int u = ub;
+        Run run;
+        uint32_t i = 0;
+        bool ok = !*abort;
+        // every converter thread passes the same named barriers: the set loop runs to the
+        // end, and after a failed wait only the bookkeeping goes on
+        while (next_run(p.t, u, ue, run)) {
+            // the earlier tiles' MMAs must be done before operand B and s_ref change
+            for (uint32_t j = i > kAStages ? i - kAStages : 0u; ok && j < i; j++)
+                ok = mbar_wait(AEMPTY((int)(j % kAStages)), (j / kAStages) & 1u, lim, abort);
+            ok = cvt_bar_and(ok && !*abort);
+            if (!ok) {
+                i += (uint32_t)run.ntiles;
+                continue;
             }
-        };
-        // write tile `tile`'s A operand into buffer `buf` (threads = rows)
-        auto stage = [&](int tile, int buf) {
-            const int p = tile * kTileRows + tid;
-            const bool live = p < R;
-            const float4 *x4 = reinterpret_cast<const float4 *>(pts + (row0 + (live ? p : 0)) * D);
-            float h[D], l[D];
-#pragma unroll
-            for (int a4 = 0; a4 < D / 4; a4++) {
-                float vv[4];
-                if (kPre) {
-#pragma unroll
-                    for (int q = 0; q < 4; q++) vv[q] = xp[(4 * a4 + q) % (kPre ? D : 1)];
-                } else {
-                    const float4 v = __ldg(&x4[a4]);
-                    vv[0] = v.x;
-                    vv[1] = v.y;
-                    vv[2] = v.z;
-                    vv[3] = v.w;
+            const int k = run.k, np = (k + 15) & ~15;
+            const float *cen = p.centers + run.c0 * D;
+            {   // reference point: the mean of the set's centers
+                constexpr int G = 128 / D;
+                const int at = r % D, g = r / D;
+                float m = 0.0f;
+                if (g < G)
+                    for (int j = g; j < k; j += G) m = __fadd_rn(m, __ldg(&cen[(size_t)j * D + at]));
+                s_part[r] = m;
+                if (r == 0) s_cmax2 = 0.0f;
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (r < D) {
+                    float tot = 0.0f;
+                    for (int q = 0; q < G; q++) tot = __fadd_rn(tot, s_part[q * D + r]);
+                    s_ref[r] = __fdiv_rn(tot, (float)k);
                 }
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const int a = 4 * a4 + q;
-                    const float xc = live ? __fsub_rn(vv[q], s_ref[a]) : 0.0f;
-                    h[a] = O::rnd(xc);
-                    l[a] = O::rnd(__fsub_rn(xc, h[a]));
-                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
             }
-            put_row<D, MODE>(sa0 + buf * L::kABytes, tid, [&](int e) { return a_elem<D, MODE>(e, h, l, live); });
-            load_rows(tile + 1);           // in flight while this tile's MMAs and epilogue run
-        };
-        auto issue = [&](int buf) {
-            issue_mma<D, MODE>(tmem + (uint32_t)buf * ncols, smem_u32(sa0 + buf * L::kABytes), smem_u32(sb), idesc,
-                               smem_u32(&mbar[buf]));
-        };
-        auto stage_issue = [&](int tile, int buf) -> bool {
-            stage(tile, buf);
+            // operand B: row j = [H | L | norm parts] of -2 c~_j (zero rows past k)
+            for (int j = r; j < np; j += 128) {
+                float n2 = 0.0f;
+#pragma unroll 4
+                for (int a4 = 0; a4 < D / 4; a4++) {
+                    float4 c4 = j < k ? __ldg(reinterpret_cast<const float4 *>(cen + (size_t)j * D) + a4)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+                    float cc[4] = {c4.x, c4.y, c4.z, c4.w}, H[4], Lo[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        cc[q] = j < k ? __fsub_rn(cc[q], s_ref[4 * a4 + q]) : 0.0f;
+                        n2 = __fmaf_rn(cc[q], cc[q], n2);
+                        const float m2 = -2.0f * cc[q];                 // exact
+                        H[q] = O::rnd(m2);
+                        Lo[q] = O::rnd(__fsub_rn(m2, H[q]));
+                    }
+                    put4<D, MODE>(sb, j, 4 * a4, H[0], H[1], H[2], H[3]);
+                    if (O::kSplit) put4<D, MODE>(sb, j, D + 4 * a4, Lo[0], Lo[1], Lo[2], Lo[3]);
+                }
+                float np_[4] = {0.f, 0.f, 0.f, 0.f};
+                {
+                    float rem = n2;
+#pragma unroll
+                    for (int q = 0; q < O::kNormParts; q++) {
+                        np_[q] = j < k ? O::rnd(rem) : 0.0f;
+                        rem = __fsub_rn(rem, np_[q]);
+                    }
+                }
+                put4<D, MODE>(sb, j, L::kParts * D, np_[0], np_[1], np_[2], np_[3]);
+#pragma unroll
+                for (int e = 4; e < O::kMmaK; e += 4) put4<D, MODE>(sb, j, L::kParts * D + e, 0.f, 0.f, 0.f, 0.f);
+                if (j < k) atomicMax(reinterpret_cast<int *>(&s_cmax2), __float_as_int(n2));   // non-negative
+            }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-            if (s_fail) return false;
-            if (tid == 0) issue(buf);
-            issued[buf]++;
-            return true;
-        };
-
-        load_rows(0);
-        bool ok = ntiles == 0 || stage_issue(0, 0);
-        for (int i = 0; ok && i < ntiles; i++) {
-            const int buf = nbuf == 2 ? (i & 1) : 0;
-            // two deep: the next tile's MMAs run while this tile's epilogue does
-            if (nbuf == 2 && i + 1 < ntiles && !stage_issue(i + 1, buf ^ 1)) break;
-            if (!mbar_wait(smem_u32(&mbar[buf]), uses[buf] & 1u)) s_fail = 1;
-            uses[buf]++;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            __syncthreads();
-            if (s_fail) break;
-
-            // ---- epilogue: this thread's row is TMEM lane tid of region `buf`
-            const int p = i * kTileRows + tid;
-            const bool live = p < R;
-            const float4 *x4 = reinterpret_cast<const float4 *>(pts + (row0 + (live ? p : 0)) * D);
-            float xv[D], xn2 = 0.0f;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            const float cmax = sqrtf(s_cmax2);
+            for (int tt = 0; tt < run.ntiles; tt++, i++) {
+                const int xs = (int)(i % kXStages), a = (int)(i % kAStages), m = (int)(i % kMeta);
+                if (ok)
+                    ok = mbar_wait(XFULL(xs), (i / kXStages) & 1u, lim, abort) &&
+                         (i < kAStages || mbar_wait(AEMPTY(a), (i / kAStages - 1) & 1u, lim, abort)) &&
+                         (i < kMeta || mbar_wait(MEMPTY(m), (i / kMeta - 1) & 1u, lim, abort));
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) continue;
+                const bool live = tt * kTileRows + r < run.R;
+                const unsigned char *xt = sx + (size_t)xs * L::kXBytes;
+                unsigned char *at = sa + (size_t)a * L::kABytes;
+                float xn2 = 0.0f;
+#pragma unroll 4
+                for (int a4 = 0; a4 < D / 4; a4++) {
+                    const int bx = (4 * a4) / L::kXBoxCols, c = ((4 * a4) % L::kXBoxCols) / 4;
+                    const float4 v = *reinterpret_cast<const float4 *>(xt + (size_t)bx * L::kXBoxBytes +
+                                                                       xbox_off<D, MODE>(r, c));
+                    float xv[4] = {v.x, v.y, v.z, v.w}, h[4], lo[4];
 #pragma unroll
-            for (int a4 = 0; a4 < D / 4; a4++) {
-                const float4 v = __ldg(&x4[a4]);
-                xv[4 * a4 + 0] = v.x;
-                xv[4 * a4 + 1] = v.y;
-                xv[4 * a4 + 2] = v.z;
-                xv[4 * a4 + 3] = v.w;
-            }
-#pragma unroll
-            for (int a = 0; a < D; a++) {
-                const float xc = __fsub_rn(xv[a], s_ref[a]);
-                xn2 = __fmaf_rn(xc, xc, xn2);
-            }
-            const uint32_t trow = tmem + (uint32_t)buf * ncols + ((uint32_t)(warp * 32) << 16);
-            // pass 1: the smallest v_j (four independent chains)
-            const float kInf = __int_as_float(0x7f800000);
-            float m4[4] = {kInf, kInf, kInf, kInf};
-            for (int cb = 0; cb < k; cb += 32) {
-                float v[32];
-                tmem_ld32(trow + (uint32_t)cb, v);
-#pragma unroll
-                for (int q = 0; q < 32; q++) m4[q & 3] = fminf(m4[q & 3], cb + q < k ? v[q] : kInf);
-            }
-            const float best = fminf(fminf(m4[0], m4[1]), fminf(m4[2], m4[3]));
-            // E bounds the error of every v_j; the float32 direct sums have their own error
-            // (<= (d+3) 2^-24 of a distance, at most (||x~|| + cmax)^2), added so that no center
-            // left out could win the float32 direct comparison
-            const float xn = sqrtf(xn2);
-            const float E = alpha * xn * cmax + beta * cmax * cmax +
-                            (float)(2 * (D + 3)) * 0x1p-24f * (xn + cmax) * (xn + cmax) + 0x1p-100f;
-            const float thr = best + 2.0f * E;
-            // pass 2: every center within 2E of the best (the best among them), as a list of
-            // 8-bit indices (k <= 256), in ascending index
-            unsigned long long cl = 0ull;
-            int nc = 0;
-            for (int cb = 0; cb < k; cb += 32) {
-                float v[32];
-                tmem_ld32(trow + (uint32_t)cb, v);
-#pragma unroll
-                for (int q = 0; q < 32; q++) {
-                    if (cb + q < k && v[q] <= thr) {
-                        if (nc < 8) cl |= (unsigned long long)(cb + q) << (8 * nc);
-                        nc++;
+                    for (int q = 0; q < 4; q++) {
+                        const float xc = live ? __fsub_rn(xv[q], s_ref[4 * a4 + q]) : 0.0f;
+                        xn2 = __fmaf_rn(xc, xc, xn2);
+                        h[q] = O::rnd(xc);
+                        lo[q] = O::rnd(__fsub_rn(xc, h[q]));
                     }
+                    put4<D, MODE>(at, r, 4 * a4, h[0], h[1], h[2], h[3]);
+                    if (O::kSplit) put4<D, MODE>(at, r, D + 4 * a4, lo[0], lo[1], lo[2], lo[3]);
+                }
+                const float one = live ? 1.0f : 0.0f;
+                put4<D, MODE>(at, r, L::kParts * D, one, one, O::kNormParts > 2 ? one : 0.0f, 0.0f);
+#pragma unroll
+                for (int e = 4; e < O::kMmaK; e += 4) put4<D, MODE>(at, r, L::kParts * D + e, 0.f, 0.f, 0.f, 0.f);
+                meta[m].xn[r] = sqrtf(xn2);
+                if (r == 0) {
+                    meta[m].cmax = cmax;
+                    meta[m].k = run.k;
+                    meta[m].nvalid = min(kTileRows, run.R - tt * kTileRows);
+                    meta[m].row0 = run.row0 + (int64_t)tt * kTileRows;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(XEMPTY(xs));
+                    mbar_arrive(AFULL(a));
+                    mbar_arrive(MFULL(m));
                 }
             }
-            int bj = (int)(cl & 0xFFu);
-            const bool tie = live && nc > 1;
-            if (__any_sync(0xffffffffu, tie)) {
-                // near tie: re-score the candidates with the float32 direct sum, lowest index
-                // among equal sums (the float32 path's choice); past 8 candidates, all centers
-                auto direct = [&](int j) {
-                    const float *cj = cen + (size_t)j * D;
-                    float dd = 0.0f;
+        }
+    } else {
+        // ---- epilogue warpgroup g = warp / 4 takes the tiles i with i % 2 == g
+        const int g = warp >> 2, q4 = warp & 3, r = q4 * 32 + lane;
+        const float kInf = __int_as_float(0x7f800000);
+        constexpr int kTerms = (O::kSplit ? 3 : 1) * D + O::kMmaK;   // products accumulated per v_j
+        // error bound of v_j (factor 2 margin): products (eta_p each, the -2 counted), float32
+        // accumulation over the terms (2^-22 of the magnitude sum per term, allowing for
+        // non-IEEE accumulation), centring (2^-24 per operand), norm parts and their sum
+        const float alpha = 2.0f * (2.0f * O::eta_p() + 2.0f * (float)kTerms * 0x1p-22f + 0x1p-22f);
+        const float beta = 2.0f * ((float)kTerms * 0x1p-22f + (float)(D + 4) * 0x1p-24f + 0x1p-22f);
+        uint32_t n_tie = 0, n_row = 0;
+        int u = ub;
+        Run run;
+        uint32_t i = 0;
+        bool ok = !*abort;
+        while (ok && next_run(p.t, u, ue, run)) {
+            for (int tt = 0; tt < run.ntiles; tt++, i++) {
+                if ((int)(i & 1u) != g) continue;
+                const int m = (int)(i % kMeta);
+                ok = mbar_wait(TFULL(g), (i >> 1) & 1u, lim, abort) && mbar_wait(MFULL(m), (i / kMeta) & 1u, lim, abort);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const int k = meta[m].k;
+                const float cmax = meta[m].cmax, xn = meta[m].xn[r];
+                const bool live = r < meta[m].nvalid;
+                const int64_t row = meta[m].row0 + r;
+                const uint32_t taddr = tmem + (uint32_t)g * p.ncols + ((uint32_t)(q4 * 32) << 16);
+                // pass 1: the smallest of the k values (four independent chains; two 32-column
+                // loads in flight per wait)
+                float m4[4] = {kInf, kInf, kInf, kInf};
+                for (int cb = 0; cb < k; cb += 64) {
+                    uint32_t v0[32], v1[32];
+                    const bool two = cb + 32 < k;
+                    tmem_ld32_nowait(taddr + (uint32_t)cb, v0);
+                    if (two) tmem_ld32_nowait(taddr + (uint32_t)(cb + 32), v1);
+                    tmem_wait();
+                    if (cb + 64 <= k) {
 #pragma unroll
-                    for (int a = 0; a < D; a++) {
-                        const float tq = __fsub_rn(xv[a], cj[a]);      // shared or global (generic)
-                        dd = __fmaf_rn(tq, tq, dd);
-                    }
-                    return dd;
-                };
-                const int nlist = tie ? (nc <= 8 ? nc : k) : 0;
-                const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)nlist);
-                float bd = kInf;
-                int bjj = bj;
-                for (int c = 0; c < nmax; c++) {
-                    if (c < nlist) {
-                        const int j = nc <= 8 ? (int)((cl >> (8 * c)) & 0xFFu) : c;
-                        const float dd = direct(j);
-                        if (dd < bd) {                     // ascending j: strict keeps the lowest
-                            bd = dd;
-                            bjj = j;
+                        for (int q = 0; q < 32; q++) m4[q & 3] = fminf(m4[q & 3], __uint_as_float(v0[q]));
+#pragma unroll
+                        for (int q = 0; q < 32; q++) m4[q & 3] = fminf(m4[q & 3], __uint_as_float(v1[q]));
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 32; q++)
+                            m4[q & 3] = fminf(m4[q & 3], cb + q < k ? __uint_as_float(v0[q]) : kInf);
+                        if (two) {
+#pragma unroll
+                            for (int q = 0; q < 32; q++)
+                                m4[q & 3] = fminf(m4[q & 3], cb + 32 + q < k ? __uint_as_float(v1[q]) : kInf);
                         }
                     }
                 }
-                if (tie) bj = bjj;
-            }
-            n_tie += tie;
-            n_live += live;
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            if (live) {
-                const int64_t row = row0 + p;
-                labels[row] = bj;
-                if (trace) trace[trace_off + row] = bj;
-                if (sacc) {
-                    atomicAdd(&scnt[bj], 1);
-                    const size_t e0 = (size_t)bj * DS;
+                const float b1 = fminf(fminf(m4[0], m4[1]), fminf(m4[2], m4[3]));
+                // E bounds the error of every v_j; the float32 direct sums have their own error
+                // (<= (d+3) 2^-24 of a distance, at most (||x~|| + cmax)^2), added so that no
+                // center left out could win the float32 direct comparison
+                const float E = alpha * xn * cmax + beta * cmax * cmax +
+                                (float)(2 * (D + 3)) * 0x1p-24f * (xn + cmax) * (xn + cmax) + 0x1p-100f;
+                const float thr = b1 + 2.0f * E;
+                // pass 2: the centers with v_j <= thr as a bit mask (word c: centers 32c .. 32c+31);
+                // one bit is the label, more a near tie
+                uint32_t w[8];
 #pragma unroll
-                    for (int a = 0; a < D; a++) {
-                        const unsigned long long q = to_fix(xv[a]);
-                        atomicAdd(&shi[e0 + a], (uint32_t)(q >> 16));
-                        atomicAdd(&slo[e0 + a], (uint32_t)(q & 0xFFFFu));
+                for (int c = 0; c < 8; c++) {
+                    w[c] = 0u;
+                    if (32 * c < k) {
+                        uint32_t v[32];
+                        tmem_ld32_nowait(taddr + (uint32_t)(32 * c), v);
+                        tmem_wait();
+#pragma unroll
+                        for (int q = 0; q < 32; q++)
+                            w[c] |= (__uint_as_float(v[q]) <= thr && 32 * c + q < k) ? (1u << q) : 0u;
                     }
-                } else {                           // sums too large for shared memory
-                    atomicAdd(&count[c0 + bj], 1);
-#pragma unroll
-                    for (int a = 0; a < D; a++) atomicAdd(&acc[(c0 + bj) * D + a], to_fix(xv[a]));
                 }
-            }
-            if (sacc && (i + 1) % kFoldTiles == 0 && i + 1 < ntiles) {
-                __syncthreads();
-                flush_sums(shi, slo, scnt, k, c0, acc, count, D);
-            }
-            // one deep: the next tile after this epilogue released TMEM and the A buffer
-            if (nbuf == 1 && i + 1 < ntiles) {
-                __syncthreads();
-                if (!stage_issue(i + 1, 0)) break;
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(TEMPTY(g));
+                int nc = 0, first = 0;
+#pragma unroll
+                for (int c = 7; c >= 0; c--) {
+                    nc += __popc(w[c]);
+                    if (w[c]) first = 32 * c + __ffs(w[c]) - 1;
+                }
+                if (live) {
+                    p.labels[row] = nc > 1 ? (int32_t)kTieBit : first;
+                    n_tie += nc > 1;
+                    n_row++;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(MEMPTY(m));
             }
         }
-        __syncthreads();
-        if (sacc) flush_sums(shi, slo, scnt, k, c0, acc, count, D);
-        if (s_fail) break;
-    }
-    {   // statistics: rows re-scored in float32 / rows assigned here
         const uint32_t nt = __reduce_add_sync(0xffffffffu, n_tie);
-        const uint32_t nl = __reduce_add_sync(0xffffffffu, n_live);
+        const uint32_t nr = __reduce_add_sync(0xffffffffu, n_row);
         if (lane == 0) {
             atomicAdd(&s_stat[0], nt);
-            atomicAdd(&s_stat[1], nl);
+            atomicAdd(&s_stat[1], nr);
         }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (tid == 0) {
-        if (s_stat[0]) atomicAdd(&flags[2], s_stat[0]);
-        if (s_stat[1]) atomicAdd(&flags[3], s_stat[1]);
-    }
-    if (s_fail) {
-        // a commit never arrived: report, and give the MMAs still in flight a bounded
-        // grace period before the tensor memory is released
-        if (tid == 0) atomicOr(&flags[1], 4u);
-        for (int b = 0; b < 2; b++)
-            if (uses[b] < issued[b]) mbar_wait(smem_u32(&mbar[b]), uses[b] & 1u);
-    }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)nbuf * ncols));
+    if (tid == 0) {
+        if (s_stat[0]) atomicAdd(&p.flags[2], s_stat[0]);
+        if (s_stat[1]) atomicAdd(&p.flags[3], s_stat[1]);
+        if (s_abort) atomicOr(&p.flags[1], 4u);
+    }
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2u * p.ncols));
+}
+
+// ---------------------------------------------------------------- sums and near ties
+// After the tensor-core assignment the thread of a near-tie row loads the row and re-scores
+// its candidates (or all centers when they were more than kMaxCand)
+// with PSCL_PREC_FP32's arithmetic -- t = RN(x_a - c_a), acc = RN(t t + acc) in ascending a,
+// the lowest index among equal sums -- so the label is the float32 direct winner.  Then each
+// row's coordinates are added to its center's exact 32.32 fixed-point sum (a warp takes its
+// rows one at a time, lane a attribute a), as two 32-bit
+// halves in shared memory (hi, lo <= 2^16 per row from fix_parts, so 32768 rows fit before
+// a fold), folded into the 64-bit global sums at the end of each run of one set.
+// Persistent: CTA c serves the units [split[c], split[c + 1]).  Also writes the final
+// labels and the label trace.
+constexpr int kFoldRows = 32768;
+
+template <int D>
+__host__ __device__ constexpr int sum_threads()
+{
+    return D <= 64 ? 512 : 256;          // a near tie's row is held in registers
+}
+
+template <int D>
+__global__ void __launch_bounds__(sum_threads<D>()) k_tc_sums(const float *__restrict__ pts,
+                                                             const float *__restrict__ centers, SegTable t,
+                                                             const int32_t *split, int32_t *labels,
+                                                             int32_t *trace, int64_t trace_off,
+                                                             unsigned long long *acc, int32_t *count, int kmax)
+{
+    constexpr int NT = sum_threads<D>();
+    constexpr int DS = D | 1;            // odd stride: lanes adding one attribute of different centers spread over banks
+    extern __shared__ uint32_t sm[];
+    uint32_t *shi = sm;
+    uint32_t *slo = shi + (size_t)kmax * DS;
+    int32_t *scnt = reinterpret_cast<int32_t *>(slo + (size_t)kmax * DS);
+    constexpr int DC = D + 4;            // centers' stride: float4 rows on distinct banks per quarter warp
+    float *scen = reinterpret_cast<float *>(sm + ((2 * (size_t)kmax * DS + (size_t)kmax + 3) & ~(size_t)3));
+    const int tid = threadIdx.x;
+    const int ub = split[blockIdx.x], ue = split[blockIdx.x + 1];
+    int u = ub;
+    Run run;
+    while (next_run(t, u, ue, run)) {
+        const int k = run.k;
+        const float *cen = centers + run.c0 * D;
+        for (int e = tid; e < k * DS; e += NT) {
+            shi[e] = 0u;
+            slo[e] = 0u;
+        }
+        for (int j = tid; j < k; j += NT) scnt[j] = 0;
+        for (int e = tid; e < k * D; e += NT) scen[(e / D) * DC + e % D] = __ldg(&cen[e]);
+        __syncthreads();
+        for (int p0 = 0; p0 < run.R; p0 += NT) {
+            const int pr = p0 + tid;
+            const bool live = pr < run.R;
+            const int64_t row = run.row0 + (live ? pr : 0);
+            int32_t lab = live ? labels[row] : 0;
+            const bool tie = live && ((uint32_t)lab & kTieBit);
+            if (!tie && (uint32_t)lab >= (uint32_t)k) lab = 0;   // only after an assignment that gave up
+            // near ties: the whole warp re-scores every center for one such row at a time
+            // (lane l takes centers l, l + 32, ..., two at a time; the row in every lane's
+            // registers, the centers in shared memory as float4 at a stride of D + 4 floats,
+            // which keeps a quarter warp's 128-bit loads on distinct banks)
+            {
+                const int lane = tid & 31;
+                uint32_t tm = __ballot_sync(0xffffffffu, tie);
+                while (tm) {
+                    const int src = __ffs(tm) - 1;
+                    tm &= tm - 1u;
+                    const int64_t trow = __shfl_sync(0xffffffffu, row, src);
+                    float x[D];
+                    {
+                        const float4 *x4 = reinterpret_cast<const float4 *>(pts + trow * D);
+#pragma unroll
+                        for (int a4 = 0; a4 < D / 4; a4++) {
+                            const float4 v = __ldg(&x4[a4]);          // the same address in every lane
+                            x[4 * a4 + 0] = v.x;
+                            x[4 * a4 + 1] = v.y;
+                            x[4 * a4 + 2] = v.z;
+                            x[4 * a4 + 3] = v.w;
+                        }
+                    }
+                    float bd = __int_as_float(0x7f800000);
+                    int bj = 0x7fffffff;
+                    for (int j = lane; j < k; j += 64) {
+                        const bool two = j + 32 < k;
+                        const float4 *c0 = reinterpret_cast<const float4 *>(scen + (size_t)j * DC);
+                        const float4 *c1 = reinterpret_cast<const float4 *>(scen + (size_t)(two ? j + 32 : j) * DC);
+                        float d0 = 0.0f, d1 = 0.0f;
+#pragma unroll
+                        for (int a4 = 0; a4 < D / 4; a4++) {
+                            const float4 u = c0[a4], v = c1[a4];
+                            float t;
+                            t = __fsub_rn(x[4 * a4 + 0], u.x); d0 = __fmaf_rn(t, t, d0);
+                            t = __fsub_rn(x[4 * a4 + 0], v.x); d1 = __fmaf_rn(t, t, d1);
+                            t = __fsub_rn(x[4 * a4 + 1], u.y); d0 = __fmaf_rn(t, t, d0);
+                            t = __fsub_rn(x[4 * a4 + 1], v.y); d1 = __fmaf_rn(t, t, d1);
+                            t = __fsub_rn(x[4 * a4 + 2], u.z); d0 = __fmaf_rn(t, t, d0);
+                            t = __fsub_rn(x[4 * a4 + 2], v.z); d1 = __fmaf_rn(t, t, d1);
+                            t = __fsub_rn(x[4 * a4 + 3], u.w); d0 = __fmaf_rn(t, t, d0);
+                            t = __fsub_rn(x[4 * a4 + 3], v.w); d1 = __fmaf_rn(t, t, d1);
+                        }
+                        if (d0 < bd) {               // ascending j in the lane: strict keeps the lowest
+                            bd = d0;
+                            bj = j;
+                        }
+                        if (two && d1 < bd) {
+                            bd = d1;
+                            bj = j + 32;
+                        }
+                    }
+#pragma unroll
+                    for (int o = 16; o; o >>= 1) {
+                        const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+                        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+                        if (od < bd || (od == bd && oj < bj)) {
+                            bd = od;
+                            bj = oj;
+                        }
+                    }
+                    if (lane == src) lab = bj;
+                }
+            }
+            if (live) {
+                labels[row] = lab;
+                if (trace) trace[trace_off + row] = lab;
+                atomicAdd(&scnt[lab], 1);
+            }
+            // sums, one row at a time per warp: lane a adds attribute a (+ 32 ...) of the row,
+            // so an atomic instruction touches consecutive words of one center (no bank
+            // conflicts) and the row is read in coalesced pieces
+            {
+                const int lane = tid & 31;
+                const int64_t wrow0 = run.row0 + p0 + (tid & ~31);
+                const int nrows = min(32, run.R - (p0 + (tid & ~31)));
+                constexpr int PL = (D + 31) / 32;    // attributes per lane
+                // the warp's 32 rows are all loaded before the first atomic
+                float xv[32][PL];
+#pragma unroll
+                for (int r = 0; r < 32; r++)
+#pragma unroll
+                    for (int e = 0; e < PL; e++) {
+                        const int at = lane + 32 * e;
+                        xv[r][e] = (r < nrows && at < D) ? __ldg(&pts[(wrow0 + r) * D + at]) : 0.0f;
+                    }
+#pragma unroll
+                for (int r = 0; r < 32; r++) {
+                    const int lr = __shfl_sync(0xffffffffu, lab, r);
+                    if (r < nrows) {
+#pragma unroll
+                        for (int e = 0; e < PL; e++) {
+                            const int at = lane + 32 * e;
+                            if (at < D) {
+                                uint32_t hi, lo;
+                                fix_parts(xv[r][e], hi, lo);
+                                atomicAdd(&shi[(size_t)lr * DS + at], hi);
+                                atomicAdd(&slo[(size_t)lr * DS + at], lo);
+                            }
+                        }
+                    }
+                }
+            }
+            const bool fold = (p0 + NT) % kFoldRows == 0 || p0 + NT >= run.R;
+            if (fold) {
+                __syncthreads();
+                for (int e = tid; e < k * D; e += NT) {
+                    const int c = e / D, es = c * DS + (e - c * D);
+                    const unsigned long long v = ((unsigned long long)shi[es] << 16) + slo[es];
+                    if (v) atomicAdd(&acc[run.c0 * D + e], v);
+                    shi[es] = 0u;
+                    slo[es] = 0u;
+                }
+                for (int j = tid; j < k; j += NT) {
+                    if (scnt[j]) atomicAdd(&count[run.c0 + j], scnt[j]);
+                    scnt[j] = 0;
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- host side
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver the runtime uses (looked up once, thread-safe).
+EncodeTiled encode_tiled()
+{
+    static const EncodeTiled fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        cudaGetLastError();
+        return reinterpret_cast<EncodeTiled>(f);
+    }();
+    return fn;
+}
+
+// The points' tensor map: rows of D floats, boxes of 128 rows x kXBoxCols attributes with
+// the bank swizzle whose span is the box row.  Checked here before any launch: a base
+// address and a row stride on 16-byte boundaries, box sizes within 256 elements and a box
+// row that is a multiple of 16 bytes.
+template <int D, int MODE>
+cudaError_t make_xmap(const float *pts, int64_t rows, CUtensorMap *map)
+{
+    using L = TcLayout<D, MODE>;
+    static_assert((L::kXBoxCols * 4) % 16 == 0 && L::kXBoxCols <= 256, "TMA box row");
+    if (((uintptr_t)pts & 15u) != 0 || (D * 4) % 16 != 0 || rows < 1 || rows >= ((int64_t)1 << 32))
+        return cudaErrorInvalidValue;
+    EncodeTiled enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)D * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)L::kXBoxCols, (cuuint32_t)kTileRows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUtensorMapSwizzle sw = L::kXBoxCols * 4 == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : L::kXBoxCols * 4 == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                  : L::kXBoxCols * 4 == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                                           : CU_TENSOR_MAP_SWIZZLE_NONE;
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(pts), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 template <int D, int MODE>
-size_t tc_smem_bytes(int kmax, int nbuf, bool sacc, bool scent = false)
+size_t assign_smem(int kmax)
 {
     using L = TcLayout<D, MODE>;
     const int np = (kmax + 15) & ~15;
-    const size_t b = ((size_t)(np / 8) * L::kGroup + 127) & ~(size_t)127;
-    return (size_t)nbuf * L::kABytes + b + (scent ? (size_t)kmax * D * 4 : 0) +
-           (sacc ? (size_t)kmax * (D | 1) * 4 * 2 + (size_t)kmax * 4 : 0) + 1024;
+    return 1024 + (size_t)kXStages * L::kXBytes + (size_t)kAStages * L::kABytes + (size_t)(np / 8) * L::kGroup +
+           (size_t)kMeta * sizeof(TileMeta);
 }
 
-// Two operand buffers and TMEM regions (MMA of the next tile under the epilogue of this
-// one) when two regions fit in 256 columns and two A buffers in shared memory, else one.
-template <int D, int MODE>
-int tc_nbuf(int kmax)
+template <int D>
+size_t sums_smem(int kmax)
 {
-    if (tmem_cols((kmax + 15) & ~15) > 128) return 1;
-    return tc_smem_bytes<D, MODE>(kmax, 2, false) <= kTcSmemMax ? 2 : 1;
+    return ((((size_t)2 * kmax * (D | 1) + (size_t)kmax + 3) & ~(size_t)3) + (size_t)kmax * (D + 4)) * 4;
 }
 
 template <int D, int MODE>
-cudaError_t tc_dispatch(const LloydBuffers &b, const SegTable &t, int iter, int unit_lo, int unit_hi, int kmax,
-                        uint32_t *flags, int sm_count, cudaStream_t st, KTimer *kt)
+cudaError_t tc_dispatch(const LloydBuffers &b, const SegTable &t, int iter, int kmax, uint32_t *flags, int sm_count,
+                        cudaStream_t st, KTimer *kt)
 {
-    const int nbuf = tc_nbuf<D, MODE>(kmax);
-    const uint32_t ncols = tmem_cols((kmax + 15) & ~15);
-    // exact sums in shared memory when they fit next to the operands (else global atomics),
-    // then the float32 centers for the re-scoring when they fit too (else read through L1)
-    const int sacc = tc_smem_bytes<D, MODE>(kmax, nbuf, true) <= kTcSmemMax;
-    const int scent = tc_smem_bytes<D, MODE>(kmax, nbuf, sacc != 0, true) <= kTcSmemMax;
-    const size_t smem = tc_smem_bytes<D, MODE>(kmax, nbuf, sacc != 0, scent != 0);
-    auto kern = k_lloyd_assign_tc<D, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    CUtensorMap map;
+    cudaError_t e = make_xmap<D, MODE>(b.pts, b.rows, &map);
     if (e != cudaSuccess) return e;
-    const int32_t *split = nullptr;
-    int grid = unit_hi - unit_lo;
-    if (t.split && unit_lo == 0 && unit_hi == t.n_units) {
-        // persistent: as many CTAs per SM as shared memory, registers and the 512 TMEM
-        // columns allow (<= 4), counted here (the occupancy query answers 1 for this kernel)
-        cudaFuncAttributes fa;
-        e = cudaFuncGetAttributes(&fa, kern);
-        if (e != cudaSuccess) return e;
-        int dev = 0, smem_sm = 0, reserved = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
-            return e;
-        if ((e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess)
-            return e;
-        const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + reserved);
-        const int by_regs = 65536 / (((fa.numRegs + 7) & ~7) * kTcThreads);
-        const int by_tmem = (int)(512 / ((uint32_t)nbuf * ncols));
-        const int m = std::max(1, std::min(std::min(by_smem, by_regs), std::min(by_tmem, 4)));
-        split = t.split + t.split_off[m];
-        grid = m * sm_count;
-    }
+    TcArgs a;
+    a.centers = b.centers;
+    a.labels = b.labels;
+    a.t = t;
+    a.flags = flags;
+    a.wait_limit = b.wait_limit ? b.wait_limit : kDefaultWait;
+    a.stall = b.tc_stall;
+    a.npmax = (kmax + 15) & ~15;
+    a.ncols = tmem_cols(a.npmax);
+    const size_t smem = assign_smem<D, MODE>(kmax);
+    auto ka = k_tc_assign<D, MODE>;
+    if ((e = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+    // as many CTAs per SM as registers, shared memory and the 512 TMEM columns allow (<= 4):
+    // every resident CTA must get its TMEM at once
+    int occ = 1;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ka, kTcThreads, smem)) != cudaSuccess) return e;
+    const int ma = std::max(1, std::min(std::min(occ, (int)(512u / (2u * a.ncols))), 4));
+    a.split = t.split + t.split_off[ma];
     kt->begin(st);
-    kern<<<grid, kTcThreads, smem, st>>>(b.pts, t, split, unit_lo, b.centers, b.acc, b.count, b.labels, b.trace,
-                                         (int64_t)iter * b.rows, kmax, nbuf, ncols, sacc, scent, flags);
+    ka<<<ma * sm_count, kTcThreads, smem, st>>>(map, a);
     kt->end(PSCL_K_LLOYD_ASSIGN, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // sums: four CTAs' unit ranges per SM whatever fits at once, so that the block scheduler
+    // evens out ranges whose near ties cost more
+    const size_t ss = sums_smem<D>(kmax);
+    auto ks = k_tc_sums<D>;
+    if ((e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss)) != cudaSuccess) return e;
+    const int m = 4;
+    kt->begin(st);
+    ks<<<m * sm_count, sum_threads<D>(), ss, st>>>(b.pts, b.centers, t, t.split + t.split_off[m], b.labels,
+                                                   b.trace, (int64_t)iter * b.rows, b.acc, b.count, kmax);
+    kt->end(PSCL_K_LLOYD_SUMS, st);
     return cudaGetLastError();
 }
 
 template <int MODE>
-cudaError_t tc_by_d(const LloydBuffers &b, const SegTable &t, int d, int iter, int unit_lo, int unit_hi, int kmax,
-                    uint32_t *flags, int sm_count, cudaStream_t st, KTimer *kt)
+cudaError_t tc_by_d(const LloydBuffers &b, const SegTable &t, int d, int iter, int kmax, uint32_t *flags,
+                    int sm_count, cudaStream_t st, KTimer *kt)
 {
     switch (d) {
-    case 4: return tc_dispatch<4, MODE>(b, t, iter, unit_lo, unit_hi, kmax, flags, sm_count, st, kt);
-    case 8: return tc_dispatch<8, MODE>(b, t, iter, unit_lo, unit_hi, kmax, flags, sm_count, st, kt);
-    case 16: return tc_dispatch<16, MODE>(b, t, iter, unit_lo, unit_hi, kmax, flags, sm_count, st, kt);
-    case 32: return tc_dispatch<32, MODE>(b, t, iter, unit_lo, unit_hi, kmax, flags, sm_count, st, kt);
-    case 64: return tc_dispatch<64, MODE>(b, t, iter, unit_lo, unit_hi, kmax, flags, sm_count, st, kt);
+    case 16: return tc_dispatch<16, MODE>(b, t, iter, kmax, flags, sm_count, st, kt);
+    case 32: return tc_dispatch<32, MODE>(b, t, iter, kmax, flags, sm_count, st, kt);
+    case 64: return tc_dispatch<64, MODE>(b, t, iter, kmax, flags, sm_count, st, kt);
+    case 128: return tc_dispatch<128, MODE>(b, t, iter, kmax, flags, sm_count, st, kt);
     default: return cudaErrorInvalidValue;
     }
 }
 
 template <int MODE>
-size_t smem_by_d(int d, int kmax)
+bool fits_by_d(int d, int kmax)
 {
     switch (d) {
-    case 4: return tc_smem_bytes<4, MODE>(kmax, 1, false);
-    case 8: return tc_smem_bytes<8, MODE>(kmax, 1, false);
-    case 16: return tc_smem_bytes<16, MODE>(kmax, 1, false);
-    case 32: return tc_smem_bytes<32, MODE>(kmax, 1, false);
-    case 64: return tc_smem_bytes<64, MODE>(kmax, 1, false);
-    default: return ~(size_t)0;
+    case 16: return assign_smem<16, MODE>(kmax) <= kTcSmemMax && sums_smem<16>(kmax) <= kTcSmemMax;
+    case 32: return assign_smem<32, MODE>(kmax) <= kTcSmemMax && sums_smem<32>(kmax) <= kTcSmemMax;
+    case 64: return assign_smem<64, MODE>(kmax) <= kTcSmemMax && sums_smem<64>(kmax) <= kTcSmemMax;
+    case 128: return assign_smem<128, MODE>(kmax) <= kTcSmemMax && sums_smem<128>(kmax) <= kTcSmemMax;
+    default: return false;
     }
 }
 
@@ -690,33 +1011,29 @@ int mode_of(int prec)
 
 }  // namespace
 
-// The tensor-core assignment serves d in {4, 8, 16, 32, 64}, at most 256 centers per set
-// and sets whose operands fit in 200 KB of shared memory (the exact sums go to shared
-// memory when they fit too, else straight to the global sums); every other case takes
+// The tensor-core assignment serves d in {16, 32, 64, 128} and at most 256 centers per
+// set whose operands, point tiles and sums fit in shared memory; every other case takes
 // the float32 direct kernel (same labels).
 bool tc_supported(int d, int kmax, int prec)
 {
-    if (kmax < 1 || kmax > 256) return false;
-    size_t need;
+    if (kmax < 1 || kmax > 256 || !encode_tiled()) return false;
     switch (mode_of(prec)) {
-    case kModeBf16: need = smem_by_d<kModeBf16>(d, kmax); break;
-    case kModeTf32x3: need = smem_by_d<kModeTf32x3>(d, kmax); break;
-    case kModeBf16x3: need = smem_by_d<kModeBf16x3>(d, kmax); break;
-    default: need = smem_by_d<kModeTf32>(d, kmax); break;
+    case kModeBf16: return fits_by_d<kModeBf16>(d, kmax);
+    case kModeTf32x3: return fits_by_d<kModeTf32x3>(d, kmax);
+    case kModeBf16x3: return fits_by_d<kModeBf16x3>(d, kmax);
+    default: return fits_by_d<kModeTf32>(d, kmax);
     }
-    return need <= kTcSmemMax;
 }
 
-cudaError_t launch_lloyd_assign_tc(const LloydBuffers &b, const SegTable &t, int d, int iter, int unit_lo,
-                                   int unit_hi, int kmax, int prec, uint32_t *flags, int sm_count, cudaStream_t st,
-                                   KTimer *kt)
+cudaError_t launch_lloyd_assign_tc(const LloydBuffers &b, const SegTable &t, int d, int iter, int kmax, int prec,
+                                   uint32_t *flags, int sm_count, cudaStream_t st, KTimer *kt)
 {
-    if (unit_hi <= unit_lo) return cudaSuccess;
+    if (!t.split) return cudaErrorInvalidValue;
     switch (mode_of(prec)) {
-    case kModeBf16: return tc_by_d<kModeBf16>(b, t, d, iter, unit_lo, unit_hi, kmax, flags, sm_count, st, kt);
-    case kModeTf32x3: return tc_by_d<kModeTf32x3>(b, t, d, iter, unit_lo, unit_hi, kmax, flags, sm_count, st, kt);
-    case kModeBf16x3: return tc_by_d<kModeBf16x3>(b, t, d, iter, unit_lo, unit_hi, kmax, flags, sm_count, st, kt);
-    default: return tc_by_d<kModeTf32>(b, t, d, iter, unit_lo, unit_hi, kmax, flags, sm_count, st, kt);
+    case kModeBf16: return tc_by_d<kModeBf16>(b, t, d, iter, kmax, flags, sm_count, st, kt);
+    case kModeTf32x3: return tc_by_d<kModeTf32x3>(b, t, d, iter, kmax, flags, sm_count, st, kt);
+    case kModeBf16x3: return tc_by_d<kModeBf16x3>(b, t, d, iter, kmax, flags, sm_count, st, kt);
+    default: return tc_by_d<kModeTf32>(b, t, d, iter, kmax, flags, sm_count, st, kt);
     }
 }
 

@@ -46,6 +46,24 @@ struct PeelCtl {
     uint32_t passes;                     //   distance passes over the points left
 };
 
+// v (a scaled coordinate, in [0, 1]) times 2^32 rounded to the nearest integer, ties to
+// even, as hi 2^16 + lo with lo <= 2^16: s = v 2^16 is exact, hi = floor(s), the fraction
+// s - hi and its product with 2^16 are exact, and only lo is rounded.  Two 32-bit
+// conversions: the 64-bit float-to-integer conversion runs on the float64 pipe.
+__device__ __forceinline__ void fix_parts(float v, uint32_t &hi, uint32_t &lo)
+{
+    const float s = v * 65536.0f;
+    hi = __float2uint_rz(s);
+    lo = __float2uint_rn((s - __uint2float_rz(hi)) * 65536.0f);
+}
+
+__device__ __forceinline__ unsigned long long fix_of(float v)
+{
+    uint32_t hi, lo;
+    fix_parts(v, hi, lo);
+    return ((unsigned long long)hi << 16) + lo;
+}
+
 // Job flags read by the host at every synchronisation.
 //   [0] != 0: an input value is not finite
 //   [1] bit 0: the peel's float32 bound was contradicted (internal error)
@@ -185,6 +203,8 @@ struct LloydBuffers {
     // w x to its center's sum and w to its count; such runs use the float32 assignment
     // with global 64-bit sums (w q needs up to 63 bits).
     const int32_t *weights = nullptr;
+    uint32_t wait_limit = 0;         // polls of the tensor-core kernel's bounded waits (0: default)
+    int tc_stall = 0;                // test hook: the tensor-core kernel waits once on a barrier nothing completes
 };
 cudaError_t launch_lloyd_init(const LloydBuffers &b, const SegTable &t, int d, int64_t P,
                               uint64_t seed, uint32_t stage, int first_k, int kmax,
@@ -203,9 +223,10 @@ cudaError_t launch_seg_sse(const float *pts, const SegTable &t, const int32_t *s
 
 // lloyd_tc.cu
 bool tc_supported(int d, int kmax, int prec);
-cudaError_t launch_lloyd_assign_tc(const LloydBuffers &b, const SegTable &t, int d, int iter, int unit_lo,
-                                   int unit_hi, int kmax, int prec, uint32_t *flags, int sm_count, cudaStream_t st,
-                                   KTimer *kt);
+// Assignment on the tensor cores and the exact sums of the iteration (two persistent
+// launches over all units; needs t.split).
+cudaError_t launch_lloyd_assign_tc(const LloydBuffers &b, const SegTable &t, int d, int iter, int kmax, int prec,
+                                   uint32_t *flags, int sm_count, cudaStream_t st, KTimer *kt);
 cudaError_t launch_final_sse(const float *x, int64_t n, int d, const float *centers, int k,
                              int32_t *labels, double *blk_sse, double *sse, uint32_t *ticket,
                              int sm_count, cudaStream_t st, KTimer *kt);
