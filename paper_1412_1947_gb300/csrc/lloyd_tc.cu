@@ -50,7 +50,7 @@ constexpr int kCvtWarp0 = 8;              // converter warps 8..11
 constexpr int kProdWarp = 12;
 constexpr int kMmaWarp = 13;
 constexpr int kTcThreads = 14 * 32;
-constexpr int kXStages = 2;               // float32 point tiles in flight
+constexpr int kXStages = 2;               // float32 point tiles in flight (deeper rings measured no faster)
 constexpr int kAStages = 2;               // operand A buffers
 constexpr int kMeta = 8;                  // per-tile metadata ring (tiles in flight < kMeta)
 constexpr unsigned kDefaultWait = 1u << 26;
@@ -311,7 +311,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_assign(const __grid_consta
     // boundary (the bank swizzle of the point boxes repeats every 8 rows of 128 bytes)
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char *sx = smem;
-    unsigned char *sa = sx + kXStages * L::kXBytes;
+    constexpr int XS = kXStages;
+    unsigned char *sa = sx + (size_t)XS * L::kXBytes;
     unsigned char *sb = sa + kAStages * L::kABytes;
     TileMeta *meta = reinterpret_cast<TileMeta *>(sb + (size_t)(p.npmax / 8) * L::kGroup);
     __shared__ __align__(8) uint64_t bars[2 * kXStages + 2 * kAStages + 4 + 2 * kMeta + 1];
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_assign(const __grid_consta
         s_abort = 0;
         s_stat[0] = 0u;
         s_stat[1] = 0u;
-        for (int s = 0; s < kXStages; s++) {
+        for (int s = 0; s < XS; s++) {
             mbar_init(XFULL(s), 1);
             mbar_init(XEMPTY(s), 4);
         }
@@ -385,8 +386,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_assign(const __grid_consta
             bool ok = true;
             while (ok && next_run(p.t, u, ue, run)) {
                 for (int tt = 0; tt < run.ntiles; tt++, i++) {
-                    const int s = (int)(i % kXStages);
-                    const uint32_t use = i / kXStages;
+                    const int s = (int)(i % (uint32_t)XS);
+                    const uint32_t use = i / (uint32_t)XS;
                     if (use > 0 && !mbar_wait(XEMPTY(s), (use - 1) & 1u, lim, abort)) {
                         ok = false;
                         break;
@@ -399,8 +400,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_assign(const __grid_consta
                 }
             }
             if (*abort)   // copies still in flight land before the CTA leaves
-                for (uint32_t j = issued > kXStages ? issued - kXStages : 0u; j < issued; j++)
-                    mbar_drain(XFULL((int)(j % kXStages)), (j / kXStages) & 1u, lim);
+                for (uint32_t j = issued > (uint32_t)XS ? issued - (uint32_t)XS : 0u; j < issued; j++)
+                    mbar_drain(XFULL((int)(j % (uint32_t)XS)), (j / (uint32_t)XS) & 1u, lim);
         }
     } else if (warp == kMmaWarp) {
         // ---- MMA issue: one thread
@@ -532,9 +533,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_assign(const __grid_consta
             asm volatile("bar.sync 1, 128;" ::: "memory");
             const float cmax = sqrtf(s_cmax2);
             for (int tt = 0; tt < run.ntiles; tt++, i++) {
-                const int xs = (int)(i % kXStages), a = (int)(i % kAStages), m = (int)(i % kMeta);
+                const int xs = (int)(i % (uint32_t)XS), a = (int)(i % kAStages), m = (int)(i % kMeta);
                 if (ok)
-                    ok = mbar_wait(XFULL(xs), (i / kXStages) & 1u, lim, abort) &&
+                    ok = mbar_wait(XFULL(xs), (i / (uint32_t)XS) & 1u, lim, abort) &&
                          (i < kAStages || mbar_wait(AEMPTY(a), (i / kAStages - 1) & 1u, lim, abort)) &&
                          (i < kMeta || mbar_wait(MEMPTY(m), (i / kMeta - 1) & 1u, lim, abort));
                 ok = __all_sync(0xffffffffu, ok);
@@ -816,36 +817,38 @@ __global__ void __launch_bounds__(sum_threads<D>()) k_tc_sums(const float *__res
                 if (trace) trace[trace_off + row] = lab;
                 atomicAdd(&scnt[lab], 1);
             }
-            // sums, one row at a time per warp: lane a adds attribute a (+ 32 ...) of the row,
-            // so an atomic instruction touches consecutive words of one center (no bank
-            // conflicts) and the row is read in coalesced pieces
+            // sums, RPI rows at a time per warp (lane a adds attribute a % D of row a / D; for
+            // D >= 32 one row, lane a attributes a, a + 32, ...), so an atomic instruction
+            // touches consecutive words of one center per row (no bank conflicts within a row)
+            // and the rows are read in coalesced pieces
             {
                 const int lane = tid & 31;
                 const int64_t wrow0 = run.row0 + p0 + (tid & ~31);
                 const int nrows = min(32, run.R - (p0 + (tid & ~31)));
-                constexpr int PL = (D + 31) / 32;    // attributes per lane
+                constexpr int RPI = D < 32 ? 32 / D : 1;       // rows per instruction
+                constexpr int PL = D < 32 ? 1 : D / 32;        // attributes per lane
+                constexpr int NI = 32 / RPI;                   // instructions per 32 rows
+                const int sub = D < 32 ? lane / D : 0, at0 = D < 32 ? lane % D : lane;
                 // the warp's 32 rows are all loaded before the first atomic
-                float xv[32][PL];
+                float xv[NI][PL];
 #pragma unroll
-                for (int r = 0; r < 32; r++)
+                for (int r = 0; r < NI; r++)
 #pragma unroll
                     for (int e = 0; e < PL; e++) {
-                        const int at = lane + 32 * e;
-                        xv[r][e] = (r < nrows && at < D) ? __ldg(&pts[(wrow0 + r) * D + at]) : 0.0f;
+                        const int rr = r * RPI + sub;
+                        xv[r][e] = rr < nrows ? __ldg(&pts[(wrow0 + rr) * D + at0 + 32 * e]) : 0.0f;
                     }
 #pragma unroll
-                for (int r = 0; r < 32; r++) {
-                    const int lr = __shfl_sync(0xffffffffu, lab, r);
-                    if (r < nrows) {
+                for (int r = 0; r < NI; r++) {
+                    const int rr = r * RPI + sub;
+                    const int lr = __shfl_sync(0xffffffffu, lab, rr);
+                    if (rr < nrows) {
 #pragma unroll
                         for (int e = 0; e < PL; e++) {
-                            const int at = lane + 32 * e;
-                            if (at < D) {
-                                uint32_t hi, lo;
-                                fix_parts(xv[r][e], hi, lo);
-                                atomicAdd(&shi[(size_t)lr * DS + at], hi);
-                                atomicAdd(&slo[(size_t)lr * DS + at], lo);
-                            }
+                            uint32_t hi, lo;
+                            fix_parts(xv[r][e], hi, lo);
+                            atomicAdd(&shi[(size_t)lr * DS + at0 + 32 * e], hi);
+                            atomicAdd(&slo[(size_t)lr * DS + at0 + 32 * e], lo);
                         }
                     }
                 }
