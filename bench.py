@@ -8,6 +8,10 @@ replayed).  Workload: 2^20 points, d=16, 64 Gaussian blobs (sigma ~ U[0.2, 1]) +
 uniform outliers, subclusters of 4096 (256 of them), 64 local centers, 25 Lloyd
 iterations, final k=64.
 
+Arithmetic: by default the assignment runs on the tensor cores (--prec tc: TF32x3 or
+BF16x3 contraction, near ties re-decided in float32), which assigns exactly as the float32
+direct form does; --prec fp32 runs the float32 direct kernel.
+
 Metric: Lloyd distance evaluations per second of the whole job,
     sum over subclusters of |s| * k_eff * iters + pooled * final_k * iters,
 divided by the job's device time (so peel, scaling and SSE count against it).
@@ -36,11 +40,28 @@ from paper_1412_1947_gb300 import synth  # noqa: E402
 METRIC = "Lloyd dist-evals/s"
 UNIT = "dist-evals/s"
 L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2
-FP32_ALU_PEAK = 152 * 128 * 2 * 2.07e9   # SMs x FP32 lanes x 2 flop (FMA) x max SM clock
-# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it stands, by
-# (kernel, workload): 296.5 MB + 180.3 MB for the peel on the 2^20 x 16 workload
-# (profiles/k_peel_n1048576_d16.md).  Drop an entry when its kernel changes.
-NCU_TRAFFIC = {("peel", "n1048576_d16_N4096_k64_f64"): 476.76e6}
+TF32_PER_BF16 = 1.1 / 2.25          # nominal dense TF32 : BF16 tensor rate of the part
+
+
+def tc_mode(prec: str, w: synth.Workload) -> str:
+    """The arithmetic the local Lloyd runs in: "tc" is the split mode the library picks for
+    the shape (TF32x3 where its tiles fit one CTA's shared memory, else BF16x3)."""
+    if prec != "tc":
+        return prec
+    return "tf32x3" if w.d <= 32 or (w.d == 64 and w.local_k <= 16) else "bf16x3"
+
+
+def measured_peaks():
+    """The machine's measured peaks (HBM copy GB/s; cuBLAS bf16 TFLOP/s burst and sustained),
+    else the earlier GB300 measurement used as fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return {"hbm_gbs": float(m["hbm_gbs"]), "bf16_tflops": float(m["bf16_tflops"]),
+                "bf16_tflops_sustained": float(m.get("bf16_tflops_sustained", m["bf16_tflops"])),
+                "kind": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "kind": "fallback"}
 
 
 def replica_max(x: float, dist=None) -> float:
@@ -151,19 +172,20 @@ def cpu_model() -> str:
     return platform.machine()
 
 
-def cpu_baseline(w: synth.Workload, n_sample: int, reps: int = 1):
+def cpu_baseline(w: synth.Workload, n_sample: int):
+    """The oracle on the workload's full data once (all host threads), and on an n_sample
+    sample of the same recipe with one thread."""
     threads = os.cpu_count() or 1
+    secs = run_oracle_once(w, w.points(), threads)
     ws = oracle_sample(w, n_sample)
-    raw = ws.points()
-    secs = min(run_oracle_once(ws, raw, threads) for _ in range(reps))
-    secs1 = run_oracle_once(ws, raw, 1)
-    ev = workload_evals(ws)
-    return {"value": ev / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"the whole two-level job (scale, peel, Lloyd, final Lloyd, SSE) on n={ws.n} "
-                      f"points of the same recipe ({-(-ws.n // w.N)} subclusters of {w.N}), "
-                      f"{secs:.2f} s, float64 C oracle, OpenMP over subclusters",
+    secs1 = run_oracle_once(ws, ws.points(), 1)
+    return {"value": workload_evals(w) / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"the whole two-level job (scale, peel, Lloyd, final Lloyd, SSE) on the full workload "
+                      f"(n={w.n}, {-(-w.n // w.N)} subclusters of {w.N}), once, {secs:.2f} s, float64 C "
+                      f"oracle, OpenMP over subclusters",
             "cpu": cpu_model(),
-            "single_thread": {"value": ev / secs1, "unit": UNIT, "seconds": secs1}}
+            "single_thread": {"value": workload_evals(ws) / secs1, "unit": UNIT, "seconds": secs1,
+                              "sample": f"n={ws.n} points of the same recipe"}}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -220,6 +242,7 @@ def main_arm(args, w: synth.Workload):
     x_dev = torch.from_numpy(raw).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    fma_tflops = B.pscl_measure_fp32_fma(local)
     ctx = B.pscl_ctx_create(local, 0, stream.cuda_stream)
     job = B.Job(x_dev, ctx=ctx)
     job.option(B.PSCL_OPT_GRAPH)
@@ -323,29 +346,56 @@ def main_arm(args, w: synth.Workload):
     job.close()
     B.pscl_ctx_destroy(ctx)
 
-    # ---- roofline of the dominant kernel
-    name, (nl, ms) = max(kt.items(), key=lambda kv: kv[1][1])
+    # ---- rooflines: the dominant kernel, and the assignment against its own measured peak
+    pk = measured_peaks()
+    of = "of measured" if pk["kind"] == "measured" else "of fallback"
     S = -(-wr.n // wr.N)
-    if name == "lloyd_assign":
-        flops = evals * 3 * wr.d                     # (x-c), square, add per attribute
-        roof = {"kernel": "k_lloyd_assign (float32 direct)", "bound": "alu",
-                "achieved": flops / (ms * 1e-3) / 1e12, "peak": FP32_ALU_PEAK / 1e12, "unit": "TFLOP/s",
-                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                "per_launch_ms": ms / nl, "launches": nl, "traffic": None}
+
+    def hbm_roof(kname, byts):
+        n_l, t_ms = kt[kname]
+        r = {"kernel": kname, "bound": "hbm", "achieved": byts / (t_ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
+             "unit": "GB/s", "peak_kind": f"{of} HBM copy", "per_launch_ms": t_ms / n_l, "launches": n_l,
+             "traffic": None, "algorithmic_bytes": byts}
+        r["frac"] = r["achieved"] / r["peak"]
+        return r
+
+    def assign_roof():
+        n_l, t_ms = kt["lloyd_assign"]
+        flops = 2 * wr.d * evals                      # the contraction: 2d flops per evaluation
+        tc = args.prec != "fp32" and assigned > 0
+        mode = tc_mode(args.prec, wr)
+        if tc:
+            peak = pk["bf16_tflops"] * (1.0 if mode.startswith("bf16") else TF32_PER_BF16)
+            kind = f"{of} cuBLAS bf16 burst" + ("" if mode.startswith("bf16") else " x nominal tf32/bf16")
+        else:
+            peak = fma_tflops
+            kind = "measured float32 FMA rate (pscl_measure_fp32_fma, 2 flop per FMA)"
+        r = {"kernel": f"k_tc_assign (tcgen05, {mode})" if tc else "k_lloyd_assign (float32 direct)",
+             "bound": "tensor" if tc else "alu", "achieved": flops / (t_ms * 1e-3) / 1e12, "peak": peak,
+             "unit": "TFLOP/s", "peak_kind": kind, "per_launch_ms": t_ms / n_l, "launches": n_l, "traffic": None,
+             "algorithmic_flops": flops,
+             # d*4/k bytes per evaluation: each point read once per iteration serves k distances
+             "achieved_gbs": evals * wr.d * 4 / wr.local_k / (t_ms * 1e-3) / 1e9}
+        if tc and "lloyd_sums" in kt:
+            r["sums_pass_ms"] = kt["lloyd_sums"][1]
+        r["frac"] = r["achieved"] / r["peak"]
+        return r
+
+    name = max(kt.items(), key=lambda kv: kv[1][1])[0]
+    if name == "peel":
+        # one read of the remaining points per round: sum over rounds of n_r * d * 4 bytes
+        roof = hbm_roof("peel", sum(wr.n - r * wr.N for r in range(S)) * wr.d * 4)
+        roof["us_per_round"] = 1e3 * kt["peel"][1] / S
+    elif name == "lloyd_assign":
+        roof = assign_roof()
     else:
-        # the peel: one read of the remaining points per round (sum over rounds of n_r*d*4)
-        rem = sum(wr.n - r * wr.N for r in range(S))
-        byts = rem * wr.d * 4 if name == "peel" else wr.n * wr.d * 4 * 2
-        roof = {"kernel": name, "bound": "hbm", "achieved": byts / (ms * 1e-3) / 1e9,
-                "peak": 6691.5, "unit": "GB/s", "peak_kind": "measured (MEASURED_PEAKS hbm_gbs)",
-                "per_launch_ms": ms / nl, "launches": nl, "traffic": NCU_TRAFFIC.get((name, w.name)),
-                "algorithmic_bytes": byts}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+        roof = hbm_roof(name, wr.n * wr.d * 4 * 2)
 
     value = evals * world / (mean_ms * 1e-3)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else args.prec + "+f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else tc_mode(args.prec, wr) + "+f32",
+            "data": "synthetic",
             "near_ties": {"rechecked_rows": rechecked, "tensor_core_rows": assigned},
             "config": config_of(wr, {"parallelism": f"replicas{world}" if world > 1 else "single"}),
             "latency_ms": {"p50": statistics.median(step_ms),
@@ -355,6 +405,7 @@ def main_arm(args, w: synth.Workload):
                     "h2d_bytes_per_step": int(raw.nbytes), "d2h_bytes_per_step": wr.final_k * wr.d * 4 + 8},
             "gpu_launches": int(launches_per_step * args.steps),
             "roofline": roof,
+            "roofline_assign": assign_roof(),
             "kernels_ms": {k: round(v[1], 4) for k, v in kt.items()},
             "kernel_launches": {k: v[0] for k, v in kt.items()},
             "phase_ms": {"scale": float(phases[0]), "peel": float(phases[1]), "local_lloyd": float(phases[2]),
@@ -440,14 +491,15 @@ def main_uneven(args):
             e2e_s.append(time.perf_counter() - t0)
     e2e_mean = statistics.mean(e2e_s)
     d = raw.shape[1]
-    flops = evals * 3 * d
+    flops = evals * 2 * d                 # the contraction: 2d flops per distance evaluation
     roof = {"kernel": "Lloyd iterations (k_lloyd_assign + finalize)", "bound": "alu",
-            "achieved": flops / (lloyd_ms * 1e-3) / 1e12, "peak": FP32_ALU_PEAK / 1e12, "unit": "TFLOP/s",
-            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz", "traffic": None}
+            "achieved": flops / (lloyd_ms * 1e-3) / 1e12, "peak": B.pscl_measure_fp32_fma(0), "unit": "TFLOP/s",
+            "peak_kind": "measured float32 FMA rate (pscl_measure_fp32_fma, 2 flop per FMA)", "traffic": None}
     roof["frac"] = roof["achieved"] / roof["peak"]
     line = {"metric": METRIC, "value": evals / (mean_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else args.prec + "+f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else tc_mode(args.prec, synth.MEDIUM) + "+f32",
+            "data": "synthetic",
             "config": {"workload": "uneven2048_d32_k8to256_it25", "instances": len(sizes), "rows": int(sizes.sum()),
                        "d": d, "iters": iters, "l2": "inputs (3 GB) larger than L2",
                        "tuned": {"unit_rows": unit_rows, "rows_per_thread": "1" if rpt else "default"}},
@@ -665,8 +717,10 @@ def main():
     ap.add_argument("--oracle-n", type=int, default=1 << 17)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16", "tf32x3", "bf16x3"],
-                    help="arithmetic of the Lloyd assignment (tf32/bf16: tensor cores + float32 near-tie recheck)")
+    ap.add_argument("--prec", default="tc", choices=["fp32", "tf32", "bf16", "tf32x3", "bf16x3", "tc"],
+                    help="arithmetic of the Lloyd assignment (tf32/bf16: tensor cores + float32 near-tie "
+                         "recheck; tc: the split mode that serves the shape, TF32x3 else BF16x3; every mode "
+                         "assigns exactly as fp32)")
     args = ap.parse_args()
     if args.workload == "serving":
         if args.impl == "reference":

@@ -60,16 +60,21 @@ typedef enum { PSCL_F32 = 0, PSCL_BF16 = 1 } pscl_dtype;
  *  PSCL_PREC_TF32X3, PSCL_PREC_BF16X3: the same with every operand split into a high
  *      and a low TF32 / BF16 part and the three leading products summed in one
  *      contraction (far fewer near ties to re-decide).
- *  The contraction covers d in {4, 8, 16, 32, 64} and at most 256 centers per point set;
- *  other shapes use the float32 direct sum.  The near-tie bound is rigorous, so every
- *  mode assigns exactly as PSCL_PREC_FP32 does.  Every mode yields the same partition
- *  into subclusters; the update step is the same exact fixed-point mean in all modes. */
+ *  PSCL_PREC_TC: per point set, TF32X3 where its operands fit one CTA's shared memory,
+ *      else BF16X3 (the split mode that serves the shape; the result is the same).
+ *  The contraction covers d in {16, 32, 64, 128} and at most 256 centers per point set
+ *  whose operand tiles fit one CTA's shared memory (d = 128 only in BF16 with 16
+ *  centers, d = 64 in TF32X3 only with 16); other shapes use the float32 direct sum.
+ *  The near-tie bound is rigorous, so every mode assigns exactly as PSCL_PREC_FP32 does.
+ *  Every mode yields the same partition into subclusters; the update step is the same
+ *  exact fixed-point mean in all modes. */
 typedef enum {
     PSCL_PREC_FP32 = 0,
     PSCL_PREC_TF32 = 1,
     PSCL_PREC_BF16 = 2,
     PSCL_PREC_TF32X3 = 3,
-    PSCL_PREC_BF16X3 = 4
+    PSCL_PREC_BF16X3 = 4,
+    PSCL_PREC_TC = 5
 } pscl_prec;
 
 /* Job options (pscl_job_set_option). */
@@ -249,6 +254,14 @@ int pscl_get_recheck_stats(pscl_job *job, int64_t *rechecked, int64_t *assigned)
 /* Device time of the phases of the last run in milliseconds: [0] scale, [1] peel,
  * [2] local Lloyd (incl. init), [3] final Lloyd, [4] SSE pass. */
 int pscl_get_phase_ms(pscl_job *job, float *ms5);
+
+/* Measured float32 FMA throughput of `device` in TFLOP/s (2 flops per FMA): independent
+ * FMA chains on every SM at full occupancy, timed with CUDA events, best of five after a
+ * warm-up.  The peak that the float32 direct assignment (one subtract and one FMA per
+ * attribute of a distance) is graded against; not part of the method.  Allocates and
+ * frees a few KB of device memory; takes some tens of milliseconds.
+ * Errors: PSCL_EINVAL (tflops NULL), PSCL_ECUDA. */
+int pscl_measure_fp32_fma(int device, double *tflops);
 
 /* Nearest center and sum of squared errors of n points, allocating nothing.
  *

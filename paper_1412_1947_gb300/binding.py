@@ -18,8 +18,9 @@ LIB_PATH = os.path.join(_PKG, "libpscl.so")
 PSCL_OK, PSCL_EINVAL, PSCL_ESTATE, PSCL_ENOMEM, PSCL_EBUSY, PSCL_ETIMEOUT, PSCL_ECUDA = range(7)
 PSCL_F32, PSCL_BF16 = 0, 1
 PSCL_PREC_FP32, PSCL_PREC_TF32, PSCL_PREC_BF16, PSCL_PREC_TF32X3, PSCL_PREC_BF16X3 = 0, 1, 2, 3, 4
+PSCL_PREC_TC = 5
 PRECISIONS = {"fp32": PSCL_PREC_FP32, "tf32": PSCL_PREC_TF32, "bf16": PSCL_PREC_BF16,
-              "tf32x3": PSCL_PREC_TF32X3, "bf16x3": PSCL_PREC_BF16X3}
+              "tf32x3": PSCL_PREC_TF32X3, "bf16x3": PSCL_PREC_BF16X3, "tc": PSCL_PREC_TC}
 PSCL_OPT_PLAIN_LLOYD, PSCL_OPT_TRACE_LABELS, PSCL_OPT_INIT_FIRST_K, PSCL_OPT_GRAPH = 1, 2, 3, 4
 PSCL_OPT_KERNEL_TIMING, PSCL_OPT_UNIT_ROWS, PSCL_OPT_ROWS_PER_THREAD, PSCL_OPT_POOL_WEIGHTED = 5, 6, 7, 8
 PSCL_OPT_PEEL_ROUNDS, PSCL_OPT_WAIT_LIMIT, PSCL_OPT_TEST_STALL = 9, 10, 11
@@ -50,6 +51,7 @@ SIGNATURES = {
     "pscl_get_phase_ms": (_I, [_P, _P]),
     "pscl_get_kernel_times": (_I, [_P, _P, _P]),
     "pscl_get_recheck_stats": (_I, [_P, _P, _P]),
+    "pscl_measure_fp32_fma": (_I, [_I, _P]),
     "pscl_assign_sse_noalloc": (_I, [_P, _I64, _I32, _P, _I32, _P, _P, _P]),
     "pscl_job_footprint": (_I, [_P, _I64, _I32, _I64, _I32, _I32, _I32, _I, _I, _I, _P]),
     "pscl_server_create": (_I, [_P, _I32, _SZ, _P]),
@@ -251,6 +253,13 @@ def pscl_get_phase_ms(job):
     ms = np.empty(5, np.float32)
     _chk(lib().pscl_get_phase_ms(job, _ptr(ms)))
     return ms
+
+
+def pscl_measure_fp32_fma(device=0):
+    """Measured float32 FMA throughput of the device in TFLOP/s (2 flops per FMA)."""
+    t = C.c_double()
+    _chk(lib().pscl_measure_fp32_fma(device, C.byref(t)))
+    return t.value
 
 
 def pscl_get_recheck_stats(job):

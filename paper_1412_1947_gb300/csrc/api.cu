@@ -519,7 +519,7 @@ static int build_lloyd_plan(Owner *j, LloydPlan &p, const std::vector<int64_t> &
 
 static int check_prec(int prec)
 {
-    if (prec < PSCL_PREC_FP32 || prec > PSCL_PREC_BF16X3)
+    if (prec < PSCL_PREC_FP32 || prec > PSCL_PREC_TC)
         return fail(PSCL_EINVAL, "unknown precision %d", prec);
     return PSCL_OK;
 }

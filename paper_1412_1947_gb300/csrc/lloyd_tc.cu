@@ -122,6 +122,14 @@ __device__ __forceinline__ bool cvt_bar_and(bool ok)
     return r != 0;
 }
 
+// CTAs of the assignment kernel per SM the register budget is set for: two for narrow
+// points, whose per-tile work is short and whose pipeline latency a second CTA hides
+template <int D>
+__host__ __device__ constexpr int tc_min_blocks()
+{
+    return D <= 32 ? 2 : 1;
+}
+
 // ---------------------------------------------------------------- TMA
 // One box of the tensor map (x = attribute, y = row) into shared memory at dst; the bytes
 // complete a transaction on the mbarrier at mbar.  Coordinates: x is a multiple of 32
@@ -302,7 +310,7 @@ __device__ __forceinline__ bool next_run(const SegTable &t, int &u, int ue, Run 
 }
 
 template <int D, int MODE>
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_assign(const __grid_constant__ CUtensorMap xmap, const TcArgs p)
+__global__ void __launch_bounds__(kTcThreads, tc_min_blocks<D>()) k_tc_assign(const __grid_constant__ CUtensorMap xmap, const TcArgs p)
 {
     using O = Op<MODE>;
     using L = TcLayout<D, MODE>;
@@ -613,17 +621,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_assign(const __grid_consta
                 // pass 1: the smallest of the k values (four independent chains; two 32-column
                 // loads in flight per wait)
                 float m4[4] = {kInf, kInf, kInf, kInf};
-                for (int cb = 0; cb < k; cb += 64) {
+                constexpr bool kLean = tc_min_blocks<D>() > 1;     // one load in flight: fewer registers
+                constexpr int kStep = kLean ? 32 : 64;
+                for (int cb = 0; cb < k; cb += kStep) {
                     uint32_t v0[32], v1[32];
-                    const bool two = cb + 32 < k;
+                    const bool two = !kLean && cb + 32 < k;
                     tmem_ld32_nowait(taddr + (uint32_t)cb, v0);
                     if (two) tmem_ld32_nowait(taddr + (uint32_t)(cb + 32), v1);
                     tmem_wait();
-                    if (cb + 64 <= k) {
+                    if (cb + kStep <= k) {
 #pragma unroll
                         for (int q = 0; q < 32; q++) m4[q & 3] = fminf(m4[q & 3], __uint_as_float(v0[q]));
+                        if (!kLean) {
 #pragma unroll
-                        for (int q = 0; q < 32; q++) m4[q & 3] = fminf(m4[q & 3], __uint_as_float(v1[q]));
+                            for (int q = 0; q < 32; q++) m4[q & 3] = fminf(m4[q & 3], __uint_as_float(v1[q]));
+                        }
                     } else {
 #pragma unroll
                         for (int q = 0; q < 32; q++)
@@ -1012,6 +1024,13 @@ int mode_of(int prec)
     }
 }
 
+// PSCL_PREC_TC: TF32x3 where its operands fit, else BF16x3.
+int resolve_prec(int d, int kmax, int prec)
+{
+    if (prec != PSCL_PREC_TC) return prec;
+    return fits_by_d<kModeTf32x3>(d, kmax) ? PSCL_PREC_TF32X3 : PSCL_PREC_BF16X3;
+}
+
 }  // namespace
 
 // The tensor-core assignment serves d in {16, 32, 64, 128} and at most 256 centers per
@@ -1020,7 +1039,7 @@ int mode_of(int prec)
 bool tc_supported(int d, int kmax, int prec)
 {
     if (kmax < 1 || kmax > 256 || !encode_tiled()) return false;
-    switch (mode_of(prec)) {
+    switch (mode_of(resolve_prec(d, kmax, prec))) {
     case kModeBf16: return fits_by_d<kModeBf16>(d, kmax);
     case kModeTf32x3: return fits_by_d<kModeTf32x3>(d, kmax);
     case kModeBf16x3: return fits_by_d<kModeBf16x3>(d, kmax);
@@ -1032,7 +1051,7 @@ cudaError_t launch_lloyd_assign_tc(const LloydBuffers &b, const SegTable &t, int
                                    uint32_t *flags, int sm_count, cudaStream_t st, KTimer *kt)
 {
     if (!t.split) return cudaErrorInvalidValue;
-    switch (mode_of(prec)) {
+    switch (mode_of(resolve_prec(d, kmax, prec))) {
     case kModeBf16: return tc_by_d<kModeBf16>(b, t, d, iter, kmax, flags, sm_count, st, kt);
     case kModeTf32x3: return tc_by_d<kModeTf32x3>(b, t, d, iter, kmax, flags, sm_count, st, kt);
     case kModeBf16x3: return tc_by_d<kModeBf16x3>(b, t, d, iter, kmax, flags, sm_count, st, kt);

@@ -48,3 +48,12 @@ def test_null_arguments_are_rejected():
     assert lib.pscl_job_sync(None) == binding.PSCL_EINVAL
     assert lib.pscl_scale_features(None) == binding.PSCL_EINVAL
     assert b"NULL" in lib.pscl_last_error()
+    assert lib.pscl_measure_fp32_fma(0, None) == binding.PSCL_EINVAL
+
+
+@pytest.mark.gpu
+def test_measured_fma_rate_is_plausible():
+    # 152 SMs x 128 lanes x 2 flop at 1-2.1 GHz: between about 39 and 81 TFLOP/s; the
+    # bound is loose on both sides so that clocks under another load still pass
+    t = binding.pscl_measure_fp32_fma(0)
+    assert 20.0 < t < 100.0, t

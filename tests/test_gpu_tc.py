@@ -18,6 +18,8 @@ def served(d, k, prec):
     64, 128}, k <= 256, and the two operand stages, two point stages and operand B within
     one CTA's shared memory (which leaves out d = 64 in TF32x3 above 16 centers and d = 128
     except BF16 with 16 centers)."""
+    if prec == B.PSCL_PREC_TC:
+        return served(d, k, B.PSCL_PREC_TF32X3) or served(d, k, B.PSCL_PREC_BF16X3)
     if d not in (16, 32, 64, 128) or k > 256:
         return False
     if d == 64 and prec == B.PSCL_PREC_TF32X3:
@@ -28,7 +30,7 @@ def served(d, k, prec):
 
 
 PRECS = [("tf32", B.PSCL_PREC_TF32), ("bf16", B.PSCL_PREC_BF16), ("tf32x3", B.PSCL_PREC_TF32X3),
-         ("bf16x3", B.PSCL_PREC_BF16X3)]
+         ("bf16x3", B.PSCL_PREC_BF16X3), ("tc", B.PSCL_PREC_TC)]
 
 
 @pytest.mark.parametrize("name,prec", PRECS)
@@ -86,7 +88,7 @@ def test_tensor_core_falls_back_above_256_centers():
 
 
 @pytest.mark.parametrize("name,prec", [("tf32", B.PSCL_PREC_TF32), ("bf16", B.PSCL_PREC_BF16),
-                                       ("bf16x3", B.PSCL_PREC_BF16X3)])
+                                       ("bf16x3", B.PSCL_PREC_BF16X3), ("tc", B.PSCL_PREC_TC)])
 def test_tensor_core_256_centers_of_64_attributes(name, prec):
     # the precision workload's set shape: 256 centers of 64 attributes, the largest operand
     # B and the largest shared sums; labels and centers still equal the float32 path
