@@ -282,7 +282,9 @@ int pscl_measure_fp32_fma(int device, double *tflops);
  * keeps the last call's contents (the counter is cleared at the start of each call), so
  * calls whose work overlaps on the GPU race: order them on one stream or synchronise.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  Nothing is allocated or freed.
+ * make that first call before any stream capture.  The address is looked up again when
+ * the current context is not the one it was found in (after cudaDeviceReset, say); that
+ * call too must come before any capture.  Nothing is allocated or freed.
  * Errors: PSCL_EINVAL, PSCL_ECUDA (see pscl_last_error()). */
 int pscl_assign_sse_noalloc(const float *points, int64_t n, int32_t d, const float *centers,
                             int32_t k, int32_t *labels, double *sse, void *stream);

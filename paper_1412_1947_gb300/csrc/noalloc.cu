@@ -8,6 +8,7 @@
 // SSE step of pscl_cluster, but its scratch (one float64 partial sum per thread block and a
 // completion ticket) lives in the file-scope array below instead of memory the library
 // allocates.  The caller supplies the points, the centers and the two outputs.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -28,13 +29,48 @@ static __device__ __align__(256) unsigned char g_sse_scratch[kNoAllocBytes];
 
 std::mutex g_setup_mu;
 void *g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};
 int g_sm_count[kMaxDevices] = {};
 
-// Once per device, with that device current: the device address of the scratch array.
+// The unique id of the calling thread's current context (cuCtxGetId; ids are never reused
+// within a process), 0 if there is none or the driver cannot say.
+unsigned long long current_ctx_id()
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static const GetCurrent get_cur = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        cudaGetLastError();
+        return reinterpret_cast<GetCurrent>(f);
+    }();
+    static const GetId get_id = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        cudaGetLastError();
+        return reinterpret_cast<GetId>(f);
+    }();
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_cur || !get_id || get_cur(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// With the device current: the device address of the scratch array in the current
+// context, looked up again whenever the context differs from the one it was found in
+// (a device reset or a rebuilt primary context loads the module afresh, possibly at
+// another address).
 cudaError_t scratch_for_device(int dev, void **addr, int *sms)
 {
     std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long id = current_ctx_id();
+    if (!g_scratch_addr[dev] || id == 0 || id != g_ctx_id[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_sse_scratch);
         if (e != cudaSuccess) return e;
@@ -43,6 +79,7 @@ cudaError_t scratch_for_device(int dev, void **addr, int *sms)
         if (e != cudaSuccess) return e;
         g_sm_count[dev] = n;
         g_scratch_addr[dev] = p;
+        g_ctx_id[dev] = current_ctx_id();      // the lookup made the context current if it was not
     }
     *addr = g_scratch_addr[dev];
     *sms = g_sm_count[dev];

@@ -114,30 +114,41 @@ void start(pscl_server *s, Slot &sl, Ticket *t)
     if (s->in_use > s->peak) s->peak = s->in_use;
 }
 
-// The job on slot sl has finished on the device: collect its results, release it.
-void finish(pscl_server *s, Slot &sl)
+// A finished job's results copied to host memory and its device memory released.  Called
+// by the worker WITHOUT the lock (the copies block), on a ticket already taken off its
+// slot; the ticket stays RUNNING and its bytes counted until settle().
+void collect(Ticket *t)
 {
-    Ticket *t = sl.cur;
-    sl.cur = nullptr;
     const pscl_job_desc &d = t->desc;
     t->centers.resize((size_t)d.final_k * d.d);
     if (d.want_labels) t->labels.resize((size_t)d.n);
-    int rc = pscl_get_result(t->job, t->centers.data(), d.want_labels ? t->labels.data() : nullptr, &t->sse);
-    if (rc) {
-        fail_ticket(t, rc, pscl_last_error());
+    t->err = pscl_get_result(t->job, t->centers.data(), d.want_labels ? t->labels.data() : nullptr, &t->sse);
+    if (t->err) t->msg = pscl_last_error();
+    pscl_job_destroy(t->job);
+    t->job = nullptr;
+}
+
+// The collected job's state, the counters and the bytes in use; with the lock held.
+void settle(pscl_server *s, Ticket *t)
+{
+    if (t->err) {
+        fail_ticket(t, t->err, t->msg.c_str());
         s->failed++;
     } else {
         t->state = PSCL_JOB_DONE;
         t->t_done = Clock::now();
         s->completed++;
     }
-    pscl_job_destroy(t->job);
-    t->job = nullptr;
     s->in_use -= t->footprint;
 }
 
+// A job waiting for memory is passed over when a job behind it starts; after this many
+// times, no later job starts ahead of it.
+constexpr int kMaxPassedOver = 32;
+
 void admit(pscl_server *s)
 {
+    std::vector<Ticket *> waiting;        // earlier jobs of this pass that did not fit
     for (auto it = s->queue.begin(); it != s->queue.end();) {
         Slot *free_slot = nullptr;
         for (auto &sl : s->slots)
@@ -151,10 +162,14 @@ void admit(pscl_server *s)
             it = s->queue.erase(it);
             start(s, *free_slot, t);
             if (t->state == PSCL_JOB_FAILED) s->cv.notify_all();
+            else
+                for (Ticket *w : waiting) w->passed_over++;     // t went ahead of each of them
             continue;
         }
-        // does not fit yet: later jobs may go ahead, until this one has waited long enough
-        if (++t->passed_over >= 32) return;
+        // does not fit yet: later jobs may go ahead, unless this one has been passed over
+        // enough times already
+        if (t->passed_over >= kMaxPassedOver) return;
+        waiting.push_back(t);
         ++it;
     }
 }
@@ -163,9 +178,11 @@ void loop(pscl_server *s)
 {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
+    std::vector<Ticket *> done;
     for (;;) {
         bool progress = false;
         int64_t running = 0;
+        done.clear();
         for (auto &sl : s->slots) {
             if (!sl.cur) continue;
             const cudaError_t q = cudaEventQuery(sl.cur->done);
@@ -174,10 +191,18 @@ void loop(pscl_server *s)
                 continue;
             }
             if (q != cudaSuccess) cudaGetLastError();      // the job's own sync reports it
-            finish(s, sl);
+            done.push_back(sl.cur);
+            sl.cur = nullptr;
+        }
+        if (!done.empty()) {
+            // results are copied without the lock: submit, poll and wait go on meanwhile
+            lk.unlock();
+            for (Ticket *t : done) collect(t);
+            lk.lock();
+            for (Ticket *t : done) settle(s, t);
+            s->cv.notify_all();
             progress = true;
         }
-        if (progress) s->cv.notify_all();
         if (s->stop && running == 0) break;
         if (!s->stop) {
             const size_t before = s->queue.size();

@@ -131,6 +131,46 @@ def test_wait_times_out_and_arrivals_overlap():
             assert ts[0] < tb[2]               # admitted before the big job was done
 
 
+def test_a_waiting_job_is_passed_over_only_by_jobs_that_start():
+    # Backfill: a large job that does not fit while another large one runs lets the small
+    # jobs behind it start.  It counts as passed over once per job that starts ahead of it,
+    # not once per scheduler pass (which would reach the limit within a few ms and then
+    # hold every later job back), so small jobs that arrive 5 ms later still start while
+    # the first large job runs; results stay exact.
+    import torch
+    big = [torch.from_numpy(synth.mixture(1 << 21, 32, 64, seed=s)).cuda() for s in (11, 12)]
+    smalls = make_jobs(3, seed=55)                 # as many as the slots left free
+    dev = [torch.from_numpy(jb["points"]).cuda() for jb in smalls]
+    ctx = B.pscl_ctx_create(0)
+    fp_big = B.pscl_job_footprint(ctx, 1 << 21, 32, 8192, 64, 64, 40)
+    fp_small = max(B.pscl_job_footprint(ctx, len(jb["points"]), jb["points"].shape[1], jb["N"], jb["local_k"],
+                                        jb["final_k"], jb["iters"]) for jb in smalls)
+    budget = 2 * fp_big - 1                        # the two large jobs never fit together
+    assert fp_big + 3 * fp_small <= budget
+    with B.Server(slots=4, hbm_budget_bytes=budget, ctx=ctx) as s:
+        t0 = time.perf_counter()
+        t_big = [s.submit(x, 8192, 64, 64, 40, 3) for x in big]
+        sub_big1 = 1e3 * (time.perf_counter() - t0)
+        time.sleep(0.005)                          # the second large job waits meanwhile
+        ts, sub = [], []
+        for x, jb in zip(dev, smalls):
+            sub.append(1e3 * (time.perf_counter() - t0))
+            ts.append(s.submit(x, jb["N"], jb["local_k"], jb["final_k"], jb["iters"], jb["seed"], want_labels=True))
+        for t in t_big + ts:
+            s.wait(t)
+        _, _, _, tb0 = s.fetch(t_big[0])
+        _, _, _, tb1 = s.fetch(t_big[1])
+        for t, jb, sb in zip(ts, smalls, sub):
+            c, lab, sse, tt = s.fetch(t)
+            ref = run_alone(jb)
+            np.testing.assert_array_equal(c, ref[0])
+            np.testing.assert_array_equal(lab, ref[1])
+            assert sse == ref[2]
+            assert sb + tt[0] < tb0[2], (sb, tt, tb0)    # admitted before the first large job was done
+        assert sub_big1 + tb1[0] + 0.1 >= tb0[2]         # the second large job waited for the first
+    B.pscl_ctx_destroy(ctx)
+
+
 def test_served_jobs_match_the_oracle():
     # a seeded sample of the serving recipe (n and final k log-uniform, d in {8, 32, 128},
     # half of the jobs stored in bfloat16, 25 iterations) served together; each job equals
