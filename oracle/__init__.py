@@ -158,6 +158,29 @@ def lloyd(pts: np.ndarray, init_centers: np.ndarray, iters: int, force=None, tie
     return c, lab, hist[:iters], cnt, nf.value, nb.value
 
 
+def standard_kmeans(x: np.ndarray, init_centers: np.ndarray, iters: int):
+    """One-level ("standard") k-means, Lloyd's algorithm as Section I describes it: every
+    point goes to the center at the smallest squared Euclidean distance (the lowest index
+    among equal distances), then every center moves to the mean of its points (a center
+    with none stays).  The method reduces to it with one subcluster and one local center
+    per point.  Written apart from the C oracle's Lloyd, in vectorised float64 numpy, so
+    that the two-level oracle can be pinned against something other than itself.
+    Returns (centers, labels, SSE after each iteration's update)."""
+    pts = np.asarray(x, np.float64)
+    c = np.array(init_centers, np.float64, copy=True)
+    lab = np.zeros(len(pts), np.int64)
+    hist = []
+    for _ in range(iters):
+        d2 = ((pts[:, None, :] - c[None, :, :]) ** 2).sum(axis=2)
+        lab = d2.argmin(axis=1)
+        for j in range(len(c)):
+            members = pts[lab == j]
+            if len(members):
+                c[j] = members.mean(axis=0)
+        hist.append(float(((pts - c[lab]) ** 2).sum()))
+    return c, lab, np.array(hist)
+
+
 def lloyd_seeded(pts: np.ndarray, k: int, iters: int, seed: int, stage: int = 0, segment: int = 0,
                  first_k: bool = False):
     pts = np.ascontiguousarray(pts, np.float32)

@@ -249,9 +249,21 @@ def test_two_level_reduces_to_standard_kmeans():
     pooled = r.local_centers.astype(np.float32)
     assert sorted(map(tuple, pooled.tolist())) == sorted(map(tuple, r.scaled.tolist()))
     init = pooled[oracle.init_indices(seed, 1, 0, n, k)].astype(np.float64)
-    c, lab, hist, _, _, _ = oracle.lloyd(r.scaled, init, T)
+    # against the separately written one-level k-means (numpy), not the oracle's own Lloyd
+    c, lab, hist = oracle.standard_kmeans(r.scaled, init, T)
     np.testing.assert_allclose(r.final_centers, c, rtol=0, atol=1e-14)
     np.testing.assert_allclose(r.final_sse_hist, hist, rtol=1e-13, atol=0)
+
+
+def test_standard_kmeans_on_a_hand_worked_case():
+    # four points on a line, two centers: assignments and means by hand
+    x = np.array([[0.0], [1.0], [9.0], [10.0]])
+    c, lab, hist = oracle.standard_kmeans(x, np.array([[0.0], [1.0]]), 2)
+    # iteration 1: {0} -> 0, {1, 9, 10} -> 1 (mean 20/3); iteration 2: {0, 1} -> 0 (0.5),
+    # {9, 10} -> 1 (9.5)
+    np.testing.assert_array_equal(lab, [0, 0, 1, 1])
+    np.testing.assert_allclose(c, [[0.5], [9.5]])
+    np.testing.assert_allclose(hist, [(1 - 20 / 3) ** 2 + (9 - 20 / 3) ** 2 + (10 - 20 / 3) ** 2, 4 * 0.25])
 
 
 def test_two_level_one_iteration_matches_vectorised_lloyd():
