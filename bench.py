@@ -715,6 +715,9 @@ def main():
     ap.add_argument("--serve-jobs", type=int, default=200)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--oracle-n", type=int, default=1 << 17)
+    ap.add_argument("--n", type=int, default=0,
+                    help="run the workload's recipe at n points (same N, k, iterations), e.g. for a "
+                         "profiler capture of a small case; 0 = the workload's own n")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--prec", default="tc", choices=["fp32", "tf32", "bf16", "tf32x3", "bf16x3", "tc"],
@@ -743,6 +746,8 @@ def main():
             main_uneven(args)
         return
     w = {"small": synth.SMALL, "medium": synth.MEDIUM, "large": synth.LARGE}[args.workload]
+    if args.n:
+        w = synth.scaled_down(w, args.n)
     if args.impl == "reference":
         reference_arm(args, w)
     else:

@@ -778,6 +778,9 @@ static int run_lloyd(pscl_job *j, const LloydPlan &p, const float *pts, float *c
     b.trace = trace;
     b.rows = p.rows;
     b.weights = weights;
+    // the near ties' candidate masks borrow the peel's bucket lists (d * ord_ld words, idle
+    // once the peel is done; 8 words per row fit whenever d >= 8)
+    if (j->pb.ord && (size_t)p.rows * 8 <= (size_t)j->d * (size_t)j->pb.ord_ld) b.tmask = j->pb.ord;
     b.wait_limit = j->wait_limit;
     b.tc_stall = j->test_stall == 2;
     CU(launch_lloyd_init(b, t, j->d, p.P, seed, stage, j->first_k, p.kmax, st, &j->kt));
@@ -1162,6 +1165,7 @@ struct pscl_batch : Owner {
     float *centers = nullptr;
     unsigned long long *acc = nullptr;
     int32_t *cnt = nullptr, *labels = nullptr, *out_labels = nullptr, *trace = nullptr;
+    uint32_t *tmask = nullptr;        // rows x 8 (tensor-core precisions only)
     int64_t trace_len = 0;
     double *unit_sse = nullptr, *seg_sse = nullptr;
     uint32_t *flags = nullptr;
@@ -1345,6 +1349,7 @@ static int batch_enqueue(pscl_batch *b, int iters, uint64_t seed, int prec, bool
     lb.labels = b->labels;
     lb.trace = b->trace_on ? b->trace : nullptr;
     lb.rows = b->rows;
+    lb.tmask = b->tmask;
     const int64_t P = b->plan.P;
     CU(launch_lloyd_init(lb, t, b->d, P, seed, 0u, 0, b->plan.kmax, st, &b->kt));
     if (events) CU(cudaEventRecord(b->ev[0], st));
@@ -1387,6 +1392,8 @@ extern "C" int pscl_batch_run(pscl_batch *b, int32_t iters, uint64_t seed, int p
         if (tl) TRY(A(b, &b->trace, tl));
     }
     b->iters = iters;
+    // the tensor-core assignment's candidate masks: 8 words per row, allocated once
+    if (prec != PSCL_PREC_FP32 && !b->tmask) TRY(A(b, &b->tmask, (size_t)b->rows * 8));
     if (!b->graph) return batch_enqueue(b, iters, seed, prec, true);
     const uint64_t key[6] = {(uint64_t)iters, seed, (uint64_t)prec, (uint64_t)(b->trace_on | b->plain << 1),
                              (uint64_t)b->unit_rows, (uint64_t)b->rpt};

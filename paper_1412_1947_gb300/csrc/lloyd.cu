@@ -619,7 +619,7 @@ cudaError_t launch_lloyd_iter(const LloydBuffers &b, int32_t *count_next, const 
                               KTimer *kt, int rows_per_thread)
 {
     cudaError_t e;
-    if (prec != PSCL_PREC_FP32 && !b.weights && t.split && unit_lo == 0 && unit_hi == t.n_units &&
+    if (prec != PSCL_PREC_FP32 && !b.weights && b.tmask && t.split && unit_lo == 0 && unit_hi == t.n_units &&
         tc_supported(d, kmax, prec)) {
         e = launch_lloyd_assign_tc(b, t, d, iter, kmax, prec, flags, sm_count, st, kt);
     } else switch (d) {

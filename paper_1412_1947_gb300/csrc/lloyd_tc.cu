@@ -277,6 +277,7 @@ struct TileMeta {
 struct TcArgs {
     const float *centers;
     int32_t *labels;
+    uint32_t *tmask;             // 8 words per row: a near tie's candidate centers
     SegTable t;
     const int32_t *split;        // CTA c serves the units [split[c], split[c + 1])
     uint32_t *flags;
@@ -680,6 +681,11 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<D>()) k_tc_assign(co
                 }
                 if (live) {
                     p.labels[row] = nc > 1 ? (int32_t)kTieBit : first;
+                    if (nc > 1) {        // the candidates, for the sums pass to re-score
+                        uint4 *mk = reinterpret_cast<uint4 *>(p.tmask + (size_t)row * 8);
+                        mk[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                        mk[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                    }
                     n_tie += nc > 1;
                     n_row++;
                 }
@@ -706,12 +712,12 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<D>()) k_tc_assign(co
 }
 
 // ---------------------------------------------------------------- sums and near ties
-// After the tensor-core assignment the thread of a near-tie row loads the row and re-scores
-// its candidates (or all centers when they were more than kMaxCand)
+// After the tensor-core assignment a warp re-scores each near-tie row against the candidate
+// centers the assignment marked for it (those within twice the error bound of the best)
 // with PSCL_PREC_FP32's arithmetic -- t = RN(x_a - c_a), acc = RN(t t + acc) in ascending a,
 // the lowest index among equal sums -- so the label is the float32 direct winner.  Then each
 // row's coordinates are added to its center's exact 32.32 fixed-point sum (a warp takes its
-// rows one at a time, lane a attribute a), as two 32-bit
+// rows a few at a time, lane a attribute a), as two 32-bit
 // halves in shared memory (hi, lo <= 2^16 per row from fix_parts, so 32768 rows fit before
 // a fold), folded into the 64-bit global sums at the end of each run of one set.
 // Persistent: CTA c serves the units [split[c], split[c + 1]).  Also writes the final
@@ -728,6 +734,7 @@ template <int D>
 __global__ void __launch_bounds__(sum_threads<D>()) k_tc_sums(const float *__restrict__ pts,
                                                              const float *__restrict__ centers, SegTable t,
                                                              const int32_t *split, int32_t *labels,
+                                                             const uint32_t *__restrict__ tmask,
                                                              int32_t *trace, int64_t trace_off,
                                                              unsigned long long *acc, int32_t *count, int kmax)
 {
@@ -760,10 +767,11 @@ __global__ void __launch_bounds__(sum_threads<D>()) k_tc_sums(const float *__res
             int32_t lab = live ? labels[row] : 0;
             const bool tie = live && ((uint32_t)lab & kTieBit);
             if (!tie && (uint32_t)lab >= (uint32_t)k) lab = 0;   // only after an assignment that gave up
-            // near ties: the whole warp re-scores every center for one such row at a time
-            // (lane l takes centers l, l + 32, ..., two at a time; the row in every lane's
-            // registers, the centers in shared memory as float4 at a stride of D + 4 floats,
-            // which keeps a quarter warp's 128-bit loads on distinct banks)
+            // near ties: the whole warp re-scores one such row at a time, lane l the row's
+            // candidate centers l, l + 32, ... (the bits of its mask; every center left out
+            // lies beyond the float32 direct sum's error of the best), the row in every
+            // lane's registers, the centers in shared memory as float4 at a stride of
+            // D + 4 floats (a quarter warp's 128-bit loads on distinct banks)
             {
                 const int lane = tid & 31;
                 uint32_t tm = __ballot_sync(0xffffffffu, tie);
@@ -783,33 +791,30 @@ __global__ void __launch_bounds__(sum_threads<D>()) k_tc_sums(const float *__res
                             x[4 * a4 + 3] = v.w;
                         }
                     }
+                    const uint4 *mk = reinterpret_cast<const uint4 *>(tmask + trow * 8);
+                    const uint4 ma = __ldg(mk), mb = __ldg(mk + 1);
+                    const uint32_t wd[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
                     float bd = __int_as_float(0x7f800000);
                     int bj = 0x7fffffff;
-                    for (int j = lane; j < k; j += 64) {
-                        const bool two = j + 32 < k;
-                        const float4 *c0 = reinterpret_cast<const float4 *>(scen + (size_t)j * DC);
-                        const float4 *c1 = reinterpret_cast<const float4 *>(scen + (size_t)(two ? j + 32 : j) * DC);
-                        float d0 = 0.0f, d1 = 0.0f;
 #pragma unroll
-                        for (int a4 = 0; a4 < D / 4; a4++) {
-                            const float4 u = c0[a4], v = c1[a4];
-                            float t;
-                            t = __fsub_rn(x[4 * a4 + 0], u.x); d0 = __fmaf_rn(t, t, d0);
-                            t = __fsub_rn(x[4 * a4 + 0], v.x); d1 = __fmaf_rn(t, t, d1);
-                            t = __fsub_rn(x[4 * a4 + 1], u.y); d0 = __fmaf_rn(t, t, d0);
-                            t = __fsub_rn(x[4 * a4 + 1], v.y); d1 = __fmaf_rn(t, t, d1);
-                            t = __fsub_rn(x[4 * a4 + 2], u.z); d0 = __fmaf_rn(t, t, d0);
-                            t = __fsub_rn(x[4 * a4 + 2], v.z); d1 = __fmaf_rn(t, t, d1);
-                            t = __fsub_rn(x[4 * a4 + 3], u.w); d0 = __fmaf_rn(t, t, d0);
-                            t = __fsub_rn(x[4 * a4 + 3], v.w); d1 = __fmaf_rn(t, t, d1);
-                        }
-                        if (d0 < bd) {               // ascending j in the lane: strict keeps the lowest
-                            bd = d0;
-                            bj = j;
-                        }
-                        if (two && d1 < bd) {
-                            bd = d1;
-                            bj = j + 32;
+                    for (int c = 0; c < 8; c++) {
+                        const int j = 32 * c + lane;
+                        if (j < k && ((wd[c] >> lane) & 1u)) {
+                            const float4 *c0 = reinterpret_cast<const float4 *>(scen + (size_t)j * DC);
+                            float d0 = 0.0f;
+#pragma unroll
+                            for (int a4 = 0; a4 < D / 4; a4++) {
+                                const float4 u = c0[a4];
+                                float t;
+                                t = __fsub_rn(x[4 * a4 + 0], u.x); d0 = __fmaf_rn(t, t, d0);
+                                t = __fsub_rn(x[4 * a4 + 1], u.y); d0 = __fmaf_rn(t, t, d0);
+                                t = __fsub_rn(x[4 * a4 + 2], u.z); d0 = __fmaf_rn(t, t, d0);
+                                t = __fsub_rn(x[4 * a4 + 3], u.w); d0 = __fmaf_rn(t, t, d0);
+                            }
+                            if (d0 < bd) {           // ascending j in the lane: strict keeps the lowest
+                                bd = d0;
+                                bj = j;
+                            }
                         }
                     }
 #pragma unroll
@@ -821,6 +826,7 @@ __global__ void __launch_bounds__(sum_threads<D>()) k_tc_sums(const float *__res
                             bj = oj;
                         }
                     }
+                    if ((uint32_t)bj >= (uint32_t)k) bj = 0;     // no candidate: only after an assignment that gave up
                     if (lane == src) lab = bj;
                 }
             }
@@ -957,6 +963,7 @@ cudaError_t tc_dispatch(const LloydBuffers &b, const SegTable &t, int iter, int 
     TcArgs a;
     a.centers = b.centers;
     a.labels = b.labels;
+    a.tmask = b.tmask;
     a.t = t;
     a.flags = flags;
     a.wait_limit = b.wait_limit ? b.wait_limit : kDefaultWait;
@@ -984,7 +991,7 @@ cudaError_t tc_dispatch(const LloydBuffers &b, const SegTable &t, int iter, int 
     const int m = 4;
     kt->begin(st);
     ks<<<m * sm_count, sum_threads<D>(), ss, st>>>(b.pts, b.centers, t, t.split + t.split_off[m], b.labels,
-                                                   b.trace, (int64_t)iter * b.rows, b.acc, b.count, kmax);
+                                                   b.tmask, b.trace, (int64_t)iter * b.rows, b.acc, b.count, kmax);
     kt->end(PSCL_K_LLOYD_SUMS, st);
     return cudaGetLastError();
 }

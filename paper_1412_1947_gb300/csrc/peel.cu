@@ -1619,16 +1619,23 @@ __global__ void __launch_bounds__(kPermThreads) k_perm_count(const uint32_t *__r
     cnt[(size_t)t * G + c] = h[t];
 }
 
-// Exclusive scan of the 256 x G counts in place (digit-major): one block of 1024 threads.
+// Exclusive scan of the 256 x G counts in place (digit-major): one block of 1024 threads,
+// each taking a run of consecutive counts (a multiple of 4, read and written as uint4 with
+// several loads in flight: the scan is a chain of L2 round trips, not a bandwidth cost).
 __global__ void __launch_bounds__(1024) k_perm_scan(uint32_t *cnt, uint32_t total)
 {
     __shared__ uint32_t ws[32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const uint32_t per = (total + 1023u) / 1024u;
-    const uint32_t b = (uint32_t)t * per, e = min(total, b + per);
+    const uint32_t per = (((total + 1023u) / 1024u) + 3u) & ~3u;        // total = 256 G, a multiple of 4
+    const uint32_t b = min(total, (uint32_t)t * per), e = min(total, b + per);
+    uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
     uint32_t s = 0;
-    for (uint32_t i = b; i < e; i++) s += cnt[i];
-    uint32_t inc = warp_incl_scan(s);
+#pragma unroll 8
+    for (uint32_t i = b; i < e; i += 4) {
+        const uint4 v = c4[i / 4];
+        s += v.x + v.y + v.z + v.w;
+    }
+    const uint32_t inc = warp_incl_scan(s);
     if (lane == 31) ws[w] = inc;
     __syncthreads();
     if (w == 0) {
@@ -1637,10 +1644,16 @@ __global__ void __launch_bounds__(1024) k_perm_scan(uint32_t *cnt, uint32_t tota
     }
     __syncthreads();
     uint32_t run = ws[w] + inc - s;
-    for (uint32_t i = b; i < e; i++) {
-        const uint32_t v = cnt[i];
-        cnt[i] = run;
-        run += v;
+#pragma unroll 8
+    for (uint32_t i = b; i < e; i += 4) {
+        const uint4 v = c4[i / 4];
+        uint4 o;
+        o.x = run;
+        o.y = run + v.x;
+        o.z = o.y + v.y;
+        o.w = o.z + v.z;
+        run = o.w + v.w;
+        c4[i / 4] = o;
     }
 }
 

@@ -203,6 +203,9 @@ struct LloydBuffers {
     // w x to its center's sum and w to its count; such runs use the float32 assignment
     // with global 64-bit sums (w q needs up to 63 bits).
     const int32_t *weights = nullptr;
+    // 8 words per row (or NULL): the tensor-core assignment marks a near tie's candidate
+    // centers here (bit j of word j / 32), the sums pass re-scores only those
+    uint32_t *tmask = nullptr;
     uint32_t wait_limit = 0;         // polls of the tensor-core kernel's bounded waits (0: default)
     int tc_stall = 0;                // test hook: the tensor-core kernel waits once on a barrier nothing completes
 };
