@@ -492,9 +492,20 @@ def main_uneven(args):
     e2e_mean = statistics.mean(e2e_s)
     d = raw.shape[1]
     flops = evals * 2 * d                 # the contraction: 2d flops per distance evaluation
-    roof = {"kernel": "Lloyd iterations (k_lloyd_assign + finalize)", "bound": "alu",
-            "achieved": flops / (lloyd_ms * 1e-3) / 1e12, "peak": B.pscl_measure_fp32_fma(0), "unit": "TFLOP/s",
-            "peak_kind": "measured float32 FMA rate (pscl_measure_fp32_fma, 2 flop per FMA)", "traffic": None}
+    if args.prec == "fp32":
+        roof = {"kernel": "Lloyd iterations (k_lloyd_assign + finalize)", "bound": "alu",
+                "achieved": flops / (lloyd_ms * 1e-3) / 1e12, "peak": B.pscl_measure_fp32_fma(0),
+                "unit": "TFLOP/s", "peak_kind": "measured float32 FMA rate (pscl_measure_fp32_fma, 2 flop per FMA)",
+                "traffic": None}
+    else:
+        mode = tc_mode(args.prec, synth.MEDIUM)       # d = 32: TF32x3 under "tc"
+        pk = measured_peaks()
+        roof = {"kernel": f"Lloyd iterations (k_tc_assign {mode} + k_tc_sums + finalize)", "bound": "tensor",
+                "achieved": flops / (lloyd_ms * 1e-3) / 1e12,
+                "peak": pk["bf16_tflops"] * (1.0 if mode.startswith("bf16") else TF32_PER_BF16), "unit": "TFLOP/s",
+                "peak_kind": ("of measured" if pk["kind"] == "measured" else "of fallback") + " cuBLAS bf16 burst"
+                             + ("" if mode.startswith("bf16") else " x nominal tf32/bf16"),
+                "traffic": None}
     roof["frac"] = roof["achieved"] / roof["peak"]
     line = {"metric": METRIC, "value": evals / (mean_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
