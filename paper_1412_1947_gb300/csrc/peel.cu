@@ -876,15 +876,21 @@ __device__ __noinline__ void settle_group(const PeelArgs &a, const float *Ls, ui
 
 // The next landmark (attributes j_first, j_first + j_step, ...): in each attribute the
 // smallest value among the points left (rnd >= live_from), found from the bucket order:
-// from the attribute's bucket pointer on, the first non-empty bucket whose entries include
-// a point left holds it; buckets whose entries are all gone are passed for good.
+// from the attribute's bucket pointer on, the first bucket whose entries include a point
+// left holds it; buckets whose entries are all gone are passed for good.  The buckets are
+// examined kThreads at a time, a thread checking the first kPeek entries of its bucket
+// (their ids and rounds loaded together), so a run of emptied buckets costs one step per
+// kThreads of them; a larger bucket whose first kPeek entries are gone, and the first
+// bucket with a point left, are then scanned by the whole CTA.
+constexpr int kPeek = 16;
+
 __device__ __noinline__ void find_landmark(const PeelArgs &a, int j_first, int j_step, uint32_t live_from)
 {
     PeelCtl *ctl = a.ctl;
     const int d = a.d;
     const uint32_t nbk = a.nbk;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    __shared__ uint32_t red_a[kW], red_b[kW];
+    __shared__ uint32_t red_a[kW], red_u[kW], red_b[kW];
     __shared__ uint32_t s_st, s_en;
     for (int j = j_first; j >= 0 && j < d; j += j_step) {
         const uint4 *bj = a.bcs + (size_t)j * nbk;
@@ -892,25 +898,44 @@ __device__ __noinline__ void find_landmark(const PeelArgs &a, int j_first, int j
         uint32_t b = __ldcg(&ctl->lptr[j]);       // the buckets before b hold no point left
         uint32_t mnb = kGone;
         while (b < nbk) {
-            // the first non-empty bucket from b on
+            // bucket b + t: 1 = a point left among its first kPeek entries, 2 = more
+            // entries than that and none of those left, 0 = nothing left
             const uint32_t bb = b + (uint32_t)t;
             const uint4 e = bb < nbk ? __ldcg(&bj[bb]) : make_uint4(0u, 0u, 0u, 0u);
-            uint32_t fb = warp_min(e.x > 0 ? bb : kGone);
-            if (lane == 0) red_a[w] = fb;
-            __syncthreads();
-            fb = red_a[0];
+            int state = 0;
+            if (e.x > 0) {
+                uint32_t ids[kPeek];
 #pragma unroll
-            for (int q = 1; q < kW; q++) fb = min(fb, red_a[q]);
+                for (int i = 0; i < kPeek; i++) ids[i] = e.y + i < e.z ? __ldcg(&oj[e.y + i]) : kGone;
+#pragma unroll
+                for (int i = 0; i < kPeek; i++)
+                    if (ids[i] != kGone && __ldcg(&a.rnd[ids[i]]) >= live_from) state = 1;
+                if (state == 0 && e.z > e.y + kPeek) state = 2;
+            }
+            uint32_t fa = warp_min(state == 1 ? bb : kGone), fu = warp_min(state == 2 ? bb : kGone);
+            if (lane == 0) {
+                red_a[w] = fa;
+                red_u[w] = fu;
+            }
+            __syncthreads();
+            fa = red_a[0];
+            fu = red_u[0];
+#pragma unroll
+            for (int q = 1; q < kW; q++) {
+                fa = min(fa, red_a[q]);
+                fu = min(fu, red_u[q]);
+            }
+            const uint32_t fb = min(fa, fu);
             if (bb == fb) {
                 s_st = e.y;
                 s_en = e.z;
             }
             __syncthreads();
-            if (fb == kGone) {
+            if (fb == kGone) {                     // kThreads buckets with nothing left
                 b += kThreads;
                 continue;
             }
-            // the smallest value among its entries left
+            // the smallest value among the entries of fb left (the whole CTA)
             const uint32_t st = s_st, en = s_en;
             uint32_t lm = kGone;
             for (uint32_t q = st + t; q < en; q += kThreads) {
@@ -930,7 +955,7 @@ __device__ __noinline__ void find_landmark(const PeelArgs &a, int j_first, int j
                 b = fb;
                 break;
             }
-            b = fb + 1;                            // every entry of fb is gone
+            b = fb + 1;                            // every entry of fb is gone (a large bucket)
         }
         if (t == 0) {
             ctl->lptr[j] = b;
