@@ -877,11 +877,12 @@ __device__ __noinline__ void settle_group(const PeelArgs &a, const float *Ls, ui
 // The next landmark (attributes j_first, j_first + j_step, ...): in each attribute the
 // smallest value among the points left (rnd >= live_from), found from the bucket order:
 // from the attribute's bucket pointer on, the first bucket whose entries include a point
-// left holds it; buckets whose entries are all gone are passed for good.  The buckets are
-// examined kThreads at a time, a thread checking the first kPeek entries of its bucket
-// (their ids and rounds loaded together), so a run of emptied buckets costs one step per
-// kThreads of them; a larger bucket whose first kPeek entries are gone, and the first
-// bucket with a point left, are then scanned by the whole CTA.
+// left holds it.  A point taken stays taken (live_from only grows), so each bucket's start
+// is moved past the entries found gone and a bucket whose start reaches its end is passed
+// for good: every entry is found gone at most once per run.  Buckets are examined kThreads
+// at a time, a thread peeking at the next kPeek entries of its bucket (their loads issued
+// together); a bucket that still has entries after those, and the first bucket with a
+// point left, are scanned by the whole CTA.
 constexpr int kPeek = 16;
 
 __device__ __noinline__ void find_landmark(const PeelArgs &a, int j_first, int j_step, uint32_t live_from)
@@ -890,27 +891,33 @@ __device__ __noinline__ void find_landmark(const PeelArgs &a, int j_first, int j
     const int d = a.d;
     const uint32_t nbk = a.nbk;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    __shared__ uint32_t red_a[kW], red_u[kW], red_b[kW];
+    __shared__ uint32_t red_a[kW], red_u[kW], red_b[kW], red_p[kW];
     __shared__ uint32_t s_st, s_en;
     for (int j = j_first; j >= 0 && j < d; j += j_step) {
-        const uint4 *bj = a.bcs + (size_t)j * nbk;
+        uint4 *bj = a.bcs + (size_t)j * nbk;
         const uint32_t *oj = a.ord + (size_t)j * a.ord_ld;
         uint32_t b = __ldcg(&ctl->lptr[j]);       // the buckets before b hold no point left
         uint32_t mnb = kGone;
         while (b < nbk) {
-            // bucket b + t: 1 = a point left among its first kPeek entries, 2 = more
-            // entries than that and none of those left, 0 = nothing left
+            // bucket b + t: 1 = a point left among its next kPeek entries, 2 = entries left
+            // to look at after those, 0 = nothing left
             const uint32_t bb = b + (uint32_t)t;
-            const uint4 e = bb < nbk ? __ldcg(&bj[bb]) : make_uint4(0u, 0u, 0u, 0u);
+            uint4 e = bb < nbk ? __ldcg(&bj[bb]) : make_uint4(0u, 0u, 0u, 0u);
             int state = 0;
-            if (e.x > 0) {
+            if (e.y < e.z) {
                 uint32_t ids[kPeek];
 #pragma unroll
                 for (int i = 0; i < kPeek; i++) ids[i] = e.y + i < e.z ? __ldcg(&oj[e.y + i]) : kGone;
+                uint32_t first = kPeek;
 #pragma unroll
-                for (int i = 0; i < kPeek; i++)
-                    if (ids[i] != kGone && __ldcg(&a.rnd[ids[i]]) >= live_from) state = 1;
-                if (state == 0 && e.z > e.y + kPeek) state = 2;
+                for (int i = kPeek - 1; i >= 0; i--)
+                    if (ids[i] != kGone && __ldcg(&a.rnd[ids[i]]) >= live_from) first = (uint32_t)i;
+                const uint32_t adv = first < kPeek ? first : min((uint32_t)kPeek, e.z - e.y);
+                if (adv) {
+                    e.y += adv;
+                    reinterpret_cast<uint32_t *>(&bj[bb])[1] = e.y;     // entries before e.y are gone
+                }
+                state = first < kPeek ? 1 : (e.y < e.z ? 2 : 0);
             }
             uint32_t fa = warp_min(state == 1 ? bb : kGone), fu = warp_min(state == 2 ? bb : kGone);
             if (lane == 0) {
@@ -935,27 +942,39 @@ __device__ __noinline__ void find_landmark(const PeelArgs &a, int j_first, int j
                 b += kThreads;
                 continue;
             }
-            // the smallest value among the entries of fb left (the whole CTA)
+            // bucket fb, the whole CTA: the smallest value among its entries left and the
+            // first of them (its start moves there, or to its end)
             const uint32_t st = s_st, en = s_en;
-            uint32_t lm = kGone;
+            uint32_t lm = kGone, fp = en;
             for (uint32_t q = st + t; q < en; q += kThreads) {
                 const uint32_t id = __ldcg(&oj[q]);
-                if (__ldcg(&a.rnd[id]) >= live_from)
+                if (__ldcg(&a.rnd[id]) >= live_from) {
                     lm = min(lm, __float_as_uint(__ldg(&a.x[(size_t)id * d + j])));
+                    fp = min(fp, q);
+                }
             }
             lm = warp_min(lm);
-            if (lane == 0) red_b[w] = lm;
+            fp = warp_min(fp);
+            if (lane == 0) {
+                red_b[w] = lm;
+                red_p[w] = fp;
+            }
             __syncthreads();
             lm = red_b[0];
+            fp = red_p[0];
 #pragma unroll
-            for (int q = 1; q < kW; q++) lm = min(lm, red_b[q]);
+            for (int q = 1; q < kW; q++) {
+                lm = min(lm, red_b[q]);
+                fp = min(fp, red_p[q]);
+            }
+            if (t == 0 && fp > st) reinterpret_cast<uint32_t *>(&bj[fb])[1] = fp;
             __syncthreads();
             if (lm != kGone) {
                 mnb = lm;
                 b = fb;
                 break;
             }
-            b = fb + 1;                            // every entry of fb is gone (a large bucket)
+            b = fb + 1;                            // every entry of fb is gone
         }
         if (t == 0) {
             ctl->lptr[j] = b;
