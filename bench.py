@@ -542,7 +542,7 @@ def main_uneven(args):
 
 def main_serving(args):
     """The job server under load: a stream of two-level jobs of mixed shapes (n log-uniform
-    in [1e4, 1e6], d in {8, 32, 128}, final k log-uniform in [8, 1024], N = n/64, 25
+    in [1e4, --serve-n-max], d in {8, 32, 128}, final k log-uniform in [8, 1024], N = n/64, 25
     iterations), points generated on the device; one saturated pass (all jobs submitted at
     once) gives the peak jobs/s, then Poisson arrivals at 0.5x and 0.8x of it give the
     latency percentiles.  Printed as its own line (not the default workload)."""
@@ -556,7 +556,7 @@ def main_serving(args):
 
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    jobs = synth.serving_stream(args.serve_jobs, synth.BASE_SEED + 4)
+    jobs = synth.serving_stream(args.serve_jobs, synth.BASE_SEED + 4, n_range=(1e4, args.serve_n_max))
     pts = [synth.mixture_device(j["n"], j["d"], j["blobs"], j["seed"], dev) for j in jobs]
     pts = [x.to(torch.bfloat16) if j["bf16"] else x for j, x in zip(jobs, pts)]
     torch.cuda.synchronize()
@@ -614,10 +614,12 @@ def main_serving(args):
             "warmup": 1, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (bf16 storage for half the jobs)",
             "data": "synthetic (generated on the device)",
-            "config": {"workload": f"serving{len(jobs)}_n1e4to1e6_d8-32-128_k8to1024", "jobs": len(jobs),
+            "config": {"workload": f"serving{len(jobs)}_n1e4to{args.serve_n_max:.0e}_d8-32-128_k8to1024".replace("+0", ""),
+                       "jobs": len(jobs),
                        "slots": args.serve_slots, "hbm_budget_bytes": budget, "iters": 25,
                        "bf16_jobs": sum(j["bf16"] for j in jobs),
-                       "note": "n scaled down 10x from the 1e4..1e7 stream"},
+                       "points": int(sum(j["n"] for j in jobs)),
+                       "note": "n log-uniform in [1e4, %.0e]" % args.serve_n_max},
             "saturated": {"jobs_per_s": peak, "p50_ms": ls[len(ls) // 2],
                           "p99_ms": ls[min(len(ls) - 1, int(0.99 * len(ls)))],
                           "dist_evals_per_s": evals / wall, "max_running": st["max_running"],
@@ -725,6 +727,9 @@ def main():
                     help="float32 assignment: 0 default, 1 one row per thread, 2 eight rows (d <= 16)")
     ap.add_argument("--serve-jobs", type=int, default=200)
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-n-max", type=float, default=1e6,
+                    help="largest n of the serving stream (n is log-uniform in [1e4, this]); 1e7 is the "
+                         "stream's stated range, 1e6 keeps a run within a minute")
     ap.add_argument("--oracle-n", type=int, default=1 << 17)
     ap.add_argument("--n", type=int, default=0,
                     help="run the workload's recipe at n points (same N, k, iterations), e.g. for a "

@@ -124,7 +124,11 @@ typedef enum {
      *    than the grid gives, 2 = the tensor-core assignment waits once on a barrier that
      *    nothing completes; either wait gives up after PSCL_OPT_WAIT_LIMIT polls and the
      *    job reports PSCL_ETIMEOUT.  For tests of the give-up path; default 0. */
-    PSCL_OPT_TEST_STALL = 11
+    PSCL_OPT_TEST_STALL = 11,
+    /* Jobs only: most thread blocks of the peel's cooperative launch, 0 = as many as fit
+     *    (two per SM).  A smaller grid lets the peels of several jobs run side by side; a
+     *    tuning choice: results do not depend on it. */
+    PSCL_OPT_PEEL_GRID = 12
 } pscl_option;
 
 /* The library's kernels, for pscl_get_kernel_times. */
@@ -160,7 +164,10 @@ const char *pscl_last_error(void);
  *   points            n x d row-major, float32 or bfloat16 (dtype), on the host (points_on_device = 0; copied
  *                     to the device before the call returns its status) or on the
  *                     context's device (points_on_device = 1; read later, by
- *                     pscl_scale_features).
+ *                     pscl_scale_features, on the context's stream: their writes must
+ *                     be complete or queued on that stream first -- a context created
+ *                     with a NULL stream has its own non-blocking stream, which does not
+ *                     wait for work on the legacy default stream).
  * Errors: PSCL_EINVAL (NULL pointer, n < 1, d outside 1..1024, dtype not PSCL_F32 / PSCL_BF16),
  *         PSCL_ENOMEM (over budget), PSCL_ECUDA. */
 int pscl_job_create(pscl_ctx *ctx, const void *points, int dtype, int64_t n, int32_t d,

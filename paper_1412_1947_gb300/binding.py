@@ -23,7 +23,7 @@ PRECISIONS = {"fp32": PSCL_PREC_FP32, "tf32": PSCL_PREC_TF32, "bf16": PSCL_PREC_
               "tf32x3": PSCL_PREC_TF32X3, "bf16x3": PSCL_PREC_BF16X3, "tc": PSCL_PREC_TC}
 PSCL_OPT_PLAIN_LLOYD, PSCL_OPT_TRACE_LABELS, PSCL_OPT_INIT_FIRST_K, PSCL_OPT_GRAPH = 1, 2, 3, 4
 PSCL_OPT_KERNEL_TIMING, PSCL_OPT_UNIT_ROWS, PSCL_OPT_ROWS_PER_THREAD, PSCL_OPT_POOL_WEIGHTED = 5, 6, 7, 8
-PSCL_OPT_PEEL_ROUNDS, PSCL_OPT_WAIT_LIMIT, PSCL_OPT_TEST_STALL = 9, 10, 11
+PSCL_OPT_PEEL_ROUNDS, PSCL_OPT_WAIT_LIMIT, PSCL_OPT_TEST_STALL, PSCL_OPT_PEEL_GRID = 9, 10, 11, 12
 
 # entry point -> (restype, argtypes); the list is the C ABI of include/pscl.h
 _P, _I, _I32, _I64, _U64, _SZ = C.c_void_p, C.c_int, C.c_int32, C.c_int64, C.c_uint64, C.c_size_t

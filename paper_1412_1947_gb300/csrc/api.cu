@@ -99,6 +99,7 @@ struct pscl_job : Owner {
     int peel_rounds = 0;              // rounds per distance pass of the peel (0: default)
     uint32_t wait_limit = 0;          // polls of a bounded device-side wait (0: default)
     int test_stall = 0;               // test hook: a wait that cannot complete (1 peel, 2 tensor core)
+    int peel_grid = 0;                // most CTAs of the peel's launch (0: as many as fit)
     KTimer kt;                        // launch counts (+ events when timing) of the last run
     // input and scaling
     int dtype = PSCL_F32;
@@ -383,6 +384,11 @@ extern "C" int pscl_job_set_option(pscl_job *j, int opt, int64_t v)
     case PSCL_OPT_TEST_STALL:
         if (v < 0 || v > 2) return fail(PSCL_EINVAL, "test stall must be 0, 1 or 2");
         j->test_stall = (int)v;
+        break;
+    case PSCL_OPT_PEEL_GRID:
+        if (v < 0 || v > (1 << 20)) return fail(PSCL_EINVAL, "peel grid must be 0..2^20");
+        j->peel_grid = (int)v;
+        drop_graph(j);
         break;
     case PSCL_OPT_POOL_WEIGHTED:
         // the weights sum to n in an int32 count, and w x to at most n 2^32 in 64 bits
@@ -822,6 +828,7 @@ static int enqueue_subcluster(pscl_job *j, bool events)
     j->pb.rounds_per_pass = j->peel_rounds;
     j->pb.wait_limit = j->wait_limit;
     j->pb.stall_first_barrier = j->test_stall == 1;
+    j->pb.max_grid = j->peel_grid;
     if (j->coop) {
         CU(cudaEventRecord(j->coop_ev[0], st));
         CU(cudaStreamWaitEvent(j->coop, j->coop_ev[0], 0));

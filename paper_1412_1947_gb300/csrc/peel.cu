@@ -1788,6 +1788,7 @@ cudaError_t peel_launch(const PeelBuffers &b, int64_t n, int d, int64_t N, int s
     if (grid > kMaxPeelGrid) grid = kMaxPeelGrid;
     const int64_t want = (n + 63) / 64;             // at least ~64 points per CTA
     if (grid > want) grid = std::max<int64_t>(1, want);
+    if (b.max_grid > 0 && grid > b.max_grid) grid = b.max_grid;
     PeelArgs a;
     a.x = b.x;
     a.d = d;

@@ -163,6 +163,7 @@ struct PeelBuffers {
     int rounds_per_pass;             // rounds one distance pass may serve (1..kMaxEpoch; 0: default)
     uint32_t wait_limit;             // polls of a bounded wait before it gives up (0: default)
     int stall_first_barrier;         // test hook: the first grid barrier waits for one CTA too many
+    int max_grid = 0;                // most CTAs of the launch (0: as many as fit)
 };
 // Buckets of the per-attribute orders the peel builds for n points.
 uint32_t peel_buckets(int64_t n);

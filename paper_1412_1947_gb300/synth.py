@@ -153,8 +153,14 @@ def mixture_device(n: int, d: int, blobs: int, seed: int, device, sigma_range=(0
     sig = sigma_range[0] + (sigma_range[1] - sigma_range[0]) * torch.rand(blobs, generator=g, device=device,
                                                                          dtype=torch.float64)
     which = torch.randint(0, blobs, (n,), generator=g, device=device)
-    z = torch.randn((n, d), generator=g, device=device, dtype=torch.float64)
-    return (means[which] + z * sig[which][:, None]).to(torch.float32).contiguous()
+    out = torch.empty((n, d), device=device, dtype=torch.float32)
+    step = max(1, (1 << 24) // d)            # rows per chunk: float64 temporaries stay ~130 MB
+    for r0 in range(0, n, step):
+        r1 = min(n, r0 + step)
+        z = torch.randn((r1 - r0, d), generator=g, device=device, dtype=torch.float64)
+        w = which[r0:r1]
+        out[r0:r1] = (means[w] + z * sig[w][:, None]).to(torch.float32)
+    return out
 
 
 def serving_stream(count: int, seed: int, n_range=(1e4, 1e6), dims=(8, 32, 128), k_range=(8, 1024)):

@@ -69,3 +69,19 @@ def test_duplicated_points():
     base = synth.mixture(6000, 8, 6, seed=606)
     raw = np.concatenate([base, base])
     _check(raw, 512, 8)
+
+
+@pytest.mark.parametrize("cap", [1, 7, 16, 19, 76])
+def test_partition_does_not_depend_on_the_grid(cap):
+    # PSCL_OPT_PEEL_GRID caps the cooperative launch (a grid under 16 CTAs has no
+    # landmark-only CTAs, every CTA then does both); the partition is the oracle's
+    raw = synth.mixture(6000, 16, 8, outlier_frac=0.01, seed=91)
+    N = 250
+    with B.Job(raw) as j:
+        j.option(B.PSCL_OPT_PEEL_GRID, cap)
+        j.steps(N, 4, 4, 1, 3)
+        perm, off = j.partition()
+        x = j.scaled()
+    operm, ooff, _ = oracle.peel(x, N)
+    np.testing.assert_array_equal(off, ooff)
+    np.testing.assert_array_equal(perm, operm)
