@@ -267,6 +267,7 @@ __device__ double dist64(const float *__restrict__ row, const float *Ls, int d)
 __device__ __forceinline__ void dist_ff(const float *__restrict__ row, const float *Ls, int d, float &h, float &l)
 {
     float hi = 0.0f, lo = 0.0f;
+#pragma unroll 4
     for (int j = 0; j < d; j++) {
         const float a = __ldg(&row[j]), b = Ls[j];
         const float s = __fsub_rn(a, b);
@@ -757,11 +758,24 @@ __device__ __noinline__ void settle_group(const PeelArgs &a, const float *Ls, ui
     const uint32_t q1 = __ldcg(&ctl->g_q1[g]), q2 = __ldcg(&ctl->g_q2[g]);
     const uint32_t ne = __ldcg(&ctl->gcnt[g]);
     // points certainly before the group: certain points of rounds up to q1 and the
-    // entries of the groups before it, whose regions precede the group's
-    uint32_t before = 0, off = 0;
-    for (uint32_t r = 0; r <= q1; r++) before += __ldcg(&ctl->cert[r]);
-    for (uint32_t h = 0; h < g; h++) off += __ldcg(&ctl->gcnt[h]);
-    before += off;
+    // entries of the groups before it, whose regions precede the group's (q1, g < 32:
+    // lane i of warp 0 loads round i's and group i's counts)
+    __shared__ uint32_t s_before, s_off;
+    if (t < 32) {
+        uint32_t cb = (uint32_t)t <= q1 ? __ldcg(&ctl->cert[t]) : 0u;
+        uint32_t go = (uint32_t)t < g ? __ldcg(&ctl->gcnt[t]) : 0u;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            cb += __shfl_xor_sync(0xffffffffu, cb, o);
+            go += __shfl_xor_sync(0xffffffffu, go, o);
+        }
+        if (t == 0) {
+            s_before = cb + go;
+            s_off = go;
+        }
+    }
+    __syncthreads();
+    const uint32_t before = s_before, off = s_off;
     const bool staged = ne <= (uint32_t)kStage;
     uint64_t *stk = reinterpret_cast<uint64_t *>(scr + kStageOff);
     uint32_t *stp = scr + kStageOff + 2 * kStage;
@@ -1581,15 +1595,25 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
                 s_cc[t] = off;                       // the group's region in gkey / gpos
             }
             __syncthreads();
-            for (uint32_t e = c * kThreads + t; e < nlist; e += G * kThreads) {
-                const uint32_t k = __ldcg(&a.band_k32[e]);
-                const uint32_t pos = __ldcg(&a.band_pos[e]);
+            // one slot claim per warp and group: the entries of a pass crowd into a few
+            // groups, whose fill counters would otherwise take one contended atomic each
+            for (uint32_t b0 = c * kThreads; b0 < nlist; b0 += G * kThreads) {     // warp-uniform bound
+                const uint32_t e = b0 + (uint32_t)t;
+                const bool v = e < nlist;
+                const uint32_t k = v ? __ldcg(&a.band_k32[e]) : 0u;
+                const uint32_t pos = v ? __ldcg(&a.band_pos[e]) : 0u;
                 uint32_t g = 0;
                 while (g + 1 < ng && k > s_gout[g]) g++;
-                const uint64_t dk = dff_key(a.x + (size_t)(pos & kPosMask) * d, Ls, d);
-                const uint32_t slot = s_cc[g] + atomicAdd(&ctl->gfill[g], 1u);
-                a.gkey[slot] = dk;
-                a.gpos[slot] = pos;
+                const uint32_t lane = (uint32_t)t & 31u;
+                const uint32_t peers = __match_any_sync(0xffffffffu, v ? g : 0xFFFFFFFFu);
+                const uint32_t leader = (uint32_t)__ffs(peers) - 1u;
+                uint32_t slot = 0;
+                if (v && lane == leader) slot = atomicAdd(&ctl->gfill[g], (uint32_t)__popc(peers));
+                slot = __shfl_sync(0xffffffffu, slot, (int)leader) + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+                if (v) {
+                    a.gkey[s_cc[g] + slot] = dff_key(a.x + (size_t)(pos & kPosMask) * d, Ls, d);
+                    a.gpos[s_cc[g] + slot] = pos;
+                }
             }
             if (!grid_sync(ctl, a.flags, gen, lim)) return;
             for (uint32_t g = c; g < ng; g += G) settle_group(a, Ls, g, r0, K, scr);
