@@ -132,6 +132,9 @@ struct pscl_job : Owner {
     int final_k = 0, fiters = 0, fprec = 0;
     uint64_t fseed = 0;
     LloydPlan fp;
+    // the SSE pass's row tables: all n rows as one set of 256 centers (final_k > 256) and of
+    // the remaining final_k mod 256 centers (final_k itself when it is at most 256)
+    LloydPlan sp256, sprem;
     float *cf = nullptr;
     unsigned long long *acc_f = nullptr;
     int32_t *cnt_f = nullptr;
@@ -667,6 +670,22 @@ static int plan_cluster(pscl_job *j, int32_t final_k, int32_t iters, uint64_t se
         j->acc_f = nullptr;
         j->cnt_f = nullptr;
         j->lab_f = nullptr;
+        // the SSE pass's tables for a search in chunks of 256 centers (tensor-core modes)
+        {
+            for (LloydPlan *q : {&j->sp256, &j->sprem}) {
+                job_free(j, q->d_seg_start);
+                job_free(j, q->d_i32);
+                job_free(j, q->d_split);
+                q->d_seg_start = nullptr;
+                q->d_i32 = nullptr;
+                q->d_split = nullptr;
+            }
+            std::vector<int64_t> s0(1, 0);
+            std::vector<int32_t> sn(1, (int32_t)j->n);
+            const int32_t rem = final_k % 256;
+            if (final_k > 256) TRY(build_lloyd_plan(j, j->sp256, s0, sn, std::vector<int32_t>(1, 256)));
+            if (final_k <= 256 || rem) TRY(build_lloyd_plan(j, j->sprem, s0, sn, std::vector<int32_t>(1, final_k <= 256 ? final_k : rem)));
+        }
         TRY(A(j, &j->cf, (size_t)final_k * d));
         TRY(A(j, &j->acc_f, (size_t)final_k * d));
         TRY(A(j, &j->cnt_f, 2 * (size_t)final_k));
@@ -731,6 +750,12 @@ static size_t job_footprint(int64_t n, int d, int64_t N, int local_k, int final_
     b += r256(8) + r256((4 + 3 * (size_t)uf + 1) * 4) + r256(split * 4);
     b += r256((size_t)final_k * d * 4) + r256((size_t)final_k * d * 8) + r256(2 * (size_t)final_k * 4) +
          r256((size_t)P * 4);
+    {   // the SSE pass's row tables (one set of n rows; one or two of them)
+        const int64_t tn = unit_target(n, sm, 0);
+        const int64_t un = (n + unit_size(n, tn) - 1) / unit_size(n, tn);
+        const int tables = (final_k > 256 ? 1 : 0) + (final_k <= 256 || final_k % 256 ? 1 : 0);
+        b += (size_t)tables * (r256(8) + r256((4 + 3 * (size_t)un + 1) * 4) + r256(split * 4));
+    }
     b += r256((size_t)n * 4) + r256((size_t)sse_grid(n, sm) * 8) + r256(8);
     if (trace) b += r256((size_t)iters * P * 4);
     return b;
@@ -854,8 +879,19 @@ static int enqueue_cluster(pscl_job *j, bool events)
     TRY(run_lloyd(j, j->fp, j->cl, j->cf, j->acc_f, j->cnt_f, j->lab_f, j->trace_f, j->fiters, j->fseed, 1u,
                   false, j->fprec, w));
     if (events) CU(cudaEventRecord(j->ev[4], st));
-    CU(launch_final_sse(j->x, j->n, j->d, j->cf, j->final_k, j->labels, j->blk_sse, j->sse, j->tickets + 1,
-                        j->ctx->sm_count, st, &j->kt));
+    // the SSE pass: on the tensor cores in chunks of 256 centers where the mode and the shape
+    // allow (its row state borrows the peel's bucket lists, idle by now), else float32
+    if (j->fprec != PSCL_PREC_FP32 && j->pb.ord && tc_sse_supported(j->d, j->final_k, j->fprec) &&
+        (size_t)4 * j->n + 1 <= (size_t)j->d * (size_t)j->pb.ord_ld && j->n < ((int64_t)1 << 31)) {
+        const SegTable t256 = (j->final_k > 256 ? j->sp256 : j->sprem).table();
+        const SegTable trem = (j->final_k <= 256 || j->final_k % 256 ? j->sprem : j->sp256).table();
+        CU(launch_final_sse_tc(j->x, j->n, j->d, j->cf, j->final_k, t256, trem, j->pb.ord, j->labels, j->blk_sse,
+                               j->sse, j->tickets + 1, j->fprec, j->flags, j->wait_limit, j->ctx->sm_count, st,
+                               &j->kt));
+    } else {
+        CU(launch_final_sse(j->x, j->n, j->d, j->cf, j->final_k, j->labels, j->blk_sse, j->sse, j->tickets + 1,
+                            j->ctx->sm_count, st, &j->kt));
+    }
     if (events) CU(cudaEventRecord(j->ev[5], st));
     return PSCL_OK;
 }

@@ -285,6 +285,21 @@ struct TcArgs {
     int stall;                   // test hook: wait once on a barrier nothing completes
     int npmax;                   // operand B rows (centers rounded up to 16)
     uint32_t ncols;              // TMEM columns of one accumulator
+    // Search of a whole set in chunks of centers (ref_centers != NULL): the launch covers
+    // one chunk (centers, the set of its runs); the reference point and the error bound's
+    // center norm come from all ref_k centers, so that every chunk's values compare.  Each
+    // row keeps a running state across the chunks' launches: m1 = the smallest chunk
+    // minimum, c1 = its candidate (bit 31: that chunk held more than one value within
+    // twice the bound of it), m2 = the smallest minimum of the other chunks.  The last
+    // chunk labels a row whose candidate is certain (c1 alone, m2 beyond m1 + 2E) and lists
+    // every other row in ties[1 ...] (ties[0] the count) for float32 re-scoring.
+    const float *ref_centers = nullptr;
+    int ref_k = 0;
+    int chunk_first = 0;         // index of the chunk's first center in the set
+    int first_chunk = 0, last_chunk = 0;
+    float *st_m1 = nullptr, *st_m2 = nullptr;
+    int32_t *st_c1 = nullptr;
+    uint32_t *ties = nullptr;
 };
 
 // A run: consecutive units of one set in a CTA's range, streamed as 128-row tiles.
@@ -489,22 +504,35 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<D>()) k_tc_assign(co
             }
             const int k = run.k, np = (k + 15) & ~15;
             const float *cen = p.centers + run.c0 * D;
-            {   // reference point: the mean of the set's centers
+            // the centers the reference point and the bound's center norm come from: the
+            // set's (or, for a chunk of a whole-set search, all of the set's)
+            const float *rcen = p.ref_centers ? p.ref_centers : cen;
+            const int rk = p.ref_centers ? p.ref_k : k;
+            {   // reference point: the mean of those centers
                 constexpr int G = 128 / D;
                 const int at = r % D, g = r / D;
                 float m = 0.0f;
                 if (g < G)
-                    for (int j = g; j < k; j += G) m = __fadd_rn(m, __ldg(&cen[(size_t)j * D + at]));
+                    for (int j = g; j < rk; j += G) m = __fadd_rn(m, __ldg(&rcen[(size_t)j * D + at]));
                 s_part[r] = m;
                 if (r == 0) s_cmax2 = 0.0f;
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 if (r < D) {
                     float tot = 0.0f;
                     for (int q = 0; q < G; q++) tot = __fadd_rn(tot, s_part[q * D + r]);
-                    s_ref[r] = __fdiv_rn(tot, (float)k);
+                    s_ref[r] = __fdiv_rn(tot, (float)rk);
                 }
                 asm volatile("bar.sync 1, 128;" ::: "memory");
             }
+            if (p.ref_centers)       // the bound's center norm over the whole set
+                for (int j = r; j < rk; j += 128) {
+                    float n2 = 0.0f;
+                    for (int a = 0; a < D; a++) {
+                        const float c = __fsub_rn(__ldg(&rcen[(size_t)j * D + a]), s_ref[a]);
+                        n2 = __fmaf_rn(c, c, n2);
+                    }
+                    atomicMax(reinterpret_cast<int *>(&s_cmax2), __float_as_int(n2));
+                }
             // operand B: row j = [H | L | norm parts] of -2 c~_j (zero rows past k)
             for (int j = r; j < np; j += 128) {
                 float n2 = 0.0f;
@@ -679,7 +707,43 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<D>()) k_tc_assign(co
                     nc += __popc(w[c]);
                     if (w[c]) first = 32 * c + __ffs(w[c]) - 1;
                 }
-                if (live) {
+                if (p.ref_centers) {
+                    // a chunk of a whole-set search: fold this chunk into the row's state
+                    bool tie_row = false;
+                    if (live) {
+                        const int32_t cand = (p.chunk_first + first) | (nc > 1 ? (int32_t)kTieBit : 0);
+                        float m1 = b1, m2 = kInf;
+                        int32_t c1 = cand;
+                        if (!p.first_chunk) {
+                            m1 = p.st_m1[row];
+                            m2 = p.st_m2[row];
+                            c1 = p.st_c1[row];
+                            if (b1 < m1) {
+                                m2 = fminf(m2, m1);
+                                m1 = b1;
+                                c1 = cand;
+                            } else {
+                                m2 = fminf(m2, b1);
+                            }
+                        }
+                        if (p.last_chunk) {
+                            const bool unique = !((uint32_t)c1 & kTieBit) && m2 > m1 + 2.0f * E;
+                            p.labels[row] = unique ? c1 : (int32_t)kTieBit;
+                            tie_row = !unique;
+                        } else {
+                            p.st_m1[row] = m1;
+                            p.st_m2[row] = m2;
+                            p.st_c1[row] = c1;
+                        }
+                    }
+                    if (p.last_chunk) {      // the rows left for float32 re-scoring, listed
+                        const uint32_t bm = __ballot_sync(0xffffffffu, tie_row);
+                        uint32_t base = 0;
+                        if (lane == 0 && bm) base = atomicAdd(&p.ties[0], (uint32_t)__popc(bm));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (tie_row) p.ties[1 + base + __popc(bm & ((1u << lane) - 1u))] = (uint32_t)row;
+                    }
+                } else if (live) {
                     p.labels[row] = nc > 1 ? (int32_t)kTieBit : first;
                     if (nc > 1) {        // the candidates, for the sums pass to re-score
                         uint4 *mk = reinterpret_cast<uint4 *>(p.tmask + (size_t)row * 8);
@@ -891,6 +955,113 @@ __global__ void __launch_bounds__(sum_threads<D>()) k_tc_sums(const float *__res
     }
 }
 
+// ---------------------------------------------------------------- whole-set search: ties, SSE
+// The rows a whole-set search (the SSE pass) could not decide: a warp per row, lane l the
+// centers l, l + 32, ..., with PSCL_PREC_FP32's arithmetic (t = RN(x_a - c_a), acc =
+// RN(t t + acc) in ascending a; the lowest index among equal sums), so the label is the
+// float32 direct winner.
+template <int D>
+__global__ void __launch_bounds__(256) k_tc_rescore_ties(const float *__restrict__ x, const float *__restrict__ centers,
+                                                         int k, int32_t *labels, const uint32_t *ties)
+{
+    const uint32_t nt = __ldcg(&ties[0]);
+    const int lane = threadIdx.x & 31;
+    const uint32_t nw = gridDim.x * (blockDim.x / 32);
+    for (uint32_t q = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; q < nt; q += nw) {
+        const int64_t row = __ldcg(&ties[1 + q]);
+        float xr[D];
+        const float4 *x4 = reinterpret_cast<const float4 *>(x + row * D);
+#pragma unroll
+        for (int a4 = 0; a4 < D / 4; a4++) {
+            const float4 v = __ldg(&x4[a4]);               // the same address in every lane
+            xr[4 * a4 + 0] = v.x;
+            xr[4 * a4 + 1] = v.y;
+            xr[4 * a4 + 2] = v.z;
+            xr[4 * a4 + 3] = v.w;
+        }
+        float bd = __int_as_float(0x7f800000);
+        int bj = 0x7fffffff;
+        for (int j = lane; j < k; j += 32) {
+            const float4 *c4 = reinterpret_cast<const float4 *>(centers + (size_t)j * D);
+            float acc = 0.0f;
+#pragma unroll
+            for (int a4 = 0; a4 < D / 4; a4++) {
+                const float4 u = __ldg(&c4[a4]);
+                float t;
+                t = __fsub_rn(xr[4 * a4 + 0], u.x); acc = __fmaf_rn(t, t, acc);
+                t = __fsub_rn(xr[4 * a4 + 1], u.y); acc = __fmaf_rn(t, t, acc);
+                t = __fsub_rn(xr[4 * a4 + 2], u.z); acc = __fmaf_rn(t, t, acc);
+                t = __fsub_rn(xr[4 * a4 + 3], u.w); acc = __fmaf_rn(t, t, acc);
+            }
+            if (acc < bd) {                                // ascending j in the lane
+                bd = acc;
+                bj = j;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+            if (od < bd || (od == bd && oj < bj)) {
+                bd = od;
+                bj = oj;
+            }
+        }
+        if (lane == 0) labels[row] = (uint32_t)bj < (uint32_t)k ? bj : 0;
+    }
+}
+
+// The SSE from the labels: each point's float32 direct distance to its center, added in
+// double per thread, per block in a fixed tree and over blocks in block order -- the rows of
+// a thread, the tree and the block order of the float32 SSE pass (same grid, 256 threads),
+// so the value is the same bit for bit.
+template <int D>
+__global__ void __launch_bounds__(256) k_sse_from_labels(const float *__restrict__ x, int64_t n,
+                                                         const float *__restrict__ centers, int k,
+                                                         const int32_t *__restrict__ labels, double *blk_sse,
+                                                         double *sse, uint32_t *ticket)
+{
+    constexpr int NT = 256;
+    double part = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * NT;
+    const int64_t nround = (n + stride - 1) / stride;
+    for (int64_t it = 0; it < nround; it++) {
+        const int64_t i = it * stride + (int64_t)blockIdx.x * NT + threadIdx.x;
+        if (i < n) {
+            int32_t l = labels[i];
+            if ((uint32_t)l >= (uint32_t)k) l = 0;          // only after a search that gave up
+            const float *xr = x + i * D, *cr = centers + (size_t)l * D;
+            float acc = 0.0f;
+#pragma unroll
+            for (int a = 0; a < D; a++) {
+                const float t = __fsub_rn(__ldg(&xr[a]), __ldg(&cr[a]));
+                acc = __fmaf_rn(t, t, acc);
+            }
+            part = __dadd_rn(part, (double)acc);
+        }
+    }
+    for (int o = 16; o; o >>= 1) part = __dadd_rn(part, __shfl_down_sync(0xffffffffu, part, o));
+    __shared__ double ws[NT / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = ws[0];
+        for (int w = 1; w < NT / 32; w++) b = __dadd_rn(b, ws[w]);
+        blk_sse[blockIdx.x] = b;
+    }
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last || threadIdx.x != 0) return;
+    __threadfence();
+    double tot = 0.0;
+    for (unsigned b = 0; b < gridDim.x; b++) tot = __dadd_rn(tot, __ldcg(&blk_sse[b]));
+    *sse = tot;
+    *ticket = 0;
+}
+
 // ---------------------------------------------------------------- host side
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -996,6 +1167,81 @@ cudaError_t tc_dispatch(const LloydBuffers &b, const SegTable &t, int iter, int 
     return cudaGetLastError();
 }
 
+// The SSE pass on the tensor cores: the k centers in chunks of up to 256, one assignment
+// launch per chunk (rows keep their running state), the undecided rows re-scored in
+// float32, then the SSE from the labels.
+template <int D, int MODE>
+cudaError_t sse_tc_dispatch(const float *x, int64_t n, const float *centers, int k, const SegTable &t256,
+                            const SegTable &trem, uint32_t *scratch, int32_t *labels, double *blk_sse, double *sse,
+                            uint32_t *ticket, uint32_t *flags, unsigned wait_limit, int sm_count, cudaStream_t st,
+                            KTimer *kt)
+{
+    CUtensorMap map;
+    cudaError_t e = make_xmap<D, MODE>(x, n, &map);
+    if (e != cudaSuccess) return e;
+    float *m1 = reinterpret_cast<float *>(scratch);
+    float *m2 = m1 + n;
+    int32_t *c1 = reinterpret_cast<int32_t *>(m2 + n);
+    uint32_t *ties = reinterpret_cast<uint32_t *>(c1 + n);
+    if ((e = cudaMemsetAsync(ties, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+    auto ka = k_tc_assign<D, MODE>;
+    const int nch = (k + 255) / 256;
+    for (int c = 0; c < nch; c++) {
+        const int kc = std::min(256, k - 256 * c);
+        const SegTable &t = kc == 256 ? t256 : trem;
+        TcArgs a;
+        a.centers = centers + (size_t)256 * c * D;
+        a.labels = labels;
+        a.tmask = nullptr;
+        a.t = t;
+        a.flags = flags;
+        a.wait_limit = wait_limit ? wait_limit : kDefaultWait;
+        a.stall = 0;
+        a.npmax = (kc + 15) & ~15;
+        a.ncols = tmem_cols(a.npmax);
+        a.ref_centers = centers;
+        a.ref_k = k;
+        a.chunk_first = 256 * c;
+        a.first_chunk = c == 0;
+        a.last_chunk = c == nch - 1;
+        a.st_m1 = m1;
+        a.st_m2 = m2;
+        a.st_c1 = c1;
+        a.ties = ties;
+        const size_t smem = assign_smem<D, MODE>(kc);
+        if ((e = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        int occ = 1;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ka, kTcThreads, smem)) != cudaSuccess) return e;
+        const int ma = std::max(1, std::min(std::min(occ, (int)(512u / (2u * a.ncols))), 4));
+        a.split = t.split + t.split_off[ma];
+        kt->begin(st);
+        ka<<<ma * sm_count, kTcThreads, smem, st>>>(map, a);
+        kt->end(PSCL_K_FINAL_SSE, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    kt->begin(st);
+    k_tc_rescore_ties<D><<<4 * sm_count, 256, 0, st>>>(x, centers, k, labels, ties);
+    k_sse_from_labels<D><<<sse_grid(n, sm_count), 256, 0, st>>>(x, n, centers, k, labels, blk_sse, sse, ticket);
+    kt->end(PSCL_K_FINAL_SSE, st);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t sse_tc_by_d(int d, const float *x, int64_t n, const float *centers, int k, const SegTable &t256,
+                        const SegTable &trem, uint32_t *scratch, int32_t *labels, double *blk_sse, double *sse,
+                        uint32_t *ticket, uint32_t *flags, unsigned wait_limit, int sm_count, cudaStream_t st,
+                        KTimer *kt)
+{
+    switch (d) {
+    case 16: return sse_tc_dispatch<16, MODE>(x, n, centers, k, t256, trem, scratch, labels, blk_sse, sse, ticket, flags, wait_limit, sm_count, st, kt);
+    case 32: return sse_tc_dispatch<32, MODE>(x, n, centers, k, t256, trem, scratch, labels, blk_sse, sse, ticket, flags, wait_limit, sm_count, st, kt);
+    case 64: return sse_tc_dispatch<64, MODE>(x, n, centers, k, t256, trem, scratch, labels, blk_sse, sse, ticket, flags, wait_limit, sm_count, st, kt);
+    case 128: return sse_tc_dispatch<128, MODE>(x, n, centers, k, t256, trem, scratch, labels, blk_sse, sse, ticket, flags, wait_limit, sm_count, st, kt);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 template <int MODE>
 cudaError_t tc_by_d(const LloydBuffers &b, const SegTable &t, int d, int iter, int kmax, uint32_t *flags,
                     int sm_count, cudaStream_t st, KTimer *kt)
@@ -1051,6 +1297,26 @@ bool tc_supported(int d, int kmax, int prec)
     case kModeTf32x3: return fits_by_d<kModeTf32x3>(d, kmax);
     case kModeBf16x3: return fits_by_d<kModeBf16x3>(d, kmax);
     default: return fits_by_d<kModeTf32>(d, kmax);
+    }
+}
+
+bool tc_sse_supported(int d, int k, int prec)
+{
+    return k >= 1 && tc_supported(d, std::min(k, 256), prec) &&
+           (k <= 256 || tc_supported(d, 256, prec));
+}
+
+cudaError_t launch_final_sse_tc(const float *x, int64_t n, int d, const float *centers, int k, const SegTable &t256,
+                                const SegTable &trem, uint32_t *scratch, int32_t *labels, double *blk_sse,
+                                double *sse, uint32_t *ticket, int prec, uint32_t *flags, unsigned wait_limit,
+                                int sm_count, cudaStream_t st, KTimer *kt)
+{
+    const int ck = std::min(k, 256);
+    switch (mode_of(resolve_prec(d, ck, prec))) {
+    case kModeBf16: return sse_tc_by_d<kModeBf16>(d, x, n, centers, k, t256, trem, scratch, labels, blk_sse, sse, ticket, flags, wait_limit, sm_count, st, kt);
+    case kModeTf32x3: return sse_tc_by_d<kModeTf32x3>(d, x, n, centers, k, t256, trem, scratch, labels, blk_sse, sse, ticket, flags, wait_limit, sm_count, st, kt);
+    case kModeBf16x3: return sse_tc_by_d<kModeBf16x3>(d, x, n, centers, k, t256, trem, scratch, labels, blk_sse, sse, ticket, flags, wait_limit, sm_count, st, kt);
+    default: return sse_tc_by_d<kModeTf32>(d, x, n, centers, k, t256, trem, scratch, labels, blk_sse, sse, ticket, flags, wait_limit, sm_count, st, kt);
     }
 }
 

@@ -227,6 +227,15 @@ cudaError_t launch_seg_sse(const float *pts, const SegTable &t, const int32_t *s
 
 // lloyd_tc.cu
 bool tc_supported(int d, int kmax, int prec);
+// The SSE pass (labels and sum as launch_final_sse gives them) on the tensor cores for k
+// centers in chunks of up to 256.  t256 / trem: the n rows as one set of 256 centers and of
+// the k mod 256 remaining ones (k itself when k <= 256), with CTA splits; scratch: 4 n + 1
+// words (row state and the list of rows re-scored in float32).
+bool tc_sse_supported(int d, int k, int prec);
+cudaError_t launch_final_sse_tc(const float *x, int64_t n, int d, const float *centers, int k, const SegTable &t256,
+                                const SegTable &trem, uint32_t *scratch, int32_t *labels, double *blk_sse,
+                                double *sse, uint32_t *ticket, int prec, uint32_t *flags, unsigned wait_limit,
+                                int sm_count, cudaStream_t st, KTimer *kt);
 // Assignment on the tensor cores and the exact sums of the iteration (two persistent
 // launches over all units; needs t.split).
 cudaError_t launch_lloyd_assign_tc(const LloydBuffers &b, const SegTable &t, int d, int iter, int kmax, int prec,

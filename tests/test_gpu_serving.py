@@ -40,7 +40,8 @@ def run_alone(job):
 
 
 @pytest.mark.parametrize("n,d,N,lk,fk,T,host", [(10000, 8, 157, 8, 8, 3, True), (50000, 32, 782, 12, 40, 2, False),
-                                                 (4096, 4, 256, 16, 3, 20, False)])
+                                                 (4096, 4, 256, 16, 3, 20, False), (50000, 32, 782, 12, 300, 2, False),
+                                                 (50000, 16, 782, 12, 512, 2, True)])
 def test_footprint_is_the_allocated_bytes(n, d, N, lk, fk, T, host):
     import torch
     pts = synth.mixture(n, d, 5, seed=n)

@@ -112,3 +112,22 @@ def test_tensor_core_oracle_parity(name, prec, n, d, N, lk, fk, T):
     o = run_oracle(raw, N, lk, fk, T, seed=11, gpu=g)
     compare(g, o)
     assert g.assigned > 0
+
+
+@pytest.mark.parametrize("name,prec", [("tc", B.PSCL_PREC_TC), ("bf16", B.PSCL_PREC_BF16)])
+@pytest.mark.parametrize("n,d,N,lk,fk", [
+    (40000, 64, 2000, 64, 1000),       # four chunks of centers, the last of 232
+    (30000, 16, 1500, 40, 512),        # two full chunks
+    (20000, 32, 1000, 20, 300),        # one full chunk and 44 more
+    (9000, 32, 1000, 16, 100),         # one chunk
+])
+def test_sse_pass_in_center_chunks(name, prec, n, d, N, lk, fk):
+    # the SSE pass on the tensor cores, the centers in chunks of up to 256: labels and the
+    # SSE equal the float32 pass bit for bit (near ties and rows another chunk comes close
+    # to re-scored in float32; the SSE summed in the float32 pass's order)
+    raw = synth.mixture(n, d, 50, outlier_frac=0.01, seed=2300 + fk)
+    ref = run_gpu(raw, N, lk, fk, 3, seed=5, trace=False)
+    got = run_gpu(raw, N, lk, fk, 3, seed=5, trace=False, prec=prec)
+    np.testing.assert_array_equal(got.final_centers, ref.final_centers)
+    np.testing.assert_array_equal(got.labels, ref.labels)
+    assert got.sse == ref.sse
