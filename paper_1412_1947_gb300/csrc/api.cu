@@ -135,6 +135,8 @@ struct pscl_job : Owner {
     // the SSE pass's row tables: all n rows as one set of 256 centers (final_k > 256) and of
     // the remaining final_k mod 256 centers (final_k itself when it is at most 256)
     LloydPlan sp256, sprem;
+    // the final Lloyd's row tables for the same chunked search (final_k > 256 only)
+    LloydPlan fp256, fprem;
     float *cf = nullptr;
     unsigned long long *acc_f = nullptr;
     int32_t *cnt_f = nullptr;
@@ -672,7 +674,7 @@ static int plan_cluster(pscl_job *j, int32_t final_k, int32_t iters, uint64_t se
         j->lab_f = nullptr;
         // the SSE pass's tables for a search in chunks of 256 centers (tensor-core modes)
         {
-            for (LloydPlan *q : {&j->sp256, &j->sprem}) {
+            for (LloydPlan *q : {&j->sp256, &j->sprem, &j->fp256, &j->fprem}) {
                 job_free(j, q->d_seg_start);
                 job_free(j, q->d_i32);
                 job_free(j, q->d_split);
@@ -685,6 +687,11 @@ static int plan_cluster(pscl_job *j, int32_t final_k, int32_t iters, uint64_t se
             const int32_t rem = final_k % 256;
             if (final_k > 256) TRY(build_lloyd_plan(j, j->sp256, s0, sn, std::vector<int32_t>(1, 256)));
             if (final_k <= 256 || rem) TRY(build_lloyd_plan(j, j->sprem, s0, sn, std::vector<int32_t>(1, final_k <= 256 ? final_k : rem)));
+            if (final_k > 256) {
+                std::vector<int32_t> sp(1, (int32_t)j->P);
+                TRY(build_lloyd_plan(j, j->fp256, s0, sp, std::vector<int32_t>(1, 256)));
+                if (rem) TRY(build_lloyd_plan(j, j->fprem, s0, sp, std::vector<int32_t>(1, rem)));
+            }
         }
         TRY(A(j, &j->cf, (size_t)final_k * d));
         TRY(A(j, &j->acc_f, (size_t)final_k * d));
@@ -755,6 +762,12 @@ static size_t job_footprint(int64_t n, int d, int64_t N, int local_k, int final_
         const int64_t un = (n + unit_size(n, tn) - 1) / unit_size(n, tn);
         const int tables = (final_k > 256 ? 1 : 0) + (final_k <= 256 || final_k % 256 ? 1 : 0);
         b += (size_t)tables * (r256(8) + r256((4 + 3 * (size_t)un + 1) * 4) + r256(split * 4));
+        if (final_k > 256) {   // the final Lloyd's, over the P pooled rows
+            const int ftables = 1 + (final_k % 256 ? 1 : 0);
+            const int64_t tp = unit_target(P, sm, 0);
+            const int64_t up = (P + unit_size(P, tp) - 1) / unit_size(P, tp);
+            b += (size_t)ftables * (r256(8) + r256((4 + 3 * (size_t)up + 1) * 4) + r256(split * 4));
+        }
     }
     b += r256((size_t)n * 4) + r256((size_t)sse_grid(n, sm) * 8) + r256(8);
     if (trace) b += r256((size_t)iters * P * 4);
@@ -812,6 +825,15 @@ static int run_lloyd(pscl_job *j, const LloydPlan &p, const float *pts, float *c
     // the near ties' candidate masks borrow the peel's bucket lists (d * ord_ld words, idle
     // once the peel is done; 8 words per row fit whenever d >= 8)
     if (j->pb.ord && (size_t)p.rows * 8 <= (size_t)j->d * (size_t)j->pb.ord_ld) b.tmask = j->pb.ord;
+    // the pooled set past 256 centers: the chunked search's tables, its row state in the same
+    // idle lists (4 rows + 1 words)
+    if (stage == 1 && j->final_k > 256 && j->fp256.d_split && b.tmask &&
+        (size_t)4 * p.rows + 1 <= (size_t)j->d * (size_t)j->pb.ord_ld) {
+        b.chunk256 = j->fp256.table();
+        b.chunkrem = (j->final_k % 256 ? j->fprem : j->fp256).table();
+        b.has_chunks = true;
+        b.chunk_scratch = j->pb.ord;
+    }
     b.wait_limit = j->wait_limit;
     b.tc_stall = j->test_stall == 2;
     CU(launch_lloyd_init(b, t, j->d, p.P, seed, stage, j->first_k, p.kmax, st, &j->kt));

@@ -622,6 +622,9 @@ cudaError_t launch_lloyd_iter(const LloydBuffers &b, int32_t *count_next, const 
     if (prec != PSCL_PREC_FP32 && !b.weights && b.tmask && t.split && unit_lo == 0 && unit_hi == t.n_units &&
         tc_supported(d, kmax, prec)) {
         e = launch_lloyd_assign_tc(b, t, d, iter, kmax, prec, flags, sm_count, st, kt);
+    } else if (prec != PSCL_PREC_FP32 && !b.weights && b.has_chunks && b.chunk_scratch && t.n_seg == 1 &&
+               kmax > 256 && unit_lo == 0 && unit_hi == t.n_units && tc_sse_supported(d, kmax, prec)) {
+        e = launch_lloyd_chunks_tc(b, d, iter, kmax, prec, flags, sm_count, st, kt);
     } else switch (d) {
     case 2: e = assign_dispatch<2>(b, t, d, iter, unit_lo, unit_hi, kmax, rows_per_thread, st, kt); break;
     case 4: e = assign_dispatch<4>(b, t, d, iter, unit_lo, unit_hi, kmax, rows_per_thread, st, kt); break;

@@ -1167,14 +1167,13 @@ cudaError_t tc_dispatch(const LloydBuffers &b, const SegTable &t, int iter, int 
     return cudaGetLastError();
 }
 
-// The SSE pass on the tensor cores: the k centers in chunks of up to 256, one assignment
-// launch per chunk (rows keep their running state), the undecided rows re-scored in
-// float32, then the SSE from the labels.
+// A whole-set search on the tensor cores: the k centers in chunks of up to 256, one
+// assignment launch per chunk (rows keep their running state), then the undecided rows
+// re-scored in float32.  Leaves every row's float32 direct label in labels.
 template <int D, int MODE>
-cudaError_t sse_tc_dispatch(const float *x, int64_t n, const float *centers, int k, const SegTable &t256,
-                            const SegTable &trem, uint32_t *scratch, int32_t *labels, double *blk_sse, double *sse,
-                            uint32_t *ticket, uint32_t *flags, unsigned wait_limit, int sm_count, cudaStream_t st,
-                            KTimer *kt)
+cudaError_t chunk_search(const float *x, int64_t n, const float *centers, int k, const SegTable &t256,
+                         const SegTable &trem, uint32_t *scratch, int32_t *labels, uint32_t *flags,
+                         unsigned wait_limit, int sm_count, cudaStream_t st, KTimer *kt, int ktag)
 {
     CUtensorMap map;
     cudaError_t e = make_xmap<D, MODE>(x, n, &map);
@@ -1217,14 +1216,87 @@ cudaError_t sse_tc_dispatch(const float *x, int64_t n, const float *centers, int
         a.split = t.split + t.split_off[ma];
         kt->begin(st);
         ka<<<ma * sm_count, kTcThreads, smem, st>>>(map, a);
-        kt->end(PSCL_K_FINAL_SSE, st);
+        kt->end(ktag, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     kt->begin(st);
     k_tc_rescore_ties<D><<<4 * sm_count, 256, 0, st>>>(x, centers, k, labels, ties);
+    kt->end(ktag, st);
+    return cudaGetLastError();
+}
+
+// The exact sums of one iteration from the labels, in global memory (sets too large for a
+// CTA's shared memory): a thread per row adds its 32.32 fixed-point coordinates and its
+// count with 64-bit atomics (integer sums: the order does not matter); writes the trace.
+template <int D>
+__global__ void __launch_bounds__(256) k_tc_global_sums(const float *__restrict__ pts, int64_t rows,
+                                                        const int32_t *__restrict__ labels, int k, int32_t *trace,
+                                                        int64_t trace_off, unsigned long long *acc, int32_t *count)
+{
+    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        int32_t l = labels[row];
+        if ((uint32_t)l >= (uint32_t)k) l = 0;              // only after a search that gave up
+        if (trace) trace[trace_off + row] = l;
+        atomicAdd(&count[l], 1);
+        const float4 *x4 = reinterpret_cast<const float4 *>(pts + row * D);
+        unsigned long long *al = acc + (size_t)l * D;
+#pragma unroll 4
+        for (int a4 = 0; a4 < D / 4; a4++) {
+            const float4 v = __ldg(&x4[a4]);
+            atomicAdd(&al[4 * a4 + 0], fix_of(v.x));
+            atomicAdd(&al[4 * a4 + 1], fix_of(v.y));
+            atomicAdd(&al[4 * a4 + 2], fix_of(v.z));
+            atomicAdd(&al[4 * a4 + 3], fix_of(v.w));
+        }
+    }
+}
+
+// The SSE pass on the tensor cores: the chunked search, then the SSE from the labels.
+template <int D, int MODE>
+cudaError_t sse_tc_dispatch(const float *x, int64_t n, const float *centers, int k, const SegTable &t256,
+                            const SegTable &trem, uint32_t *scratch, int32_t *labels, double *blk_sse, double *sse,
+                            uint32_t *ticket, uint32_t *flags, unsigned wait_limit, int sm_count, cudaStream_t st,
+                            KTimer *kt)
+{
+    cudaError_t e = chunk_search<D, MODE>(x, n, centers, k, t256, trem, scratch, labels, flags, wait_limit, sm_count,
+                                          st, kt, PSCL_K_FINAL_SSE);
+    if (e != cudaSuccess) return e;
+    kt->begin(st);
     k_sse_from_labels<D><<<sse_grid(n, sm_count), 256, 0, st>>>(x, n, centers, k, labels, blk_sse, sse, ticket);
     kt->end(PSCL_K_FINAL_SSE, st);
     return cudaGetLastError();
+}
+
+// One Lloyd iteration of a single set with more than 256 centers on the tensor cores: the
+// chunked search, then the exact sums from the labels (the update follows separately).
+template <int D, int MODE>
+cudaError_t lloyd_chunks_dispatch(const LloydBuffers &b, int iter, int k, uint32_t *flags, int sm_count,
+                                  cudaStream_t st, KTimer *kt)
+{
+    cudaError_t e = chunk_search<D, MODE>(b.pts, b.rows, b.centers, k, b.chunk256, b.chunkrem, b.chunk_scratch,
+                                          b.labels, flags, b.wait_limit, sm_count, st, kt, PSCL_K_LLOYD_ASSIGN);
+    if (e != cudaSuccess) return e;
+    int64_t g = (b.rows + 255) / 256;
+    if (g > (int64_t)sm_count * 8) g = (int64_t)sm_count * 8;
+    kt->begin(st);
+    k_tc_global_sums<D><<<(int)std::max<int64_t>(1, g), 256, 0, st>>>(b.pts, b.rows, b.labels, k, b.trace,
+                                                                        (int64_t)iter * b.rows, b.acc, b.count);
+    kt->end(PSCL_K_LLOYD_SUMS, st);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t lloyd_chunks_by_d(int d, const LloydBuffers &b, int iter, int k, uint32_t *flags, int sm_count,
+                              cudaStream_t st, KTimer *kt)
+{
+    switch (d) {
+    case 16: return lloyd_chunks_dispatch<16, MODE>(b, iter, k, flags, sm_count, st, kt);
+    case 32: return lloyd_chunks_dispatch<32, MODE>(b, iter, k, flags, sm_count, st, kt);
+    case 64: return lloyd_chunks_dispatch<64, MODE>(b, iter, k, flags, sm_count, st, kt);
+    case 128: return lloyd_chunks_dispatch<128, MODE>(b, iter, k, flags, sm_count, st, kt);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 template <int MODE>
@@ -1304,6 +1376,17 @@ bool tc_sse_supported(int d, int k, int prec)
 {
     return k >= 1 && tc_supported(d, std::min(k, 256), prec) &&
            (k <= 256 || tc_supported(d, 256, prec));
+}
+
+cudaError_t launch_lloyd_chunks_tc(const LloydBuffers &b, int d, int iter, int k, int prec, uint32_t *flags,
+                                   int sm_count, cudaStream_t st, KTimer *kt)
+{
+    switch (mode_of(resolve_prec(d, 256, prec))) {
+    case kModeBf16: return lloyd_chunks_by_d<kModeBf16>(d, b, iter, k, flags, sm_count, st, kt);
+    case kModeTf32x3: return lloyd_chunks_by_d<kModeTf32x3>(d, b, iter, k, flags, sm_count, st, kt);
+    case kModeBf16x3: return lloyd_chunks_by_d<kModeBf16x3>(d, b, iter, k, flags, sm_count, st, kt);
+    default: return lloyd_chunks_by_d<kModeTf32>(d, b, iter, k, flags, sm_count, st, kt);
+    }
 }
 
 cudaError_t launch_final_sse_tc(const float *x, int64_t n, int d, const float *centers, int k, const SegTable &t256,

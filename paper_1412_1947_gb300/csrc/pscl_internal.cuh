@@ -207,6 +207,12 @@ struct LloydBuffers {
     // 8 words per row (or NULL): the tensor-core assignment marks a near tie's candidate
     // centers here (bit j of word j / 32), the sums pass re-scores only those
     uint32_t *tmask = nullptr;
+    // a single set of more than 256 centers on the tensor cores: the rows as one set of 256
+    // and of the remaining centers, with CTA splits (has_chunks), and 4 rows + 1 words of
+    // scratch for the chunked search
+    SegTable chunk256{}, chunkrem{};
+    bool has_chunks = false;
+    uint32_t *chunk_scratch = nullptr;
     uint32_t wait_limit = 0;         // polls of the tensor-core kernel's bounded waits (0: default)
     int tc_stall = 0;                // test hook: the tensor-core kernel waits once on a barrier nothing completes
 };
@@ -232,6 +238,10 @@ bool tc_supported(int d, int kmax, int prec);
 // the k mod 256 remaining ones (k itself when k <= 256), with CTA splits; scratch: 4 n + 1
 // words (row state and the list of rows re-scored in float32).
 bool tc_sse_supported(int d, int k, int prec);
+// One Lloyd iteration of a single set of k > 256 centers on the tensor cores (b.has_chunks):
+// labels by the chunked search, then the exact sums; the update is launched separately.
+cudaError_t launch_lloyd_chunks_tc(const LloydBuffers &b, int d, int iter, int k, int prec, uint32_t *flags,
+                                   int sm_count, cudaStream_t st, KTimer *kt);
 cudaError_t launch_final_sse_tc(const float *x, int64_t n, int d, const float *centers, int k, const SegTable &t256,
                                 const SegTable &trem, uint32_t *scratch, int32_t *labels, double *blk_sse,
                                 double *sse, uint32_t *ticket, int prec, uint32_t *flags, unsigned wait_limit,

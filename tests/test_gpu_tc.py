@@ -121,13 +121,16 @@ def test_tensor_core_oracle_parity(name, prec, n, d, N, lk, fk, T):
     (20000, 32, 1000, 20, 300),        # one full chunk and 44 more
     (9000, 32, 1000, 16, 100),         # one chunk
 ])
-def test_sse_pass_in_center_chunks(name, prec, n, d, N, lk, fk):
+def test_final_stage_in_center_chunks(name, prec, n, d, N, lk, fk):
     # the SSE pass on the tensor cores, the centers in chunks of up to 256: labels and the
     # SSE equal the float32 pass bit for bit (near ties and rows another chunk comes close
     # to re-scored in float32; the SSE summed in the float32 pass's order)
+    # (past 256 centers the pooled set's Lloyd iterations take the same chunked search, its
+    # sums then in global memory: the label trace and the centers equal the float32 run's)
     raw = synth.mixture(n, d, 50, outlier_frac=0.01, seed=2300 + fk)
-    ref = run_gpu(raw, N, lk, fk, 3, seed=5, trace=False)
-    got = run_gpu(raw, N, lk, fk, 3, seed=5, trace=False, prec=prec)
+    ref = run_gpu(raw, N, lk, fk, 3, seed=5)
+    got = run_gpu(raw, N, lk, fk, 3, seed=5, prec=prec)
+    np.testing.assert_array_equal(got.trace_final, ref.trace_final)
     np.testing.assert_array_equal(got.final_centers, ref.final_centers)
     np.testing.assert_array_equal(got.labels, ref.labels)
     assert got.sse == ref.sse
