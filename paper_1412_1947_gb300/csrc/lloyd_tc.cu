@@ -795,7 +795,7 @@ __host__ __device__ constexpr int sum_threads()
 }
 
 template <int D>
-__global__ void __launch_bounds__(sum_threads<D>()) k_tc_sums(const float *__restrict__ pts,
+__global__ void __launch_bounds__(sum_threads<D>(), D <= 32 ? 2 : 1) k_tc_sums(const float *__restrict__ pts,
                                                              const float *__restrict__ centers, SegTable t,
                                                              const int32_t *split, int32_t *labels,
                                                              const uint32_t *__restrict__ tmask,
@@ -831,67 +831,62 @@ __global__ void __launch_bounds__(sum_threads<D>()) k_tc_sums(const float *__res
             int32_t lab = live ? labels[row] : 0;
             const bool tie = live && ((uint32_t)lab & kTieBit);
             if (!tie && (uint32_t)lab >= (uint32_t)k) lab = 0;   // only after an assignment that gave up
-            // near ties: the whole warp re-scores one such row at a time, lane l the row's
-            // candidate centers l, l + 32, ... (the bits of its mask; every center left out
-            // lies beyond the float32 direct sum's error of the best), the row in every
-            // lane's registers, the centers in shared memory as float4 at a stride of
-            // D + 4 floats (a quarter warp's 128-bit loads on distinct banks)
+            // near ties: lane i of a warp re-scores the warp's i-th tie row against the row's
+            // candidate centers (the bits of its mask; every center left out lies beyond the
+            // float32 direct sum's error of the best), the centers read from shared memory as
+            // float4 at a stride of D + 4 floats; the labels go back by shuffles
             {
                 const int lane = tid & 31;
-                uint32_t tm = __ballot_sync(0xffffffffu, tie);
-                while (tm) {
-                    const int src = __ffs(tm) - 1;
-                    tm &= tm - 1u;
+                const uint32_t tm = __ballot_sync(0xffffffffu, tie);
+                if (tm) {
+                    const int nt = __popc(tm);
+                    const int src = lane < nt ? (int)__fns(tm, 0u, lane + 1) : 0;
                     const int64_t trow = __shfl_sync(0xffffffffu, row, src);
-                    float x[D];
-                    {
+                    int32_t mylab = 0;
+                    if (lane < nt) {
+                        float x[D];
                         const float4 *x4 = reinterpret_cast<const float4 *>(pts + trow * D);
 #pragma unroll
                         for (int a4 = 0; a4 < D / 4; a4++) {
-                            const float4 v = __ldg(&x4[a4]);          // the same address in every lane
+                            const float4 v = __ldg(&x4[a4]);
                             x[4 * a4 + 0] = v.x;
                             x[4 * a4 + 1] = v.y;
                             x[4 * a4 + 2] = v.z;
                             x[4 * a4 + 3] = v.w;
                         }
-                    }
-                    const uint4 *mk = reinterpret_cast<const uint4 *>(tmask + trow * 8);
-                    const uint4 ma = __ldg(mk), mb = __ldg(mk + 1);
-                    const uint32_t wd[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
-                    float bd = __int_as_float(0x7f800000);
-                    int bj = 0x7fffffff;
+                        const uint4 *mk = reinterpret_cast<const uint4 *>(tmask + trow * 8);
+                        const uint4 ma = __ldg(mk), mb = __ldg(mk + 1);
+                        const uint32_t wd[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
+                        float bd = __int_as_float(0x7f800000);
 #pragma unroll
-                    for (int c = 0; c < 8; c++) {
-                        const int j = 32 * c + lane;
-                        if (j < k && ((wd[c] >> lane) & 1u)) {
-                            const float4 *c0 = reinterpret_cast<const float4 *>(scen + (size_t)j * DC);
-                            float d0 = 0.0f;
+                        for (int c = 0; c < 8; c++) {
+                            uint32_t bits = 32 * c < k ? wd[c] : 0u;
+                            while (bits) {             // ascending candidates: strict keeps the lowest
+                                const int j = 32 * c + __ffs(bits) - 1;
+                                bits &= bits - 1u;
+                                if (j >= k) break;
+                                const float4 *c0 = reinterpret_cast<const float4 *>(scen + (size_t)j * DC);
+                                float d0 = 0.0f;
 #pragma unroll
-                            for (int a4 = 0; a4 < D / 4; a4++) {
-                                const float4 u = c0[a4];
-                                float t;
-                                t = __fsub_rn(x[4 * a4 + 0], u.x); d0 = __fmaf_rn(t, t, d0);
-                                t = __fsub_rn(x[4 * a4 + 1], u.y); d0 = __fmaf_rn(t, t, d0);
-                                t = __fsub_rn(x[4 * a4 + 2], u.z); d0 = __fmaf_rn(t, t, d0);
-                                t = __fsub_rn(x[4 * a4 + 3], u.w); d0 = __fmaf_rn(t, t, d0);
-                            }
-                            if (d0 < bd) {           // ascending j in the lane: strict keeps the lowest
-                                bd = d0;
-                                bj = j;
+                                for (int a4 = 0; a4 < D / 4; a4++) {
+                                    const float4 u = c0[a4];
+                                    float t;
+                                    t = __fsub_rn(x[4 * a4 + 0], u.x); d0 = __fmaf_rn(t, t, d0);
+                                    t = __fsub_rn(x[4 * a4 + 1], u.y); d0 = __fmaf_rn(t, t, d0);
+                                    t = __fsub_rn(x[4 * a4 + 2], u.z); d0 = __fmaf_rn(t, t, d0);
+                                    t = __fsub_rn(x[4 * a4 + 3], u.w); d0 = __fmaf_rn(t, t, d0);
+                                }
+                                if (d0 < bd) {
+                                    bd = d0;
+                                    mylab = j;
+                                }
                             }
                         }
                     }
-#pragma unroll
-                    for (int o = 16; o; o >>= 1) {
-                        const float od = __shfl_xor_sync(0xffffffffu, bd, o);
-                        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-                        if (od < bd || (od == bd && oj < bj)) {
-                            bd = od;
-                            bj = oj;
-                        }
-                    }
-                    if ((uint32_t)bj >= (uint32_t)k) bj = 0;     // no candidate: only after an assignment that gave up
-                    if (lane == src) lab = bj;
+                    // the q-th tie lane of the warp gets the label lane q found
+                    const int q = __popc(tm & ((1u << lane) - 1u));
+                    const int32_t res = __shfl_sync(0xffffffffu, mylab, q);
+                    if (tie) lab = res;
                 }
             }
             if (live) {
