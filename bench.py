@@ -557,6 +557,7 @@ def main_serving(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     jobs = synth.serving_stream(args.serve_jobs, synth.BASE_SEED + 4, n_range=(1e4, args.serve_n_max))
+    prec = B.PRECISIONS[args.prec]
     pts = [synth.mixture_device(j["n"], j["d"], j["blobs"], j["seed"], dev) for j in jobs]
     pts = [x.to(torch.bfloat16) if j["bf16"] else x for j, x in zip(jobs, pts)]
     torch.cuda.synchronize()
@@ -574,7 +575,7 @@ def main_serving(args):
             for i, (j, x) in enumerate(zip(jobs, pts)):
                 if rate:
                     time.sleep(rnd.expovariate(rate))
-                tickets[i] = srv.submit(x, j["N"], j["local_k"], j["final_k"], j["iters"], j["seed"])
+                tickets[i] = srv.submit(x, j["N"], j["local_k"], j["final_k"], j["iters"], j["seed"], prec=prec)
 
         th = threading.Thread(target=submitter)
         th.start()
@@ -604,7 +605,7 @@ def main_serving(args):
     for i in sample:
         j = jobs[i]
         with B.Job(pts[i]) as jb:
-            jb.run(j["N"], j["local_k"], j["final_k"], j["iters"], j["seed"])
+            jb.run(j["N"], j["local_k"], j["final_k"], j["iters"], j["seed"], prec)
             c, _, sse = jb.result(labels=False)
         same += int(np.array_equal(c, res[i][0]) and sse == res[i][1])
     ls = sorted(lat_sat)
@@ -612,7 +613,9 @@ def main_serving(args):
                 for j in jobs)
     line = {"metric": "serving jobs/s", "value": peak, "unit": "jobs/s", "n_gpus": 1, "steps": 1,
             "warmup": 1, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 (bf16 storage for half the jobs)",
+            "vs_baseline": None,
+            "dtype": ("f32" if args.prec == "fp32" else args.prec + " (split mode per shape) + f32")
+                     + " (bf16 storage for half the jobs)",
             "data": "synthetic (generated on the device)",
             "config": {"workload": f"serving{len(jobs)}_n1e4to{args.serve_n_max:.0e}_d8-32-128_k8to1024".replace("+0", ""),
                        "jobs": len(jobs),
