@@ -62,6 +62,8 @@ constexpr int kW = kThreads / 32;
 constexpr uint32_t kInfBits = 0x7f800000u;
 constexpr uint32_t kGone = 0xFFFFFFFFu;       // key past the end of a list
 constexpr uint32_t kNone = 0xFFFFFFFFu;       // round of a point not assigned (yet)
+constexpr int kBkGroup = 16;                   // attributes per sweep of the bucket build
+constexpr int kBkUnroll = 4;                   // (point, attribute) pairs per thread at a time
 constexpr int kKeyCache = 4096;               // keys and ids of a slice kept in shared memory, if it fits
 constexpr int kSelBins = 2048;
 constexpr int kSelList = 1024;
@@ -1404,23 +1406,46 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
         for (uint32_t q = t; q < s1 - s0; q += kThreads) sfl[q] = kFlNone;
 
     // ---- before the first epoch: per attribute, the point ids by value bucket (counting sort)
+    // The attributes go in groups of kBkGroup, each group one grid-stride sweep over its
+    // (point, attribute) pairs, kBkUnroll pairs per thread at a time (their loads, then
+    // their atomics, then their stores, so that each thread keeps several of each in
+    // flight).  A sweep writes the lists through kBkGroup x nbk cursors, few enough that
+    // the partly written sectors at the cursors stay in L2 until they fill.
     {
         const uint32_t nbk = a.nbk;
-        const uint64_t stride = (uint64_t)G * kThreads;
-        const uint32_t si = (uint32_t)(stride / (uint64_t)d), sj = (uint32_t)(stride % (uint64_t)d);
-        const uint64_t e0 = (uint64_t)c * kThreads + t;
+        const uint32_t stride = G * (uint32_t)kThreads;
+        const uint32_t e0 = c * (uint32_t)kThreads + (uint32_t)t;
         for (int pass = 0; pass < 2; pass++) {
-            uint32_t i = (uint32_t)(e0 / (uint64_t)d), j = (uint32_t)(e0 % (uint64_t)d);
-            while (i < n) {
-                const float v = __ldg(&a.x[(size_t)i * d + j]);
-                uint32_t *cnt = &a.bcnt[(size_t)j * nbk + bucket_of(v, nbk)];
-                if (pass == 0) atomicAdd(cnt, 1u);
-                else a.ord[(size_t)j * a.ord_ld + atomicAdd(cnt, 1u)] = i;
-                i += si;
-                j += sj;
-                if (j >= (uint32_t)d) {
-                    j -= (uint32_t)d;
-                    i++;
+            for (int j0 = 0; j0 < d; j0 += kBkGroup) {
+                const uint32_t w = (uint32_t)min(kBkGroup, d - j0);
+                const uint32_t si = stride / w, sj = stride % w;
+                uint32_t i = e0 / w, j = e0 % w;
+                while (i < n) {
+                    uint32_t pi[kBkUnroll], pj[kBkUnroll], pb[kBkUnroll];
+#pragma unroll
+                    for (int u = 0; u < kBkUnroll; u++) {
+                        pi[u] = i;
+                        pj[u] = (uint32_t)j0 + j;
+                        pb[u] = i < n ? bucket_of(__ldg(&a.x[(size_t)i * d + j0 + j]), nbk) : 0u;
+                        i += si;
+                        j += sj;
+                        if (j >= w) {
+                            j -= w;
+                            i++;
+                        }
+                    }
+                    if (pass == 0) {
+#pragma unroll
+                        for (int u = 0; u < kBkUnroll; u++)
+                            if (pi[u] < n) atomicAdd(&a.bcnt[(size_t)pj[u] * nbk + pb[u]], 1u);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < kBkUnroll; u++)
+                            if (pi[u] < n) pb[u] = atomicAdd(&a.bcnt[(size_t)pj[u] * nbk + pb[u]], 1u);
+#pragma unroll
+                        for (int u = 0; u < kBkUnroll; u++)
+                            if (pi[u] < n) a.ord[(size_t)pj[u] * a.ord_ld + pb[u]] = pi[u];
+                    }
                 }
             }
             if (!grid_sync(ctl, a.flags, gen, lim, pass == 0 ? a.stall : 0u)) return;
