@@ -309,6 +309,7 @@ def main_arm(args, w: synth.Workload):
         job_k.steps(wr.N, wr.local_k, wr.final_k, wr.iters, seed, prec)
         kt = job_k.kernel_times()
     rechecked, assigned = job_k.recheck_stats()
+    peel_epochs, peel_passes, peel_updates = job_k.peel_stats()
     phases = job_k.phase_ms()
     job_k.close()
 
@@ -397,6 +398,7 @@ def main_arm(args, w: synth.Workload):
             "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else tc_mode(args.prec, wr) + "+f32",
             "data": "synthetic",
             "near_ties": {"rechecked_rows": rechecked, "tensor_core_rows": assigned},
+            "peel": {"epochs": peel_epochs, "distance_passes": peel_passes, "key_updates": peel_updates},
             "config": config_of(wr, {"parallelism": f"replicas{world}" if world > 1 else "single"}),
             "latency_ms": {"p50": statistics.median(step_ms),
                            "p99": sorted(step_ms)[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]},

@@ -258,6 +258,12 @@ int pscl_get_kernel_times(pscl_job *job, int64_t *launches, float *ms);
  * *rechecked rows re-decided by the float32 direct distance out of *assigned rows
  * (both 0 under PSCL_PREC_FP32).  Either pointer may be NULL. */
 int pscl_get_recheck_stats(pscl_job *job, int64_t *rechecked, int64_t *assigned);
+/* Statistics of the last equal-sized subclustering (Algorithm 1 steps 2-5): *epochs
+ * (rounds committed together from one landmark), *passes (distance passes over the points
+ * left: one per landmark change) and *key_updates (of those passes, the ones that updated
+ * the keys from the few attributes whose landmark value moved instead of recomputing
+ * them).  PSCL_ESTATE if no such subclustering ran on the job.  Pointers may be NULL. */
+int pscl_get_peel_stats(pscl_job *job, int64_t *epochs, int64_t *passes, int64_t *key_updates);
 /* Device time of the phases of the last run in milliseconds: [0] scale, [1] peel,
  * [2] local Lloyd (incl. init), [3] final Lloyd, [4] SSE pass. */
 int pscl_get_phase_ms(pscl_job *job, float *ms5);

@@ -51,6 +51,7 @@ SIGNATURES = {
     "pscl_get_phase_ms": (_I, [_P, _P]),
     "pscl_get_kernel_times": (_I, [_P, _P, _P]),
     "pscl_get_recheck_stats": (_I, [_P, _P, _P]),
+    "pscl_get_peel_stats": (_I, [_P, _P, _P, _P]),
     "pscl_measure_fp32_fma": (_I, [_I, _P]),
     "pscl_assign_sse_noalloc": (_I, [_P, _I64, _I32, _P, _I32, _P, _P, _P]),
     "pscl_job_footprint": (_I, [_P, _I64, _I32, _I64, _I32, _I32, _I32, _I, _I, _I, _P]),
@@ -266,6 +267,13 @@ def pscl_get_recheck_stats(job):
     a, b = C.c_int64(), C.c_int64()
     _chk(lib().pscl_get_recheck_stats(job, C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def pscl_get_peel_stats(job):
+    """(epochs, distance passes, passes that updated the keys) of the last peel."""
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+    _chk(lib().pscl_get_peel_stats(job, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
 
 
 def pscl_get_kernel_times(job):
@@ -575,6 +583,9 @@ class Job:
 
     def recheck_stats(self):
         return pscl_get_recheck_stats(self.h)
+
+    def peel_stats(self):
+        return pscl_get_peel_stats(self.h)
 
     def close(self):
         if self.h is not None:

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -1202,6 +1203,22 @@ extern "C" int pscl_get_recheck_stats(pscl_job *j, int64_t *rechecked, int64_t *
     CU(cudaMemcpy(h, j->flags, sizeof h, cudaMemcpyDeviceToHost));
     if (rechecked) *rechecked = h[2];
     if (assigned) *assigned = h[3];
+    return PSCL_OK;
+}
+
+extern "C" int pscl_get_peel_stats(pscl_job *j, int64_t *epochs, int64_t *passes, int64_t *key_updates)
+{
+    TRY(pscl_job_sync(j));
+    if (!j->pb.ctl) return fail(PSCL_ESTATE, "no equal-sized subclustering has run on this job");
+    uint32_t v[3];
+    static_assert(offsetof(PeelCtl, passes) == offsetof(PeelCtl, epochs) + 4 &&
+                      offsetof(PeelCtl, key_updates) == offsetof(PeelCtl, epochs) + 8,
+                  "the statistics are adjacent");
+    CU(cudaMemcpy(v, reinterpret_cast<const char *>(j->pb.ctl) + offsetof(PeelCtl, epochs), sizeof v,
+                  cudaMemcpyDeviceToHost));
+    if (epochs) *epochs = v[0];
+    if (passes) *passes = v[1];
+    if (key_updates) *key_updates = v[2];
     return PSCL_OK;
 }
 

@@ -37,6 +37,21 @@
 //      and those (in practice exact ties) are ranked by float64 and index.
 // The partition is therefore exactly the float64 definition's, whatever float32 does.
 //
+// Most landmark changes move one or two attributes (the others keep a holder).  The pass
+// after such a change reads only the attributes that moved: with J those attributes, o_j
+// the old and l_j the new value, the squared distance changes by exactly
+//     sum_{j in J} (l_j - o_j)(l_j + o_j - 2 x_j),
+// which is added to every live key in float32.  The keys' error bound then takes the form
+// |delta32 - delta64| <= eps*delta32 + ea with eps and ea carried from pass to pass: a
+// full pass sets (eps0, ea0) = ((d+4) 2^-23, 2^-120), and an update with C = sum_J (l_j - o_j)
+// gives eps' = eps + 2^-23 and ea' = ea + (5 eps + (16 + 4|J|) 2^-24) C (the update's own
+// rounding, the old key's error carried to the new key, and the float64 definition's;
+// scaled values lie in [0, 1]).  Phase C uses the carried bound; a full pass is taken
+// instead when J spans many 32-byte sectors of a row, when more than kIncMax attributes
+// moved, or when eps would pass 1.5 eps0 or ea an eighth of eps0 times the last epoch's
+// first boundary key (the landmark sits at the corner of the minima, so the boundary keys
+// are large and ea stays a small share of the bands' width).
+//
 // Points never move: CTA c owns the index slice [c n/G, (c+1) n/G) and keeps the ids of its
 // points left in a list, in ascending order, with their keys by list position.  Every
 // point gets its round in rnd[]; after the launch a stable counting sort by round packs
@@ -64,6 +79,7 @@ constexpr uint32_t kGone = 0xFFFFFFFFu;       // key past the end of a list
 constexpr uint32_t kNone = 0xFFFFFFFFu;       // round of a point not assigned (yet)
 constexpr int kBkGroup = 16;                   // attributes per sweep of the bucket build
 constexpr int kBkUnroll = 4;                   // (point, attribute) pairs per thread at a time
+constexpr int kIncMax = 8;                     // moved attributes a pass may update keys for
 constexpr int kKeyCache = 4096;               // keys and ids of a slice kept in shared memory, if it fits
 constexpr int kSelBins = 2048;
 constexpr int kSelList = 1024;
@@ -307,18 +323,17 @@ __device__ __forceinline__ uint64_t dff_key(const float *__restrict__ row, const
 }
 
 // Cut-offs of phase C from the 22-bit key prefix [A, B] of a boundary's float32 key.
-// With eps = (d+4) 2^-23 and ea = 2^-120 the boundary's delta64 lies in
+// With |delta32 - delta64| <= eps delta32 + ea (eps <= 1/3) the boundary's delta64 lies in
 // [A(1-eps) - ea, B(1+eps) + ea]; a point is certainly before it if delta32 (1+eps) + ea
 // is below that interval, which holds for delta32 < A(1-2eps) - 2ea, and certainly after
 // it if delta32 (1-eps) - ea is above it, which holds for delta32 > B(1+3eps) + 3ea.  Both
 // cut-offs are evaluated in float32 rounded towards the safe side.
-__device__ void band_cutoffs(uint32_t b0, uint32_t b1, int d, uint32_t &in_key, uint32_t &out_key)
+__device__ void band_cutoffs(uint32_t b0, uint32_t b1, float eps, float ea, uint32_t &in_key, uint32_t &out_key)
 {
     const uint32_t lo = (b0 << 21) | (b1 << 10), hi = lo | 0x3FFu;
     const float A = __uint_as_float(lo), B = __uint_as_float(hi);
-    const float eps = (float)(d + 4) * 0x1p-23f;
-    const float in_thr = __fsub_rd(__fmul_rd(A, __fsub_rd(1.0f, 2.0f * eps)), 0x1p-119f);
-    const float out_thr = __fadd_ru(__fmul_ru(B, __fadd_ru(1.0f, 3.0f * eps)), 0x1.8p-119f);
+    const float in_thr = __fsub_rd(__fmul_rd(A, __fsub_rd(1.0f, 2.0f * eps)), 2.0f * ea);
+    const float out_thr = __fadd_ru(__fmul_ru(B, __fadd_ru(1.0f, __fmul_ru(3.0f, eps))), __fmul_ru(3.0f, ea));
     in_key = in_thr > 0.0f ? __float_as_uint(in_thr) : 0u;
     out_key = __float_as_uint(out_thr);
 }
@@ -578,24 +593,32 @@ __host__ __device__ constexpr int kCoopBatch()
     return 16 / (D / 4) >= 4 ? 4 : (16 / (D / 4) >= 1 ? 16 / (D / 4) : 1);
 }
 
-// A live point equal to the landmark in some attribute: counted per such attribute and
-// flagged for the epochs' holder bookkeeping.
+__device__ __forceinline__ bool in_mask(const uint32_t *jm, int j)
+{
+    return (jm[j >> 5] >> (j & 31)) & 1u;
+}
+
+// A live point equal to the landmark in some attribute: counted per such attribute whose
+// landmark value is new (jm; the counts of the others carry over) and flagged for the
+// epochs' holder bookkeeping.
 __device__ __forceinline__ void note_holder(const float *__restrict__ row, const float *Ls, int d, uint8_t *fl,
-                                            uint32_t *chold)
+                                            uint32_t *chold, const uint32_t *jm)
 {
     for (int j = 0; j < d; j++)
-        if (__ldg(&row[j]) == Ls[j]) atomicAdd(&chold[j], 1u);
+        if (__ldg(&row[j]) == Ls[j] && in_mask(jm, j)) atomicAdd(&chold[j], 1u);
     *fl |= kFlHold;
 }
 
 // Phase A: every live point's float32 key, stored by list position (shared memory when
-// kc, else kpos: the slice's keys) and counted in the first-digit histogram sh; holders counted per attribute and
-// flagged in their position's state byte (pfl: the slice's, by list position).  Out of line, so that
-// the register allocation of the kernel's other phases does not carry its loads in flight.
+// kc, else kpos: the slice's keys) and counted in the first-digit histogram sh; holders
+// counted per attribute of jm and flagged in their position's state byte (pfl: the
+// slice's, by list position).  Out of line, so that the register allocation of the
+// kernel's other phases does not carry its loads in flight.
 template <int D>
 __device__ __noinline__ void phase_keys(const float *__restrict__ x, const float *Ls, int d, uint32_t n_live,
                                         uint32_t s0, bool first, bool kc, const uint32_t *sid, const uint32_t *glin,
-                                        uint32_t *skey, uint32_t *kpos, uint32_t *sh, uint8_t *pfl, uint32_t *chold)
+                                        uint32_t *skey, uint32_t *kpos, uint32_t *sh, uint8_t *pfl, uint32_t *chold,
+                                        const uint32_t *jm)
 {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     auto LID = [&](uint32_t q) -> uint32_t { return first ? s0 + q : kc ? sid[q] : __ldcg(&glin[q]); };
@@ -691,10 +714,10 @@ __device__ __noinline__ void phase_keys(const float *__restrict__ x, const float
                             for (int f = 0; f < F; f++) {
                                 const float4 vv = __ldg(r4 + P * f);
                                 const int j = 4 * (sl + P * f);
-                                if (vv.x == Ls[j + 0]) atomicAdd(&chold[j + 0], 1u);
-                                if (vv.y == Ls[j + 1]) atomicAdd(&chold[j + 1], 1u);
-                                if (vv.z == Ls[j + 2]) atomicAdd(&chold[j + 2], 1u);
-                                if (vv.w == Ls[j + 3]) atomicAdd(&chold[j + 3], 1u);
+                                if (vv.x == Ls[j + 0] && in_mask(jm, j + 0)) atomicAdd(&chold[j + 0], 1u);
+                                if (vv.y == Ls[j + 1] && in_mask(jm, j + 1)) atomicAdd(&chold[j + 1], 1u);
+                                if (vv.z == Ls[j + 2] && in_mask(jm, j + 2)) atomicAdd(&chold[j + 2], 1u);
+                                if (vv.w == Ls[j + 3] && in_mask(jm, j + 3)) atomicAdd(&chold[j + 3], 1u);
                             }
                             pfl[rpos] |= kFlHold;
                         }
@@ -724,9 +747,68 @@ __device__ __noinline__ void phase_keys(const float *__restrict__ x, const float
             for (int q = 0; q < B; q++) dl[q] = dist32<D>(x + (size_t)ids[q] * d, Ls, d, hz[q]);
 #pragma unroll
             for (int q = 0; q < B; q++) {
-                if (lv[q] && hz[q]) note_holder(x + (size_t)ids[q] * d, Ls, d, &pfl[base + q * kThreads + t], chold);
+                if (lv[q] && hz[q])
+                    note_holder(x + (size_t)ids[q] * d, Ls, d, &pfl[base + q * kThreads + t], chold, jm);
                 key_out(lv[q], base + q * kThreads + t, __float_as_uint(dl[q]));
             }
+        }
+    }
+}
+
+// Phase A after a landmark change in the nj attributes jj (ascending; old values jo, new
+// values jl): every live key moves by the change of its squared distance,
+// sum_i (jl_i - jo_i)(jl_i + jo_i - 2 x_{jj_i}) (FMA chain in float32), read from those
+// attributes only; the result is clamped at 0, stored in place and counted in sh, and the
+// holders of the new values are counted and flagged as in phase_keys.
+template <int D>
+__device__ __noinline__ void phase_inc(const float *__restrict__ x, int d, uint32_t n_live, bool kc,
+                                       const uint32_t *sid, const uint32_t *glin, uint32_t *skey, uint32_t *kpos,
+                                       uint32_t *sh, uint8_t *pfl, uint32_t *chold, uint32_t nj, const int *jj,
+                                       const float *jo, const float *jl)
+{
+    constexpr int U = 4;                                   // list positions per thread in flight
+    const int t = threadIdx.x, lane = t & 31;
+    const size_t dd = (size_t)(D > 0 ? D : d);
+    for (uint32_t q0 = 0; q0 < n_live; q0 += U * kThreads) {          // block-uniform bound
+        uint32_t id[U], key[U], hold = 0;
+        float acc[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t qi = q0 + u * kThreads + t;
+            const bool v = qi < n_live;
+            id[u] = v ? (kc ? sid[qi] : __ldcg(&glin[qi])) : kGone;
+            key[u] = v ? (kc ? skey[qi] : __ldcg(&kpos[qi])) : 0u;
+            acc[u] = 0.0f;
+        }
+        for (uint32_t i = 0; i < nj; i++) {
+            const int j = jj[i];
+            const float ln = jl[i], c = __fsub_rn(ln, jo[i]), sm = __fadd_rn(ln, jo[i]);
+            float v[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) v[u] = id[u] != kGone ? __ldg(&x[(size_t)id[u] * dd + j]) : ln;
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                acc[u] = __fmaf_rn(c, __fmaf_rn(-2.0f, v[u], sm), acc[u]);
+                if (v[u] == ln && id[u] != kGone) {
+                    atomicAdd(&chold[j], 1u);
+                    hold |= 1u << u;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t qi = q0 + u * kThreads + t;
+            const bool live = id[u] != kGone;
+            const float kv = __fadd_rn(__uint_as_float(key[u]), acc[u]);
+            const uint32_t k = kv > 0.0f ? __float_as_uint(kv) : 0u;
+            if (live) {
+                if (kc) skey[qi] = k;
+                else kpos[qi] = k;
+                if ((hold >> u) & 1u) pfl[qi] |= kFlHold;
+            }
+            const uint32_t b = live ? (k >> 21) : kGone;
+            const uint32_t peers = __match_any_sync(0xffffffffu, b);
+            if (live && lane == __ffs(peers) - 1) atomicAdd(&sh[b], (uint32_t)__popc(peers));
         }
     }
 }
@@ -993,8 +1075,10 @@ __device__ __noinline__ void find_landmark(const PeelArgs &a, int j_first, int j
             b = fb + 1;                            // every entry of fb is gone
         }
         if (t == 0) {
+            const uint32_t nb = mnb == kGone ? kInfBits : mnb;
             ctl->lptr[j] = b;
-            ctl->Lbits[j] = mnb == kGone ? kInfBits : mnb;
+            if (nb != __ldcg(&ctl->Lbits[j])) ctl->chold[j] = 0;    // a new value: its holders are counted again
+            ctl->Lbits[j] = nb;
         }
     }
 }
@@ -1004,8 +1088,8 @@ __device__ __noinline__ void find_landmark(const PeelArgs &a, int j_first, int j
 // whose bands overlap into groups.  Warp w resolves boundaries w, w + kW, ...: lane i sums
 // second-digit bins [64 i, 64 i + 64) in two halves, a warp scan finds the lane holding
 // the rank, and that lane walks the half holding it (its loads issued together).
-__device__ __noinline__ void resolve_cutoffs(PeelCtl *ctl, uint32_t K, int d, const uint32_t *sb, const uint32_t *sr,
-                                             const uint32_t *sslot, uint32_t nslot)
+__device__ __noinline__ void resolve_cutoffs(PeelCtl *ctl, uint32_t K, float keps, float kabs, const uint32_t *sb,
+                                             const uint32_t *sr, const uint32_t *sslot, uint32_t nslot)
 {
     __shared__ uint32_t s_b1[kMaxEpoch];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -1050,7 +1134,7 @@ __device__ __noinline__ void resolve_cutoffs(PeelCtl *ctl, uint32_t K, int d, co
         uint32_t ng = 0, gi = 0, go = 0;
         for (uint32_t q = 0; q < K; q++) {
             uint32_t ik, ok;
-            band_cutoffs(sb[q], s_b1[q], d, ik, ok);
+            band_cutoffs(sb[q], s_b1[q], keps, kabs, ik, ok);
             if (ng > 0 && ik <= go) {
                 go = max(go, ok);
                 ctl->g_out[ng - 1] = go;
@@ -1067,6 +1151,7 @@ __device__ __noinline__ void resolve_cutoffs(PeelCtl *ctl, uint32_t K, int d, co
         }
         ctl->n_groups = ng;
         ctl->n_slots = nslot;
+        ctl->kref = __uint_as_float(sb[0] << 21);
     }
 }
 
@@ -1099,15 +1184,13 @@ __device__ __noinline__ void commit_count(const PeelArgs &a, const float *Ls, ui
     qs = block_min(qs);
     const uint32_t kc_ = qs < K ? qs + 1u : K;
     const bool changed = qs < K;
+    // the holders that leave with the committed rounds (an attribute whose landmark value
+    // changes has its count cleared by find_landmark and counted again by the next pass)
     for (int j = t; j < d; j += kThreads) {
-        if (changed) {
-            ctl->chold[j] = 0;
-        } else {
-            uint32_t gone = 0;
+        uint32_t gone = 0;
 #pragma unroll
-            for (int r = 0; r < kMaxEpoch; r++) gone += r < (int)kc_ ? __ldcg(&ctl->hcnt[j][r]) : 0u;
-            ctl->chold[j] = __ldcg(&ctl->chold[j]) - gone;
-        }
+        for (int r = 0; r < kMaxEpoch; r++) gone += r < (int)kc_ ? __ldcg(&ctl->hcnt[j][r]) : 0u;
+        ctl->chold[j] = __ldcg(&ctl->chold[j]) - gone;
     }
     if (t < (int)K && __ldcg(&ctl->cert[t]) + __ldcg(&ctl->bnd[t]) != N) atomicOr(&a.flags[1], 1u);
     if (changed)
@@ -1380,10 +1463,19 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
     __shared__ uint32_t s_cc[kMaxEpoch], s_gc[kMaxEpoch];
     __shared__ uint32_t s_nslot, s_glast;
     __shared__ uint8_t s_map[kHistBins];
+    // the previous epoch's landmark; the attributes whose landmark value is new (mask) and,
+    // for an update of the keys, those attributes with their old and new values
+    __shared__ float Lold[D > 0 ? D : kMaxD];
+    __shared__ uint32_t s_jm[kMaxD / 32];
+    __shared__ int s_ij[kIncMax];
+    __shared__ float s_io[kIncMax], s_il[kIncMax];
+    __shared__ uint32_t s_nj;
+    __shared__ int s_inc;
+    __shared__ float s_keps, s_kabs;
     PeelCtl *ctl = a.ctl;
     const int d = a.d;
     const uint32_t n = (uint32_t)a.n, N = (uint32_t)a.N;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const unsigned G = gridDim.x, c = blockIdx.x;
     const unsigned lim = a.spin;
     // With 16 CTAs or more, the last Gl CTAs own no points and only build landmarks, which
@@ -1490,6 +1582,10 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
     bool first = true;           // the first epoch: a slice's list is the slice itself
     bool need_keys = true;       // the landmark changed: the keys must be computed
     uint32_t r0 = 0;             // the epoch's first round
+    // the keys' error bound |delta32 - delta64| <= k_eps delta32 + k_abs (thread 0 keeps it,
+    // the same in every CTA) and the key updates since the last full pass
+    const double eps0 = (double)(d + 4) * 0x1p-23;
+    double k_eps = eps0, k_abs = 0x1p-120;
     // boundaries the next epoch tries: all it may after an epoch that kept its landmark,
     // twice the rounds committed after one whose landmark changed (most such runs are
     // short, and each boundary's work is lost when the landmark changes before it)
@@ -1499,7 +1595,10 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
         auto LID = [&](uint32_t q) -> uint32_t { return first ? s0 + q : kc ? sid[q] : __ldcg(&gid[q]); };
         auto LKEY = [&](uint32_t q) -> uint32_t { return kc ? skey[q] : __ldcg(&gkp[q]); };
         const ListView LV{first, kc, s0, sid, skey, sfl, gid, gkp, gfl, gid2, gkp2, gfl2};
-        for (int j = t; j < d; j += kThreads) Ls[j] = __uint_as_float(__ldcg(&ctl->Lbits[j]));
+        for (int j = t; j < d; j += kThreads) {
+            Lold[j] = Ls[j];
+            Ls[j] = __uint_as_float(__ldcg(&ctl->Lbits[j]));
+        }
         __syncthreads();
         if (nl_tot <= N) {                            // the last subcluster: all that is left
             for (uint32_t q = t; q < n_live; q += kThreads) a.rnd[LID(q)] = r0;
@@ -1511,10 +1610,65 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
 
         // ---- A: float32 distances of the points left, the first histogram, the holders
         if (need_keys) {
+            // the attributes whose landmark value is new (all of them at first)
+            for (int j0 = w * 32; j0 < d; j0 += kW * 32) {
+                const int j = j0 + lane;
+                const bool mv = j < d && (first || __float_as_uint(Ls[j]) != __float_as_uint(Lold[j]));
+                const uint32_t m = __ballot_sync(0xffffffffu, mv);
+                if (lane == 0) s_jm[j0 >> 5] = m;
+            }
             for (int b = t; b < kHistBins; b += kThreads) scr[b] = 0;
             __syncthreads();
-            phase_keys<D>(a.x, Ls, d, n_live, s0, first, kc, sid, gid, skey, gkp, scr, pfl,
-                          ctl->chold);
+            if (t == 0) {
+                // an update of the keys, or a full pass (the same choice in every CTA)
+                uint32_t nj = 0, nsec = 0, last_sec = kGone;
+                double cs = 0.0;
+                bool fin = true;
+                for (int wd = 0; wd < (d + 31) / 32; wd++) {
+                    uint32_t m = s_jm[wd];
+                    while (m) {
+                        const int j = wd * 32 + __ffs(m) - 1;
+                        m &= m - 1u;
+                        if (nj < (uint32_t)kIncMax) {
+                            s_ij[nj] = j;
+                            s_io[nj] = Lold[j];
+                            s_il[nj] = Ls[j];
+                            const float c = __fsub_rn(Ls[j], Lold[j]);
+                            fin = fin && c >= 0.0f && c <= 1.0f;
+                            cs += (double)c;
+                        }
+                        nj++;
+                        if ((uint32_t)(j >> 3) != last_sec) {
+                            nsec++;
+                            last_sec = (uint32_t)(j >> 3);
+                        }
+                    }
+                }
+                const double ne = k_eps + 0x1p-23;
+                const double na = k_abs + (5.0 * k_eps + (16.0 + 4.0 * nj) * 0x1p-24) * cs * (1.0 + 0x1p-20);
+                // the absolute term stays below an eighth of the relative one at the last
+                // epoch's first boundary, so the bands widen little
+                const double kref = (double)__ldcg(&ctl->kref);
+                const bool inc = !first && fin && nj >= 1 && nj <= (uint32_t)kIncMax && nsec * 160u < 12u * (uint32_t)d &&
+                                 ne <= 1.5 * eps0 && na <= 0.125 * eps0 * kref;
+                if (inc) {
+                    k_eps = ne;
+                    k_abs = na;
+                } else {
+                    k_eps = eps0;
+                    k_abs = 0x1p-120;
+                }
+                s_nj = inc ? nj : 0u;
+                s_inc = inc ? 1 : 0;
+                if (inc && c == 0) ctl->key_updates += 1;
+                s_keps = __double2float_ru(k_eps);
+                s_kabs = __double2float_ru(k_abs);
+            }
+            __syncthreads();
+            if (s_inc)
+                phase_inc<D>(a.x, d, n_live, kc, sid, gid, skey, gkp, scr, pfl, ctl->chold, s_nj, s_ij, s_io, s_il);
+            else
+                phase_keys<D>(a.x, Ls, d, n_live, s0, first, kc, sid, gid, skey, gkp, scr, pfl, ctl->chold, s_jm);
             __syncthreads();
             for (int b = t; b < kHistBins; b += kThreads)
                 if (scr[b]) atomicAdd(&ctl->h0[b], scr[b]);
@@ -1588,7 +1742,7 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
         }
         // the last CTA to arrive turns each boundary's bins into its band cut-offs, and
         // merges boundaries whose bands overlap into groups
-        if (!grid_sync_last(ctl, a.flags, gen, lim, [&]() { resolve_cutoffs(ctl, K, d, s_b, s_r, s_slot, s_nslot); }))
+        if (!grid_sync_last(ctl, a.flags, gen, lim, [&]() { resolve_cutoffs(ctl, K, s_keps, s_kabs, s_b, s_r, s_slot, s_nslot); }))
             return;
 
         // ---- C: classify every point left: certainly in a round of the epoch, in a band, or later

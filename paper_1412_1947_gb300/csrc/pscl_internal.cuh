@@ -35,6 +35,7 @@ struct PeelCtl {
     uint32_t gfill[kMaxEpoch];           // of those, regrouped into the group's region so far
     uint32_t g_in[kMaxEpoch], g_out[kMaxEpoch];   // a group's band: keys in [g_in, g_out]
     uint32_t g_q1[kMaxEpoch], g_q2[kMaxEpoch];    // a group's first and last boundary
+    float kref;                          // lower end of the first boundary's key bin, last epoch
     uint32_t n_slots;                    // first-digit bins with a second-digit histogram
     uint32_t n_groups;
     uint32_t band_cnt;                   // band entries listed this epoch
@@ -43,7 +44,8 @@ struct PeelCtl {
     uint32_t bar_count;                  // grid barrier: arrivals since the launch
     uint32_t abort;                      // set when a barrier wait gave up
     uint32_t epochs;                     // statistics: epochs run,
-    uint32_t passes;                     //   distance passes over the points left
+    uint32_t passes;                     //   distance passes over the points left,
+    uint32_t key_updates;                //   of which updates of the keys in a few attributes
 };
 
 // v (a scaled coordinate, in [0, 1]) times 2^32 rounded to the nearest integer, ties to

@@ -85,3 +85,22 @@ def test_partition_does_not_depend_on_the_grid(cap):
     operm, ooff, _ = oracle.peel(x, N)
     np.testing.assert_array_equal(off, ooff)
     np.testing.assert_array_equal(perm, operm)
+
+
+@pytest.mark.parametrize("n,d,blobs,N", [(1 << 17, 64, 256, 1024), (1 << 18, 16, 64, 1024)])
+def test_key_updates_keep_the_partition(n, d, blobs, N):
+    # 128 and 256 rounds on the two measured shapes' recipes, scaled down: most landmark changes
+    # move one or two attributes, so most passes update the keys from those attributes
+    # (with the carried error bound) instead of recomputing them; the partition is still
+    # the oracle's bit for bit
+    raw = synth.mixture(n, d, blobs, seed=607 + d)
+    with B.Job(raw) as j:
+        j.steps(N, 2, 2, 1, 3)
+        perm, off = j.partition()
+        x = j.scaled()
+        epochs, passes, updates = j.peel_stats()
+    print(f"epochs {epochs} passes {passes} key updates {updates}")
+    assert 0 < updates < passes <= epochs
+    operm, ooff, _ = oracle.peel(x, N, select=True)
+    np.testing.assert_array_equal(off, ooff)
+    np.testing.assert_array_equal(perm, operm)
