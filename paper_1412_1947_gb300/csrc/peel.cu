@@ -536,6 +536,7 @@ __device__ __forceinline__ uint32_t bucket_of(float v, uint32_t nb)
 // ------------------------------------------------------------------ the kernel
 struct PeelArgs {
     const float *x;
+    const float *xt;             // d x n: the points by attribute (or NULL: the updates read x)
     int d;
     int64_t n, N, S;
     uint32_t *rnd;
@@ -761,14 +762,17 @@ __device__ __noinline__ void phase_keys(const float *__restrict__ x, const float
 // attributes only; the result is clamped at 0, stored in place and counted in sh, and the
 // holders of the new values are counted and flagged as in phase_keys.
 template <int D>
-__device__ __noinline__ void phase_inc(const float *__restrict__ x, int d, uint32_t n_live, bool kc,
-                                       const uint32_t *sid, const uint32_t *glin, uint32_t *skey, uint32_t *kpos,
-                                       uint32_t *sh, uint8_t *pfl, uint32_t *chold, uint32_t nj, const int *jj,
-                                       const float *jo, const float *jl)
+__device__ __noinline__ void phase_inc(const float *__restrict__ x, const float *__restrict__ xt, uint32_t n, int d,
+                                       uint32_t n_live, bool kc, const uint32_t *sid, const uint32_t *glin,
+                                       uint32_t *skey, uint32_t *kpos, uint32_t *sh, uint8_t *pfl, uint32_t *chold,
+                                       uint32_t nj, const int *jj, const float *jo, const float *jl)
 {
     constexpr int U = 4;                                   // list positions per thread in flight
     const int t = threadIdx.x, lane = t & 31;
-    const size_t dd = (size_t)(D > 0 ? D : d);
+    // attribute j of point i at src[i * ps + j * as]: the by-attribute copy (a CTA's ids
+    // ascend, so a warp's loads fall close together) or the rows
+    const float *src = xt ? xt : x;
+    const size_t ps = xt ? 1 : (size_t)(D > 0 ? D : d), as = xt ? (size_t)n : 1;
     for (uint32_t q0 = 0; q0 < n_live; q0 += U * kThreads) {          // block-uniform bound
         uint32_t id[U], key[U], hold = 0;
         float acc[U];
@@ -785,7 +789,7 @@ __device__ __noinline__ void phase_inc(const float *__restrict__ x, int d, uint3
             const float ln = jl[i], c = __fsub_rn(ln, jo[i]), sm = __fadd_rn(ln, jo[i]);
             float v[U];
 #pragma unroll
-            for (int u = 0; u < U; u++) v[u] = id[u] != kGone ? __ldg(&x[(size_t)id[u] * dd + j]) : ln;
+            for (int u = 0; u < U; u++) v[u] = id[u] != kGone ? __ldg(&src[(size_t)id[u] * ps + (size_t)j * as]) : ln;
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 acc[u] = __fmaf_rn(c, __fmaf_rn(-2.0f, v[u], sm), acc[u]);
@@ -1666,7 +1670,8 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
             }
             __syncthreads();
             if (s_inc)
-                phase_inc<D>(a.x, d, n_live, kc, sid, gid, skey, gkp, scr, pfl, ctl->chold, s_nj, s_ij, s_io, s_il);
+                phase_inc<D>(a.x, a.xt, n, d, n_live, kc, sid, gid, skey, gkp, scr, pfl, ctl->chold, s_nj, s_ij, s_io,
+                             s_il);
             else
                 phase_keys<D>(a.x, Ls, d, n_live, s0, first, kc, sid, gid, skey, gkp, scr, pfl, ctl->chold, s_jm);
             __syncthreads();
@@ -1843,6 +1848,36 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
     }
 }
 
+// ------------------------------------------------------------------ the points by attribute
+// x (n x d, by point) into xt (d x n, by attribute) for the peel's key updates: 32 x 32
+// tiles through shared memory, so that both the reads (32 attributes of a point) and the
+// writes (32 points of an attribute) are coalesced.
+constexpr int kTrThreads = 256;
+constexpr size_t kTransposeBytes = size_t(96) << 20;
+
+__global__ void __launch_bounds__(kTrThreads) k_transpose(const float *__restrict__ x, int64_t n, int d,
+                                                          float *__restrict__ xt)
+{
+    __shared__ float tile[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t tiles_c = (d + 31) / 32;
+    const int64_t tiles = (n + 31) / 32 * tiles_c;
+    for (int64_t tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
+        const int64_t r0 = tt / tiles_c * 32;
+        const int c0 = (int)(tt % tiles_c) * 32;
+        for (int k = ty; k < 32; k += kTrThreads / 32) {
+            const int64_t r = r0 + k;
+            if (r < n && c0 + tx < d) tile[k][tx] = __ldg(&x[r * d + c0 + tx]);
+        }
+        __syncthreads();
+        for (int k = ty; k < 32; k += kTrThreads / 32) {
+            const int64_t r = r0 + tx;
+            if (r < n && c0 + k < d) xt[(size_t)(c0 + k) * (size_t)n + (size_t)r] = tile[tx][k];
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------ packing by round
 // Stable counting sort of the points by round (8 bits of it per pass): the subclusters,
 // each in ascending point index.  Chunk c of the items is [c m/G, (c+1) m/G).
@@ -1994,6 +2029,10 @@ cudaError_t peel_launch(const PeelBuffers &b, int64_t n, int d, int64_t N, int s
     if (b.max_grid > 0 && grid > b.max_grid) grid = b.max_grid;
     PeelArgs a;
     a.x = b.x;
+    // the points by attribute for the key updates, in xseg (idle until the subclusters are
+    // gathered after the launch), where the rows do not fit in L2: an update then reads 4
+    // bytes of each point left instead of a 32-byte sector of its row
+    a.xt = (size_t)n * d * sizeof(float) > kTransposeBytes ? b.xseg : nullptr;
     a.d = d;
     a.n = n;
     a.N = N;
@@ -2030,6 +2069,10 @@ cudaError_t peel_launch(const PeelBuffers &b, int64_t n, int d, int64_t N, int s
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     kt->begin(st);
+    if (a.xt) {                  // timed and counted with the peel it serves
+        k_transpose<<<sm_count * 8, kTrThreads, 0, st>>>(b.x, n, d, b.xseg);
+        kt->launches[PSCL_K_PEEL]++;
+    }
     e = cudaLaunchKernelEx(&cfg, k_peel<D>, a);
     kt->end(PSCL_K_PEEL, st);
     if (e != cudaSuccess) return e;

@@ -87,12 +87,14 @@ def test_partition_does_not_depend_on_the_grid(cap):
     np.testing.assert_array_equal(perm, operm)
 
 
-@pytest.mark.parametrize("n,d,blobs,N", [(1 << 17, 64, 256, 1024), (1 << 18, 16, 64, 1024)])
+@pytest.mark.parametrize("n,d,blobs,N", [(1 << 17, 64, 256, 1024), (1 << 18, 16, 64, 1024),
+                                         (1 << 18, 128, 256, 8192)])
 def test_key_updates_keep_the_partition(n, d, blobs, N):
     # 128 and 256 rounds on the two measured shapes' recipes, scaled down: most landmark changes
     # move one or two attributes, so most passes update the keys from those attributes
     # (with the carried error bound) instead of recomputing them; the partition is still
-    # the oracle's bit for bit
+    # the oracle's bit for bit.  The third case (128 MB of points, more than L2 holds)
+    # reads the moved attributes from the copy of the points by attribute
     raw = synth.mixture(n, d, blobs, seed=607 + d)
     with B.Job(raw) as j:
         j.steps(N, 2, 2, 1, 3)
