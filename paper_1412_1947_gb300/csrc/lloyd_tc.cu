@@ -61,6 +61,22 @@ enum TcMode { kModeTf32 = 0, kModeBf16 = 1, kModeTf32x3 = 2, kModeBf16x3 = 3 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// min(a, b, c) in one instruction (sm_100 and later)
+__device__ __forceinline__ float min3f(float a, float b, float c)
+{
+    float m;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(m) : "f"(a), "f"(b), "f"(c));
+    return m;
+}
+
+// all ones if v <= thr, else 0
+__device__ __forceinline__ uint32_t le_mask(float v, float thr)
+{
+    uint32_t s;
+    asm("set.le.u32.f32 %0, %1, %2;" : "=r"(s) : "f"(v), "f"(thr));
+    return s;
+}
+
 // ---------------------------------------------------------------- mbarriers
 __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count)
 {
@@ -262,6 +278,14 @@ __device__ __forceinline__ void put4(unsigned char *base, int r, int e0, float a
     }
 }
 
+// Four bfloat16 elements (e0 % 4 == 0) of row r of a bfloat16 operand, already packed in pairs.
+template <int D, int MODE>
+__device__ __forceinline__ void put4_bits(unsigned char *base, int r, int e0, uint32_t lo, uint32_t hi)
+{
+    *reinterpret_cast<uint2 *>(base + op_off<D, MODE>(r, e0)) = make_uint2(lo, hi);
+}
+
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<const uint32_t *>(&v); }
 
 // ---------------------------------------------------------------- the assignment kernel
 // Per-tile data the converters hand to the epilogue (a ring of kMeta entries).
@@ -586,16 +610,33 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<D>()) k_tc_assign(co
                     const int bx = (4 * a4) / L::kXBoxCols, c = ((4 * a4) % L::kXBoxCols) / 4;
                     const float4 v = *reinterpret_cast<const float4 *>(xt + (size_t)bx * L::kXBoxBytes +
                                                                        xbox_off<D, MODE>(r, c));
-                    float xv[4] = {v.x, v.y, v.z, v.w}, h[4], lo[4];
+                    float xv[4] = {v.x, v.y, v.z, v.w}, xc[4];
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
-                        const float xc = live ? __fsub_rn(xv[q], s_ref[4 * a4 + q]) : 0.0f;
-                        xn2 = __fmaf_rn(xc, xc, xn2);
-                        h[q] = O::rnd(xc);
-                        lo[q] = O::rnd(__fsub_rn(xc, h[q]));
+                        xc[q] = live ? __fsub_rn(xv[q], s_ref[4 * a4 + q]) : 0.0f;
+                        xn2 = __fmaf_rn(xc[q], xc[q], xn2);
                     }
-                    put4<D, MODE>(at, r, 4 * a4, h[0], h[1], h[2], h[3]);
-                    if (O::kSplit) put4<D, MODE>(at, r, D + 4 * a4, lo[0], lo[1], lo[2], lo[3]);
+                    if constexpr (O::kBf16) {
+                        // pairs rounded to bfloat16 in one conversion each, written as they are
+                        const __nv_bfloat162 h01 = __floats2bfloat162_rn(xc[0], xc[1]);
+                        const __nv_bfloat162 h23 = __floats2bfloat162_rn(xc[2], xc[3]);
+                        put4_bits<D, MODE>(at, r, 4 * a4, bf2_bits(h01), bf2_bits(h23));
+                        if (O::kSplit) {
+                            const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+                            const __nv_bfloat162 l01 = __floats2bfloat162_rn(__fsub_rn(xc[0], f01.x), __fsub_rn(xc[1], f01.y));
+                            const __nv_bfloat162 l23 = __floats2bfloat162_rn(__fsub_rn(xc[2], f23.x), __fsub_rn(xc[3], f23.y));
+                            put4_bits<D, MODE>(at, r, D + 4 * a4, bf2_bits(l01), bf2_bits(l23));
+                        }
+                    } else {
+                        float h[4], lo[4];
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            h[q] = O::rnd(xc[q]);
+                            lo[q] = O::rnd(__fsub_rn(xc[q], h[q]));
+                        }
+                        put4<D, MODE>(at, r, 4 * a4, h[0], h[1], h[2], h[3]);
+                        if (O::kSplit) put4<D, MODE>(at, r, D + 4 * a4, lo[0], lo[1], lo[2], lo[3]);
+                    }
                 }
                 const float one = live ? 1.0f : 0.0f;
                 put4<D, MODE>(at, r, L::kParts * D, one, one, O::kNormParts > 2 ? one : 0.0f, 0.0f);
@@ -660,10 +701,13 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<D>()) k_tc_assign(co
                     tmem_wait();
                     if (cb + kStep <= k) {
 #pragma unroll
-                        for (int q = 0; q < 32; q++) m4[q & 3] = fminf(m4[q & 3], __uint_as_float(v0[q]));
+                        for (int q = 0; q < 32; q += 2)
+                            m4[(q >> 1) & 3] = min3f(m4[(q >> 1) & 3], __uint_as_float(v0[q]), __uint_as_float(v0[q + 1]));
                         if (!kLean) {
 #pragma unroll
-                            for (int q = 0; q < 32; q++) m4[q & 3] = fminf(m4[q & 3], __uint_as_float(v1[q]));
+                            for (int q = 0; q < 32; q += 2)
+                                m4[(q >> 1) & 3] =
+                                    min3f(m4[(q >> 1) & 3], __uint_as_float(v1[q]), __uint_as_float(v1[q + 1]));
                         }
                     } else {
 #pragma unroll
@@ -690,12 +734,13 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<D>()) k_tc_assign(co
                 for (int c = 0; c < 8; c++) {
                     w[c] = 0u;
                     if (32 * c < k) {
-                        uint32_t v[32];
+                        uint32_t v[32], acc = 0u;
                         tmem_ld32_nowait(taddr + (uint32_t)(32 * c), v);
                         tmem_wait();
 #pragma unroll
-                        for (int q = 0; q < 32; q++)
-                            w[c] |= (__uint_as_float(v[q]) <= thr && 32 * c + q < k) ? (1u << q) : 0u;
+                        for (int q = 0; q < 32; q++) acc |= le_mask(__uint_as_float(v[q]), thr) & (1u << q);
+                        const int rem = k - 32 * c;          // columns past k hold no center
+                        w[c] = rem >= 32 ? acc : acc & ((1u << rem) - 1u);
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
