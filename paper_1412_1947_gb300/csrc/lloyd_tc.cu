@@ -901,30 +901,57 @@ __global__ void __launch_bounds__(sum_threads<D>(), D <= 32 ? 2 : 1) k_tc_sums(c
                         }
                         const uint4 *mk = reinterpret_cast<const uint4 *>(tmask + trow * 8);
                         const uint4 ma = __ldg(mk), mb = __ldg(mk + 1);
-                        const uint32_t wd[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
+                        uint32_t wd[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
+#pragma unroll
+                        for (int c = 0; c < 8; c++) {      // no bit at or past k
+                            const int rem = k - 32 * c;
+                            wd[c] &= rem >= 32 ? 0xffffffffu : rem > 0 ? (1u << rem) - 1u : 0u;
+                        }
+                        // the candidates in ascending order, two at a time (two independent
+                        // chains); strict comparisons in that order keep the lowest index
+                        // (the words move down as they empty: registers, no indexed access)
+                        int base = 0, left = 8;
+                        auto next = [&](int &j) -> bool {
+                            while (wd[0] == 0u && left > 1) {
+#pragma unroll
+                                for (int q = 0; q < 7; q++) wd[q] = wd[q + 1];
+                                wd[7] = 0u;
+                                base += 32;
+                                left--;
+                            }
+                            if (wd[0] == 0u) return false;
+                            j = base + __ffs(wd[0]) - 1;
+                            wd[0] &= wd[0] - 1u;
+                            return true;
+                        };
                         float bd = __int_as_float(0x7f800000);
+                        int j0, j1;
+                        while (next(j0)) {
+                            const bool two = next(j1);
+                            if (!two) j1 = j0;
+                            const float4 *c0 = reinterpret_cast<const float4 *>(scen + (size_t)j0 * DC);
+                            const float4 *c1 = reinterpret_cast<const float4 *>(scen + (size_t)j1 * DC);
+                            float d0 = 0.0f, d1 = 0.0f;
 #pragma unroll
-                        for (int c = 0; c < 8; c++) {
-                            uint32_t bits = 32 * c < k ? wd[c] : 0u;
-                            while (bits) {             // ascending candidates: strict keeps the lowest
-                                const int j = 32 * c + __ffs(bits) - 1;
-                                bits &= bits - 1u;
-                                if (j >= k) break;
-                                const float4 *c0 = reinterpret_cast<const float4 *>(scen + (size_t)j * DC);
-                                float d0 = 0.0f;
-#pragma unroll
-                                for (int a4 = 0; a4 < D / 4; a4++) {
-                                    const float4 u = c0[a4];
-                                    float t;
-                                    t = __fsub_rn(x[4 * a4 + 0], u.x); d0 = __fmaf_rn(t, t, d0);
-                                    t = __fsub_rn(x[4 * a4 + 1], u.y); d0 = __fmaf_rn(t, t, d0);
-                                    t = __fsub_rn(x[4 * a4 + 2], u.z); d0 = __fmaf_rn(t, t, d0);
-                                    t = __fsub_rn(x[4 * a4 + 3], u.w); d0 = __fmaf_rn(t, t, d0);
-                                }
-                                if (d0 < bd) {
-                                    bd = d0;
-                                    mylab = j;
-                                }
+                            for (int a4 = 0; a4 < D / 4; a4++) {
+                                const float4 u = c0[a4], w4 = c1[a4];
+                                float t, y;
+                                t = __fsub_rn(x[4 * a4 + 0], u.x); d0 = __fmaf_rn(t, t, d0);
+                                y = __fsub_rn(x[4 * a4 + 0], w4.x); d1 = __fmaf_rn(y, y, d1);
+                                t = __fsub_rn(x[4 * a4 + 1], u.y); d0 = __fmaf_rn(t, t, d0);
+                                y = __fsub_rn(x[4 * a4 + 1], w4.y); d1 = __fmaf_rn(y, y, d1);
+                                t = __fsub_rn(x[4 * a4 + 2], u.z); d0 = __fmaf_rn(t, t, d0);
+                                y = __fsub_rn(x[4 * a4 + 2], w4.z); d1 = __fmaf_rn(y, y, d1);
+                                t = __fsub_rn(x[4 * a4 + 3], u.w); d0 = __fmaf_rn(t, t, d0);
+                                y = __fsub_rn(x[4 * a4 + 3], w4.w); d1 = __fmaf_rn(y, y, d1);
+                            }
+                            if (d0 < bd) {
+                                bd = d0;
+                                mylab = j0;
+                            }
+                            if (two && d1 < bd) {
+                                bd = d1;
+                                mylab = j1;
                             }
                         }
                     }
