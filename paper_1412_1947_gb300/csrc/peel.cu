@@ -92,6 +92,7 @@ static_assert(kStageOff % 2 == 0, "staged 64-bit keys are 8-byte aligned");
 constexpr int kPeelDynWords = kScrWords + 2 * kKeyCache + kKeyCache / 4;
 constexpr int kQT = 8;                        // tiles of kThreads items per compaction scan
 constexpr int kCB = 8;                        // keys per thread in flight when classifying
+constexpr int kHoldBatch = 8;                 // state bytes per thread in flight when finding holders
 // State byte of each list position: bit 7 set once the point has held some attribute's
 // landmark value (it then holds it while it is left); bits 0..6 its place in the current
 // epoch: a round 0..kMaxEpoch-1 it is certainly in, kFlBand (in a band), kFlNone.
@@ -817,6 +818,15 @@ __device__ __noinline__ void phase_inc(const float *__restrict__ x, const float 
     }
 }
 
+// A holder's key, as the candidate largest key of each attribute whose landmark value it
+// holds.
+__device__ __forceinline__ void note_hold_key(const float *__restrict__ row, const float *Ls, int d, uint32_t key,
+                                              uint32_t *hmax)
+{
+    for (int j = 0; j < d; j++)
+        if (__ldg(&row[j]) == Ls[j]) atomicMax(&hmax[j], key);
+}
+
 // A holder of some attribute's landmark value assigned to round rr of the epoch: counted
 // per attribute it holds.
 __device__ __forceinline__ void count_holder(const float *__restrict__ x, const float *Ls, int d, uint32_t id,
@@ -1092,12 +1102,33 @@ __device__ __noinline__ void find_landmark(const PeelArgs &a, int j_first, int j
 // whose bands overlap into groups.  Warp w resolves boundaries w, w + kW, ...: lane i sums
 // second-digit bins [64 i, 64 i + 64) in two halves, a warp scan finds the lane holding
 // the rank, and that lane walks the half holding it (its loads issued together).
-__device__ __noinline__ void resolve_cutoffs(PeelCtl *ctl, uint32_t K, float keps, float kabs, const uint32_t *sb,
-                                             const uint32_t *sr, const uint32_t *sslot, uint32_t nslot)
+__device__ __noinline__ void resolve_cutoffs(PeelCtl *ctl, uint32_t Kb, uint32_t N, int d, float keps, float kabs,
+                                             const uint32_t *sb, const uint32_t *sr, const uint32_t *sslot,
+                                             const uint32_t *sbin, uint32_t nslot)
 {
     __shared__ uint32_t s_b1[kMaxEpoch];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     if (t < kMaxEpoch) s_b1[t] = 0;
+    // the rounds this landmark can serve: up to the one in which the last holder of some
+    // attribute's landmark value leaves (the landmark changes after it).  That holder's key
+    // m (the smallest over the attributes of their holders' largest key) is at most the
+    // c-th smallest live key, c read off the histograms (the second digit where m's bin has
+    // one), so it leaves at the latest in round (c - 1) / N; the boundaries past that
+    // round are not resolved (a prediction that falls short costs one more epoch)
+    uint32_t m = kGone;
+    for (int j = t; j < d; j += kThreads) m = min(m, __ldcg(&ctl->hmax[j]));
+    m = block_min(m);
+    const uint32_t mb0 = m >> 21, mb1 = (m >> 10) & (kHistBins - 1);
+    int slot = -1;
+    for (uint32_t q = 0; q < nslot; q++)
+        if (sbin[q] == mb0) slot = (int)q;
+    uint32_t cnt = 0;
+    for (int b = t; b < kHistBins; b += kThreads) {
+        if ((uint32_t)b < mb0 || ((uint32_t)b == mb0 && slot < 0)) cnt += __ldcg(&ctl->h0[b]);
+        if (slot >= 0 && (uint32_t)b <= mb1) cnt += __ldcg(&ctl->h1[slot][b]);
+    }
+    cnt = block_sum(cnt);
+    const uint32_t K = min(Kb, (cnt > 0 ? (cnt - 1) / N : 0u) + 1u);
     __syncthreads();
     for (uint32_t q = (uint32_t)w; q < K; q += kW) {
         const uint4 *h4 = reinterpret_cast<const uint4 *>(ctl->h1[sslot[q]] + lane * 64);
@@ -1155,6 +1186,7 @@ __device__ __noinline__ void resolve_cutoffs(PeelCtl *ctl, uint32_t K, float kep
         }
         ctl->n_groups = ng;
         ctl->n_slots = nslot;
+        ctl->k_eff = K;
         ctl->kref = __uint_as_float(sb[0] << 21);
     }
 }
@@ -1197,8 +1229,10 @@ __device__ __noinline__ void commit_count(const PeelArgs &a, const float *Ls, ui
         ctl->chold[j] = __ldcg(&ctl->chold[j]) - gone;
     }
     if (t < (int)K && __ldcg(&ctl->cert[t]) + __ldcg(&ctl->bnd[t]) != N) atomicOr(&a.flags[1], 1u);
-    if (changed)
+    if (changed) {
         for (int b = t; b < kHistBins; b += kThreads) ctl->h0[b] = 0;
+        for (int j = t; j < d; j += kThreads) ctl->hmax[j] = 0;    // recomputed by the next pass
+    }
     if (a.landmarks)
         for (uint32_t e = t; e < kc_ * (uint32_t)d; e += kThreads)
             a.landmarks[(size_t)(r0 + e / d) * d + e % d] = Ls[e % d];
@@ -1590,10 +1624,6 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
     // the same in every CTA) and the key updates since the last full pass
     const double eps0 = (double)(d + 4) * 0x1p-23;
     double k_eps = eps0, k_abs = 0x1p-120;
-    // boundaries the next epoch tries: all it may after an epoch that kept its landmark,
-    // twice the rounds committed after one whose landmark changed (most such runs are
-    // short, and each boundary's work is lost when the landmark changes before it)
-    uint32_t kcap = a.kmax;
     for (;;) {
         const uint32_t nl_tot = n - r0 * N;
         auto LID = [&](uint32_t q) -> uint32_t { return first ? s0 + q : kc ? sid[q] : __ldcg(&gid[q]); };
@@ -1610,7 +1640,7 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
                 for (int j = t; j < d; j += kThreads) a.landmarks[(size_t)r0 * d + j] = Ls[j];
             break;
         }
-        const uint32_t K = min(kcap, (nl_tot + N - 1) / N - 1u);   // boundaries of the epoch
+        const uint32_t Kb = min(a.kmax, (nl_tot + N - 1) / N - 1u);   // boundaries phase B locates
 
         // ---- A: float32 distances of the points left, the first histogram, the holders
         if (need_keys) {
@@ -1675,6 +1705,21 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
             else
                 phase_keys<D>(a.x, Ls, d, n_live, s0, first, kc, sid, gid, skey, gkp, scr, pfl, ctl->chold, s_jm);
             __syncthreads();
+            // each attribute's largest holder key (the holders are the flagged points left)
+            for (uint32_t q0 = 0; q0 < n_live; q0 += kHoldBatch * kThreads) {
+                uint8_t f[kHoldBatch];
+#pragma unroll
+                for (int u = 0; u < kHoldBatch; u++) {
+                    const uint32_t qi = q0 + u * kThreads + t;
+                    f[u] = qi < n_live ? pfl[qi] : (uint8_t)0;
+                }
+#pragma unroll
+                for (int u = 0; u < kHoldBatch; u++)
+                    if (f[u] & kFlHold) {
+                        const uint32_t qi = q0 + u * kThreads + t;
+                        note_hold_key(a.x + (size_t)LID(qi) * d, Ls, d, LKEY(qi), ctl->hmax);
+                    }
+            }
             for (int b = t; b < kHistBins; b += kThreads)
                 if (scr[b]) atomicAdd(&ctl->h0[b], scr[b]);
             if (!grid_sync(ctl, a.flags, gen, lim)) return;
@@ -1693,7 +1738,7 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
             for (int q = 0; q < per; q++) s += l0[q];
             uint32_t tot;
             const uint32_t e0 = block_excl_scan(s, tot);
-            for (uint32_t q = 0; q < K; q++) {
+            for (uint32_t q = 0; q < Kb; q++) {
                 const uint32_t target = (q + 1) * N - 1u;
                 if (target >= e0 && target < e0 + s) {
                     uint32_t cc = e0;
@@ -1711,7 +1756,7 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
             __syncthreads();
             if (t == 0) {
                 uint32_t ns = 0;
-                for (uint32_t q = 0; q < K; q++) {
+                for (uint32_t q = 0; q < Kb; q++) {
                     if (q == 0 || s_b[q] != s_b[q - 1]) s_sbin[ns++] = s_b[q];
                     s_slot[q] = ns - 1;
                 }
@@ -1747,8 +1792,11 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
         }
         // the last CTA to arrive turns each boundary's bins into its band cut-offs, and
         // merges boundaries whose bands overlap into groups
-        if (!grid_sync_last(ctl, a.flags, gen, lim, [&]() { resolve_cutoffs(ctl, K, s_keps, s_kabs, s_b, s_r, s_slot, s_nslot); }))
+        if (!grid_sync_last(ctl, a.flags, gen, lim, [&]() {
+                resolve_cutoffs(ctl, Kb, N, d, s_keps, s_kabs, s_b, s_r, s_slot, s_sbin, s_nslot);
+            }))
             return;
+        const uint32_t K = __ldcg(&ctl->k_eff);       // boundaries of the epoch
 
         // ---- C: classify every point left: certainly in a round of the epoch, in a band, or later
         const uint32_t ng = __ldcg(&ctl->n_groups);
@@ -1843,7 +1891,6 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
         first = false;
         need_keys = changed;
         r0 += kcm;
-        kcap = changed ? min(a.kmax, max(2u, 2u * kcm)) : a.kmax;
         if (!grid_sync(ctl, a.flags, gen, lim)) return;
     }
 }

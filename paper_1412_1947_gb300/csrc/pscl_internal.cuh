@@ -28,6 +28,7 @@ struct PeelCtl {
     uint32_t Lbits[kMaxD];               // landmark of the current epoch (float bits)
     uint32_t lptr[kMaxD];                // per attribute: buckets in front of it hold no remaining point
     uint32_t chold[kMaxD];               // live points whose attribute j equals L_j
+    uint32_t hmax[kMaxD];                // the largest key among them (since the last pass)
     uint32_t hcnt[kMaxD][kMaxEpoch];     // of those, the ones assigned to each round of the epoch
     uint32_t cert[kMaxEpoch];            // points certainly in each round of the epoch
     uint32_t bnd[kMaxEpoch];             // band points settled into each round of the epoch
@@ -39,6 +40,7 @@ struct PeelCtl {
     uint32_t n_slots;                    // first-digit bins with a second-digit histogram
     uint32_t n_groups;
     uint32_t band_cnt;                   // band entries listed this epoch
+    uint32_t k_eff;                      // boundaries the epoch resolves (rounds it can commit)
     uint32_t k_commit;                   // rounds the epoch commits
     uint32_t l_changed;                  // the landmark changes after them
     uint32_t bar_count;                  // grid barrier: arrivals since the launch
