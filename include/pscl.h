@@ -110,11 +110,12 @@ typedef enum {
      *    Lloyd then runs in float32 (prec ignored) with global 64-bit sums.  Needs
      *    n < 2^31 (else PSCL_EINVAL).  Default 0 (unweighted). */
     PSCL_OPT_POOL_WEIGHTED = 8,
-    /* Jobs only: rounds of the peel that one pass of landmark distances may serve, 1..16,
-     *    0 = the default (8).  The landmark changes only after every remaining point holding
+    /* Jobs only: rounds of the peel that one pass of landmark distances may serve, 1..32,
+     *    0 = the default (32).  The landmark changes only after every remaining point holding
      *    some attribute's minimum has been taken, and until then the next round is the next
-     *    N points of the same order, so one pass settles up to this many rounds at once.  A
-     *    tuning choice: results do not depend on it. */
+     *    N points of the same order, so one pass settles up to this many rounds at once (an
+     *    epoch resolves only the rounds before the last holder of some attribute's value
+     *    leaves, read off the keys).  A tuning choice: results do not depend on it. */
     PSCL_OPT_PEEL_ROUNDS = 9,
     /* Polls of every bounded device-side wait (the peel's grid barriers, the tensor-core
      *    assignment's commit waits) before it gives up and the job reports PSCL_ETIMEOUT;

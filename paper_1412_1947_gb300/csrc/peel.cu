@@ -100,7 +100,7 @@ constexpr uint8_t kFlHold = 0x80;
 constexpr uint8_t kFlBand = 0x7E;
 constexpr uint8_t kFlNone = 0x7F;
 constexpr uint32_t kPosMask = 0x7FFFFFFFu;    // a band entry's id; bit 31 carries its hold flag
-constexpr int kDefaultRounds = 16;            // rounds per distance pass by default
+constexpr int kDefaultRounds = 32;            // rounds per distance pass by default
 constexpr int kSlotsSmem = kScrWords / kHistBins;   // second-digit histograms counted in shared memory
 constexpr unsigned kDefaultSpin = 1u << 25;   // ~1-2 s of polling per barrier at most
 

@@ -19,7 +19,7 @@ constexpr int kFixShift = 32;        // fixed-point scale 2^32 of the centroid s
 constexpr int kMaxPeelGrid = 2048;   // CTAs of the persistent peel launch
 
 // Rounds one peel epoch may select from one set of distances (boundaries per epoch).
-constexpr int kMaxEpoch = 16;
+constexpr int kMaxEpoch = 32;
 
 // Device-resident control block of one persistent peel launch (cleared before it).
 struct PeelCtl {

@@ -30,7 +30,7 @@ def _check(raw, N, rounds):
     np.testing.assert_array_equal(perm, operm)
 
 
-@pytest.mark.parametrize("rounds", [1, 2, 5, 16])
+@pytest.mark.parametrize("rounds", [1, 2, 5, 16, 32])
 def test_mixture(rounds):
     _check(synth.mixture(30000, 16, 20, outlier_frac=0.01, seed=600), 1000, rounds)
 
