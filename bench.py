@@ -243,6 +243,7 @@ def main_arm(args, w: synth.Workload):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     fma_tflops = B.pscl_measure_fp32_fma(local)
+    barrier_us = B.pscl_measure_grid_barrier(local)
     ctx = B.pscl_ctx_create(local, 0, stream.cuda_stream)
     job = B.Job(x_dev, ctx=ctx)
     job.option(B.PSCL_OPT_GRAPH)
@@ -309,7 +310,7 @@ def main_arm(args, w: synth.Workload):
         job_k.steps(wr.N, wr.local_k, wr.final_k, wr.iters, seed, prec)
         kt = job_k.kernel_times()
     rechecked, assigned = job_k.recheck_stats()
-    peel_epochs, peel_passes, peel_updates = job_k.peel_stats()
+    peel_epochs, peel_passes, peel_updates, peel_barriers = job_k.peel_stats()
     phases = job_k.phase_ms()
     job_k.close()
 
@@ -408,6 +409,11 @@ def main_arm(args, w: synth.Workload):
             "gpu_launches": int(launches_per_step * args.steps),
             "roofline": roof,
             "roofline_assign": assign_roof(),
+            # the peel's latency floor: its grid barriers at the measured cost of one
+            "peel_latency": {"bound": "grid barriers", "grid_barrier_us": barrier_us, "barriers": peel_barriers,
+                             "floor_ms": peel_barriers * barrier_us / 1e3, "peel_ms": kt["peel"][1],
+                             "frac": peel_barriers * barrier_us / 1e3 / kt["peel"][1],
+                             "peak_kind": "measured (pscl_measure_grid_barrier, the peel's barrier in its launch shape)"},
             "kernels_ms": {k: round(v[1], 4) for k, v in kt.items()},
             "kernel_launches": {k: v[0] for k, v in kt.items()},
             "phase_ms": {"scale": float(phases[0]), "peel": float(phases[1]), "local_lloyd": float(phases[2]),

@@ -261,10 +261,12 @@ int pscl_get_kernel_times(pscl_job *job, int64_t *launches, float *ms);
 int pscl_get_recheck_stats(pscl_job *job, int64_t *rechecked, int64_t *assigned);
 /* Statistics of the last equal-sized subclustering (Algorithm 1 steps 2-5): *epochs
  * (rounds committed together from one landmark), *passes (distance passes over the points
- * left: one per landmark change) and *key_updates (of those passes, the ones that updated
+ * left: one per landmark change), *key_updates (of those passes, the ones that updated
  * the keys from the few attributes whose landmark value moved instead of recomputing
- * them).  PSCL_ESTATE if no such subclustering ran on the job.  Pointers may be NULL. */
-int pscl_get_peel_stats(pscl_job *job, int64_t *epochs, int64_t *passes, int64_t *key_updates);
+ * them) and *barriers (grid-wide barriers the launch passed).  PSCL_ESTATE if no such
+ * subclustering ran on the job.  Pointers may be NULL. */
+int pscl_get_peel_stats(pscl_job *job, int64_t *epochs, int64_t *passes, int64_t *key_updates,
+                        int64_t *barriers);
 /* Device time of the phases of the last run in milliseconds: [0] scale, [1] peel,
  * [2] local Lloyd (incl. init), [3] final Lloyd, [4] SSE pass. */
 int pscl_get_phase_ms(pscl_job *job, float *ms5);
@@ -276,6 +278,14 @@ int pscl_get_phase_ms(pscl_job *job, float *ms5);
  * frees a few KB of device memory; takes some tens of milliseconds.
  * Errors: PSCL_EINVAL (tflops NULL), PSCL_ECUDA. */
 int pscl_measure_fp32_fma(int device, double *tflops);
+
+/* Measurement service beside the method: the time of one grid-wide barrier of the peel's
+ * own implementation (monotonic arrival counter, release on arrival, acquire while
+ * polling, bounded waits) in the peel's launch shape on `device` (its block size, shared
+ * memory and CTAs per SM), the best of three runs of 2000 barriers in a row, in
+ * microseconds: the latency floor that the peel's barriers put under its epochs.
+ * PSCL_EINVAL if us is NULL, PSCL_ECUDA on a CUDA error, PSCL_ETIMEOUT if a wait gave up. */
+int pscl_measure_grid_barrier(int device, double *us);
 
 /* Nearest center and sum of squared errors of n points, allocating nothing.
  *

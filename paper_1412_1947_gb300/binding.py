@@ -51,7 +51,8 @@ SIGNATURES = {
     "pscl_get_phase_ms": (_I, [_P, _P]),
     "pscl_get_kernel_times": (_I, [_P, _P, _P]),
     "pscl_get_recheck_stats": (_I, [_P, _P, _P]),
-    "pscl_get_peel_stats": (_I, [_P, _P, _P, _P]),
+    "pscl_get_peel_stats": (_I, [_P, _P, _P, _P, _P]),
+    "pscl_measure_grid_barrier": (_I, [_I, _P]),
     "pscl_measure_fp32_fma": (_I, [_I, _P]),
     "pscl_assign_sse_noalloc": (_I, [_P, _I64, _I32, _P, _I32, _P, _P, _P]),
     "pscl_job_footprint": (_I, [_P, _I64, _I32, _I64, _I32, _I32, _I32, _I, _I, _I, _P]),
@@ -270,10 +271,17 @@ def pscl_get_recheck_stats(job):
 
 
 def pscl_get_peel_stats(job):
-    """(epochs, distance passes, passes that updated the keys) of the last peel."""
-    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
-    _chk(lib().pscl_get_peel_stats(job, C.byref(a), C.byref(b), C.byref(c)))
-    return a.value, b.value, c.value
+    """(epochs, distance passes, passes that updated the keys, grid barriers) of the last peel."""
+    a, b, c, e = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+    _chk(lib().pscl_get_peel_stats(job, C.byref(a), C.byref(b), C.byref(c), C.byref(e)))
+    return a.value, b.value, c.value, e.value
+
+
+def pscl_measure_grid_barrier(device=0):
+    """Microseconds per grid barrier of the peel's implementation, in its launch shape."""
+    t = C.c_double()
+    _chk(lib().pscl_measure_grid_barrier(device, C.byref(t)))
+    return t.value
 
 
 def pscl_get_kernel_times(job):

@@ -1206,19 +1206,34 @@ extern "C" int pscl_get_recheck_stats(pscl_job *j, int64_t *rechecked, int64_t *
     return PSCL_OK;
 }
 
-extern "C" int pscl_get_peel_stats(pscl_job *j, int64_t *epochs, int64_t *passes, int64_t *key_updates)
+extern "C" int pscl_get_peel_stats(pscl_job *j, int64_t *epochs, int64_t *passes, int64_t *key_updates,
+                                   int64_t *barriers)
 {
     TRY(pscl_job_sync(j));
     if (!j->pb.ctl) return fail(PSCL_ESTATE, "no equal-sized subclustering has run on this job");
-    uint32_t v[3];
+    uint32_t v[4];
     static_assert(offsetof(PeelCtl, passes) == offsetof(PeelCtl, epochs) + 4 &&
-                      offsetof(PeelCtl, key_updates) == offsetof(PeelCtl, epochs) + 8,
+                      offsetof(PeelCtl, key_updates) == offsetof(PeelCtl, epochs) + 8 &&
+                      offsetof(PeelCtl, barriers) == offsetof(PeelCtl, epochs) + 12,
                   "the statistics are adjacent");
     CU(cudaMemcpy(v, reinterpret_cast<const char *>(j->pb.ctl) + offsetof(PeelCtl, epochs), sizeof v,
                   cudaMemcpyDeviceToHost));
     if (epochs) *epochs = v[0];
     if (passes) *passes = v[1];
     if (key_updates) *key_updates = v[2];
+    if (barriers) *barriers = v[3];
+    return PSCL_OK;
+}
+
+extern "C" int pscl_measure_grid_barrier(int device, double *us)
+{
+    if (!us) return fail(PSCL_EINVAL, "us is NULL");
+    CU(cudaSetDevice(device));
+    int sms = 0;
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    bool timed_out = false;
+    CU(measure_grid_barrier(sms, us, &timed_out));
+    if (timed_out) return fail(PSCL_ETIMEOUT, "a barrier of the measurement gave up");
     return PSCL_OK;
 }
 

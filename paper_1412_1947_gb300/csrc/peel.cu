@@ -196,6 +196,7 @@ __device__ bool grid_sync(PeelCtl *ctl, uint32_t *flags, unsigned &target, unsig
     target += gridDim.x;
     __syncthreads();
     if (threadIdx.x == 0) {
+        if (blockIdx.x == 0) ctl->barriers += 1;     // statistics (one writer)
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctl->bar_count) : "memory");
         ok = bar_wait(ctl, flags, target + extra, limit) ? 1 : 0;
     }
@@ -212,6 +213,7 @@ __device__ bool grid_sync_last(PeelCtl *ctl, uint32_t *flags, unsigned &target, 
     target += gridDim.x + 1;
     __syncthreads();
     if (threadIdx.x == 0) {
+        if (blockIdx.x == 0) ctl->barriers += 1;     // statistics (one writer)
         unsigned old;
         asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(&ctl->bar_count) : "memory");
         last = old == target - 2u;
@@ -1895,6 +1897,19 @@ __global__ void __launch_bounds__(kThreads) k_peel(PeelArgs a)
     }
 }
 
+// ------------------------------------------------------------------ barrier cost
+// The peel's grid barrier alone: `rounds` barriers in a row, in the peel's launch shape
+// (the same block size, dynamic shared memory and CTAs per SM, so the same grid), timed
+// to give the latency floor that the peel's barriers put under its epochs.
+__global__ void __launch_bounds__(kThreads) k_barrier_bench(PeelCtl *ctl, uint32_t *flags, int rounds, unsigned lim)
+{
+    extern __shared__ __align__(16) uint32_t dyn[];
+    if (threadIdx.x == 0 && rounds < 0) dyn[0] = 0;          // keeps the launch's shared memory
+    unsigned gen = 0;
+    for (int r = 0; r < rounds; r++)
+        if (!grid_sync(ctl, flags, gen, lim)) return;
+}
+
 // ------------------------------------------------------------------ the points by attribute
 // x (n x d, by point) into xt (d x n, by attribute) for the peel's key updates: 32 x 32
 // tiles through shared memory, so that both the reads (32 attributes of a point) and the
@@ -2159,6 +2174,61 @@ cudaError_t launch_gather(const float *x, const uint32_t *perm, int64_t n, int d
         k_gather_rows<false><<<(int)g, 256, 0, st>>>(x, perm, n, d, xseg);
     kt->end(PSCL_K_GATHER, st);
     return cudaGetLastError();
+}
+
+cudaError_t measure_grid_barrier(int sm_count, double *us, bool *timed_out)
+{
+    const size_t smem = kPeelDynWords * sizeof(uint32_t);
+    cudaError_t e = cudaFuncSetAttribute(k_barrier_bench, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // the peel's grid at full size: its CTAs per SM (capped at 4), as peel_launch sizes it
+    e = cudaFuncSetAttribute(k_peel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_peel<16>, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    int bench_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bench_sm, k_barrier_bench, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    per_sm = std::min(std::min(per_sm, 4), bench_sm);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = std::min(sm_count * per_sm, kMaxPeelGrid);
+    PeelCtl *ctl = nullptr;
+    uint32_t *flags = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    constexpr int kRounds = 2000;
+    float best = 0.0f;
+    uint32_t hf[2] = {0u, 0u};
+    if ((e = cudaMalloc(&ctl, sizeof(PeelCtl))) == cudaSuccess && (e = cudaMalloc(&flags, 8)) == cudaSuccess &&
+        (e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) == cudaSuccess &&
+        (e = cudaEventCreate(&t0)) == cudaSuccess && (e = cudaEventCreate(&t1)) == cudaSuccess) {
+        for (int r = 0; r < 4 && e == cudaSuccess; r++) {        // the first a warm-up
+            cudaMemsetAsync(ctl, 0, sizeof(PeelCtl), st);
+            cudaMemsetAsync(flags, 0, 8, st);
+            int rounds = kRounds;
+            unsigned lim = kDefaultSpin;
+            void *args[] = {&ctl, &flags, &rounds, &lim};
+            cudaEventRecord(t0, st);
+            e = cudaLaunchCooperativeKernel((const void *)k_barrier_bench, dim3(grid), dim3(kThreads), args, smem, st);
+            cudaEventRecord(t1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            if (e == cudaSuccess) e = cudaMemcpy(hf, flags, 8, cudaMemcpyDeviceToHost);
+            float ms = 0.0f;
+            if (e == cudaSuccess) cudaEventElapsedTime(&ms, t0, t1);
+            if (r > 0 && (best == 0.0f || ms < best)) best = ms;
+            if (hf[1]) break;
+        }
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (st) cudaStreamDestroy(st);
+    cudaFree(flags);
+    cudaFree(ctl);
+    if (e != cudaSuccess) return e;
+    *timed_out = hf[1] != 0u;
+    *us = 1e3 * (double)best / kRounds;
+    return cudaSuccess;
 }
 
 uint32_t peel_buckets(int64_t n)

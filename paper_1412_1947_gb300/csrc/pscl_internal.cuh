@@ -47,7 +47,8 @@ struct PeelCtl {
     uint32_t abort;                      // set when a barrier wait gave up
     uint32_t epochs;                     // statistics: epochs run,
     uint32_t passes;                     //   distance passes over the points left,
-    uint32_t key_updates;                //   of which updates of the keys in a few attributes
+    uint32_t key_updates;                //   of which updates of the keys in a few attributes,
+    uint32_t barriers;                   //   grid-wide barriers passed
 };
 
 // v (a scaled coordinate, in [0, 1]) times 2^32 rounded to the nearest integer, ties to
@@ -169,6 +170,9 @@ struct PeelBuffers {
     int stall_first_barrier;         // test hook: the first grid barrier waits for one CTA too many
     int max_grid = 0;                // most CTAs of the launch (0: as many as fit)
 };
+// Time per grid-wide barrier of the peel's own implementation, in the peel's launch shape
+// (pscl_measure_grid_barrier).
+cudaError_t measure_grid_barrier(int sm_count, double *us, bool *timed_out);
 // Buckets of the per-attribute orders the peel builds for n points.
 uint32_t peel_buckets(int64_t n);
 // CTAs of the counting sort that packs the subclusters after the peel (pcnt: 256 x this).

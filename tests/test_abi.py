@@ -57,3 +57,14 @@ def test_measured_fma_rate_is_plausible():
     # bound is loose on both sides so that clocks under another load still pass
     t = binding.pscl_measure_fp32_fma(0)
     assert 20.0 < t < 100.0, t
+
+
+def test_grid_barrier_measurement_rejects_null():
+    lib = binding.lib()
+    assert lib.pscl_measure_grid_barrier(0, None) == binding.PSCL_EINVAL
+
+
+@pytest.mark.gpu
+def test_measured_grid_barrier_is_plausible():
+    us = binding.pscl_measure_grid_barrier(0)
+    assert 0.05 < us < 100.0

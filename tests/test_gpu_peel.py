@@ -100,9 +100,12 @@ def test_key_updates_keep_the_partition(n, d, blobs, N):
         j.steps(N, 2, 2, 1, 3)
         perm, off = j.partition()
         x = j.scaled()
-        epochs, passes, updates = j.peel_stats()
-    print(f"epochs {epochs} passes {passes} key updates {updates}")
+        epochs, passes, updates, barriers = j.peel_stats()
+    print(f"epochs {epochs} passes {passes} key updates {updates} barriers {barriers}")
     assert 0 < updates < passes <= epochs
+    # the bucket lists: 3 (after the counts, their scan and the places); every epoch 5,
+    # and one more with a distance pass
+    assert barriers == 3 + 5 * epochs + passes
     operm, ooff, _ = oracle.peel(x, N, select=True)
     np.testing.assert_array_equal(off, ooff)
     np.testing.assert_array_equal(perm, operm)
