@@ -26,16 +26,22 @@ def _delta64(x, L):
     return acc
 
 
-def epoch_peel(x, N, K, stats=None):
-    """The kernel's epoch bookkeeping in plain numpy; returns (perm, seg_off)."""
+def epoch_peel(x, N, K, stats=None, predict=False):
+    """The kernel's epoch bookkeeping in plain numpy; returns (perm, seg_off).  With
+    predict, an epoch resolves only the rounds up to the one in which the last holder of
+    some attribute's landmark value leaves at the latest: m = the smallest over the
+    attributes of their holders' largest distance (taken at the pass), c = the live
+    distances <= m, the last round (c - 1) // N (the kernel reads c off its histograms,
+    an upper bound of the same kind)."""
     n, d = x.shape
     rnd = np.full(n, -1, np.int64)
     live = np.ones(n, bool)
     L = x.min(axis=0)                     # the first landmark (0 for scaled data)
-    r0, passes, epochs = 0, 0, 0
+    r0, passes, epochs, short = 0, 0, 0, 0
     need_keys = True
     chold = None
     delta = None
+    hmax = None
     while True:
         ids = np.flatnonzero(live)
         if len(ids) <= N:
@@ -45,7 +51,13 @@ def epoch_peel(x, N, K, stats=None):
         if need_keys:
             delta = _delta64(x, L)
             chold = (x[ids] == L[None, :]).sum(axis=0)      # live holders per attribute
+            held = x[ids] == L[None, :]
+            hmax = np.array([delta[ids][held[:, j]].max() if held[:, j].any() else 0.0 for j in range(d)])
             passes += 1
+        cap = Ke
+        if predict:
+            c = int(np.sum(delta[ids] <= hmax.min()))
+            Ke = min(Ke, (max(c, 1) - 1) // N + 1)
         epochs += 1
         order = ids[np.lexsort((ids, delta[ids]))]
         tent = {}
@@ -72,13 +84,14 @@ def epoch_peel(x, N, K, stats=None):
             L = x[live].min(axis=0)
         else:
             chold = chold - hcnt[:, :kcommit].sum(axis=1)
+            short += Ke < cap          # an epoch the prediction cut before the landmark changed
         need_keys = changed
         r0 += kcommit
     S = r0 + 1
     perm = np.lexsort((np.arange(n), rnd))          # by round, ascending index inside
     seg_off = np.array([np.sum(rnd < r) for r in range(S + 1)], np.int64)
     if stats is not None:
-        stats.update(passes=passes, epochs=epochs, rounds=S)
+        stats.update(passes=passes, epochs=epochs, rounds=S, short=short)
     return perm, seg_off
 
 
@@ -136,3 +149,37 @@ def test_epochs_save_distance_passes_on_the_headline_shape():
     operm, ooff, _ = oracle.peel(x, 4096)
     np.testing.assert_array_equal(perm, operm)
     assert st["passes"] < st["rounds"]
+
+
+@pytest.mark.parametrize("K", [2, 8, 32])
+def test_predicted_epochs_equal_the_per_round_peel(K):
+    raw = synth.mixture(3000, 4, 6, outlier_frac=0.02, seed=4243)
+    x, _, _ = oracle.scale(raw)
+    perm, off = epoch_peel(x, 97, K, predict=True)
+    operm, ooff, _ = oracle.peel(x, 97)
+    np.testing.assert_array_equal(off, ooff)
+    np.testing.assert_array_equal(perm, operm)
+
+
+def test_predicted_epochs_with_tied_values_and_distances():
+    g = np.random.default_rng(11)
+    raw = g.integers(0, 5, size=(2500, 3)).astype(np.float32)
+    x, _, _ = oracle.scale(raw)
+    perm, off = epoch_peel(x, 64, 32, predict=True)
+    operm, ooff, _ = oracle.peel(x, 64)
+    np.testing.assert_array_equal(off, ooff)
+    np.testing.assert_array_equal(perm, operm)
+
+
+def test_the_prediction_never_cuts_an_epoch_short():
+    # in exact arithmetic the predicted last round is at or after the round in which the
+    # landmark changes, so every epoch ends with a change or with its cap: one epoch per
+    # landmark whenever no landmark serves more rounds than the cap
+    raw = synth.mixture(65536, 16, 64, outlier_frac=0.01, seed=synth.BASE_SEED + 1)
+    x, _, _ = oracle.scale(raw)
+    st = {}
+    perm, off = epoch_peel(x, 4096, 32, st, predict=True)
+    operm, ooff, _ = oracle.peel(x, 4096)
+    np.testing.assert_array_equal(perm, operm)
+    assert st["short"] == 0
+    assert st["epochs"] == st["passes"]
