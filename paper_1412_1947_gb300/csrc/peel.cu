@@ -15,8 +15,11 @@
 // in, and the epoch commits its rounds up to the first one after which some attribute
 // has no holder of its landmark value left.  The later rounds' assignments are dropped
 // and the next epoch starts from the new landmark (a new pass of distances) or, when all
-// K rounds committed, from the same one (no pass at all).  On the headline workload
-// (2^20 points, 16 attributes, 256 rounds) the landmark changes in 50 rounds.
+// K rounds committed, from the same one (no pass at all).  K itself is read off the keys:
+// the holders' largest key per attribute bounds the round in which the landmark changes,
+// so an epoch resolves only the boundaries up to there (see resolve_cutoffs).  On the
+// headline workload (2^20 points, 16 attributes, 256 rounds) the landmark changes in 50
+// rounds, and the peel runs 50 epochs.
 //
 // Each pass works in float32 and keeps exact arithmetic for thin bands around the
 // boundaries:
